@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Benchmark of the HOPU convection hot path on one GB300 (or N independent replicas).
+
+Workload: 3D periodic box [0, 2pi]^3, 16^3 cubes x 6 tetrahedra (24,576 elements),
+order k = 3, HOPU projection order l = k-1, Taylor-Green velocity interpolated into the
+normal-continuous velocity space plus U[-1e-3, 1e-3] noise (seed 0), dt = 5e-4.
+
+One step = one explicit SSP-RK3 substep in STAGE wind mode (per stage: V_h -> L2
+projection, facet flux, volume term + lift + inverse mass, L2 -> V_h back-projection
+with the stage combination) followed by the FP64 kinetic-energy reduction of the new
+state (its L2 image).  The metric counts DOF-updates of the convection apply: L2 DOFs x
+3 applies per substep.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+(torchrun for N > 1: every rank runs the same workload on its own GPU, weak scaling,
+no data-path collective; a gloo group carries the barrier and the max over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s of HOPU convection apply, FP32 vs FP64 at stated error; % HBM peak"
+UNIT = "DOF-updates/s"
+WORKLOAD = dict(dim=3, n=16, k=3, l=2, dt=5e-4, noise=1e-3, seed=0)
+WORKLOAD_NAME = ("3D periodic box [0,2pi]^3, 16^3 cubes x 6 tets (24,576 elements), k=3, HOPU l=2, "
+                 "Taylor-Green + 1e-3 seeded noise, SSP-RK3 STAGE substeps dt=5e-4")
+APPLIES_PER_STEP = 3
+L2_FLUSH_BYTES = 256 << 20
+FAMILIES = ["v2l", "facet", "volume", "l2v_elem", "l2v_facet"]
+
+
+# ------------------------------------------------------------------ roofline arithmetic
+def shape(dim, k):
+    from math import comb
+    nb = comb(k + dim, dim)
+    nf = comb(k + dim - 1, dim - 1)
+    mv = (3 * k + 1) // 2
+    mf = (3 * k + 2) // 2
+    return dict(nb=nb, nf=nf, nloc=dim * nb, nint=dim * nb - (dim + 1) * nf, nq=mv ** dim, nqf=mf ** (dim - 1))
+
+
+def algorithmic(dim, k, E, NF, tsize):
+    """Per-launch algorithmic flops and bytes of each kernel family (STAGE wind: w = u).
+
+    Bytes count each input/output once (coefficients, geometry actually read, facet
+    moments, connectivity); flops count the contractions the method performs.
+    """
+    s = shape(dim, k)
+    nb, nf, nl, nq, nqf = s["nb"], s["nf"], s["nloc"], s["nq"], s["nqf"]
+    d = dim
+    geo_vol = (d * d + 1) * 8                       # |det J| J^-1, |det J|
+    out = {}
+    # volume: interpolate u (2 nq nb d), W = M u (2 nq d^2), test (2 nq nb 2d), lift (2 nl (d+1) nf)
+    fl = E * (2 * nq * nb * d + 2 * nq * d * d + 2 * nq * nb * 2 * d + 2 * nl * (d + 1) * nf)
+    by = E * (2 * nl * tsize + geo_vol + (d + 1) * 4) + NF * nf * d * tsize
+    out["volume"] = (fl, by)
+    # facet: two traces at nqf points (2 * 2 nqf nb d), projections and moments (~ 8 nqf nf d)
+    fl = NF * (2 * 2 * nqf * nb * d + 8 * nqf * nf * d)
+    by = NF * (2 * nl * tsize * 0 + (d + 1) * 8 + 2 * 4 + nf * d * tsize) + E * nl * tsize
+    out["facet"] = (fl, by)
+    # v2l: gather + Dinv (2 nl^2) + Piola (2 nl d)
+    out["v2l"] = (E * (2 * nl * nl + 2 * nl * d), (NF * nf + E * s["nint"]) * tsize + E * nl * tsize
+                  + E * ((d * d + 1) * 8 + (d + 1) * 4))
+    out["l2v_elem"] = (E * (2 * nl * nl + 2 * nl * d), E * nl * tsize * 2 + E * s["nint"] * tsize * 2
+                       + E * (d + 1) * nf * tsize + E * ((d * d + 1) * 8 + (d + 1) * 4))
+    out["l2v_facet"] = (NF * nf * 6, NF * nf * tsize * 4 + NF * 8)
+    return out
+
+
+def fp32_alu_peak_tflops(sm_mhz, n_sm=152):
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flop x clock."""
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops(sm_mhz, n_sm=152):
+    """GB300 FP64: 1.25 TFLOP/s nominal at 2070 MHz, scaled by the clock."""
+    return 1.25 * sm_mhz / 2070.0
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.p = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j] and "Not" not in r[5 + j]})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle worker (CPU)
+def oracle_worker(args):
+    """Runs in a child process with one BLAS thread: the FP64 CPU oracle, as it stands."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import fe, hdiv, mesh, rk
+    cfg = json.loads(args.oracle_worker)
+    dim, k, l, dt = WORKLOAD["dim"], WORKLOAD["k"], WORKLOAD["l"], WORKLOAD["dt"]
+    n = cfg["n"]
+    m = W.periodic_box_mesh(dim, n)
+    sp = hdiv.HDiv(mesh.MeshTopo(m.coords, m.elems, m.rep), fe.ref_element(dim, k))
+    u = sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, WORKLOAD["noise"], WORKLOAD["seed"])
+    res = {"n": n, "n_l2": sp.n_l2, "elements": sp.topo.n_elems}
+    if cfg["mode"] == "sample":
+        t0 = time.perf_counter()
+        u1 = rk.substeps_stage(sp, u, dt, 1, l)
+        res["seconds"] = time.perf_counter() - t0
+        res["steps"] = 1
+        np.save(cfg["out"], u1)
+    else:
+        for _ in range(cfg["warmup"]):
+            u = rk.substeps_stage(sp, u, dt, 1, l)
+        t0 = time.perf_counter()
+        for _ in range(cfg["steps"]):
+            u = rk.substeps_stage(sp, u, dt, 1, l)
+            sp.to_l2(u)
+        res["seconds"] = time.perf_counter() - t0
+        res["steps"] = cfg["steps"]
+    with open(cfg["out"] + ".json", "w") as f:
+        json.dump(res, f)
+
+
+def run_oracle(cfg: dict, timeout: float = 1800):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", json.dumps(cfg)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError("oracle worker failed:\n" + r.stdout[-2000:] + r.stderr[-4000:])
+    with open(cfg["out"] + ".json") as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------ ranks (control plane only)
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of a host scalar over all ranks (gloo); the identity on one rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Weak scaling: every rank processes units_per_rank; the job takes the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    K, Wm = args.steps, args.warmup
+    # size the per-step sample so that the whole run stays within a few minutes:
+    # time one substep on the 3^3 x 6 box, scale by n^3
+    tmp = tempfile.mkdtemp()
+    probe = run_oracle({"mode": "loop", "n": 3, "steps": 1, "warmup": 0, "out": os.path.join(tmp, "p")})
+    t3 = probe["seconds"]
+    budget = args.ref_budget_s / max(1, K + Wm)
+    n = int(max(3, min(16, math.floor(3 * (budget / t3) ** (1.0 / 3.0)))))
+    res = run_oracle({"mode": "loop", "n": n, "steps": K, "warmup": Wm, "out": os.path.join(tmp, "r")},
+                     timeout=3600)
+    secs = res["seconds"]
+    value = res["n_l2"] * APPLIES_PER_STEP * K / secs
+    sample = (f"{n}^3 x 6 tets ({res['elements']} elements, {res['n_l2']} L2 DOFs), k=3, l=2: one "
+              f"SSP-RK3 STAGE substep + L2 image per step"
+              + ("" if n == WORKLOAD["n"] else " (same workload structure on a smaller box)"))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": Wm, "ms_per_step": 1e3 * secs / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample": sample, "oracle": "numpy FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def traffic_from_profiles(kernel: str):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel is unchanged."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    ent = t.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2408_06698_gb300", "csrc", "kernels.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if ent.get("kernels_cuh_sha") != sha:
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def our_arm(args, rank, world):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2408_06698_gb300 import Hopu
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    dim, n, k, l, dt = (WORKLOAD[x] for x in ("dim", "n", "k", "l", "dt"))
+    m = W.periodic_box_mesh(dim, n)
+
+    def make(prec):
+        g = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec=prec, device=dev)
+        u0 = g.interpolate_function(W.taylor_green)
+        noise = torch.as_tensor(W.uniform_noise(g.n_hdiv, WORKLOAD["noise"], WORKLOAD["seed"]), device=dev)
+        u0 += noise.to(g.dtype)
+        return g, u0
+
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(g, state, K, Wm, profile=False, clocks=None, e2e=False):
+        uL = g.new("l2")
+        host = torch.empty(g.n_hdiv, dtype=g.dtype, pin_memory=True) if e2e else None
+        if e2e:
+            host.copy_(state)
+        with torch.cuda.stream(stream):
+            for _ in range(Wm):
+                g.rk_substep(state, dt, 1)
+                g.project("hdiv_to_l2", state, uL)
+                g.energy(uL)
+            if profile:
+                g.profile(True)
+            acc = {f: [0.0, 0] for f in FAMILIES}
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            energies = []
+            stream.synchronize()
+            barrier(world)
+            if clocks:
+                clocks.start()
+            t0 = time.perf_counter()
+            for i in range(K):
+                flush.zero_()                      # L2 flush outside the timed events
+                ev[i][0].record(stream)
+                if e2e:
+                    state.copy_(host, non_blocking=True)
+                g.rk_substep(state, dt, 1)
+                g.project("hdiv_to_l2", state, uL)
+                energies.append(g.energy(uL)[0])   # synchronises the stream
+                if e2e:
+                    host.copy_(state, non_blocking=True)
+                ev[i][1].record(stream)
+                if profile:
+                    g.profile_read(acc)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+            barrier(world)
+            ck = clocks.stop() if clocks else None
+            if profile:
+                g.profile(False)
+        dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+        return dev_ms, wall, acc, ck, energies
+
+    K, Wm = args.steps, args.warmup
+    # ---------------- FP32 headline
+    g32, s32 = make("f32")
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    dev_ms, wall, acc, ck, energies = timed_steps(g32, s32, K, Wm, profile=True, clocks=clocks)
+    tmax_ms = max_over_ranks(dev_ms, world)
+    dofs = g32.n_l2 * APPLIES_PER_STEP
+    value = whole_job_value(dofs * K, world, tmax_ms / 1e3)
+
+    # ---------------- e2e through host buffers (pinned), same metric
+    g32e, s32e = make("f32")
+    Ke = min(K, 200)
+    e_ms, _, _, _, _ = timed_steps(g32e, s32e, Ke, Wm, e2e=True)
+    e_max = max_over_ranks(e_ms, world)
+    e2e = {"value": whole_job_value(dofs * Ke, world, e_max / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": g32e.n_hdiv * 4, "d2h_bytes_per_step": g32e.n_hdiv * 4,
+           "steps": Ke, "note": "pinned host state copied in and out around every substep"}
+    del g32e, s32e
+
+    # ---------------- FP64 path (same workload, fewer steps)
+    g64, s64 = make("f64")
+    K64 = min(K, 100)
+    d64, _, acc64, _, _ = timed_steps(g64, s64, K64, min(Wm, 3), profile=True)
+    d64 = max_over_ranks(d64, world)
+    fp64 = {"value": whole_job_value(dofs * K64, world, d64 / 1e3), "unit": UNIT, "steps": K64,
+            "ms_per_step": d64 / K64}
+
+    # ---------------- roofline of the dominant kernel (FP32 run, live CUDA events)
+    alg = algorithmic(dim, k, g32.n_elems, g32.n_facets, 4)
+    dom = max(FAMILIES, key=lambda f: acc[f][0])
+    avg_ms = acc[dom][0] / max(1, acc[dom][1])
+    flops, byts = alg[dom]
+    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    ach_tflops = flops / (avg_ms / 1e3) / 1e12
+    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    traffic = traffic_from_profiles(dom)
+    roofline = {"kernel": dom, "bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach_tflops / alu_peak, "traffic": traffic,
+                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
+                               "sampled during the timed region)",
+                "achieved_bytes_gbs": byts / (avg_ms / 1e3) / 1e9,
+                "hbm_frac_of_measured": byts / (avg_ms / 1e3) / 1e9 / hbm_peak,
+                "flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
+                "avg_launch_ms": avg_ms, "launches": acc[dom][1]}
+    kernels = {f: {"ms_total": acc[f][0], "launches": acc[f][1],
+                   "avg_us": 1e3 * acc[f][0] / max(1, acc[f][1]),
+                   "gflops": alg[f][0] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9,
+                   "gbs": alg[f][1] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9} for f in FAMILIES}
+    step_bytes = sum(alg[f][1] * (acc[f][1] / max(1, K)) for f in FAMILIES)
+    hbm_step_frac = step_bytes / (dev_ms / K / 1e3) / 1e9 / hbm_peak
+    launches = sum(acc[f][1] for f in FAMILIES) + 2 * K   # + the two energy-reduction kernels
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": tmax_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "elements": g32.n_elems, "l2_dofs": g32.n_l2,
+                   "hdiv_dofs": g32.n_hdiv, "applies_per_step": APPLIES_PER_STEP,
+                   "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "fp64": fp64,
+        "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernels,
+        "kernels_f64": {f: {"avg_us": 1e3 * acc64[f][0] / max(1, acc64[f][1]), "launches": acc64[f][1]}
+                        for f in FAMILIES},
+        "energy_drift_per_step": (energies[-1] - energies[0]) / max(1, len(energies) - 1) / energies[0],
+        "wall_s_timed": wall,
+    }
+
+    # ---------------- CPU baseline (oracle, 1 thread) and the stated error
+    if rank == 0 and not args.no_cpu_baseline:
+        tmp = tempfile.mkdtemp()
+        out = os.path.join(tmp, "u1")
+        res = run_oracle({"mode": "sample", "n": n, "out": out})
+        u1 = np.load(out + ".npy")
+        cpu_value = res["n_l2"] * APPLIES_PER_STEP / res["seconds"]
+        line["cpu_baseline"] = {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one SSP-RK3 STAGE substep (3 applies + projections) of the full "
+                                          "16^3 x 6 k=3 workload, numpy FP64, 1 BLAS thread",
+                                "seconds": res["seconds"]}
+        errs = {}
+        for prec in ("f32", "f64"):
+            g, s = make(prec)
+            with torch.cuda.stream(stream):
+                g.rk_substep(s, dt, 1)
+            stream.synchronize()
+            got = s.double().cpu().numpy()
+            errs[prec] = {"max_rel": float(np.abs(got - u1).max() / np.abs(u1).max()),
+                          "l2_rel": float(np.linalg.norm(got - u1) / np.linalg.norm(u1))}
+        line["error_vs_oracle_one_substep"] = errs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget-s", type=float, default=150.0,
+                    help="seconds of oracle work the reference arm aims for (sizes its per-step sample)")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_worker:
+        oracle_worker(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    if args.impl == "reference":
+        reference_arm(args, rank)
+    else:
+        our_arm(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * hopu.h -- C ABI of libhopu, the GB300 (sm_103a) implementation of the explicit
+ * convection part of the HOPU / MCS splitting scheme of
+ *   Lederer, Mooslechner, Schoeberl, "High-order projection-based upwind method for
+ *   simulation of transitional turbulent flows" (arXiv 2408.06698).
+ *
+ * The library applies, without assembling a matrix, the projection-based high-order
+ * upwind (HOPU) convection operator of Section 3.2 (eq. "hopudefinition"; with l = -1
+ * it is the upwind form of Section 2.2, eq. "upwind") to velocity fields on affine
+ * simplicial meshes (triangles, tetrahedra), and advances such fields by explicit
+ * SSP-RK3 substeps.  The implicit Stokes / pressure solves of Section 2.3 are not
+ * part of this library.
+ *
+ * Spaces and coefficient layouts (fixed by this ABI):
+ *
+ *   Reference element.  Every element's vertices are reordered by ascending periodic
+ *   representative id; the affine map x = x_0 + J xhat uses that order.  Local facet f
+ *   is opposite local vertex f.  Facets are numbered by the lexicographic order of their
+ *   sorted representative vertex tuples.  The canonical facet normal n_F is the unit
+ *   right-hand normal of the sorted vertex tuple (3D: (P1-P0)x(P2-P0); 2D: (P1-P0)
+ *   turned by -90 degrees); side A of a facet is the element whose outward normal is
+ *   n_F, side B the other one.
+ *
+ *   L2 space [P^k(T)]^d (the discontinuous space the convection operator acts in):
+ *   u|_T(x) = sum_{a,i} u[e][a][i] phi_i(xhat(x)) e_a, with phi_i the orthonormal
+ *   Dubiner basis of the unit simplex (graded by total degree; in 3D the index runs
+ *   over n = 0..k, p = 0..n, q = 0..n-p, r = n-p-q), e_a the Cartesian unit vectors.
+ *   Element-major: index (e*d + a)*nb + i, nb = C(k+d, d).
+ *
+ *   Velocity space V_h (the normal-continuous [P^k]^d space of Section 2.2, eq.
+ *   "disc_velspace", read as BDM_k so that Pi^l = I at l = k as Section 3.2 states):
+ *     facet dofs   u[F*nf + m]            = int_F (u . n_F) q_m ds,
+ *                  q_m(x(s)) the orthonormal Dubiner basis of the unit (d-1)-simplex in
+ *                  the sorted-vertex facet parameter s, nf = C(k+d-1, d-1);
+ *     interior dofs u[NF*nf + e*nint + j] = int_That uhat . z_j dxhat,
+ *                  uhat the contravariant Piola pull-back (u = J uhat / det J), z_j the
+ *                  interior moment functions of the BDM_k element (Nedelec first kind
+ *                  of index k-1) in the basis documented in the design doc,
+ *                  nint = d*nb - (d+1)*nf.
+ *
+ *   Quadrature: collapsed Gauss-Jacobi rules, exact to degree 3k-1 on elements and 3k
+ *   on facets (Section 2.2 asks for exact integration of every form).
+ *
+ * Conventions of every call:
+ *   - Coefficient pointers are DEVICE pointers owned by the caller, in the working
+ *     precision of the context (double for HOPU_FP64, float for HOPU_FP32).  The
+ *     library never frees or keeps them beyond the call.
+ *   - Mesh arrays and *host* pointers are host memory, copied or read during the call.
+ *   - All device work is enqueued asynchronously on the context's stream (set at
+ *     create time or by hopu_set_stream); calls that return host values synchronise
+ *     that stream.
+ *   - Every call returns a hopu_status.  The first error is sticky in the context
+ *     (later calls return it unchanged until hopu_clear_error); hopu_last_error gives
+ *     its text.  No call aborts or exits the process.
+ */
+#ifndef HOPU_H
+#define HOPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hopu_ctx hopu_ctx; /* opaque; owns every device table and scratch buffer */
+
+typedef enum {
+  HOPU_OK = 0,
+  HOPU_EINVAL = -1,   /* bad argument (NULL pointer, size, enum value)               */
+  HOPU_ENOMEM = -2,   /* host or device allocation failed                            */
+  HOPU_ECUDA = -3,    /* a CUDA runtime call failed (text in hopu_last_error)        */
+  HOPU_EMESH = -4,    /* mesh is not a valid closed simplicial mesh                  */
+  HOPU_ETIMEOUT = -5, /* a bounded device-side wait ran out                          */
+  HOPU_ENOTSUP = -6   /* valid request this build does not support (e.g. boundary)  */
+} hopu_status;
+
+typedef enum { HOPU_FP64 = 0, HOPU_FP32 = 1 } hopu_prec;
+
+typedef enum {
+  HOPU_HDIV_TO_L2 = 0,      /* E      : V_h -> L2 (gather, reference change of basis, Piola) */
+  HOPU_L2_TO_HDIV = 1,      /* R E^-1 : L2 -> V_h, local functionals then averaging R        */
+  HOPU_L2_TO_HDIV_DUAL = 2  /* E^T    : restrict an L2 residual to the V_h test functions    */
+} hopu_dir;
+
+typedef enum {
+  HOPU_WIND_STAGE = 0, /* w = u at every RK stage; the state lives in V_h          */
+  HOPU_WIND_FROZEN = 1 /* w fixed for all substeps; the state lives in L2          */
+} hopu_wind;
+
+/* Mesh description (all host memory, copied by hopu_create). */
+typedef struct {
+  int dim;                        /* 2 (triangles) or 3 (tetrahedra)                        */
+  int64_t n_vertices;
+  const double* coords;           /* [n_vertices][dim], unwrapped coordinates               */
+  int64_t n_elems;
+  const int64_t* elem_vertices;   /* [n_elems][dim+1] vertex ids                            */
+  const int64_t* vertex_rep;      /* [n_vertices] periodic representative, or NULL = itself */
+} hopu_mesh_desc;
+
+typedef struct {
+  int k;          /* polynomial order, 1..5                                               */
+  int l;          /* HOPU projection order: -1 = standard upwind (ILES, Section 3.1),
+                     0..k = Pi^l of Section 3.2 (l = k: central flux)                      */
+  int prec;       /* hopu_prec                                                            */
+  int wind_mode;  /* hopu_wind, used by hopu_rk_substep                                    */
+  int tile_hint;  /* 0 = library default; reserved for launch-shape tuning                 */
+} hopu_options;
+
+/* Build a context: validate and copy the mesh, compute FP64 geometry (Jacobians, Piola
+ * maps, normals), facet pairing, reference tables, and allocate device scratch.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  On failure *out is NULL
+ * and the status says why (EMESH: non-manifold facet, a facet whose two sides agree on
+ * the normal, a degenerate element; ENOTSUP: boundary facets, k outside 1..5).        */
+hopu_status hopu_create(const hopu_mesh_desc* mesh, const hopu_options* opts,
+                        void* cuda_stream, hopu_ctx** out);
+
+/* Release every device and host resource of the context.  NULL is accepted. */
+hopu_status hopu_destroy(hopu_ctx* ctx);
+
+/* Replace the stream later calls enqueue on. */
+hopu_status hopu_set_stream(hopu_ctx* ctx, void* cuda_stream);
+
+/* Sizes of the coefficient vectors: V_h length, L2 length (n_elems*dim*nb), facets. */
+hopu_status hopu_sizes(const hopu_ctx* ctx, int64_t* n_hdiv, int64_t* n_l2, int64_t* n_facets);
+
+/* Map coefficient vectors between V_h and L2 (Section 2.3: R is the averaging operator
+ * of the element-wise BDDC preconditioner, reused here as the back-projection).
+ * in/out: device vectors of the lengths hopu_sizes gives for the two spaces.
+ * in and out must not overlap.                                                         */
+hopu_status hopu_project(hopu_ctx* ctx, int dir, const void* in, void* out);
+
+/* y_l2 = M_L^{-1} c(w; u, .), the HOPU convection operator of Section 3.2 in its
+ * conservative form  c = sum_T -int (u (x) w) : grad v
+ *                      + sum_F int [(w.n)<u> + (I-Pi^l)(1/2|w.n|(I-Pi^l)[[u]])] . [[v]],
+ * equal to the paper's form for divergence-free normal-continuous w.  du/dt = -y.
+ * w_hdiv: wind as a V_h vector; u_l2: field as an L2 vector; y_l2: output L2 vector
+ * (must not overlap the inputs).  facet_l: optional per-facet projection order
+ * (int8 device array of n_facets entries in -1..k), NULL = opts.l for every facet.     */
+hopu_status hopu_apply_convection(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2,
+                                  void* y_l2, const int8_t* facet_l);
+
+/* n_substeps explicit SSP-RK3 substeps (Shu-Osher) of du/dt = -y(u) with step dt.
+ * STAGE wind: state is a V_h vector, updated in place, w = u at every stage.
+ * FROZEN wind: state is an L2 vector updated in place; the wind is the V_h vector last
+ * given to hopu_set_frozen_wind.  On a non-default stream the substep is captured once
+ * as a CUDA graph per (state pointer, dt) and replayed n_substeps times; on the legacy
+ * default stream (NULL) the kernels are launched directly.                             */
+hopu_status hopu_rk_substep(hopu_ctx* ctx, void* state, double dt, int n_substeps);
+
+/* Set the wind used by FROZEN substeps (copied to an internal L2 buffer). */
+hopu_status hopu_set_frozen_wind(hopu_ctx* ctx, const void* w_hdiv);
+
+/* FP64 reductions (synchronises the stream):
+ *   host_out[0] = 1/2 int |u|^2                             (kinetic energy)
+ *   host_out[1] = c(w; u, u)                                (0 if w_hdiv is NULL)
+ *   host_out[2] = sum_F int 1/2 |w.n| |(I-Pi^l)[[u]]|^2     (facet dissipation; 0 if NULL)
+ * For divergence-free normal-continuous w, host_out[1] == host_out[2] >= 0.            */
+hopu_status hopu_energy(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, double* host_out);
+
+/* Physical quadrature points (host output, FP64):
+ *   which = 0: facet points [n_facets][nqf][dim], taken from side A;
+ *   which = 1: volume points [n_elems][nq][dim].
+ * count_out (may be NULL) receives the number of points.  host_out may be NULL to
+ * query the count only.                                                                */
+hopu_status hopu_points(hopu_ctx* ctx, int which, double* host_out, int64_t* count_out);
+
+/* Canonical V_h interpolant (the moments above, by the library's quadrature) of a
+ * field given at the points of hopu_points: fvals [n_facets][nqf][dim] and
+ * vvals [n_elems][nq][dim] (host, FP64).  u_hdiv: device output in working precision. */
+hopu_status hopu_interpolate(hopu_ctx* ctx, const double* fvals, const double* vvals,
+                             void* u_hdiv);
+
+/* Text of the sticky error ("" when none).  Valid until the next call on ctx.
+ * With ctx == NULL: the text of the last failed hopu_create on this thread.          */
+const char* hopu_last_error(const hopu_ctx* ctx);
+
+/* Clear the sticky error. */
+hopu_status hopu_clear_error(hopu_ctx* ctx);
+
+/* Kernel families timed by the profiling hook. */
+typedef enum {
+  HOPU_K_V2L = 0,        /* V_h -> L2 projection                                       */
+  HOPU_K_FACET = 1,      /* facet flux (traces, upwind, HOPU projections)              */
+  HOPU_K_VOLUME = 2,     /* volume term + facet lift + inverse mass (+ RK combination) */
+  HOPU_K_L2V_ELEM = 3,   /* L2 -> V_h, element-local functionals                       */
+  HOPU_K_L2V_FACET = 4,  /* L2 -> V_h, averaging R of the facet functionals            */
+  HOPU_K_COUNT = 5
+} hopu_kernel_family;
+
+/* Profiling: with enable != 0 every later kernel launch of the context is bracketed by
+ * CUDA timing events on the context stream (also inside captured substep graphs; the
+ * cached graph is re-captured when profiling is switched).                            */
+hopu_status hopu_profile(hopu_ctx* ctx, int enable);
+
+/* Synchronise the stream and ADD the device time (ms) and launch count of every
+ * profiled launch since the previous read to ms[HOPU_K_COUNT] / launches[HOPU_K_COUNT]
+ * (host arrays the caller initialises).  A replayed substep graph is read once per
+ * call: read after every hopu_rk_substep(..., n_substeps = 1) for exact totals.       */
+hopu_status hopu_profile_read(hopu_ctx* ctx, double* ms, int64_t* launches);
+
+/* Host-only self check of the reference tables of (dim, k), no GPU needed:
+ * report[0] = max relative error of the volume rule on monomials up to degree 3k-1,
+ * report[1] = same for the facet rule up to degree 3k (closed form a!b!c!/(a+b+c+d)!),
+ * report[2] = max |M - I| of the basis mass matrix (orthonormality),
+ * report[3] = max |D Dinv - I| of the degree-of-freedom matrix.                        */
+hopu_status hopu_selftest(int dim, int k, double* report);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOPU_H */

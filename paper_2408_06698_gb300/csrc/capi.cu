@@ -1,0 +1,661 @@
+// C ABI of libhopu (declared in include/hopu.h): context management, the explicit
+// SSP-RK3 substep driver with CUDA-graph replay, FP64 reductions and the host-side
+// interpolation / point queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hopu.h"
+#include "hopu_internal.h"
+#include "meshtopo.h"
+#include "reftables.h"
+
+namespace hopu {
+Ops* make_ops_2_1(bool);
+Ops* make_ops_2_2(bool);
+Ops* make_ops_2_3(bool);
+Ops* make_ops_2_4(bool);
+Ops* make_ops_3_1(bool);
+Ops* make_ops_3_2(bool);
+Ops* make_ops_3_3(bool);
+Ops* make_ops_3_4(bool);
+Ops* make_ops_3_5(bool);
+
+Ops* make_ops(int dim, int k, bool fp64) {
+  if (dim == 2) {
+    switch (k) {
+      case 1: return make_ops_2_1(fp64);
+      case 2: return make_ops_2_2(fp64);
+      case 3: return make_ops_2_3(fp64);
+      case 4: return make_ops_2_4(fp64);
+      default: return nullptr;
+    }
+  }
+  if (dim == 3) {
+    switch (k) {
+      case 1: return make_ops_3_1(fp64);
+      case 2: return make_ops_3_2(fp64);
+      case 3: return make_ops_3_3(fp64);
+      case 4: return make_ops_3_4(fp64);
+      case 5: return make_ops_3_5(fp64);
+      default: return nullptr;
+    }
+  }
+  return nullptr;
+}
+
+// ---------------------------------------------------------------- FP64 reductions
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kRedThreads];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// partial[b] = sum over this block's strided entries of |det J_e| a_t b_t
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_weighted_dot(int64_t E, int NL, int G, const double* geo,
+                                                              const T* a, const T* b, double* partial) {
+  double s = 0.0;
+  const int64_t n = E * NL;
+  for (int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; t < n; t += (int64_t)gridDim.x * kRedThreads) {
+    const int64_t e = t / NL;
+    s += geo[e * G + G - 1] * double(a[t]) * double(b[t]);
+  }
+  const double tot = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum(const double* in, int64_t n, double* out) {
+  double s = 0.0;
+  for (int64_t t = threadIdx.x; t < n; t += kRedThreads) s += in[t];
+  const double tot = block_sum(s);
+  if (threadIdx.x == 0) *out = tot;
+}
+
+}  // namespace hopu
+
+using namespace hopu;
+
+struct hopu_ctx {
+  int dim = 0, k = 0, l = -1, prec = 0, wind = 0;
+  bool fp64 = true;
+  size_t tsize = 8;
+  cudaStream_t stream = nullptr;
+  MeshTopo topo;
+  RefTables ref;
+  int64_t n_hdiv = 0, n_l2 = 0;
+  DevMesh dm;
+  DevTabs dt;
+  Ops* ops = nullptr;
+  int nsm = 1, red_blocks = 1;
+  // device memory
+  void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
+  void* d_tabs = nullptr;   // every reference table
+  void* d_gam = nullptr;    // [NF][nf][d] facet flux moments
+  void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals
+  void* d_uL = nullptr;     // L2 stage field
+  void* d_yL = nullptr;     // L2 operator output
+  void* d_wL = nullptr;     // L2 wind of apply_convection / energy
+  void* d_wfz = nullptr;    // L2 frozen wind
+  void* d_s1 = nullptr;     // RK stage vectors (max of V_h and L2 lengths)
+  void* d_s2 = nullptr;
+  double* d_diss = nullptr; // [NF]
+  double* d_red = nullptr;  // partial sums + 4 scalars
+  bool have_frozen = false;
+  // cached CUDA graph of one substep
+  cudaGraphExec_t gexec = nullptr;
+  void* g_state = nullptr;
+  double g_dt = 0.0;
+  int g_wind = -1;
+  // profiling: CUDA events around every kernel launch (pairs 0..kProfPairs-1 belong to
+  // the captured substep graph, the rest to direct launches)
+  bool prof_on = false;
+  bool capturing = false;
+  bool graph_replayed = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<std::pair<int, int>> prof_graph, prof_direct;  // (pair index, kernel family)
+  int prof_next_direct = 0;
+  int status = HOPU_OK;
+  std::string err;
+};
+
+namespace {
+
+hopu_status fail(hopu_ctx* c, int code, const std::string& msg) {
+  if (c && c->status == HOPU_OK) {
+    c->status = code;
+    c->err = msg;
+  }
+  return (hopu_status)code;
+}
+
+hopu_status cuda_fail(hopu_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, HOPU_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define HOPU_CUDA(ctx, call)                                 \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+#define HOPU_PRECHECK(ctx)                           \
+  do {                                               \
+    if (!(ctx)) return HOPU_EINVAL;                  \
+    if ((ctx)->status != HOPU_OK) return (hopu_status)(ctx)->status; \
+  } while (0)
+
+hopu_status check_launch(hopu_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  return HOPU_OK;
+}
+
+constexpr int kProfPairs = 64;
+
+// Run launch() on the context stream, bracketed by a pair of timing events when
+// profiling is on.  Inside a graph capture the event records become graph nodes, so
+// every replay re-records them.
+template <class F>
+void timed(hopu_ctx* c, int family, F&& launch) {
+  if (!c->prof_on || c->ev.empty()) {
+    launch();
+    return;
+  }
+  int p;
+  if (c->capturing) {
+    p = (int)c->prof_graph.size() % kProfPairs;
+    c->prof_graph.push_back({p, family});
+  } else {
+    p = kProfPairs + c->prof_next_direct;
+    c->prof_next_direct = (c->prof_next_direct + 1) % kProfPairs;
+    if ((int)c->prof_direct.size() >= kProfPairs) c->prof_direct.erase(c->prof_direct.begin());
+    c->prof_direct.push_back({p, family});
+  }
+  // inside a capture only the External flag turns the record into a graph node
+  const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaEventRecordWithFlags(c->ev[2 * p], c->stream, flags);
+  launch();
+  cudaEventRecordWithFlags(c->ev[2 * p + 1], c->stream, flags);
+}
+
+void free_all(hopu_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  void* ptrs[] = {c->d_mesh, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
+                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c->ops;
+}
+
+size_t align16(size_t n) { return (n + 15) / 16 * 16; }
+
+template <typename T>
+void convert(const std::vector<double>& src, std::vector<unsigned char>& dst, size_t off) {
+  T* p = reinterpret_cast<T*>(dst.data() + off);
+  for (size_t i = 0; i < src.size(); ++i) p[i] = (T)src[i];
+}
+
+// Reorder the host FP64 tables into the kernel layouts (see hopu_internal.h).
+void kernel_tables(const RefTables& R, std::vector<std::vector<double>>& out) {
+  const int d = R.dim, nb = R.nb, nf = R.nf, nq = R.nq, nqf = R.nqf, nl = R.nloc;
+  out.assign(9, {});
+  auto& Bt = out[0];
+  auto& Gt = out[1];
+  auto& TrM = out[2];
+  auto& TrP = out[3];
+  auto& Psi = out[4];
+  auto& Wf = out[5];
+  auto& DinvT = out[6];
+  auto& DT = out[7];
+  auto& Dinv = out[8];
+  Bt.resize((size_t)nb * nq);
+  Gt.resize((size_t)nb * d * nq);
+  for (int i = 0; i < nb; ++i)
+    for (int q = 0; q < nq; ++q) {
+      Bt[(size_t)i * nq + q] = R.phi[(size_t)q * nb + i];
+      for (int c = 0; c < d; ++c) Gt[((size_t)i * d + c) * nq + q] = R.wq[q] * R.dphi[((size_t)q * nb + i) * d + c];
+    }
+  TrM = R.trm;
+  TrP.resize((size_t)(d + 1) * nb * nqf);
+  for (int f = 0; f <= d; ++f)
+    for (int i = 0; i < nb; ++i)
+      for (int q = 0; q < nqf; ++q) TrP[((size_t)f * nb + i) * nqf + q] = R.phif[((size_t)f * nqf + q) * nb + i];
+  Psi.resize((size_t)nf * nqf);
+  for (int m = 0; m < nf; ++m)
+    for (int q = 0; q < nqf; ++q) Psi[(size_t)m * nqf + q] = R.psi[(size_t)q * nf + m];
+  Wf = R.wf;
+  DinvT.resize((size_t)nl * nl);
+  DT.resize((size_t)nl * nl);
+  for (int r = 0; r < nl; ++r)
+    for (int s = 0; s < nl; ++s) {
+      DinvT[(size_t)s * nl + r] = R.Dinv[(size_t)r * nl + s];
+      DT[(size_t)s * nl + r] = R.D[(size_t)r * nl + s];
+    }
+  Dinv = R.Dinv;
+}
+
+void enqueue_v2l(hopu_ctx* c, const void* uV, void* uL) {
+  timed(c, HOPU_K_V2L, [&] { c->ops->v2l(c->dm, c->dt, uV, uL, c->stream); });
+}
+
+void enqueue_l2v(hopu_ctx* c, const void* yL, bool dual, Combine cmb, void* outV) {
+  timed(c, HOPU_K_L2V_ELEM, [&] { c->ops->l2v_elem(c->dm, c->dt, yL, dual, c->d_lf, cmb, outV, c->stream); });
+  timed(c, HOPU_K_L2V_FACET, [&] { c->ops->l2v_facet(c->dm, c->d_lf, dual, cmb, outV, c->stream); });
+}
+
+hopu_status enqueue_stage_apply(hopu_ctx* c, const void* uL, const void* wL, int l, const int8_t* facet_l,
+                                double* diss, Combine cmb, void* out) {
+  timed(c, HOPU_K_FACET, [&] { c->ops->facet(c->dm, c->dt, uL, wL, l, facet_l, c->d_gam, diss, c->stream); });
+  timed(c, HOPU_K_VOLUME, [&] { c->ops->volume(c->dm, c->dt, uL, wL, c->d_gam, cmb, out, c->stream); });
+  return check_launch(c, "apply kernels");
+}
+
+// One SSP-RK3 (Shu-Osher) substep on the context stream.
+hopu_status enqueue_substep(hopu_ctx* c, void* state, double dt) {
+  const Combine st[3] = {
+      {1.0, state, 0.0, nullptr, -dt},
+      {0.75, state, 0.25, c->d_s1, -0.25 * dt},
+      {1.0 / 3.0, state, 2.0 / 3.0, c->d_s2, -2.0 / 3.0 * dt},
+  };
+  const void* in[3] = {state, c->d_s1, c->d_s2};
+  void* out[3] = {c->d_s1, c->d_s2, state};
+  for (int s = 0; s < 3; ++s) {
+    if (c->wind == HOPU_WIND_STAGE) {
+      enqueue_v2l(c, in[s], c->d_uL);
+      Combine plain;
+      hopu_status r = enqueue_stage_apply(c, c->d_uL, c->d_uL, c->l, nullptr, nullptr, plain, c->d_yL);
+      if (r != HOPU_OK) return r;
+      enqueue_l2v(c, c->d_yL, false, st[s], out[s]);
+    } else {
+      hopu_status r = enqueue_stage_apply(c, in[s], c->d_wfz, c->l, nullptr, nullptr, st[s], out[s]);
+      if (r != HOPU_OK) return r;
+    }
+  }
+  return check_launch(c, "substep kernels");
+}
+
+hopu_status weighted_dot(hopu_ctx* c, const void* a, const void* b, int slot) {
+  const int G = geo_stride(c->dim);
+  if (c->fp64)
+    k_weighted_dot<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const double*)a, (const double*)b, c->d_red);
+  else
+    k_weighted_dot<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const float*)a, (const float*)b, c->d_red);
+  k_sum<<<1, kRedThreads, 0, c->stream>>>(c->d_red, c->red_blocks, c->d_red + c->red_blocks + slot);
+  return check_launch(c, "reduction kernels");
+}
+
+}  // namespace
+
+namespace {
+thread_local std::string g_create_error;
+
+hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, void* cuda_stream, hopu_ctx** out) {
+  if (!mesh || !opts) return HOPU_EINVAL;
+  if (opts->prec != HOPU_FP64 && opts->prec != HOPU_FP32) return HOPU_EINVAL;
+  if (opts->wind_mode != HOPU_WIND_STAGE && opts->wind_mode != HOPU_WIND_FROZEN) return HOPU_EINVAL;
+  if (mesh->dim != 2 && mesh->dim != 3) return HOPU_EINVAL;
+  if (opts->k < 1 || opts->k > (mesh->dim == 2 ? 4 : 5)) return HOPU_ENOTSUP;
+  if (opts->l < -1 || opts->l > opts->k) return HOPU_EINVAL;
+  hopu_ctx* c = new (std::nothrow) hopu_ctx();
+  if (!c) return HOPU_ENOMEM;
+  c->dim = mesh->dim;
+  c->k = opts->k;
+  c->l = opts->l;
+  c->prec = opts->prec;
+  c->wind = opts->wind_mode;
+  c->fp64 = opts->prec == HOPU_FP64;
+  c->tsize = c->fp64 ? 8 : 4;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  std::string err;
+  int rc = build_mesh_topo(mesh->dim, mesh->n_vertices, mesh->coords, mesh->n_elems, mesh->elem_vertices,
+                           mesh->vertex_rep, c->topo, err);
+  if (rc != HOPU_OK) return fail(c, rc, err);
+  if (!build_ref_tables(c->dim, c->k, c->ref, err)) return fail(c, HOPU_EINVAL, err);
+  const RefTables& R = c->ref;
+  const int64_t E = c->topo.n_elems, NF = c->topo.n_facets;
+  c->n_l2 = E * R.nloc;
+  c->n_hdiv = NF * R.nf + E * R.nint;
+  c->ops = make_ops(c->dim, c->k, c->fp64);
+  if (!c->ops) return fail(c, HOPU_ENOTSUP, "no kernel family for this (dim, k)");
+  cudaError_t ce = c->ops->prepare();
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "kernel setup");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+  c->red_blocks = 2 * c->nsm;
+
+  // mesh upload
+  const int G = geo_stride(c->dim);
+  const size_t s_geo = align16(sizeof(double) * E * G), s_efc = align16(sizeof(int32_t) * E * (c->dim + 1));
+  const size_t s_f = align16(sizeof(int32_t) * NF), s_fgeo = align16(sizeof(double) * NF * (c->dim + 1));
+  std::vector<unsigned char> hm(s_geo + s_efc + 2 * s_f + s_fgeo, 0);
+  std::memcpy(hm.data(), c->topo.geo.data(), sizeof(double) * E * G);
+  std::memcpy(hm.data() + s_geo, c->topo.efc.data(), sizeof(int32_t) * E * (c->dim + 1));
+  std::memcpy(hm.data() + s_geo + s_efc, c->topo.fa.data(), sizeof(int32_t) * NF);
+  std::memcpy(hm.data() + s_geo + s_efc + s_f, c->topo.fb.data(), sizeof(int32_t) * NF);
+  std::memcpy(hm.data() + s_geo + s_efc + 2 * s_f, c->topo.fgeo.data(), sizeof(double) * NF * (c->dim + 1));
+  HOPU_CUDA(c, cudaMalloc(&c->d_mesh, hm.size()));
+  HOPU_CUDA(c, cudaMemcpy(c->d_mesh, hm.data(), hm.size(), cudaMemcpyHostToDevice));
+  unsigned char* base = static_cast<unsigned char*>(c->d_mesh);
+  c->dm.E = E;
+  c->dm.NF = NF;
+  c->dm.geo = reinterpret_cast<const double*>(base);
+  c->dm.efc = reinterpret_cast<const int32_t*>(base + s_geo);
+  c->dm.fa = reinterpret_cast<const int32_t*>(base + s_geo + s_efc);
+  c->dm.fb = reinterpret_cast<const int32_t*>(base + s_geo + s_efc + s_f);
+  c->dm.fgeo = reinterpret_cast<const double*>(base + s_geo + s_efc + 2 * s_f);
+
+  // tables upload, converted to the working precision
+  std::vector<std::vector<double>> tabs;
+  kernel_tables(R, tabs);
+  std::vector<size_t> offs;
+  size_t total = 0;
+  for (auto& t : tabs) {
+    offs.push_back(total);
+    total += align16(c->tsize * t.size());
+  }
+  std::vector<unsigned char> ht(total, 0);
+  for (size_t i = 0; i < tabs.size(); ++i) {
+    if (c->fp64) convert<double>(tabs[i], ht, offs[i]);
+    else convert<float>(tabs[i], ht, offs[i]);
+  }
+  HOPU_CUDA(c, cudaMalloc(&c->d_tabs, total));
+  HOPU_CUDA(c, cudaMemcpy(c->d_tabs, ht.data(), total, cudaMemcpyHostToDevice));
+  unsigned char* tb = static_cast<unsigned char*>(c->d_tabs);
+  const void** slots[9] = {&c->dt.Bt, &c->dt.Gt, &c->dt.TrM, &c->dt.TrP, &c->dt.Psi,
+                           &c->dt.Wf, &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv};
+  for (int i = 0; i < 9; ++i) *slots[i] = tb + offs[i];
+
+  // scratch
+  const size_t ts = c->tsize;
+  const int64_t nstate = std::max(c->n_hdiv, c->n_l2);
+  HOPU_CUDA(c, cudaMalloc(&c->d_gam, ts * NF * R.nf * c->dim));
+  HOPU_CUDA(c, cudaMalloc(&c->d_lf, ts * E * (c->dim + 1) * R.nf));
+  HOPU_CUDA(c, cudaMalloc(&c->d_uL, ts * c->n_l2));
+  HOPU_CUDA(c, cudaMalloc(&c->d_yL, ts * c->n_l2));
+  HOPU_CUDA(c, cudaMalloc(&c->d_wL, ts * c->n_l2));
+  HOPU_CUDA(c, cudaMalloc(&c->d_wfz, ts * c->n_l2));
+  HOPU_CUDA(c, cudaMalloc(&c->d_s1, ts * nstate));
+  HOPU_CUDA(c, cudaMalloc(&c->d_s2, ts * nstate));
+  HOPU_CUDA(c, cudaMalloc((void**)&c->d_diss, sizeof(double) * NF));
+  HOPU_CUDA(c, cudaMalloc((void**)&c->d_red, sizeof(double) * (c->red_blocks + 8)));
+  return HOPU_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hopu_status hopu_create(const hopu_mesh_desc* mesh, const hopu_options* opts, void* cuda_stream, hopu_ctx** out) {
+  if (!out) return HOPU_EINVAL;
+  *out = nullptr;
+  hopu_ctx* c = nullptr;
+  hopu_status r = create_impl(mesh, opts, cuda_stream, &c);
+  if (r != HOPU_OK) {
+    g_create_error = c ? c->err : std::string("invalid arguments");
+    if (c) hopu_destroy(c);
+    return r;
+  }
+  g_create_error.clear();
+  *out = c;
+  return HOPU_OK;
+}
+
+hopu_status hopu_destroy(hopu_ctx* c) {
+  if (!c) return HOPU_OK;
+  free_all(c);
+  delete c;
+  return HOPU_OK;
+}
+
+hopu_status hopu_set_stream(hopu_ctx* c, void* cuda_stream) {
+  HOPU_PRECHECK(c);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return HOPU_OK;
+}
+
+hopu_status hopu_sizes(const hopu_ctx* c, int64_t* n_hdiv, int64_t* n_l2, int64_t* n_facets) {
+  if (!c) return HOPU_EINVAL;
+  if (n_hdiv) *n_hdiv = c->n_hdiv;
+  if (n_l2) *n_l2 = c->n_l2;
+  if (n_facets) *n_facets = c->topo.n_facets;
+  return HOPU_OK;
+}
+
+hopu_status hopu_project(hopu_ctx* c, int dir, const void* in, void* out) {
+  HOPU_PRECHECK(c);
+  if (!in || !out || in == out) return fail(c, HOPU_EINVAL, "project: NULL or aliased vectors");
+  if (dir == HOPU_HDIV_TO_L2) {
+    enqueue_v2l(c, in, out);
+  } else if (dir == HOPU_L2_TO_HDIV || dir == HOPU_L2_TO_HDIV_DUAL) {
+    Combine plain;
+    enqueue_l2v(c, in, dir == HOPU_L2_TO_HDIV_DUAL, plain, out);
+  } else {
+    return fail(c, HOPU_EINVAL, "project: unknown direction");
+  }
+  return check_launch(c, "project kernels");
+}
+
+hopu_status hopu_apply_convection(hopu_ctx* c, const void* w_hdiv, const void* u_l2, void* y_l2,
+                                  const int8_t* facet_l) {
+  HOPU_PRECHECK(c);
+  if (!w_hdiv || !u_l2 || !y_l2 || y_l2 == u_l2) return fail(c, HOPU_EINVAL, "apply_convection: NULL or aliased vectors");
+  enqueue_v2l(c, w_hdiv, c->d_wL);
+  Combine plain;
+  return enqueue_stage_apply(c, u_l2, c->d_wL, c->l, facet_l, nullptr, plain, y_l2);
+}
+
+hopu_status hopu_set_frozen_wind(hopu_ctx* c, const void* w_hdiv) {
+  HOPU_PRECHECK(c);
+  if (!w_hdiv) return fail(c, HOPU_EINVAL, "set_frozen_wind: NULL wind");
+  enqueue_v2l(c, w_hdiv, c->d_wfz);
+  c->have_frozen = true;
+  return check_launch(c, "set_frozen_wind");
+}
+
+hopu_status hopu_rk_substep(hopu_ctx* c, void* state, double dt, int n_substeps) {
+  HOPU_PRECHECK(c);
+  if (!state || n_substeps < 0 || !std::isfinite(dt)) return fail(c, HOPU_EINVAL, "rk_substep: bad arguments");
+  if (c->wind == HOPU_WIND_FROZEN && !c->have_frozen) return fail(c, HOPU_EINVAL, "rk_substep: FROZEN wind not set");
+  if (n_substeps == 0) return HOPU_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HOPU_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+  const bool can_graph = (c->stream != nullptr) && cs == cudaStreamCaptureStatusNone;
+  if (!can_graph) {
+    for (int s = 0; s < n_substeps; ++s) {
+      hopu_status r = enqueue_substep(c, state, dt);
+      if (r != HOPU_OK) return r;
+    }
+    return HOPU_OK;
+  }
+  if (!c->gexec || c->g_state != state || c->g_dt != dt || c->g_wind != c->wind) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    HOPU_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->prof_graph.clear();
+    hopu_status r = enqueue_substep(c, state, dt);
+    c->capturing = false;
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+    if (r != HOPU_OK) return r;
+    if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      c->gexec = nullptr;
+      return cuda_fail(c, ie, "cudaGraphInstantiate");
+    }
+    c->g_state = state;
+    c->g_dt = dt;
+    c->g_wind = c->wind;
+  }
+  for (int s = 0; s < n_substeps; ++s) HOPU_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+  c->graph_replayed = true;
+  return HOPU_OK;
+}
+
+hopu_status hopu_energy(hopu_ctx* c, const void* w_hdiv, const void* u_l2, double* host_out) {
+  HOPU_PRECHECK(c);
+  if (!u_l2 || !host_out) return fail(c, HOPU_EINVAL, "energy: NULL pointer");
+  hopu_status r = weighted_dot(c, u_l2, u_l2, 0);
+  if (r != HOPU_OK) return r;
+  double vals[3] = {0.0, 0.0, 0.0};
+  if (w_hdiv) {
+    enqueue_v2l(c, w_hdiv, c->d_wL);
+    Combine plain;
+    r = enqueue_stage_apply(c, u_l2, c->d_wL, c->l, nullptr, c->d_diss, plain, c->d_yL);
+    if (r != HOPU_OK) return r;
+    // c(w;u,u) = sum_T |det J| u . y  (y = M^{-1} r, M = |det J| I)
+    r = weighted_dot(c, u_l2, c->d_yL, 1);
+    if (r != HOPU_OK) return r;
+    k_sum<<<1, kRedThreads, 0, c->stream>>>(c->d_diss, c->topo.n_facets, c->d_red + c->red_blocks + 2);
+    r = check_launch(c, "dissipation sum");
+    if (r != HOPU_OK) return r;
+  }
+  HOPU_CUDA(c, cudaMemcpyAsync(vals, c->d_red + c->red_blocks, sizeof(double) * (w_hdiv ? 3 : 1),
+                               cudaMemcpyDeviceToHost, c->stream));
+  HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  host_out[0] = 0.5 * vals[0];
+  host_out[1] = w_hdiv ? vals[1] : 0.0;
+  host_out[2] = w_hdiv ? vals[2] : 0.0;
+  return HOPU_OK;
+}
+
+hopu_status hopu_points(hopu_ctx* c, int which, double* host_out, int64_t* count_out) {
+  HOPU_PRECHECK(c);
+  if (which != 0 && which != 1) return fail(c, HOPU_EINVAL, "points: which must be 0 or 1");
+  const int64_t cnt = which == 0 ? c->topo.n_facets * c->ref.nqf : c->topo.n_elems * c->ref.nq;
+  if (count_out) *count_out = cnt;
+  if (!host_out) return HOPU_OK;
+  if (which == 0) facet_points(c->topo, c->ref.sq, c->ref.nqf, host_out);
+  else volume_points(c->topo, c->ref.xq, c->ref.nq, host_out);
+  return HOPU_OK;
+}
+
+hopu_status hopu_interpolate(hopu_ctx* c, const double* fvals, const double* vvals, void* u_hdiv) {
+  HOPU_PRECHECK(c);
+  if (!fvals || !vvals || !u_hdiv) return fail(c, HOPU_EINVAL, "interpolate: NULL pointer");
+  const RefTables& R = c->ref;
+  const int d = c->dim, G = geo_stride(d);
+  const int64_t NF = c->topo.n_facets, E = c->topo.n_elems;
+  std::vector<double> h((size_t)c->n_hdiv, 0.0);
+  for (int64_t F = 0; F < NF; ++F) {
+    const double* n = &c->topo.fgeo[(size_t)F * (d + 1)];
+    const double aF = n[d];
+    for (int m = 0; m < R.nf; ++m) {
+      double acc = 0.0;
+      for (int q = 0; q < R.nqf; ++q) {
+        double un = 0.0;
+        for (int a = 0; a < d; ++a) un += fvals[((size_t)F * R.nqf + q) * d + a] * n[a];
+        acc += R.wf[q] * un * R.psi[(size_t)q * R.nf + m];
+      }
+      h[(size_t)F * R.nf + m] = aF * acc;
+    }
+  }
+  std::vector<double> uhat((size_t)R.nq * d);
+  for (int64_t e = 0; e < E; ++e) {
+    const double* g = &c->topo.geo[(size_t)e * G];
+    const double det = g[2 * d * d];
+    for (int q = 0; q < R.nq; ++q)
+      for (int b = 0; b < d; ++b) {
+        double acc = 0.0;
+        for (int a = 0; a < d; ++a) acc += g[d * d + b * d + a] * vvals[((size_t)e * R.nq + q) * d + a];
+        uhat[(size_t)q * d + b] = det * acc;
+      }
+    for (int j = 0; j < R.nint; ++j) {
+      double acc = 0.0;
+      for (int q = 0; q < R.nq; ++q)
+        for (int b = 0; b < d; ++b) acc += R.wq[q] * uhat[(size_t)q * d + b] * R.z[((size_t)j * R.nq + q) * d + b];
+      h[(size_t)NF * R.nf + (size_t)e * R.nint + j] = acc;
+    }
+  }
+  std::vector<unsigned char> buf(c->tsize * h.size());
+  if (c->fp64) convert<double>(h, buf, 0);
+  else convert<float>(h, buf, 0);
+  HOPU_CUDA(c, cudaMemcpyAsync(u_hdiv, buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
+  HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOPU_OK;
+}
+
+hopu_status hopu_profile(hopu_ctx* c, int enable) {
+  HOPU_PRECHECK(c);
+  if (enable && c->ev.empty()) {
+    c->ev.resize(4 * kProfPairs, nullptr);
+    for (auto& e : c->ev) HOPU_CUDA(c, cudaEventCreate(&e));
+  }
+  if ((enable != 0) != c->prof_on && c->gexec) {  // the cached graph must be re-captured
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->prof_on = enable != 0;
+  c->prof_graph.clear();
+  c->prof_direct.clear();
+  c->graph_replayed = false;
+  return HOPU_OK;
+}
+
+hopu_status hopu_profile_read(hopu_ctx* c, double* ms, int64_t* launches) {
+  HOPU_PRECHECK(c);
+  if (!ms || !launches) return fail(c, HOPU_EINVAL, "profile_read: NULL pointer");
+  if (!c->prof_on) return HOPU_OK;
+  HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  auto add = [&](const std::vector<std::pair<int, int>>& lst) -> hopu_status {
+    for (const auto& pf : lst) {
+      float t = 0.f;
+      HOPU_CUDA(c, cudaEventElapsedTime(&t, c->ev[2 * pf.first], c->ev[2 * pf.first + 1]));
+      ms[pf.second] += t;
+      launches[pf.second] += 1;
+    }
+    return HOPU_OK;
+  };
+  if (c->graph_replayed) {
+    hopu_status r = add(c->prof_graph);
+    if (r != HOPU_OK) return r;
+  }
+  hopu_status r = add(c->prof_direct);
+  if (r != HOPU_OK) return r;
+  c->prof_direct.clear();
+  c->graph_replayed = false;
+  return HOPU_OK;
+}
+
+const char* hopu_last_error(const hopu_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+hopu_status hopu_clear_error(hopu_ctx* c) {
+  if (!c) return HOPU_EINVAL;
+  c->status = HOPU_OK;
+  c->err.clear();
+  return HOPU_OK;
+}
+
+hopu_status hopu_selftest(int dim, int k, double* report) {
+  if (!report) return HOPU_EINVAL;
+  std::string err;
+  if (!selftest_ref_tables(dim, k, report, err)) return HOPU_EINVAL;
+  return HOPU_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal interface between the C ABI (capi.cu) and the per-(dim, k, precision)
+// kernel families (ops_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hopu {
+
+// Device view of the mesh (FP64 geometry, int32 connectivity).
+struct DevMesh {
+  int64_t E = 0, NF = 0;
+  const double* geo = nullptr;   // [E][2d^2+2]: J (row-major), Jinv, det J, |det J|
+  const int32_t* efc = nullptr;  // [E][d+1]: F*4 + (sigma<0)*2 + (element is side B)
+  const int32_t* fa = nullptr;   // [NF]: element*4 + local facet of side A
+  const int32_t* fb = nullptr;   // [NF]: same for side B
+  const double* fgeo = nullptr;  // [NF][d+1]: canonical unit normal n_F, a_F = |F|/|param|
+};
+
+// Device reference tables in working precision (all element-type T, 16-byte aligned).
+struct DevTabs {
+  const void* Bt = nullptr;     // [nb][nq]        phi_i(x_q)
+  const void* Gt = nullptr;     // [nb][d][nq]     w_q d phi_i / d xhat_c (x_q)
+  const void* TrM = nullptr;    // [d+1][nf][nb]   <phi_i o xhat_f, psi_m>_facet
+  const void* TrP = nullptr;    // [d+1][nb][nqf]  phi_i(xhat_f(s_q))
+  const void* Psi = nullptr;    // [nf][nqf]       psi_m(s_q)
+  const void* Wf = nullptr;     // [nqf]           facet weights
+  const void* DinvT = nullptr;  // [nloc][nloc]    DinvT[s][r] = Dinv[r][s]
+  const void* DT = nullptr;     // [nloc][nloc]    DT[s][r]    = D[r][s]
+  const void* Dinv = nullptr;   // [nloc][nloc]    Dinv[r][s]
+};
+
+// out = a0*x0 + a1*x1 + a2*v  (x0 / x1 may be null; out may alias x0 or x1)
+struct Combine {
+  double a0 = 0.0;
+  const void* x0 = nullptr;
+  double a1 = 0.0;
+  const void* x1 = nullptr;
+  double a2 = 1.0;
+};
+
+// One family of kernels for a fixed (dim, k, precision).  Every call enqueues on the
+// given stream and returns the number of kernels it launched.
+class Ops {
+ public:
+  virtual ~Ops() {}
+  virtual cudaError_t prepare() = 0;
+  // E: V_h -> L2
+  virtual int v2l(const DevMesh&, const DevTabs&, const void* uV, void* uL, cudaStream_t) = 0;
+  // facet flux moments gam[F][nf][d] (side A; side B gets the negative) and, if diss
+  // is not null, the facet dissipation per facet.  wL == uL means w = u.
+  virtual int facet(const DevMesh&, const DevTabs&, const void* uL, const void* wL, int l,
+                    const int8_t* facet_l, void* gam, double* diss, cudaStream_t) = 0;
+  // volume term + facet lift + inverse mass, combined into out.  wL == uL means w = u.
+  virtual int volume(const DevMesh&, const DevTabs&, const void* uL, const void* wL,
+                     const void* gam, Combine c, void* out, cudaStream_t) = 0;
+  // R E^{-1} (dual = false) or E^T (dual = true), combined into outV, in two launches:
+  // the element part writes interior dofs and the local facet functionals lf
+  // [E][d+1][nf]; the facet part averages (or sums) the two copies into the facet dofs.
+  virtual int l2v_elem(const DevMesh&, const DevTabs&, const void* yL, bool dual, void* lf,
+                       Combine c, void* outV, cudaStream_t) = 0;
+  virtual int l2v_facet(const DevMesh&, const void* lf, bool dual, Combine c, void* outV,
+                        cudaStream_t) = 0;
+};
+
+Ops* make_ops(int dim, int k, bool fp64);
+
+}  // namespace hopu

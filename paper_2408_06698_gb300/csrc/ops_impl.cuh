@@ -1,0 +1,140 @@
+// Launch wrappers of one kernel family (dimension D, order K, precision T).
+#pragma once
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace hopu {
+
+template <int D, int K, typename T>
+class OpsImpl final : public Ops {
+  using S = Shape<D, K>;
+  static constexpr size_t kLimit = 200 * 1024;  // shared-memory budget per CTA
+  static constexpr size_t sz = sizeof(T);
+  static constexpr size_t r4(size_t n) { return ((n + 3) / 4) * 4; }
+
+  static constexpr size_t kTabNL = size_t(S::nloc) * S::nloc * sz;
+  static constexpr bool kProjTab = kTabNL + kWarps * 2 * S::nloc * sz <= kLimit;
+  static constexpr size_t kV2lSmem = (kProjTab ? kTabNL : 0) + kWarps * 2 * S::nloc * sz;
+  static constexpr size_t kL2vSmem = (kProjTab ? kTabNL : 0) + kWarps * S::nloc * sz;
+
+  static constexpr size_t kFacTab = r4(size_t(D + 1) * S::nb * S::nqf + S::nf * S::nqf + S::nqf) * sz;
+  static constexpr bool kFacetTab = kFacTab + kWarps * 4 * S::nloc * sz <= kLimit;
+  static constexpr size_t facet_smem(bool wsep) {
+    return (kFacetTab ? kFacTab : 0) + kWarps * (wsep ? 4 : 2) * S::nloc * sz;
+  }
+
+  static constexpr size_t kVolTab = r4(size_t(S::nb) * S::nq * (D + 1) + size_t(D + 1) * S::nf * S::nb) * sz;
+  static constexpr size_t kNG = size_t(D + 1) * S::nf * D;
+  static constexpr bool kVolumeTab = kVolTab + kWarps * (2 * S::nloc + kNG) * sz <= kLimit;
+  static constexpr size_t volume_smem(bool wsep) {
+    return (kVolumeTab ? kVolTab : 0) + kWarps * ((wsep ? 2 : 1) * S::nloc + kNG) * sz;
+  }
+
+  int nsm_ = 1;
+  int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
+
+  template <typename Kern>
+  cudaError_t setup(Kern kern, size_t smem, int threads, int* grid) {
+    cudaError_t err = cudaSuccess;
+    if (smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    int occ = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (err != cudaSuccess) return err;
+    *grid = nsm_ * std::max(occ, 1);
+    return cudaSuccess;
+  }
+
+  static int clamp_grid(int g, int64_t items, int per_block) {
+    const int64_t need = (items + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, need));
+  }
+
+ public:
+  cudaError_t prepare() override {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    const int th = 32 * kWarps;
+    if ((err = setup(k_v2l<D, K, T, kProjTab>, kV2lSmem, th, &g_v2l_)) != cudaSuccess) return err;
+    if ((err = setup(k_facet<D, K, T, false, kFacetTab>, facet_smem(false), th, &g_fac_[0])) != cudaSuccess) return err;
+    if ((err = setup(k_facet<D, K, T, true, kFacetTab>, facet_smem(true), th, &g_fac_[1])) != cudaSuccess) return err;
+    if ((err = setup(k_volume<D, K, T, false, kVolumeTab>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
+    if ((err = setup(k_volume<D, K, T, true, kVolumeTab>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_elem<D, K, T, false, kProjTab>, kL2vSmem, th, &g_elem_[0])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_elem<D, K, T, true, kProjTab>, kL2vSmem, th, &g_elem_[1])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_facet<D, K, T, false>, 0, 256, &g_fsum_)) != cudaSuccess) return err;
+    return cudaSuccess;
+  }
+
+  int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
+    const int g = clamp_grid(g_v2l_, m.E, kWarps);
+    k_v2l<D, K, T, kProjTab><<<g, 32 * kWarps, kV2lSmem, st>>>(
+        m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
+    return 1;
+  }
+
+  int facet(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, int l,
+            const int8_t* facet_l, void* gam, double* diss, cudaStream_t st) override {
+    const bool wsep = (wL != nullptr && wL != uL);
+    const int g = clamp_grid(g_fac_[wsep ? 1 : 0], m.NF, kWarps);
+    if (wsep)
+      k_facet<D, K, T, true, kFacetTab><<<g, 32 * kWarps, facet_smem(true), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), l, facet_l, static_cast<T*>(gam), diss);
+    else
+      k_facet<D, K, T, false, kFacetTab><<<g, 32 * kWarps, facet_smem(false), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), l, facet_l, static_cast<T*>(gam), diss);
+    return 1;
+  }
+
+  int volume(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* gam,
+             Combine c, void* out, cudaStream_t st) override {
+    const bool wsep = (wL != nullptr && wL != uL);
+    const int g = clamp_grid(g_vol_[wsep ? 1 : 0], m.E, kWarps);
+    if (wsep)
+      k_volume<D, K, T, true, kVolumeTab><<<g, 32 * kWarps, volume_smem(true), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(gam),
+          static_cast<T*>(out), c);
+    else
+      k_volume<D, K, T, false, kVolumeTab><<<g, 32 * kWarps, volume_smem(false), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
+          static_cast<T*>(out), c);
+    return 1;
+  }
+
+  int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,
+               void* outV, cudaStream_t st) override {
+    const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, kWarps);
+    if (dual)
+      k_l2v_elem<D, K, T, true, kProjTab><<<g, 32 * kWarps, kL2vSmem, st>>>(
+          m, static_cast<const T*>(t.Dinv), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
+    else
+      k_l2v_elem<D, K, T, false, kProjTab><<<g, 32 * kWarps, kL2vSmem, st>>>(
+          m, static_cast<const T*>(t.DT), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
+    return 1;
+  }
+
+  int l2v_facet(const DevMesh& m, const void* lf, bool dual, Combine c, void* outV, cudaStream_t st) override {
+    const int gf = clamp_grid(g_fsum_, m.NF * S::nf, 256);
+    if (dual)
+      k_l2v_facet<D, K, T, true><<<gf, 256, 0, st>>>(m, static_cast<const T*>(lf), static_cast<T*>(outV), c);
+    else
+      k_l2v_facet<D, K, T, false><<<gf, 256, 0, st>>>(m, static_cast<const T*>(lf), static_cast<T*>(outV), c);
+    return 1;
+  }
+};
+
+}  // namespace hopu
+
+#define HOPU_DEFINE_OPS(D, K)                                               \
+  namespace hopu {                                                          \
+  Ops* make_ops_##D##_##K(bool fp64) {                                      \
+    if (fp64) return new OpsImpl<D, K, double>();                           \
+    return new OpsImpl<D, K, float>();                                      \
+  }                                                                         \
+  }

@@ -1,0 +1,183 @@
+"""Python binding of libhopu: a context object whose methods mirror the C ABI calls.
+
+PyTorch provides device memory and streams; every step of the convection path runs in
+the library's CUDA kernels.  Methods take and return torch tensors on the context's
+device in the context's working precision.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int64, c_void_p
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_PREC = {"f64": L.HOPU_FP64, "f32": L.HOPU_FP32}
+_WIND = {"stage": L.HOPU_WIND_STAGE, "frozen": L.HOPU_WIND_FROZEN}
+_DIR = {"hdiv_to_l2": L.HOPU_HDIV_TO_L2, "l2_to_hdiv": L.HOPU_L2_TO_HDIV, "l2_to_hdiv_dual": L.HOPU_L2_TO_HDIV_DUAL}
+
+
+class Hopu:
+    """One mesh, one order k, one precision: mirrors a ``hopu_ctx``.
+
+    coords [nv, d] float64, elems [ne, d+1] int64, rep [nv] int64 or None (host arrays).
+    """
+
+    def __init__(self, coords, elems, rep=None, k: int = 3, l: int = -1, prec: str = "f64",
+                 wind: str = "stage", device: str | torch.device = "cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhopu needs a CUDA device")
+        self.lib = L.load()
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float64 if prec == "f64" else torch.float32
+        self.prec, self.k, self.l, self.wind = prec, k, l, wind
+        self._coords = np.ascontiguousarray(coords, dtype=np.float64)
+        self._elems = np.ascontiguousarray(elems, dtype=np.int64)
+        self._rep = None if rep is None else np.ascontiguousarray(rep, dtype=np.int64)
+        self.dim = int(self._coords.shape[1])
+        desc = L.MeshDesc(self.dim, self._coords.shape[0], self._coords.ctypes.data, self._elems.shape[0],
+                          self._elems.ctypes.data, None if self._rep is None else self._rep.ctypes.data)
+        opts = L.Options(k, l, _PREC[prec], _WIND[wind], 0)
+        self.ctx = c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.hopu_create(byref(desc), byref(opts), c_void_p(self._stream()), byref(self.ctx))
+        if st != L.HOPU_OK:
+            raise L.HopuError(st, "hopu_create", self.lib.hopu_last_error(None).decode())
+        nh, nl, nf = c_int64(), c_int64(), c_int64()
+        self.lib.hopu_sizes(self.ctx, byref(nh), byref(nl), byref(nf))
+        self.n_hdiv, self.n_l2, self.n_facets = nh.value, nl.value, nf.value
+        self.n_elems = int(self._elems.shape[0])
+
+    # ------------------------------------------------------------------ plumbing
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _sync_stream(self):
+        self._check(self.lib.hopu_set_stream(self.ctx, c_void_p(self._stream())), "hopu_set_stream")
+
+    def _check(self, st: int, where: str):
+        if st != L.HOPU_OK:
+            raise L.HopuError(st, where, self.lib.hopu_last_error(self.ctx).decode())
+
+    def _vec(self, t: torch.Tensor, n: int, name: str) -> int:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name}: expected contiguous {self.dtype} tensor of {n} entries on {self.device}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+        return t.data_ptr()
+
+    def new(self, space: str) -> torch.Tensor:
+        n = self.n_hdiv if space == "hdiv" else self.n_l2
+        return torch.empty(n, dtype=self.dtype, device=self.device)
+
+    # ------------------------------------------------------------------ the C ABI calls
+    def project(self, direction: str, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        d = _DIR[direction]
+        nin, nout = (self.n_hdiv, self.n_l2) if d == L.HOPU_HDIV_TO_L2 else (self.n_l2, self.n_hdiv)
+        if out is None:
+            out = torch.empty(nout, dtype=self.dtype, device=self.device)
+        self._sync_stream()
+        self._check(self.lib.hopu_project(self.ctx, d, self._vec(x, nin, "in"), self._vec(out, nout, "out")),
+                    "hopu_project")
+        return out
+
+    def apply_convection(self, w_hdiv, u_l2, out=None, facet_l=None) -> torch.Tensor:
+        if out is None:
+            out = self.new("l2")
+        fl = None
+        if facet_l is not None:
+            if facet_l.dtype != torch.int8 or facet_l.numel() != self.n_facets or facet_l.device != self.device:
+                raise ValueError("facet_l must be an int8 device tensor with one entry per facet")
+            fl = facet_l.contiguous().data_ptr()
+        self._sync_stream()
+        self._check(self.lib.hopu_apply_convection(self.ctx, self._vec(w_hdiv, self.n_hdiv, "w_hdiv"),
+                                                   self._vec(u_l2, self.n_l2, "u_l2"),
+                                                   self._vec(out, self.n_l2, "y_l2"), fl), "hopu_apply_convection")
+        return out
+
+    def set_frozen_wind(self, w_hdiv: torch.Tensor):
+        self._sync_stream()
+        self._check(self.lib.hopu_set_frozen_wind(self.ctx, self._vec(w_hdiv, self.n_hdiv, "w_hdiv")),
+                    "hopu_set_frozen_wind")
+
+    def rk_substep(self, state: torch.Tensor, dt: float, n_substeps: int = 1) -> torch.Tensor:
+        n = self.n_hdiv if self.wind == "stage" else self.n_l2
+        self._sync_stream()
+        self._check(self.lib.hopu_rk_substep(self.ctx, self._vec(state, n, "state"), float(dt), int(n_substeps)),
+                    "hopu_rk_substep")
+        return state
+
+    def energy(self, u_l2: torch.Tensor, w_hdiv: torch.Tensor | None = None):
+        out = (c_double * 3)()
+        self._sync_stream()
+        wp = None if w_hdiv is None else self._vec(w_hdiv, self.n_hdiv, "w_hdiv")
+        self._check(self.lib.hopu_energy(self.ctx, wp, self._vec(u_l2, self.n_l2, "u_l2"), out), "hopu_energy")
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def points(self, which: str) -> np.ndarray:
+        w = 0 if which == "facet" else 1
+        cnt = c_int64()
+        self._check(self.lib.hopu_points(self.ctx, w, None, byref(cnt)), "hopu_points")
+        buf = np.empty((cnt.value, self.dim), dtype=np.float64)
+        self._check(self.lib.hopu_points(self.ctx, w, buf.ctypes.data, None), "hopu_points")
+        return buf
+
+    def interpolate(self, fvals: np.ndarray, vvals: np.ndarray, out: torch.Tensor | None = None) -> torch.Tensor:
+        fvals = np.ascontiguousarray(fvals, dtype=np.float64)
+        vvals = np.ascontiguousarray(vvals, dtype=np.float64)
+        if out is None:
+            out = self.new("hdiv")
+        self._sync_stream()
+        self._check(self.lib.hopu_interpolate(self.ctx, fvals.ctypes.data, vvals.ctypes.data,
+                                              self._vec(out, self.n_hdiv, "u_hdiv")), "hopu_interpolate")
+        return out
+
+    def interpolate_function(self, fun) -> torch.Tensor:
+        """Canonical interpolant of a callable of points [.., d] -> [.., d]."""
+        fp = self.points("facet")
+        vp = self.points("volume")
+        return self.interpolate(fun(fp), fun(vp))
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.hopu_profile(self.ctx, int(bool(enable))), "hopu_profile")
+
+    def profile_read(self, acc: dict | None = None) -> dict:
+        """Add per-kernel-family device time (ms) and launch counts into acc."""
+        n = len(L.KERNEL_FAMILIES)
+        ms, cnt = (c_double * n)(), (c_int64 * n)()
+        self._check(self.lib.hopu_profile_read(self.ctx, ms, cnt), "hopu_profile_read")
+        acc = acc if acc is not None else {f: [0.0, 0] for f in L.KERNEL_FAMILIES}
+        for i, f in enumerate(L.KERNEL_FAMILIES):
+            acc[f][0] += ms[i]
+            acc[f][1] += cnt[i]
+        return acc
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.hopu_destroy(self.ctx)
+            self.ctx = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # substep launch counts (kernels per call), for the bench's launch accounting
+    def launches_per_substep(self) -> int:
+        return 15 if self.wind == "stage" else 6
+
+
+def selftest(dim: int, k: int):
+    """Host-only check of the library's reference tables (no GPU needed)."""
+    lib = L.load()
+    rep = (c_double * 4)()
+    st = lib.hopu_selftest(dim, k, rep)
+    if st != L.HOPU_OK:
+        raise L.HopuError(st, "hopu_selftest")
+    return list(rep)

@@ -1,0 +1,196 @@
+"""GPU parity: every C-ABI call of libhopu against the FP64 oracle, element by element.
+
+Inputs are seeded and synthetic; the oracle gets exactly the values the GPU gets (FP32
+runs feed the oracle the FP32-rounded inputs, so the comparison measures the kernels'
+arithmetic).  Tolerances (relative to the largest reference entry):
+  FP64: 1e-12 (the oracle and the kernels differ only in summation order);
+  FP32: 1e-6 on the operator output (BASELINE's stated FP32 bound), 2e-6 on projections
+        whose condition number is bounded by cond(D) <= 120.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import convection as C
+from oracle import fe, fields, hdiv, mesh, rk
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-6}
+CASES = [(2, 4, 2), (2, 8, 2), (3, 3, 2), (3, 4, 3), (3, 3, 4), (3, 3, 5)]
+
+
+def _mk(dim, n, k, prec, l=-1, wind="stage"):
+    from paper_2408_06698_gb300 import Hopu
+    m = W.periodic_box_mesh(dim, n)
+    g = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec=prec, wind=wind)
+    topo = mesh.MeshTopo(m.coords, m.elems, m.rep)
+    sp = hdiv.HDiv(topo, fe.ref_element(dim, k))
+    return g, sp
+
+
+def _dev(g, x):
+    return torch.as_tensor(np.ascontiguousarray(x).reshape(-1), dtype=g.dtype, device=g.device)
+
+
+def _host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _rounded(g, x):
+    """What the GPU actually sees: the input rounded to the working precision."""
+    return _host(_dev(g, x)).reshape(np.shape(x))
+
+
+def _rel(got, ref):
+    return float(np.abs(np.asarray(got).reshape(-1) - np.asarray(ref).reshape(-1)).max() / np.abs(ref).max())
+
+
+def _ptol(prec):
+    return TOL[prec] * (2.0 if prec == "f32" else 1.0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dim,n,k", CASES)
+def test_sizes_and_projections(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec)
+    assert (g.n_hdiv, g.n_l2, g.n_facets) == (sp.n_hdiv, sp.n_l2, sp.topo.n_facets)
+    rng = np.random.default_rng(100 + dim * 10 + k)
+    uV = _rounded(g, rng.standard_normal(sp.n_hdiv))
+    got = _host(g.project("hdiv_to_l2", _dev(g, uV)))
+    assert _rel(got, sp.to_l2(uV)) < _ptol(prec)
+    uL = _rounded(g, rng.standard_normal((sp.topo.n_elems, dim, sp.ref.nb)))
+    got = _host(g.project("l2_to_hdiv", _dev(g, uL)))
+    assert _rel(got, sp.from_l2(uL)) < _ptol(prec)
+    got = _host(g.project("l2_to_hdiv_dual", _dev(g, uL)))
+    assert _rel(got, sp.dual(uL)) < _ptol(prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dim,n,k", CASES)
+def test_apply_convection(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec)
+    rng = np.random.default_rng(200 + dim * 10 + k)
+    wV = _rounded(g, rng.standard_normal(sp.n_hdiv))
+    uL = _rounded(g, rng.standard_normal((sp.topo.n_elems, dim, sp.ref.nb)))
+    wL = sp.to_l2(wV)
+    y = _host(g.apply_convection(_dev(g, wV), _dev(g, uL)))          # the context's l = -1
+    assert _rel(y, C.apply(sp.topo, sp.ref, wL, uL, -1)) < TOL[prec]
+    for l in sorted({0, k - 1, k}):                                    # uniform per-facet orders
+        fl = torch.full((sp.topo.n_facets,), l, dtype=torch.int8, device=g.device)
+        y = _host(g.apply_convection(_dev(g, wV), _dev(g, uL), facet_l=fl))
+        ref = C.apply(sp.topo, sp.ref, wL, uL, l)
+        assert _rel(y, ref) < TOL[prec], (l, _rel(y, ref))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 4, 3)])
+def test_apply_per_facet_order(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec)
+    rng = np.random.default_rng(300)
+    lF = rng.integers(-1, k + 1, size=sp.topo.n_facets).astype(np.int8)
+    wV = _rounded(g, rng.standard_normal(sp.n_hdiv))
+    uL = _rounded(g, rng.standard_normal((sp.topo.n_elems, dim, sp.ref.nb)))
+    y = _host(g.apply_convection(_dev(g, wV), _dev(g, uL), facet_l=torch.as_tensor(lF, device=g.device)))
+    ref = C.apply(sp.topo, sp.ref, sp.to_l2(wV), uL, lF.astype(np.int64))
+    assert _rel(y, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 4, 3)])
+def test_energy_functionals(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec, l=k - 1)
+    wL = fields.curl_field(sp.topo, dim, k, fields.random_potential(dim, 7))
+    wV = _rounded(g, sp.from_l2(wL))
+    uL = _rounded(g, np.random.default_rng(400).standard_normal(wL.shape))
+    E, cval, diss = g.energy(_dev(g, uL), _dev(g, wV))
+    wLr = sp.to_l2(wV)
+    assert abs(E - C.kinetic_energy(sp.topo, uL)) < 1e-13 * E
+    ref_c = C.form_value(sp.topo, sp.ref, wLr, uL, k - 1)
+    ref_d = C.facet_dissipation(sp.topo, sp.ref, wLr, uL, k - 1)
+    tol = 1e-11 if prec == "f64" else 1e-5
+    assert abs(cval - ref_c) < tol * abs(ref_d)
+    assert abs(diss - ref_d) < tol * abs(ref_d)
+    if prec == "f64":       # the energy identity holds on the GPU too
+        assert abs(cval - diss) < 1e-11 * diss
+    E0, c0, d0 = g.energy(_dev(g, uL))
+    assert E0 == pytest.approx(E, rel=1e-15) and c0 == 0.0 and d0 == 0.0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 3, 3)])
+def test_rk_substep_stage(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec, l=k - 1)
+    uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
+    dt = 1e-2
+    stream = torch.cuda.Stream(device=g.device)
+    with torch.cuda.stream(stream):
+        s1 = _dev(g, uV)
+        g.rk_substep(s1, dt, 1)                 # direct launches
+        s3 = _dev(g, uV)
+        g.rk_substep(s3, dt, 3)                 # captured graph, replayed 3 times
+        g.rk_substep(s3, dt, 2)                 # graph reused
+    stream.synchronize()
+    ref1 = rk.substeps_stage(sp, uV, dt, 1, k - 1)
+    ref5 = rk.substeps_stage(sp, uV, dt, 5, k - 1)
+    assert _rel(_host(s1), ref1) < TOL[prec] * 2
+    assert _rel(_host(s3), ref5) < TOL[prec] * 10
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rk_substep_frozen(prec):
+    dim, n, k = 3, 3, 3
+    g, sp = _mk(dim, n, k, prec, l=k - 1, wind="frozen")
+    rng = np.random.default_rng(500)
+    wV = _rounded(g, sp.from_l2(fields.curl_field(sp.topo, dim, k, fields.random_potential(dim, 9))))
+    uL = _rounded(g, rng.standard_normal((sp.topo.n_elems, dim, sp.ref.nb)))
+    g.set_frozen_wind(_dev(g, wV))
+    s = _dev(g, uL)
+    g.rk_substep(s, 1e-2, 2)
+    torch.cuda.synchronize()
+    ref = rk.substeps_frozen(sp, wV, uL, 1e-2, 2, k - 1)
+    assert _rel(_host(s), ref) < TOL[prec] * 4
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dim,n,k", [(2, 4, 2), (3, 3, 3)])
+def test_points_and_interpolate(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec)
+    fp, vp = g.points("facet"), g.points("volume")
+    assert np.abs(fp - sp.facet_points().reshape(-1, dim)).max() < 1e-13
+    assert np.abs(vp - sp.volume_points().reshape(-1, dim)).max() < 1e-13
+    got = _host(g.interpolate_function(W.taylor_green))
+    assert _rel(got, sp.interpolate(W.taylor_green)) < (1e-13 if prec == "f64" else 2e-7)
+
+
+def test_invalid_arguments_are_reported():
+    from paper_2408_06698_gb300 import Hopu
+    from paper_2408_06698_gb300._lib import HopuError
+    m = W.periodic_box_mesh(2, 4)
+    with pytest.raises(HopuError, match="EINVAL"):
+        Hopu(m.coords, m.elems, m.rep, k=2, l=5)
+    bad = m.elems.copy()
+    bad[0, 1] = bad[0, 0]
+    with pytest.raises(HopuError, match="EMESH"):
+        Hopu(m.coords, bad, m.rep, k=2)
+    with pytest.raises(HopuError, match="ENOTSUP"):   # a non-periodic mesh has boundary facets
+        Hopu(m.coords, m.elems, None, k=2)
+    g = Hopu(m.coords, m.elems, m.rep, k=2)
+    x = g.new("hdiv")
+    with pytest.raises(ValueError):
+        g.project("hdiv_to_l2", x, out=torch.empty(3, dtype=g.dtype, device=g.device))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_size_taylor_green_apply(prec):
+    """16^3 x 6 tetrahedra, k = 3 (the benchmarked workload), every output compared."""
+    g, sp = _mk(3, 16, 3, prec, l=2)
+    uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
+    uL = sp.to_l2(uV)
+    ug = g.project("hdiv_to_l2", _dev(g, uV))
+    y = _host(g.apply_convection(_dev(g, uV), ug))
+    ref = C.apply(sp.topo, sp.ref, uL, uL, 2)
+    assert _rel(y, ref) < TOL[prec] * (1 if prec == "f64" else 2)
+    l2 = np.linalg.norm(y - ref.reshape(-1)) / np.linalg.norm(ref)
+    assert l2 < TOL[prec]
