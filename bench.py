@@ -54,21 +54,28 @@ def shape(dim, k):
 def algorithmic(dim, k, E, NF, tsize):
     """Per-launch algorithmic flops and bytes of each kernel family (STAGE wind: w = u).
 
-    Bytes count each input/output once (coefficients, geometry actually read, facet
-    moments, connectivity); flops count the contractions the method performs.
+    Bytes count each input/output once (coefficients, the geometry actually read, facet
+    moments, connectivity); flops count the contractions the kernels perform.
     """
+    from math import comb
     s = shape(dim, k)
     nb, nf, nl, nq, nqf = s["nb"], s["nf"], s["nloc"], s["nq"], s["nqf"]
+    nb1 = comb(k - 1 + dim, dim)
     d = dim
-    geo_vol = (d * d + 1) * 8                       # |det J| J^-1, |det J|
+    l = k - 1
+    nl_ = comb(l + d - 1, d - 1)
+    geo_vol = (d * d + 1) * 8                        # |det J| J^-1 and |det J| (FP64)
     out = {}
-    # volume: interpolate u (2 nq nb d), W = M u (2 nq d^2), test (2 nq nb 2d), lift (2 nl (d+1) nf)
-    fl = E * (2 * nq * nb * d + 2 * nq * d * d + 2 * nq * nb * 2 * d + 2 * nl * (d + 1) * nf)
-    by = E * (2 * nl * tsize + geo_vol + (d + 1) * 4) + NF * nf * d * tsize
+    # volume: modal gradients (2 d^2 nb1 nb) + per point u (2 nb d), grad u (2 nb1 d^2),
+    # W and div W (4 d^2), f (2 d^2 + 2 d), test (2 nb d) + facet lift (2 nl (d+1) nf)
+    per_q = 2 * nb * d + 2 * nb1 * d * d + 4 * d * d + 2 * d * d + 2 * d + 2 * nb * d
+    fl = E * (2 * d * d * nb1 * nb + nq * per_q + 2 * nl * (d + 1) * nf)
+    by = E * (2 * nl * tsize + geo_vol + (d + 1) * 4) + NF * 2 * nf * d * tsize
     out["volume"] = (fl, by)
-    # facet: two traces at nqf points (2 * 2 nqf nb d), projections and moments (~ 8 nqf nf d)
-    fl = NF * (2 * 2 * nqf * nb * d + 8 * nqf * nf * d)
-    by = NF * (2 * nl * tsize * 0 + (d + 1) * 8 + 2 * 4 + nf * d * tsize) + E * nl * tsize
+    # facet: two traces (2 * 2 nqf nb d), P^l moments and evaluation (4 nl_ d nqf), moments
+    # of the two facet fields (2 * 2 nf d nqf)
+    fl = NF * (2 * 2 * nqf * nb * d + 4 * nl_ * d * nqf + 2 * 2 * nf * d * nqf)
+    by = NF * ((d + 1) * 8 + 2 * 4 + 2 * nf * d * tsize) + E * nl * tsize
     out["facet"] = (fl, by)
     # v2l: gather + Dinv (2 nl^2) + Piola (2 nl d)
     out["v2l"] = (E * (2 * nl * nl + 2 * nl * d), (NF * nf + E * s["nint"]) * tsize + E * nl * tsize

@@ -43,8 +43,9 @@
  *
  * Conventions of every call:
  *   - Coefficient pointers are DEVICE pointers owned by the caller, in the working
- *     precision of the context (double for HOPU_FP64, float for HOPU_FP32).  The
- *     library never frees or keeps them beyond the call.
+ *     precision of the context (double for HOPU_FP64, float for HOPU_FP32), 16-byte
+ *     aligned (EINVAL otherwise; the kernels copy per-element records with cp.async).
+ *     The library never frees or keeps them beyond the call.
  *   - Mesh arrays and *host* pointers are host memory, copied or read during the call.
  *   - All device work is enqueued asynchronously on the context's stream (set at
  *     create time or by hopu_set_stream); calls that return host values synchronise

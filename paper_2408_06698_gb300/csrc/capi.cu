@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -104,7 +105,7 @@ struct hopu_ctx {
   // device memory
   void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
   void* d_tabs = nullptr;   // every reference table
-  void* d_gam = nullptr;    // [NF][nf][d] facet flux moments
+  void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major
   void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals
   void* d_uL = nullptr;     // L2 stage field
   void* d_yL = nullptr;     // L2 operator output
@@ -157,6 +158,8 @@ hopu_status cuda_fail(hopu_ctx* c, cudaError_t e, const char* where) {
     if (!(ctx)) return HOPU_EINVAL;                  \
     if ((ctx)->status != HOPU_OK) return (hopu_status)(ctx)->status; \
   } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 hopu_status check_launch(hopu_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -211,33 +214,49 @@ void convert(const std::vector<double>& src, std::vector<unsigned char>& dst, si
 }
 
 // Reorder the host FP64 tables into the kernel layouts (see hopu_internal.h).
+constexpr int kNumTables = 11;
+
 void kernel_tables(const RefTables& R, std::vector<std::vector<double>>& out) {
   const int d = R.dim, nb = R.nb, nf = R.nf, nq = R.nq, nqf = R.nqf, nl = R.nloc;
-  out.assign(9, {});
+  const int nb1 = nbasis(d, R.k - 1);
+  out.assign(kNumTables, {});
   auto& Bt = out[0];
-  auto& Gt = out[1];
-  auto& TrM = out[2];
-  auto& TrP = out[3];
-  auto& Psi = out[4];
-  auto& Wf = out[5];
-  auto& DinvT = out[6];
-  auto& DT = out[7];
-  auto& Dinv = out[8];
+  auto& Wq = out[1];
+  auto& Dm = out[2];
+  auto& TrM = out[3];
+  auto& TrP = out[4];
+  auto& Psi = out[5];
+  auto& WPsi = out[6];
+  auto& Wf = out[7];
+  auto& DinvT = out[8];
+  auto& DT = out[9];
+  auto& Dinv = out[10];
   Bt.resize((size_t)nb * nq);
-  Gt.resize((size_t)nb * d * nq);
   for (int i = 0; i < nb; ++i)
-    for (int q = 0; q < nq; ++q) {
-      Bt[(size_t)i * nq + q] = R.phi[(size_t)q * nb + i];
-      for (int c = 0; c < d; ++c) Gt[((size_t)i * d + c) * nq + q] = R.wq[q] * R.dphi[((size_t)q * nb + i) * d + c];
-    }
+    for (int q = 0; q < nq; ++q) Bt[(size_t)i * nq + q] = R.phi[(size_t)q * nb + i];
+  Wq = R.wq;
+  // modal differentiation: d phi_i / d xhat_c = sum_{j < nb(k-1)} Dm[c][j][i] phi_j, with
+  // Dm[c][j][i] = int (d phi_i / d xhat_c) phi_j (exact: degree 2k-2 <= 3k-1)
+  Dm.assign((size_t)d * nb1 * nb, 0.0);
+  for (int c = 0; c < d; ++c)
+    for (int j = 0; j < nb1; ++j)
+      for (int i = 0; i < nb; ++i) {
+        double acc = 0.0;
+        for (int q = 0; q < nq; ++q) acc += R.wq[q] * R.dphi[((size_t)q * nb + i) * d + c] * R.phi[(size_t)q * nb + j];
+        Dm[((size_t)c * nb1 + j) * nb + i] = acc;
+      }
   TrM = R.trm;
   TrP.resize((size_t)(d + 1) * nb * nqf);
   for (int f = 0; f <= d; ++f)
     for (int i = 0; i < nb; ++i)
       for (int q = 0; q < nqf; ++q) TrP[((size_t)f * nb + i) * nqf + q] = R.phif[((size_t)f * nqf + q) * nb + i];
   Psi.resize((size_t)nf * nqf);
+  WPsi.resize((size_t)nf * nqf);
   for (int m = 0; m < nf; ++m)
-    for (int q = 0; q < nqf; ++q) Psi[(size_t)m * nqf + q] = R.psi[(size_t)q * nf + m];
+    for (int q = 0; q < nqf; ++q) {
+      Psi[(size_t)m * nqf + q] = R.psi[(size_t)q * nf + m];
+      WPsi[(size_t)m * nqf + q] = R.wf[q] * R.psi[(size_t)q * nf + m];
+    }
   Wf = R.wf;
   DinvT.resize((size_t)nl * nl);
   DT.resize((size_t)nl * nl);
@@ -380,14 +399,15 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   HOPU_CUDA(c, cudaMalloc(&c->d_tabs, total));
   HOPU_CUDA(c, cudaMemcpy(c->d_tabs, ht.data(), total, cudaMemcpyHostToDevice));
   unsigned char* tb = static_cast<unsigned char*>(c->d_tabs);
-  const void** slots[9] = {&c->dt.Bt, &c->dt.Gt, &c->dt.TrM, &c->dt.TrP, &c->dt.Psi,
-                           &c->dt.Wf, &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv};
-  for (int i = 0; i < 9; ++i) *slots[i] = tb + offs[i];
+  const void** slots[kNumTables] = {&c->dt.Bt,   &c->dt.Wq,  &c->dt.Dm,    &c->dt.TrM,
+                                    &c->dt.TrP,  &c->dt.Psi, &c->dt.WPsi,  &c->dt.Wf,
+                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv};
+  for (int i = 0; i < kNumTables; ++i) *slots[i] = tb + offs[i];
 
   // scratch
   const size_t ts = c->tsize;
   const int64_t nstate = std::max(c->n_hdiv, c->n_l2);
-  HOPU_CUDA(c, cudaMalloc(&c->d_gam, ts * NF * R.nf * c->dim));
+  HOPU_CUDA(c, cudaMalloc(&c->d_gam, ts * E * (c->dim + 1) * R.nf * c->dim));
   HOPU_CUDA(c, cudaMalloc(&c->d_lf, ts * E * (c->dim + 1) * R.nf));
   HOPU_CUDA(c, cudaMalloc(&c->d_uL, ts * c->n_l2));
   HOPU_CUDA(c, cudaMalloc(&c->d_yL, ts * c->n_l2));
@@ -442,6 +462,7 @@ hopu_status hopu_sizes(const hopu_ctx* c, int64_t* n_hdiv, int64_t* n_l2, int64_
 hopu_status hopu_project(hopu_ctx* c, int dir, const void* in, void* out) {
   HOPU_PRECHECK(c);
   if (!in || !out || in == out) return fail(c, HOPU_EINVAL, "project: NULL or aliased vectors");
+  if (!aligned16(in) || !aligned16(out)) return fail(c, HOPU_EINVAL, "project: vectors must be 16-byte aligned");
   if (dir == HOPU_HDIV_TO_L2) {
     enqueue_v2l(c, in, out);
   } else if (dir == HOPU_L2_TO_HDIV || dir == HOPU_L2_TO_HDIV_DUAL) {
@@ -457,6 +478,8 @@ hopu_status hopu_apply_convection(hopu_ctx* c, const void* w_hdiv, const void* u
                                   const int8_t* facet_l) {
   HOPU_PRECHECK(c);
   if (!w_hdiv || !u_l2 || !y_l2 || y_l2 == u_l2) return fail(c, HOPU_EINVAL, "apply_convection: NULL or aliased vectors");
+  if (!aligned16(w_hdiv) || !aligned16(u_l2) || !aligned16(y_l2))
+    return fail(c, HOPU_EINVAL, "apply_convection: vectors must be 16-byte aligned");
   enqueue_v2l(c, w_hdiv, c->d_wL);
   Combine plain;
   return enqueue_stage_apply(c, u_l2, c->d_wL, c->l, facet_l, nullptr, plain, y_l2);
@@ -464,7 +487,7 @@ hopu_status hopu_apply_convection(hopu_ctx* c, const void* w_hdiv, const void* u
 
 hopu_status hopu_set_frozen_wind(hopu_ctx* c, const void* w_hdiv) {
   HOPU_PRECHECK(c);
-  if (!w_hdiv) return fail(c, HOPU_EINVAL, "set_frozen_wind: NULL wind");
+  if (!w_hdiv || !aligned16(w_hdiv)) return fail(c, HOPU_EINVAL, "set_frozen_wind: NULL or unaligned wind");
   enqueue_v2l(c, w_hdiv, c->d_wfz);
   c->have_frozen = true;
   return check_launch(c, "set_frozen_wind");
@@ -473,6 +496,7 @@ hopu_status hopu_set_frozen_wind(hopu_ctx* c, const void* w_hdiv) {
 hopu_status hopu_rk_substep(hopu_ctx* c, void* state, double dt, int n_substeps) {
   HOPU_PRECHECK(c);
   if (!state || n_substeps < 0 || !std::isfinite(dt)) return fail(c, HOPU_EINVAL, "rk_substep: bad arguments");
+  if (!aligned16(state)) return fail(c, HOPU_EINVAL, "rk_substep: state must be 16-byte aligned");
   if (c->wind == HOPU_WIND_FROZEN && !c->have_frozen) return fail(c, HOPU_EINVAL, "rk_substep: FROZEN wind not set");
   if (n_substeps == 0) return HOPU_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -517,6 +541,7 @@ hopu_status hopu_rk_substep(hopu_ctx* c, void* state, double dt, int n_substeps)
 hopu_status hopu_energy(hopu_ctx* c, const void* w_hdiv, const void* u_l2, double* host_out) {
   HOPU_PRECHECK(c);
   if (!u_l2 || !host_out) return fail(c, HOPU_EINVAL, "energy: NULL pointer");
+  if (!aligned16(u_l2) || (w_hdiv && !aligned16(w_hdiv))) return fail(c, HOPU_EINVAL, "energy: vectors must be 16-byte aligned");
   hopu_status r = weighted_dot(c, u_l2, u_l2, 0);
   if (r != HOPU_OK) return r;
   double vals[3] = {0.0, 0.0, 0.0};
@@ -555,6 +580,7 @@ hopu_status hopu_points(hopu_ctx* c, int which, double* host_out, int64_t* count
 hopu_status hopu_interpolate(hopu_ctx* c, const double* fvals, const double* vvals, void* u_hdiv) {
   HOPU_PRECHECK(c);
   if (!fvals || !vvals || !u_hdiv) return fail(c, HOPU_EINVAL, "interpolate: NULL pointer");
+  if (!aligned16(u_hdiv)) return fail(c, HOPU_EINVAL, "interpolate: output must be 16-byte aligned");
   const RefTables& R = c->ref;
   const int d = c->dim, G = geo_stride(d);
   const int64_t NF = c->topo.n_facets, E = c->topo.n_elems;

@@ -20,10 +20,12 @@ struct DevMesh {
 // Device reference tables in working precision (all element-type T, 16-byte aligned).
 struct DevTabs {
   const void* Bt = nullptr;     // [nb][nq]        phi_i(x_q)
-  const void* Gt = nullptr;     // [nb][d][nq]     w_q d phi_i / d xhat_c (x_q)
+  const void* Wq = nullptr;     // [nq]            volume weights
+  const void* Dm = nullptr;     // [d][nb(k-1)][nb] d phi_i / d xhat_c = sum_j Dm[c][j][i] phi_j
   const void* TrM = nullptr;    // [d+1][nf][nb]   <phi_i o xhat_f, psi_m>_facet
   const void* TrP = nullptr;    // [d+1][nb][nqf]  phi_i(xhat_f(s_q))
   const void* Psi = nullptr;    // [nf][nqf]       psi_m(s_q)
+  const void* WPsi = nullptr;   // [nf][nqf]       w_q psi_m(s_q)
   const void* Wf = nullptr;     // [nqf]           facet weights
   const void* DinvT = nullptr;  // [nloc][nloc]    DinvT[s][r] = Dinv[r][s]
   const void* DT = nullptr;     // [nloc][nloc]    DT[s][r]    = D[r][s]
@@ -47,8 +49,9 @@ class Ops {
   virtual cudaError_t prepare() = 0;
   // E: V_h -> L2
   virtual int v2l(const DevMesh&, const DevTabs&, const void* uV, void* uL, cudaStream_t) = 0;
-  // facet flux moments gam[F][nf][d] (side A; side B gets the negative) and, if diss
-  // is not null, the facet dissipation per facet.  wL == uL means w = u.
+  // facet flux moments, element-major: gam[e][f][nf][d] for the element e that sees the
+  // facet as its local facet f (alpha + beta on side A, alpha - beta on side B) and, if
+  // diss is not null, the facet dissipation per facet.  wL == uL means w = u.
   virtual int facet(const DevMesh&, const DevTabs&, const void* uL, const void* wL, int l,
                     const int8_t* facet_l, void* gam, double* diss, cudaStream_t) = 0;
   // volume term + facet lift + inverse mass, combined into out.  wL == uL means w = u.

@@ -13,23 +13,35 @@ class OpsImpl final : public Ops {
   static constexpr size_t sz = sizeof(T);
   static constexpr size_t r4(size_t n) { return ((n + 3) / 4) * 4; }
 
-  static constexpr size_t kTabNL = size_t(S::nloc) * S::nloc * sz;
-  static constexpr bool kProjTab = kTabNL + kWarps * 2 * S::nloc * sz <= kLimit;
-  static constexpr size_t kV2lSmem = (kProjTab ? kTabNL : 0) + kWarps * 2 * S::nloc * sz;
-  static constexpr size_t kL2vSmem = (kProjTab ? kTabNL : 0) + kWarps * S::nloc * sz;
+  static constexpr size_t kTabNL = r4(size_t(S::nloc) * S::nloc) * sz;
+  static constexpr size_t kProjWarp = 2 * kEPW * size_t(S::nloc) * sz;
+  static constexpr bool kProjTab = kTabNL + kWarps * kProjWarp <= kLimit;
+  static constexpr size_t kV2lSmem = (kProjTab ? kTabNL : 0) + kWarps * kProjWarp;
+  static constexpr size_t kL2vSmem = (kProjTab ? kTabNL : 0) + kWarps * kProjWarp;
 
-  static constexpr size_t kFacTab = r4(size_t(D + 1) * S::nb * S::nqf + S::nf * S::nqf + S::nqf) * sz;
-  static constexpr bool kFacetTab = kFacTab + kWarps * 4 * S::nloc * sz <= kLimit;
-  static constexpr size_t facet_smem(bool wsep) {
-    return (kFacetTab ? kFacTab : 0) + kWarps * (wsep ? 4 : 2) * S::nloc * sz;
+  // facet kernel: TrP, Psi, WPsi, Wf; per warp: coefficient blocks, two [nqf][4] point
+  // buffers and the [nf][4] projection moments (layout of k_facet)
+  static constexpr size_t kFacTab = r4(size_t(D + 1) * S::nb * S::nqf + 2 * S::nf * S::nqf + S::nqf) * sz;
+  static constexpr size_t facet_warp(bool wsep) {
+    return (size_t(wsep ? 4 : 2) * D * r4(S::nb) + 2 * S::nqf * 4 + S::nf * 4 + 2 * S::nf * 4) * sz;
   }
+  static constexpr bool kFacetTab = kFacTab + kWarps * facet_warp(true) <= kLimit;
+  static constexpr size_t facet_smem(bool wsep) { return (kFacetTab ? kFacTab : 0) + kWarps * facet_warp(wsep); }
 
-  static constexpr size_t kVolTab = r4(size_t(S::nb) * S::nq * (D + 1) + size_t(D + 1) * S::nf * S::nb) * sz;
-  static constexpr size_t kNG = size_t(D + 1) * S::nf * D;
-  static constexpr bool kVolumeTab = kVolTab + kWarps * (2 * S::nloc + kNG) * sz <= kLimit;
-  static constexpr size_t volume_smem(bool wsep) {
-    return (kVolumeTab ? kVolTab : 0) + kWarps * ((wsep ? 2 : 1) * S::nloc + kNG) * sz;
+  // volume kernel: Bt, Wq, Dm, TrM; per warp: coefficients, modal gradients, (W and its
+  // divergence), signed facet moments (layout of k_volume)
+  static constexpr int kNB1 = cnbasis(D, K - 1);
+  static constexpr size_t kVolTab =
+      r4(size_t(S::nb) * S::nq + S::nq + size_t(D) * kNB1 * S::nb + size_t(D + 1) * S::nf * S::nb) * sz;
+  static constexpr size_t volume_stage(bool wsep) {
+    return r4(S::nloc) * (wsep ? 2 : 1) + r4(size_t(D + 1) * S::nf * D) + 2 * r4(S::geo);
   }
+  static constexpr size_t volume_warp(bool wsep) {
+    return (2 * volume_stage(wsep) + size_t(D) * r4(S::nb) + size_t(D) * D * r4(kNB1) +
+            (wsep ? size_t(D) * r4(S::nb) + r4(kNB1) : 0)) * sz;
+  }
+  static constexpr bool kVolumeTab = kVolTab + kWarps * volume_warp(true) <= kLimit;
+  static constexpr size_t volume_smem(bool wsep) { return (kVolumeTab ? kVolTab : 0) + kWarps * volume_warp(wsep); }
 
   int nsm_ = 1;
   int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
@@ -73,7 +85,7 @@ class OpsImpl final : public Ops {
   }
 
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
-    const int g = clamp_grid(g_v2l_, m.E, kWarps);
+    const int g = clamp_grid(g_v2l_, m.E, kWarps * kEPW);
     k_v2l<D, K, T, kProjTab><<<g, 32 * kWarps, kV2lSmem, st>>>(
         m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
     return 1;
@@ -109,7 +121,7 @@ class OpsImpl final : public Ops {
 
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,
                void* outV, cudaStream_t st) override {
-    const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, kWarps);
+    const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, kWarps * kEPW);
     if (dual)
       k_l2v_elem<D, K, T, true, kProjTab><<<g, 32 * kWarps, kL2vSmem, st>>>(
           m, static_cast<const T*>(t.Dinv), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
