@@ -104,6 +104,7 @@ struct hopu_ctx {
   int nsm = 1, red_blocks = 1;
   // device memory
   void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
+  void* d_geoT = nullptr;   // working-precision geometry factors
   void* d_tabs = nullptr;   // every reference table
   void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major
   void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals
@@ -198,7 +199,7 @@ void timed(hopu_ctx* c, int family, F&& launch) {
 void free_all(hopu_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  void* ptrs[] = {c->d_mesh, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
+  void* ptrs[] = {c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
                   c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -216,8 +217,16 @@ void convert(const std::vector<double>& src, std::vector<unsigned char>& dst, si
 // Reorder the host FP64 tables into the kernel layouts (see hopu_internal.h).
 constexpr int kNumTables = 11;
 
-void kernel_tables(const RefTables& R, std::vector<std::vector<double>>& out) {
+// Row stride of the point-major tables: an odd multiple of 16 bytes (matches
+// row_stride<T> in kernels.cuh).
+int point_row_stride(int n, bool fp64) {
+  if (!fp64) return (n + 3) / 4 * 4 + (((n + 3) / 4) % 2 == 0 ? 4 : 0);
+  return (n + 1) / 2 * 2 + (((n + 1) / 2) % 2 == 0 ? 2 : 0);
+}
+
+void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double>>& out) {
   const int d = R.dim, nb = R.nb, nf = R.nf, nq = R.nq, nqf = R.nqf, nl = R.nloc;
+  const int nbq = point_row_stride(nb, fp64);
   const int nb1 = nbasis(d, R.k - 1);
   out.assign(kNumTables, {});
   auto& Bt = out[0];
@@ -231,9 +240,9 @@ void kernel_tables(const RefTables& R, std::vector<std::vector<double>>& out) {
   auto& DinvT = out[8];
   auto& DT = out[9];
   auto& Dinv = out[10];
-  Bt.resize((size_t)nb * nq);
-  for (int i = 0; i < nb; ++i)
-    for (int q = 0; q < nq; ++q) Bt[(size_t)i * nq + q] = R.phi[(size_t)q * nb + i];
+  Bt.assign((size_t)nq * nbq, 0.0);  // point-major [q][nbq]
+  for (int q = 0; q < nq; ++q)
+    for (int i = 0; i < nb; ++i) Bt[(size_t)q * nbq + i] = R.phi[(size_t)q * nb + i];
   Wq = R.wq;
   // modal differentiation: d phi_i / d xhat_c = sum_{j < nb(k-1)} Dm[c][j][i] phi_j, with
   // Dm[c][j][i] = int (d phi_i / d xhat_c) phi_j (exact: degree 2k-2 <= 3k-1)
@@ -246,10 +255,10 @@ void kernel_tables(const RefTables& R, std::vector<std::vector<double>>& out) {
         Dm[((size_t)c * nb1 + j) * nb + i] = acc;
       }
   TrM = R.trm;
-  TrP.resize((size_t)(d + 1) * nb * nqf);
+  TrP.assign((size_t)(d + 1) * nqf * nbq, 0.0);  // point-major [f][q][nbq]
   for (int f = 0; f <= d; ++f)
-    for (int i = 0; i < nb; ++i)
-      for (int q = 0; q < nqf; ++q) TrP[((size_t)f * nb + i) * nqf + q] = R.phif[((size_t)f * nqf + q) * nb + i];
+    for (int q = 0; q < nqf; ++q)
+      for (int i = 0; i < nb; ++i) TrP[((size_t)f * nqf + q) * nbq + i] = R.phif[((size_t)f * nqf + q) * nb + i];
   Psi.resize((size_t)nf * nqf);
   WPsi.resize((size_t)nf * nqf);
   for (int m = 0; m < nf; ++m)
@@ -258,14 +267,17 @@ void kernel_tables(const RefTables& R, std::vector<std::vector<double>>& out) {
       WPsi[(size_t)m * nqf + q] = R.wf[q] * R.psi[(size_t)q * nf + m];
     }
   Wf = R.wf;
-  DinvT.resize((size_t)nl * nl);
-  DT.resize((size_t)nl * nl);
+  // n_loc x n_loc tables for the projection GEMMs, [s][r] with rows padded to nlp
+  const int nlp = (nl + 3) / 4 * 4;
+  DinvT.assign((size_t)nl * nlp, 0.0);
+  DT.assign((size_t)nl * nlp, 0.0);
+  Dinv.assign((size_t)nl * nlp, 0.0);
   for (int r = 0; r < nl; ++r)
     for (int s = 0; s < nl; ++s) {
-      DinvT[(size_t)s * nl + r] = R.Dinv[(size_t)r * nl + s];
-      DT[(size_t)s * nl + r] = R.D[(size_t)r * nl + s];
+      DinvT[(size_t)s * nlp + r] = R.Dinv[(size_t)r * nl + s];
+      DT[(size_t)s * nlp + r] = R.D[(size_t)r * nl + s];
+      Dinv[(size_t)s * nlp + r] = R.Dinv[(size_t)s * nl + r];
     }
-  Dinv = R.Dinv;
 }
 
 void enqueue_v2l(hopu_ctx* c, const void* uV, void* uL) {
@@ -382,9 +394,32 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   c->dm.fb = reinterpret_cast<const int32_t*>(base + s_geo + s_efc + s_f);
   c->dm.fgeo = reinterpret_cast<const double*>(base + s_geo + s_efc + 2 * s_f);
 
+  // working-precision geometry factors, computed in FP64 and rounded once
+  {
+    const int d = c->dim, GT = geoT_stride(d);
+    std::vector<double> gt((size_t)E * GT, 0.0);
+    for (int64_t e = 0; e < E; ++e) {
+      const double* g = &c->topo.geo[(size_t)e * G];
+      const double det = g[2 * d * d], ad = g[2 * d * d + 1];
+      double* o = &gt[(size_t)e * GT];
+      for (int i = 0; i < d * d; ++i) {
+        o[i] = g[i] / det;                  // Pf = J / det J
+        o[d * d + i] = det * g[d * d + i];  // Pi = det J * Jinv
+        o[2 * d * d + i] = ad * g[d * d + i];  // M = |det J| * Jinv
+      }
+      o[3 * d * d] = 1.0 / ad;
+    }
+    std::vector<unsigned char> hg(c->tsize * gt.size());
+    if (c->fp64) convert<double>(gt, hg, 0);
+    else convert<float>(gt, hg, 0);
+    HOPU_CUDA(c, cudaMalloc(&c->d_geoT, hg.size()));
+    HOPU_CUDA(c, cudaMemcpy(c->d_geoT, hg.data(), hg.size(), cudaMemcpyHostToDevice));
+    c->dm.geoT = c->d_geoT;
+  }
+
   // tables upload, converted to the working precision
   std::vector<std::vector<double>> tabs;
-  kernel_tables(R, tabs);
+  kernel_tables(R, c->fp64, tabs);
   std::vector<size_t> offs;
   size_t total = 0;
   for (auto& t : tabs) {

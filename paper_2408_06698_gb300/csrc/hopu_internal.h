@@ -10,7 +10,9 @@ namespace hopu {
 // Device view of the mesh (FP64 geometry, int32 connectivity).
 struct DevMesh {
   int64_t E = 0, NF = 0;
-  const double* geo = nullptr;   // [E][2d^2+2]: J (row-major), Jinv, det J, |det J|
+  const double* geo = nullptr;   // [E][2d^2+2]: J (row-major), Jinv, det J, |det J| (FP64)
+  const void* geoT = nullptr;    // [E][geoT_stride(d)] in working precision, computed in FP64:
+                                 //   Pf = J / det J, Pi = det J * Jinv, M = |det J| * Jinv, 1/|det J|
   const int32_t* efc = nullptr;  // [E][d+1]: F*4 + (sigma<0)*2 + (element is side B)
   const int32_t* fa = nullptr;   // [NF]: element*4 + local facet of side A
   const int32_t* fb = nullptr;   // [NF]: same for side B
@@ -19,17 +21,18 @@ struct DevMesh {
 
 // Device reference tables in working precision (all element-type T, 16-byte aligned).
 struct DevTabs {
-  const void* Bt = nullptr;     // [nb][nq]        phi_i(x_q)
+  const void* Bt = nullptr;     // [nq][nbq]       phi_i(x_q), point-major, rows padded to nbq
+                                //                 (an odd multiple of 16 bytes)
   const void* Wq = nullptr;     // [nq]            volume weights
   const void* Dm = nullptr;     // [d][nb(k-1)][nb] d phi_i / d xhat_c = sum_j Dm[c][j][i] phi_j
   const void* TrM = nullptr;    // [d+1][nf][nb]   <phi_i o xhat_f, psi_m>_facet
-  const void* TrP = nullptr;    // [d+1][nb][nqf]  phi_i(xhat_f(s_q))
+  const void* TrP = nullptr;    // [d+1][nqf][nbq] phi_i(xhat_f(s_q)), point-major
   const void* Psi = nullptr;    // [nf][nqf]       psi_m(s_q)
   const void* WPsi = nullptr;   // [nf][nqf]       w_q psi_m(s_q)
   const void* Wf = nullptr;     // [nqf]           facet weights
-  const void* DinvT = nullptr;  // [nloc][nloc]    DinvT[s][r] = Dinv[r][s]
-  const void* DT = nullptr;     // [nloc][nloc]    DT[s][r]    = D[r][s]
-  const void* Dinv = nullptr;   // [nloc][nloc]    Dinv[r][s]
+  const void* DinvT = nullptr;  // [nloc][nlp]     DinvT[s][r] = Dinv[r][s]  (nlp = nloc rounded up to 4)
+  const void* DT = nullptr;     // [nloc][nlp]     DT[s][r]    = D[r][s]
+  const void* Dinv = nullptr;   // [nloc][nlp]     Dinv[s][r]
 };
 
 // out = a0*x0 + a1*x1 + a2*v  (x0 / x1 may be null; out may alias x0 or x1)
@@ -40,6 +43,9 @@ struct Combine {
   const void* x1 = nullptr;
   double a2 = 1.0;
 };
+
+// layout of the working-precision geometry record (offsets in elements)
+inline constexpr int geoT_stride(int d) { return ((3 * d * d + 1 + 3) / 4) * 4; }
 
 // One family of kernels for a fixed (dim, k, precision).  Every call enqueues on the
 // given stream and returns the number of kernels it launched.

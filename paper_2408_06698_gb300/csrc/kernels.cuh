@@ -34,6 +34,7 @@ struct Shape {
   static constexpr int nq = cpow(mv, D);
   static constexpr int nqf = cpow(mf, D - 1);
   static constexpr int geo = 2 * D * D + 2;
+  static constexpr int gt = geoT_stride(D);  // Pf [0, d^2), Pi [d^2, 2d^2), M [2d^2, 3d^2), 1/|det J|
   static constexpr int nvp = ((nloc + 31) / 32) * 32;  // accumulators, padded to the warp
 };
 
@@ -81,114 +82,7 @@ __device__ __forceinline__ T combine_at(const Combine& c, T v, int64_t idx) {
   return o;
 }
 
-// ------------------------------------------------------------------------------------
-// Projections: each warp handles kEPW elements at once so that every table entry read
-// from shared memory feeds kEPW FMAs (the per-element operands are stored interleaved,
-// [s][kEPW], and read with one vector load).
-constexpr int kEPW = 4;
-
-template <typename T>
-__device__ __forceinline__ void load_epw(const T* p, T (&v)[kEPW]);
-template <>
-__device__ __forceinline__ void load_epw<float>(const float* p, float (&v)[kEPW]) {
-  const float4 x = *reinterpret_cast<const float4*>(p);
-  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-template <>
-__device__ __forceinline__ void load_epw<double>(const double* p, double (&v)[kEPW]) {
-  const double2 x = *reinterpret_cast<const double2*>(p);
-  const double2 y = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-}
-
-// out[k][r] = sum_s tab[s][r] * in[s][k] for kEPW elements (in interleaved, out [k][NL]).
-template <int NL, typename T>
-__device__ __forceinline__ void epw_gemv(const T* tab, const T* in, T* out, int lane) {
-  for (int r0 = lane; r0 < NL; r0 += 64) {
-    const int r1 = r0 + 32;
-    const bool has1 = r1 < NL;
-    const int r1c = has1 ? r1 : r0;
-    T a0[kEPW], a1[kEPW];
-#pragma unroll
-    for (int k = 0; k < kEPW; ++k) a0[k] = a1[k] = T(0);
-#pragma unroll 4
-    for (int s2 = 0; s2 < NL; ++s2) {
-      T v[kEPW];
-      load_epw<T>(in + s2 * kEPW, v);
-      const T t0 = tab[s2 * NL + r0], t1 = tab[s2 * NL + r1c];
-#pragma unroll
-      for (int k = 0; k < kEPW; ++k) {
-        a0[k] = fma(t0, v[k], a0[k]);
-        a1[k] = fma(t1, v[k], a1[k]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kEPW; ++k) {
-      out[k * NL + r0] = a0[k];
-      if (has1) out[k * NL + r1] = a1[k];
-    }
-  }
-}
-
-// a1: V_h -> L2.  Per element: gather the (d+1) facet blocks with the sign sigma and the
-// interior block, reference change of basis Dinv, contravariant Piola map J / det J.
-template <int D, int K, typename T, bool STAB>
-__global__ void __launch_bounds__(32 * kWarps) k_v2l(DevMesh m, const T* __restrict__ tab,
-                                                     const T* __restrict__ uV, T* __restrict__ uL) {
-  using S = Shape<D, K>;
-  constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sbase = reinterpret_cast<T*>(smem_raw);
-  const T* E = tab;
-  T* sw = sbase;
-  if (STAB) {
-    for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) sbase[t] = tab[t];
-    E = sbase;
-    sw = sbase + r4i(NL * NL);  // keeps the per-warp buffers 16-byte aligned
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* l = sw + warp * 2 * kEPW * NL;  // [NL][kEPW] gathered local dofs
-  T* ch = l + kEPW * NL;             // [kEPW][NL] reference coefficients
-  for (int64_t e0 = ((int64_t)blockIdx.x * kWarps + warp) * kEPW; e0 < m.E;
-       e0 += (int64_t)gridDim.x * kWarps * kEPW) {
-    for (int t = lane; t < kEPW * NL; t += 32) {
-      const int k = t / NL, s2 = t - k * NL;
-      const int64_t e = e0 + k;
-      T v = T(0);
-      if (e < m.E) {
-        if (s2 < (D + 1) * NF) {
-          const int f = s2 / NF, mm = s2 - f * NF;
-          const int code = m.efc[e * (D + 1) + f];
-          v = uV[(int64_t)(code >> 2) * NF + mm];
-          if (code & 2) v = -v;
-        } else {
-          v = uV[m.NF * NF + e * NINT + (s2 - (D + 1) * NF)];
-        }
-      }
-      l[s2 * kEPW + k] = v;
-    }
-    __syncwarp();
-    epw_gemv<NL, T>(E, l, ch, lane);
-    __syncwarp();
-    for (int t = lane; t < kEPW * NL; t += 32) {
-      const int k = t / NL, idx = t - k * NL;
-      const int64_t e = e0 + k;
-      if (e >= m.E) continue;
-      const double* g = m.geo + e * S::geo;
-      const int a = idx / NB, i = idx - a * NB;
-      T acc = T(0);
-#pragma unroll
-      for (int b = 0; b < D; ++b) acc = fma(T(g[a * D + b]), ch[k * NL + b * NB + i], acc);
-      uL[e * NL + idx] = acc * T(1.0 / g[2 * D * D]);
-    }
-    __syncwarp();
-  }
-}
-
-// ------------------------------------------------------------------------------------
-// Vectorised dot product of a register array with a 16-byte aligned shared-memory row
-// (the row is padded to a multiple of 4 entries; padding entries are never used).
+// Vector views of shared memory: 16-byte loads of 4 floats or 2 doubles.
 template <typename T> struct Pack;
 template <> struct Pack<float> {
   static constexpr int W = 4;
@@ -200,6 +94,289 @@ template <> struct Pack<double> {
   using V = double2;
   __device__ __forceinline__ static void unpack(const V& v, double* o) { o[0] = v.x; o[1] = v.y; }
 };
+
+// ------------------------------------------------------------------------------------
+// Projections (a1, a7) as CTA-tiled GEMMs.  A CTA of kProjThreads threads takes a tile
+// of TE elements: it gathers their local vectors into shared memory ([element][NLQ],
+// NLQ odd so that column reads are bank-conflict free), multiplies by the n_loc x n_loc
+// reference matrix (staged once per CTA, [s][NLP] so that four rows are one 16-byte
+// load) with a 4 x 4 register tile per thread (four consecutive rows x four elements
+// strided by TE/4), and finishes with the per-element Piola / scatter step.
+constexpr int kProjThreads = 256;
+
+template <int D, int K, typename T>
+struct ProjCfg {
+  using S = Shape<D, K>;
+  static constexpr int NL = S::nloc;
+  static constexpr int RG = (NL + 3) / 4;   // row groups of four
+  static constexpr int NLP = RG * 4;        // padded table row
+  static constexpr int NLQ = (NL % 2) ? NL : NL + 1;  // odd stride of the element rows
+  static constexpr size_t TAB = size_t(NL) * NLP * sizeof(T);
+  static constexpr bool STAB = TAB <= 120 * 1024;
+  static constexpr size_t tile_bytes(int te) {  // element rows, geometry, connectivity codes
+    return ((size_t(te) * NLQ * sizeof(T) + 15) / 16) * 16 + size_t(te) * S::gt * sizeof(T) + size_t(te) * (D + 1) * 4;
+  }
+  static constexpr int TE = ((STAB ? TAB : 0) + tile_bytes(64) <= 200 * 1024) ? 64 : 32;
+  static constexpr int EG = TE / 4;          // element groups
+  static constexpr size_t TABS = STAB ? ((TAB + 15) / 16) * 16 : 0;
+  static constexpr size_t SMEM = TABS + ((tile_bytes(TE) + 15) / 16) * 16;
+};
+
+// acc[i][j] = sum_s tab[s][r0 + i] * X[k_j][s],  k_j = eg + j * EG.
+template <int NL, int NLP, int NLQ, int EG, typename T>
+__device__ __forceinline__ void tile_gemm(const T* tab, const T* X, int r0, int eg, T (&acc)[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+  for (int s2 = 0; s2 < NL; ++s2) {
+    T t[4];
+    Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(tab + s2 * NLP + r0), t);
+    if constexpr (Pack<T>::W == 2)
+      Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(tab + s2 * NLP + r0 + 2), t + 2);
+    T x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = X[(eg + j * EG) * NLQ + s2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(t[i], x[j], acc[i][j]);
+  }
+}
+
+// The GEMM step shared by both projections: X[k][s] (k < TE, s < NL) is replaced by
+// sum_s tab[s][r] X[k][s].  The result stays in registers until every thread has read X.
+template <int NL, int NLP, int NLQ, int TE, typename T>
+__device__ __forceinline__ void tile_apply(const T* tab, T* X) {
+  constexpr int EG = TE / 4, RG = (NL + 3) / 4, STEP = kProjThreads / EG;
+  constexpr int NPASS = (RG + STEP - 1) / STEP;
+  const int tid = threadIdx.x, eg = tid % EG;
+  T keep[NPASS][4][4];
+#pragma unroll
+  for (int p = 0; p < NPASS; ++p) {
+    const int rg = tid / EG + p * STEP;
+    if (rg < RG) tile_gemm<NL, NLP, NLQ, EG, T>(tab, X, rg * 4, eg, keep[p]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < NPASS; ++p) {
+    const int rg = tid / EG + p * STEP;
+    if (rg < RG) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = rg * 4 + i;
+        if (r < NL)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) X[(eg + j * EG) * NLQ + r] = keep[p][i][j];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int D, int K, typename T>
+__device__ __forceinline__ const T* proj_setup(unsigned char* smem, const T* tab) {
+  using C = ProjCfg<D, K, T>;
+  if (!C::STAB) return tab;
+  T* sT = reinterpret_cast<T*>(smem);
+  for (int t = threadIdx.x; t < C::NL * C::NLP; t += blockDim.x) sT[t] = tab[t];
+  return sT;
+}
+
+// a1: V_h -> L2.  Per element: gather the (d+1) facet blocks with the sign sigma and the
+// interior block, reference change of basis Dinv, contravariant Piola map J / det J.
+// tab = Dinv^T with rows padded to NLP: tab[s][r] = Dinv[r][s].
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(kProjThreads) k_v2l(DevMesh m, const T* __restrict__ tab,
+                                                      const T* __restrict__ uV, T* __restrict__ uL) {
+  using S = Shape<D, K>;
+  using C = ProjCfg<D, K, T>;
+  constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
+  constexpr int NLP = C::NLP, NLQ = C::NLQ, TE = C::TE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
+  const T* geoT = static_cast<const T*>(m.geoT);
+  T* sX = reinterpret_cast<T*>(smem_raw + C::TABS);         // [TE][NLQ]
+  T* sGeo = reinterpret_cast<T*>(smem_raw + C::TABS + ((size_t(TE) * NLQ * sizeof(T) + 15) / 16) * 16);
+  int* sCode = reinterpret_cast<int*>(sGeo + TE * GEO);      // [TE][D+1]
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (m.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    constexpr int IG = (TE * GEO + kProjThreads - 1) / kProjThreads;
+#pragma unroll
+    for (int it = 0; it < IG; ++it) {
+      const int t = tid + it * kProjThreads;
+      if (t < TE * GEO) sGeo[t] = (e0 + t / GEO < m.E) ? geoT[e0 * GEO + t] : T(0);
+    }
+    constexpr int IC = (TE * (D + 1) + kProjThreads - 1) / kProjThreads;
+#pragma unroll
+    for (int it = 0; it < IC; ++it) {
+      const int t = tid + it * kProjThreads;
+      if (t < TE * (D + 1)) sCode[t] = (e0 + t / (D + 1) < m.E) ? m.efc[e0 * (D + 1) + t] : 0;
+    }
+    __syncthreads();
+    constexpr int IX = (TE * NL + kProjThreads - 1) / kProjThreads;
+#pragma unroll
+    for (int it = 0; it < IX; ++it) {
+      const int t = tid + it * kProjThreads;
+      if (t >= TE * NL) break;
+      const int k = t / NL, s2 = t - k * NL;
+      const int64_t e = e0 + k;
+      T v = T(0);
+      if (e < m.E) {
+        if (s2 < (D + 1) * NF) {
+          const int f = s2 / NF, mm = s2 - f * NF;
+          const int code = sCode[k * (D + 1) + f];
+          v = uV[(int64_t)(code >> 2) * NF + mm];
+          if (code & 2) v = -v;
+        } else {
+          v = uV[m.NF * NF + e * NINT + (s2 - (D + 1) * NF)];
+        }
+      }
+      sX[k * NLQ + s2] = v;
+    }
+    __syncthreads();
+    tile_apply<NL, NLP, NLQ, TE, T>(Tb, sX);
+    for (int t = tid; t < TE * NL; t += kProjThreads) {
+      const int k = t / NL, idx = t - k * NL;
+      if (e0 + k >= m.E) continue;
+      const T* g = sGeo + k * GEO;  // Pf = J / det J
+      const int a = idx / NB, i = idx - a * NB;
+      T acc1 = T(0);
+#pragma unroll
+      for (int b = 0; b < D; ++b) acc1 = fma(g[a * D + b], sX[k * NLQ + b * NB + i], acc1);
+      uL[e0 * NL + t] = acc1;
+    }
+    __syncthreads();
+  }
+}
+
+// a7 (element part): local functionals of an L2 field.  Not dual: ell = D (det J Jinv y);
+// dual (the transpose E^T): ell = Dinv^T (J^T y / det J).  Interior rows are combined
+// into the V_h output; facet rows go to lf[e][f][m] with the sign sigma.
+// tab[s][r] (rows padded to NLP) = D[r][s] (not dual) or Dinv[s][r] (dual).
+template <int D, int K, typename T, bool DUAL>
+__global__ void __launch_bounds__(kProjThreads) k_l2v_elem(DevMesh m, const T* __restrict__ tab,
+                                                           const T* __restrict__ yL, T* __restrict__ lf,
+                                                           T* outV, Combine cmb) {
+  using S = Shape<D, K>;
+  using C = ProjCfg<D, K, T>;
+  constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
+  constexpr int NLP = C::NLP, NLQ = C::NLQ, TE = C::TE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
+  const T* geoT = static_cast<const T*>(m.geoT);
+  T* sX = reinterpret_cast<T*>(smem_raw + C::TABS);
+  T* sGeo = reinterpret_cast<T*>(smem_raw + C::TABS + ((size_t(TE) * NLQ * sizeof(T) + 15) / 16) * 16);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (m.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    constexpr int IG = (TE * GEO + kProjThreads - 1) / kProjThreads;
+#pragma unroll
+    for (int it = 0; it < IG; ++it) {
+      const int t = tid + it * kProjThreads;
+      if (t < TE * GEO) sGeo[t] = (e0 + t / GEO < m.E) ? geoT[e0 * GEO + t] : T(0);
+    }
+    __syncthreads();
+    constexpr int IX = (TE * NL + kProjThreads - 1) / kProjThreads;
+#pragma unroll
+    for (int it = 0; it < IX; ++it) {
+      const int t = tid + it * kProjThreads;
+      if (t >= TE * NL) break;
+      const int k = t / NL, s2 = t - k * NL;
+      T acc1 = T(0);
+      if (e0 + k < m.E) {
+        const T* g = sGeo + k * GEO;
+        const int b = s2 / NB, i = s2 - b * NB;
+        const T* y = yL + (e0 + k) * NL;
+        if (!DUAL) {  // Pi = det J * Jinv
+#pragma unroll
+          for (int a = 0; a < D; ++a) acc1 = fma(g[D * D + b * D + a], y[a * NB + i], acc1);
+        } else {      // Pf^T = J^T / det J
+#pragma unroll
+          for (int a = 0; a < D; ++a) acc1 = fma(g[a * D + b], y[a * NB + i], acc1);
+        }
+      }
+      sX[k * NLQ + s2] = acc1;
+    }
+    __syncthreads();
+    tile_apply<NL, NLP, NLQ, TE, T>(Tb, sX);
+    for (int t = tid; t < TE * NL; t += kProjThreads) {
+      const int k = t / NL, r = t - k * NL;
+      const int64_t e = e0 + k;
+      if (e >= m.E) continue;
+      const T v = sX[k * NLQ + r];
+      if (r < (D + 1) * NF) {
+        const int code = m.efc[e * (D + 1) + r / NF];
+        lf[e * (D + 1) * NF + r] = (code & 2) ? -v : v;
+      } else {
+        const int64_t idx = m.NF * NF + e * NINT + (r - (D + 1) * NF);
+        outV[idx] = combine_at<T>(cmb, v, idx);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Vectorised dot product of a register array with a 16-byte aligned shared-memory row
+// (the row is padded to a multiple of 4 entries; padding entries are never used).
+// Row stride (in elements) of point-major tables: a multiple of 16 bytes that is an odd
+// multiple of 16 bytes, so that 8 consecutive lanes reading 16-byte chunks of 8
+// consecutive rows hit 8 distinct bank groups.
+template <typename T>
+__host__ __device__ constexpr int row_stride(int n) {
+  return sizeof(T) == 4 ? ((n + 3) / 4 * 4 + (((n + 3) / 4) % 2 == 0 ? 4 : 0))
+                        : ((n + 1) / 2 * 2 + (((n + 1) / 2) % 2 == 0 ? 2 : 0));
+}
+
+// 16-byte shared-memory load that the compiler may not hoist out of a loop (keeps the
+// loop-invariant coefficient rows in shared memory instead of in registers).
+__device__ __forceinline__ void lds_v(const float* p, float* o) {
+  asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];\n"
+               : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void lds_v(const double* p, double* o) {
+  asm volatile("ld.shared.v2.f64 {%0,%1}, [%2];\n"
+               : "=d"(o[0]), "=d"(o[1])
+               : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+
+// x[0..N) = s[0..N) with 16-byte loads (s 16-byte aligned)
+template <int N, typename T>
+__device__ __forceinline__ void load_row(const T* s, T* x) {
+  constexpr int W = Pack<T>::W;
+#pragma unroll
+  for (int i = 0; i < N; i += W) {
+    T o[W];
+    Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(s + i), o);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (i + w < N) x[i + w] = o[w];
+  }
+}
+
+// sum_i x[i] s[i] with volatile 16-byte shared loads
+template <int N, typename T>
+__device__ __forceinline__ T dot_row_v(const T* x, const T* s) {
+  constexpr int W = Pack<T>::W;
+  T acc = T(0);
+#pragma unroll
+  for (int i = 0; i < N; i += W) {
+    T o[W];
+    lds_v(s + i, o);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (i + w < N) acc = fma(x[i + w], o[w], acc);
+  }
+  return acc;
+}
 
 template <int N, typename T>
 __device__ __forceinline__ T dot_row(const T* x, const T* s) {
@@ -248,63 +425,93 @@ __device__ __forceinline__ void warp_copy_async(void* sdst, const void* gsrc, in
 }
 
 // ------------------------------------------------------------------------------------
-// a4: facet term.  One warp per facet, lanes own facet quadrature points.  At every
-// point: w.n from the average of both sides' w (equal to w.n for normal-continuous w),
-// the jump J = u^A - u^B, (I - Pi^l) J with Pi^l the tangential P^l projection of
-// Section 3.2, h = 1/2 |w.n| (I - Pi^l) J.  Writes two sets of facet moments
-//   gam[F][0][m][a] = a_F sum_q w_q psi_m(q) (-1/2 (w.n) J_a(q))            ("alpha")
-//   gam[F][1][m][a] = a_F sum_q w_q psi_m(q) ((I - Pi^l) h)_a(q)              ("beta")
-// Side A of the facet receives alpha + beta, side B alpha - beta.  Together with the
-// volume kernel this is the conservative form of the convection operator rewritten by
-// the element-wise integration by parts, which is exact for the rules used (volume
-// degree 3k-1, facet degree 3k): every term is O(|u| |grad u|) or O(jump), so FP32
-// does not lose digits to the O(1/h) cancellation between volume and facet terms.
-// The projection of h needs no second reduction: with an orthonormal facet basis the
-// moments of (I - Pi^l) h are those of h with the tangential part of the first
-// C(l+d-1, d-1) moments removed.
+// a4: facet term.  One warp per facet.  The traces of both sides are taken in modal
+// form: tau^X_m = sum_i TrM_{f_X}[m][i] c^X_i (TrM = <phi_i o xhat_f, psi_m>, exact since
+// phi_i restricted to a facet lies in P^k(F)), so the jump J and its complement
+// (I - Pi^l) J are exact modal vectors: Pi^l (Section 3.2) keeps the tangential part of
+// the first C(l+d-1, d-1) modes (hierarchical orthonormal facet basis), i.e. modes below
+// that count keep only (J_m . n) n.  Lanes then own facet quadrature points and evaluate
+// w.n (from the average of both sides' w, equal to w.n for normal-continuous w), J and
+// (I - Pi^l) J there, and form h = 1/2 |w.n| (I - Pi^l) J and -1/2 (w.n) J.  Moments:
+//   alpha[m][a] = a_F sum_q w_q psi_m(q) (-1/2 (w.n) J_a(q)),
+//   beta[m][a]  = a_F sum_q w_q psi_m(q) ((I - Pi^l) h)_a(q),
+// where, with an orthonormal facet basis, the moments of (I - Pi^l) h are those of h
+// with the tangential part of the first modes removed.  They are written element-major:
+// gam[e][f][m][a] for the element e that sees the facet as its local facet f,
+// alpha + beta for side A and alpha - beta for side B.  Together with the volume kernel
+// this is the conservative form of the convection operator rewritten by the
+// element-wise integration by parts, which is exact for the rules used (volume degree
+// 3k-1, facet degree 3k): every term is O(|u| |grad u|) or O(jump), so FP32 does not
+// lose digits to the O(1/h) cancellation between volume and facet terms.
+template <int N, typename T>
+__device__ __forceinline__ T dot_ss(const T* p, const T* q) {
+  constexpr int W = Pack<T>::W;
+  T acc = T(0);
+#pragma unroll
+  for (int i = 0; i < N; i += W) {
+    T a[W], b[W];
+    Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p + i), a);
+    Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(q + i), b);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (i + w < N) acc = fma(a[w], b[w], acc);
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T* o) {  // 4 consecutive values, 16-byte aligned
+  Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p), o);
+  if constexpr (Pack<T>::W == 2) Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p + 2), o + 2);
+}
+
 template <int D, int K, typename T, bool WSEP, bool STAB>
 __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, const T* __restrict__ uL,
                                                        const T* __restrict__ wL, int lconst,
                                                        const int8_t* __restrict__ facet_l,
                                                        T* __restrict__ gam, double* __restrict__ diss) {
+  static_assert(STAB, "facet tables always fit in shared memory");
   using S = Shape<D, K>;
   constexpr int NB = S::nb, NF = S::nf, NL = S::nloc, NQF = S::nqf, QP = (NQF + 31) / 32;
-  constexpr int TRP = (D + 1) * NB * NQF, PSI = NF * NQF;
-  constexpr int TABN = r4i(TRP + 2 * PSI + NQF);
   constexpr int NBP = r4i(NB);
+  constexpr int TRM = (D + 1) * NF * NBP, PSI = NF * NQF;
+  constexpr int TABN = r4i(TRM + 2 * PSI + NQF);
   constexpr int CW = D * NBP;
   constexpr int SV = NQF * 4;
-  constexpr int PER_WARP = (WSEP ? 4 : 2) * CW + 2 * SV + NF * 4 + 2 * NF * 4;
+  constexpr int PER_WARP = (WSEP ? 4 : 2) * CW + 2 * SV + 2 * NF * 4 + 2 * NF * 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sbase = reinterpret_cast<T*>(smem_raw);
-  const T* TrP = static_cast<const T*>(tb.TrP);
-  const T* Psi = static_cast<const T*>(tb.Psi);
-  const T* WPsi = static_cast<const T*>(tb.WPsi);
-  const T* Wf = static_cast<const T*>(tb.Wf);
-  T* sw = sbase;
-  if (STAB) {
-    for (int t = threadIdx.x; t < TRP; t += blockDim.x) sbase[t] = TrP[t];
-    for (int t = threadIdx.x; t < PSI; t += blockDim.x) {
-      sbase[TRP + t] = Psi[t];
-      sbase[TRP + PSI + t] = WPsi[t];
+  {
+    const T* TrMg = static_cast<const T*>(tb.TrM);
+    const T* Psig = static_cast<const T*>(tb.Psi);
+    const T* WPsig = static_cast<const T*>(tb.WPsi);
+    const T* Wfg = static_cast<const T*>(tb.Wf);
+    for (int t = threadIdx.x; t < TRM; t += blockDim.x) {
+      const int row = t / NBP, i = t - row * NBP;
+      sbase[t] = (i < NB) ? TrMg[row * NB + i] : T(0);
     }
-    for (int t = threadIdx.x; t < NQF; t += blockDim.x) sbase[TRP + 2 * PSI + t] = Wf[t];
-    TrP = sbase;
-    Psi = sbase + TRP;
-    WPsi = sbase + TRP + PSI;
-    Wf = sbase + TRP + 2 * PSI;
-    sw = sbase + TABN;
+    for (int t = threadIdx.x; t < PSI; t += blockDim.x) {
+      sbase[TRM + t] = Psig[t];
+      sbase[TRM + PSI + t] = WPsig[t];
+    }
+    for (int t = threadIdx.x; t < NQF; t += blockDim.x) sbase[TRM + 2 * PSI + t] = Wfg[t];
   }
+  const T* TrM = sbase;
+  const T* Psi = sbase + TRM;
+  const T* WPsi = sbase + TRM + PSI;
+  const T* Wf = sbase + TRM + 2 * PSI;
+  T* sw = sbase + TABN;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* cA = sw + warp * PER_WARP;
   T* cB = cA + CW;
   T* wA = WSEP ? cB + CW : cA;
   T* wB = WSEP ? wA + CW : cB;
-  T* sH = cA + (WSEP ? 4 : 2) * CW;  // [NQF][4]  h, or the jump while projecting
-  T* sC = sH + SV;                   // [NQF][4]  -1/2 (w.n) J
-  T* sEta = sC + SV;                 // [NF][4]   P^l moments of the jump
-  T* sOut = sEta + NF * 4;           // [2][NF][4] alpha, beta
+  T* sH = cA + (WSEP ? 4 : 2) * CW;  // [NQF][4]   1/2 |w.n| (I - Pi^l) J
+  T* sC = sH + SV;                   // [NQF][4]   -1/2 (w.n) J
+  T* sJ = sC + SV;                   // [NF][4]    modal jump
+  T* sWv = sJ + NF * 4;              // [NF][4]    modal average wind
+  T* sOut = sWv + NF * 4;            // [2][NF][4] alpha, beta
   for (int64_t F = (int64_t)blockIdx.x * kWarps + warp; F < m.NF; F += (int64_t)gridDim.x * kWarps) {
     const int pa = m.fa[F], pb = m.fb[F];
     const int64_t eA = pa >> 2, eB = pb >> 2;
@@ -316,91 +523,67 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
     const T aF = T(fg[D]);
     const int l = facet_l ? int(facet_l[F]) : lconst;
     const int nl = (l < 0) ? 0 : cnbasis(D - 1, l);
-    for (int s = lane; s < NL; s += 32) {
-      const int a = s / NB, i = s - a * NB;
-      cA[a * NBP + i] = uL[eA * NL + s];
-      cB[a * NBP + i] = uL[eB * NL + s];
+    for (int s2 = lane; s2 < NL; s2 += 32) {
+      const int a = s2 / NB, i = s2 - a * NB;
+      cA[a * NBP + i] = uL[eA * NL + s2];
+      cB[a * NBP + i] = uL[eB * NL + s2];
       if (WSEP) {
-        wA[a * NBP + i] = wL[eA * NL + s];
-        wB[a * NBP + i] = wL[eB * NL + s];
+        wA[a * NBP + i] = wL[eA * NL + s2];
+        wB[a * NBP + i] = wL[eB * NL + s2];
       }
     }
     __syncwarp();
-    T wn[QP], J[QP][D], P[QP][D], wq[QP];
-    int qc[QP];
-#pragma unroll
-    for (int qq = 0; qq < QP; ++qq) {
-      const int q = lane + 32 * qq;
-      const bool ok = q < NQF;
-      qc[qq] = ok ? q : 0;
-      T ta[NB], tbv[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        ta[i] = TrP[(fa * NB + i) * NQF + qc[qq]];
-        tbv[i] = TrP[(fb * NB + i) * NQF + qc[qq]];
-      }
-      T s = T(0);
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T ua = dot_row<NB>(ta, cA + a * NBP);
-        const T ub = dot_row<NB>(tbv, cB + a * NBP);
-        const T wa = WSEP ? dot_row<NB>(ta, wA + a * NBP) : ua;
-        const T wb = WSEP ? dot_row<NB>(tbv, wB + a * NBP) : ub;
-        s += (wa + wb) * n[a];
-        J[qq][a] = ua - ub;
-        P[qq][a] = J[qq][a];
-      }
-      wn[qq] = T(0.5) * s;
-      wq[qq] = ok ? Wf[qc[qq]] : T(0);
+    // modal traces: jump and average wind
+    for (int v = lane; v < NF * D; v += 32) {
+      const int mm = v / D, a = v - mm * D;
+      const T* ra = TrM + (fa * NF + mm) * NBP;
+      const T* rb = TrM + (fb * NF + mm) * NBP;
+      const T ta = dot_ss<NB>(ra, cA + a * NBP), tbv = dot_ss<NB>(rb, cB + a * NBP);
+      const T wa = WSEP ? dot_ss<NB>(ra, wA + a * NBP) : ta;
+      const T wb = WSEP ? dot_ss<NB>(rb, wB + a * NBP) : tbv;
+      sJ[mm * 4 + a] = ta - tbv;
+      sWv[mm * 4 + a] = T(0.5) * (wa + wb);
     }
-    if (nl > 0) {  // (I - Pi^l) J: one reduction for the P^l moments of the jump
-#pragma unroll
-      for (int qq = 0; qq < QP; ++qq) {
-        const int q = lane + 32 * qq;
-        if (q < NQF)
-#pragma unroll
-          for (int a = 0; a < D; ++a) sH[q * 4 + a] = J[qq][a];
-      }
-      __syncwarp();
-      for (int v = lane; v < nl * D; v += 32) {
-        const int mm = v / D, a = v - mm * D;
-        T acc = T(0);
-        for (int q = 0; q < NQF; ++q) acc = fma(WPsi[mm * NQF + q], sH[q * 4 + a], acc);
-        sEta[mm * 4 + a] = acc;
-      }
-      __syncwarp();
-#pragma unroll
-      for (int qq = 0; qq < QP; ++qq) {
-        T pis[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) pis[a] = T(0);
-        for (int mm = 0; mm < nl; ++mm) {
-          const T p = Psi[mm * NQF + qc[qq]];
-#pragma unroll
-          for (int a = 0; a < D; ++a) pis[a] = fma(p, sEta[mm * 4 + a], pis[a]);
-        }
-        T dn = T(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) dn += pis[a] * n[a];
-#pragma unroll
-        for (int a = 0; a < D; ++a) P[qq][a] -= pis[a] - dn * n[a];
-      }
-      __syncwarp();  // sH is overwritten below
-    }
+    __syncwarp();
     T dsum = T(0);
 #pragma unroll
     for (int qq = 0; qq < QP; ++qq) {
       const int q = lane + 32 * qq;
-      const T aw = T(0.5) * fabs(wn[qq]);
-      T p2 = T(0);
+      const bool ok = q < NQF;
+      const int qc = ok ? q : 0;
+      T J[D], P[D], wn = T(0);
 #pragma unroll
-      for (int a = 0; a < D; ++a) p2 += P[qq][a] * P[qq][a];
-      dsum += wq[qq] * aw * p2;
-      if (q < NQF) {
+      for (int a = 0; a < D; ++a) J[a] = P[a] = T(0);
+#pragma unroll
+      for (int mm = 0; mm < NF; ++mm) {
+        const T p = Psi[mm * NQF + qc];
+        T jm[4], wv[4];
+        lds4(sJ + mm * 4, jm);
+        lds4(sWv + mm * 4, wv);
+        T jn = T(0), wvn = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          sH[q * 4 + a] = aw * P[qq][a];
-          sC[q * 4 + a] = T(-0.5) * wn[qq] * J[qq][a];
+          jn = fma(jm[a], n[a], jn);
+          wvn = fma(wv[a], n[a], wvn);
+        }
+        wn = fma(p, wvn, wn);
+        const bool low = mm < nl;  // Pi^l removes the tangential part of the low modes
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          J[a] = fma(p, jm[a], J[a]);
+          P[a] = fma(p, low ? jn * n[a] : jm[a], P[a]);
+        }
+      }
+      const T aw = T(0.5) * fabs(wn);
+      T p2 = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) p2 = fma(P[a], P[a], p2);
+      if (ok) {
+        dsum += Wf[q] * aw * p2;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          sH[q * 4 + a] = aw * P[a];
+          sC[q * 4 + a] = T(-0.5) * wn * J[a];
         }
       }
     }
@@ -413,8 +596,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       for (int a = 0; a < D; ++a) acc[a] = T(0);
       for (int q = 0; q < NQF; ++q) {
         const T wp = WPsi[mm * NQF + q];
+        T x[4];
+        lds4(src + q * 4, x);
 #pragma unroll
-        for (int a = 0; a < D; ++a) acc[a] = fma(wp, src[q * 4 + a], acc[a]);
+        for (int a = 0; a < D; ++a) acc[a] = fma(wp, x[a], acc[a]);
       }
       if (which && mm < nl) {  // (I - Pi^l) h: keep only the normal part of the low moments
         T dn = T(0);
@@ -457,19 +642,20 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
 // element's signed facet moments, geometry) is one contiguous record; a warp prefetches
 // the next element's records with cp.async while it computes the current one.
 template <int D, int K, typename T, bool WSEP, bool STAB>
-__global__ void __launch_bounds__(32 * kWarps, 2) k_volume(DevMesh m, DevTabs tb, const T* __restrict__ uL,
+__global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(DevMesh m, DevTabs tb, const T* __restrict__ uL,
                                                            const T* __restrict__ wL, const T* __restrict__ gam,
                                                            T* out, Combine cmb) {
   using S = Shape<D, K>;
   constexpr int NB = S::nb, NB1 = cnbasis(D, K - 1), NF = S::nf, NL = S::nloc, NQ = S::nq;
-  constexpr int NVP = S::nvp, CPL = NVP / 32, GEO = S::geo;
+  constexpr int NVP = S::nvp, CPL = NVP / 32, GEO = S::gt;
   constexpr int NBP = r4i(NB), NB1P = r4i(NB1);
-  constexpr int BT = NB * NQ, DM = D * NB1 * NB, TRM = (D + 1) * NF * NB;
+  constexpr int NBQ = row_stride<T>(NB);
+  constexpr int BT = NQ * NBQ, DM = D * NB1 * NB, TRM = (D + 1) * NF * NB;
   constexpr int TABN = r4i(BT + NQ + DM + TRM);
   constexpr int NG = (D + 1) * NF * D;
   // per-warp layout: two staging buffers (u record, w record, facet moments, geometry),
   // then the working arrays
-  constexpr int STU = r4i(NL), STG = r4i(NG), STGEO = 2 * r4i(GEO);  // geometry in T units
+  constexpr int STU = r4i(NL), STG = r4i(NG), STGEO = r4i(GEO);
   constexpr int STAGE = STU + (WSEP ? STU : 0) + STG + STGEO;
   constexpr int PER_WARP = 2 * STAGE + D * NBP + D * D * NB1P + (WSEP ? D * NBP + NB1P : 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -500,12 +686,12 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_volume(DevMesh m, DevTabs tb
   auto st_u = [&](int b) { return wbase + b * STAGE; };
   auto st_w = [&](int b) { return wbase + b * STAGE + STU; };
   auto st_g = [&](int b) { return wbase + b * STAGE + STU + (WSEP ? STU : 0); };
-  auto st_geo = [&](int b) { return reinterpret_cast<double*>(st_g(b) + STG); };
+  auto st_geo = [&](int b) { return st_g(b) + STG; };
   auto issue = [&](int64_t e, int b) {
     warp_copy_async<NL * (int)sizeof(T)>(st_u(b), uL + e * NL, lane);
     if (WSEP) warp_copy_async<NL * (int)sizeof(T)>(st_w(b), wL + e * NL, lane);
     warp_copy_async<NG * (int)sizeof(T)>(st_g(b), gam + e * NG, lane);
-    warp_copy_async<GEO * 8>(st_geo(b), m.geo + e * GEO, lane);
+    warp_copy_async<GEO * (int)sizeof(T)>(st_geo(b), static_cast<const T*>(m.geoT) + e * GEO, lane);
   };
   const int64_t stride = (int64_t)gridDim.x * kWarps;
   int64_t e = (int64_t)blockIdx.x * kWarps + warp;
@@ -517,15 +703,14 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_volume(DevMesh m, DevTabs tb
     cp_commit();
     cp_wait<1>();                                    // this element's copies are done
     __syncwarp();
-    const double* g = st_geo(b);
+    const T* g = st_geo(b);                          // Pf, Pi, M = |det J| Jinv, 1/|det J|
     const T* gl = st_g(b);                           // signed facet moments of the element
     T M[D][D];
-    const double ad = g[2 * D * D + 1];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int c = 0; c < D; ++c) M[a][c] = T(ad * g[D * D + a * D + c]);
-    const T invabs = T(1.0 / ad);
+      for (int c = 0; c < D; ++c) M[a][c] = g[2 * D * D + a * D + c];
+    const T invabs = g[3 * D * D];
     for (int s2 = lane; s2 < NL; s2 += 32) {
       const int a = s2 / NB, i = s2 - a * NB;
       sC[a * NBP + i] = st_u(b)[s2];
@@ -559,20 +744,19 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_volume(DevMesh m, DevTabs tb
     for (int j = 0; j < NVP; ++j) acc[j] = T(0);
     for (int q = lane; q < NQ; q += 32) {
       T ph[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) ph[i] = Bt[i * NQ + q];
+      load_row<NB>(Bt + q * NBQ, ph);
       T u[D], G[D][D], W[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        u[a] = dot_row<NB>(ph, sC + a * NBP);
+        u[a] = dot_row_v<NB>(ph, sC + a * NBP);
 #pragma unroll
-        for (int c = 0; c < D; ++c) G[a][c] = dot_row<NB1>(ph, sG + (a * D + c) * NB1P);
+        for (int c = 0; c < D; ++c) G[a][c] = dot_row_v<NB1>(ph, sG + (a * D + c) * NB1P);
       }
       T dv = T(0);
       if (WSEP) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) W[c] = dot_row<NB>(ph, sW + c * NBP);
-        dv = dot_row<NB1>(ph, sDv);
+        for (int c = 0; c < D; ++c) W[c] = dot_row_v<NB>(ph, sW + c * NBP);
+        dv = dot_row_v<NB1>(ph, sDv);
       } else {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -618,67 +802,6 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_volume(DevMesh m, DevTabs tb
 // transpose map, ell = Dinv^T (J^T y / det J)); interior rows are final, facet rows go to
 // lf[e][f][m] with the sign sigma.  Facet part (R): average (or, transposed, sum) the two
 // copies of every facet functional.
-template <int D, int K, typename T, bool DUAL, bool STAB>
-__global__ void __launch_bounds__(32 * kWarps) k_l2v_elem(DevMesh m, const T* __restrict__ tab,
-                                                          const T* __restrict__ yL, T* __restrict__ lf,
-                                                          T* outV, Combine cmb) {
-  using S = Shape<D, K>;
-  constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sbase = reinterpret_cast<T*>(smem_raw);
-  const T* Tb = tab;
-  T* sw = sbase;
-  if (STAB) {
-    for (int t = threadIdx.x; t < NL * NL; t += blockDim.x) sbase[t] = tab[t];
-    Tb = sbase;
-    sw = sbase + r4i(NL * NL);  // keeps the per-warp buffers 16-byte aligned
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* ch = sw + warp * 2 * kEPW * NL;  // [NL][kEPW] reference coefficients (interleaved)
-  T* ell = ch + kEPW * NL;            // [kEPW][NL] local functionals
-  for (int64_t e0 = ((int64_t)blockIdx.x * kWarps + warp) * kEPW; e0 < m.E;
-       e0 += (int64_t)gridDim.x * kWarps * kEPW) {
-    for (int t = lane; t < kEPW * NL; t += 32) {
-      const int k = t / NL, idx = t - k * NL;
-      const int64_t e = e0 + k;
-      T acc = T(0);
-      if (e < m.E) {
-        const double* g = m.geo + e * S::geo;
-        const int b = idx / NB, i = idx - b * NB;
-        if (!DUAL) {  // det J * Jinv * y
-          const double det = g[2 * D * D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) acc = fma(T(det * g[D * D + b * D + a]), yL[e * NL + a * NB + i], acc);
-        } else {      // J^T y / det J
-          const double inv = 1.0 / g[2 * D * D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) acc = fma(T(g[a * D + b] * inv), yL[e * NL + a * NB + i], acc);
-        }
-      }
-      ch[idx * kEPW + k] = acc;
-    }
-    __syncwarp();
-    epw_gemv<NL, T>(Tb, ch, ell, lane);
-    __syncwarp();
-    for (int t = lane; t < kEPW * NL; t += 32) {
-      const int k = t / NL, r = t - k * NL;
-      const int64_t e = e0 + k;
-      if (e >= m.E) continue;
-      const T v = ell[k * NL + r];
-      if (r < (D + 1) * NF) {
-        const int f = r / NF, mm = r - f * NF;
-        const int code = m.efc[e * (D + 1) + f];
-        lf[(e * (D + 1) + f) * NF + mm] = (code & 2) ? -v : v;
-      } else {
-        const int64_t idx = m.NF * NF + e * NINT + (r - (D + 1) * NF);
-        outV[idx] = combine_at<T>(cmb, v, idx);
-      }
-    }
-    __syncwarp();
-  }
-}
-
 template <int D, int K, typename T, bool DUAL>
 __global__ void __launch_bounds__(256) k_l2v_facet(DevMesh m, const T* __restrict__ lf, T* outV, Combine cmb) {
   constexpr int NF = Shape<D, K>::nf;

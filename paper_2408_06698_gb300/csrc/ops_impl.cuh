@@ -13,28 +13,26 @@ class OpsImpl final : public Ops {
   static constexpr size_t sz = sizeof(T);
   static constexpr size_t r4(size_t n) { return ((n + 3) / 4) * 4; }
 
-  static constexpr size_t kTabNL = r4(size_t(S::nloc) * S::nloc) * sz;
-  static constexpr size_t kProjWarp = 2 * kEPW * size_t(S::nloc) * sz;
-  static constexpr bool kProjTab = kTabNL + kWarps * kProjWarp <= kLimit;
-  static constexpr size_t kV2lSmem = (kProjTab ? kTabNL : 0) + kWarps * kProjWarp;
-  static constexpr size_t kL2vSmem = (kProjTab ? kTabNL : 0) + kWarps * kProjWarp;
+  using PC = ProjCfg<D, K, T>;
+  static constexpr size_t kProjSmem = PC::SMEM;
 
-  // facet kernel: TrP, Psi, WPsi, Wf; per warp: coefficient blocks, two [nqf][4] point
-  // buffers and the [nf][4] projection moments (layout of k_facet)
-  static constexpr size_t kFacTab = r4(size_t(D + 1) * S::nb * S::nqf + 2 * S::nf * S::nqf + S::nqf) * sz;
+  // facet kernel: padded modal trace matrices, Psi, WPsi, Wf; per warp: coefficient
+  // blocks, two [nqf][4] point buffers, modal jump / wind, moments (layout of k_facet)
+  static constexpr size_t kNBQ = row_stride<T>(S::nb);
+  static constexpr size_t kFacTab = r4(size_t(D + 1) * S::nf * r4(S::nb) + 2 * S::nf * S::nqf + S::nqf) * sz;
   static constexpr size_t facet_warp(bool wsep) {
-    return (size_t(wsep ? 4 : 2) * D * r4(S::nb) + 2 * S::nqf * 4 + S::nf * 4 + 2 * S::nf * 4) * sz;
+    return (size_t(wsep ? 4 : 2) * D * r4(S::nb) + 2 * S::nqf * 4 + 2 * S::nf * 4 + 2 * S::nf * 4) * sz;
   }
-  static constexpr bool kFacetTab = kFacTab + kWarps * facet_warp(true) <= kLimit;
-  static constexpr size_t facet_smem(bool wsep) { return (kFacetTab ? kFacTab : 0) + kWarps * facet_warp(wsep); }
+  static constexpr bool kFacetTab = true;
+  static constexpr size_t facet_smem(bool wsep) { return kFacTab + kWarps * facet_warp(wsep); }
 
   // volume kernel: Bt, Wq, Dm, TrM; per warp: coefficients, modal gradients, (W and its
   // divergence), signed facet moments (layout of k_volume)
   static constexpr int kNB1 = cnbasis(D, K - 1);
   static constexpr size_t kVolTab =
-      r4(size_t(S::nb) * S::nq + S::nq + size_t(D) * kNB1 * S::nb + size_t(D + 1) * S::nf * S::nb) * sz;
+      r4(size_t(S::nq) * kNBQ + S::nq + size_t(D) * kNB1 * S::nb + size_t(D + 1) * S::nf * S::nb) * sz;
   static constexpr size_t volume_stage(bool wsep) {
-    return r4(S::nloc) * (wsep ? 2 : 1) + r4(size_t(D + 1) * S::nf * D) + 2 * r4(S::geo);
+    return r4(S::nloc) * (wsep ? 2 : 1) + r4(size_t(D + 1) * S::nf * D) + r4(S::gt);
   }
   static constexpr size_t volume_warp(bool wsep) {
     return (2 * volume_stage(wsep) + size_t(D) * r4(S::nb) + size_t(D) * D * r4(kNB1) +
@@ -73,20 +71,20 @@ class OpsImpl final : public Ops {
     err = cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     const int th = 32 * kWarps;
-    if ((err = setup(k_v2l<D, K, T, kProjTab>, kV2lSmem, th, &g_v2l_)) != cudaSuccess) return err;
+    if ((err = setup(k_v2l<D, K, T>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, false, kFacetTab>, facet_smem(false), th, &g_fac_[0])) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, true, kFacetTab>, facet_smem(true), th, &g_fac_[1])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, false, kVolumeTab>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, true, kVolumeTab>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
-    if ((err = setup(k_l2v_elem<D, K, T, false, kProjTab>, kL2vSmem, th, &g_elem_[0])) != cudaSuccess) return err;
-    if ((err = setup(k_l2v_elem<D, K, T, true, kProjTab>, kL2vSmem, th, &g_elem_[1])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_elem<D, K, T, false>, kProjSmem, kProjThreads, &g_elem_[0])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_elem<D, K, T, true>, kProjSmem, kProjThreads, &g_elem_[1])) != cudaSuccess) return err;
     if ((err = setup(k_l2v_facet<D, K, T, false>, 0, 256, &g_fsum_)) != cudaSuccess) return err;
     return cudaSuccess;
   }
 
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
-    const int g = clamp_grid(g_v2l_, m.E, kWarps * kEPW);
-    k_v2l<D, K, T, kProjTab><<<g, 32 * kWarps, kV2lSmem, st>>>(
+    const int g = clamp_grid(g_v2l_, m.E, PC::TE);
+    k_v2l<D, K, T><<<g, kProjThreads, kProjSmem, st>>>(
         m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
     return 1;
   }
@@ -121,12 +119,12 @@ class OpsImpl final : public Ops {
 
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,
                void* outV, cudaStream_t st) override {
-    const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, kWarps * kEPW);
+    const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, PC::TE);
     if (dual)
-      k_l2v_elem<D, K, T, true, kProjTab><<<g, 32 * kWarps, kL2vSmem, st>>>(
+      k_l2v_elem<D, K, T, true><<<g, kProjThreads, kProjSmem, st>>>(
           m, static_cast<const T*>(t.Dinv), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
     else
-      k_l2v_elem<D, K, T, false, kProjTab><<<g, 32 * kWarps, kL2vSmem, st>>>(
+      k_l2v_elem<D, K, T, false><<<g, kProjThreads, kProjSmem, st>>>(
           m, static_cast<const T*>(t.DT), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
     return 1;
   }
