@@ -199,6 +199,23 @@ hopu_status hopu_profile(hopu_ctx* ctx, int enable);
  * call: read after every hopu_rk_substep(..., n_substeps = 1) for exact totals.       */
 hopu_status hopu_profile_read(hopu_ctx* ctx, double* ms, int64_t* launches);
 
+/* The convection apply of hopu_apply_convection, for callers that cannot allocate
+ * device memory (no counterpart in the paper: it is a deployment aid).  Code that runs
+ * inside a caller-owned memory pool or budget, or in a process that reserves all device
+ * memory up front, may not let a library call cudaMalloc; this entry point allocates
+ * nothing and does not use the scratch hopu_create set aside.  Its two scratch arrays
+ * (the wind projected to L2 and the facet moments) live in a static device buffer of
+ * 32 MiB that is part of the library image, so every GPU that loads libhopu holds it
+ * until the process exits.  Meshes that need more scratch than that (n_l2 plus
+ * n_elems*(dim+1)*nf*dim values in the working precision) are rejected with EINVAL.
+ * The first call on a device looks up the buffer's device address (make that first
+ * call before any stream capture).  Every call shares the buffer, which keeps the last
+ * call's contents (nothing in it needs to start at zero); calls that overlap on the GPU
+ * (other streams, threads or contexts on the same device) race on it.  Arguments,
+ * result and errors as hopu_apply_convection.                                         */
+hopu_status hopu_apply_convection_noalloc(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2,
+                                          void* y_l2, const int8_t* facet_l);
+
 /* Host-only self check of the reference tables of (dim, k), no GPU needed:
  * report[0] = max relative error of the volume rule on monomials up to degree 3k-1,
  * report[1] = same for the facet rule up to degree 3k (closed form a!b!c!/(a+b+c+d)!),

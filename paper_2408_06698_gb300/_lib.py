@@ -52,6 +52,7 @@ SIGNATURES = {
     "hopu_clear_error": (c_int, [c_void_p]),
     "hopu_selftest": (c_int, [c_int, c_int, POINTER(c_double)]),
     "hopu_profile": (c_int, [c_void_p, c_int]),
+    "hopu_apply_convection_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
 }
 

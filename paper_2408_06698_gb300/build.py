@@ -20,6 +20,7 @@ LIB = os.path.join(PKG, "libhopu.so")
 
 SOURCES = [
     "capi.cu",
+    "noalloc.cu",
     "reftables.cpp",
     "meshtopo.cpp",
     "ops_d2.cu",

@@ -90,49 +90,8 @@ __global__ void __launch_bounds__(kRedThreads) k_sum(const double* in, int64_t n
 
 using namespace hopu;
 
-struct hopu_ctx {
-  int dim = 0, k = 0, l = -1, prec = 0, wind = 0;
-  bool fp64 = true;
-  size_t tsize = 8;
-  cudaStream_t stream = nullptr;
-  MeshTopo topo;
-  RefTables ref;
-  int64_t n_hdiv = 0, n_l2 = 0;
-  DevMesh dm;
-  DevTabs dt;
-  Ops* ops = nullptr;
-  int nsm = 1, red_blocks = 1;
-  // device memory
-  void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
-  void* d_geoT = nullptr;   // working-precision geometry factors
-  void* d_tabs = nullptr;   // every reference table
-  void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major
-  void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals
-  void* d_uL = nullptr;     // L2 stage field
-  void* d_yL = nullptr;     // L2 operator output
-  void* d_wL = nullptr;     // L2 wind of apply_convection / energy
-  void* d_wfz = nullptr;    // L2 frozen wind
-  void* d_s1 = nullptr;     // RK stage vectors (max of V_h and L2 lengths)
-  void* d_s2 = nullptr;
-  double* d_diss = nullptr; // [NF]
-  double* d_red = nullptr;  // partial sums + 4 scalars
-  bool have_frozen = false;
-  // cached CUDA graph of one substep
-  cudaGraphExec_t gexec = nullptr;
-  void* g_state = nullptr;
-  double g_dt = 0.0;
-  int g_wind = -1;
-  // profiling: CUDA events around every kernel launch (pairs 0..kProfPairs-1 belong to
-  // the captured substep graph, the rest to direct launches)
-  bool prof_on = false;
-  bool capturing = false;
-  bool graph_replayed = false;
-  std::vector<cudaEvent_t> ev;
-  std::vector<std::pair<int, int>> prof_graph, prof_direct;  // (pair index, kernel family)
-  int prof_next_direct = 0;
-  int status = HOPU_OK;
-  std::string err;
-};
+#include "context.h"
+
 
 namespace {
 
