@@ -148,6 +148,14 @@ hopu_status hopu_apply_convection(hopu_ctx* ctx, const void* w_hdiv, const void*
  * default stream (NULL) the kernels are launched directly.                             */
 hopu_status hopu_rk_substep(hopu_ctx* ctx, void* state, double dt, int n_substeps);
 
+/* Per-substep kinetic energy (row a8 of the hot path), kept on the device: with a log
+ * set, every later substep (also when replayed from its CUDA graph) writes
+ * 1/2 int |u|^2 of the state at the start of that substep, in FP64, to
+ * dev_log[i % capacity] for the i-th substep since this call (the L2 image of the state
+ * is the one the first RK stage computes anyway).  dev_log: caller-owned device array of
+ * capacity doubles; NULL with capacity 0 switches logging off.                         */
+hopu_status hopu_set_energy_log(hopu_ctx* ctx, double* dev_log, int64_t capacity);
+
 /* Set the wind used by FROZEN substeps (copied to an internal L2 buffer). */
 hopu_status hopu_set_frozen_wind(hopu_ctx* ctx, const void* w_hdiv);
 

@@ -45,6 +45,7 @@ SIGNATURES = {
     "hopu_apply_convection": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_rk_substep": (c_int, [c_void_p, c_void_p, c_double, c_int]),
     "hopu_set_frozen_wind": (c_int, [c_void_p, c_void_p]),
+    "hopu_set_energy_log": (c_int, [c_void_p, c_void_p, c_int64]),
     "hopu_energy": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     "hopu_points": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_int64)]),
     "hopu_interpolate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -79,6 +79,20 @@ __global__ void __launch_bounds__(kRedThreads) k_weighted_dot(int64_t E, int NL,
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
+// Sum the block partials and append 1/2 * total to a ring buffer at the device-side
+// position *pos (advanced by one), so replayed graphs log every substep.
+__global__ void __launch_bounds__(kRedThreads) k_sum_log(const double* in, int64_t n, double* log,
+                                                         int64_t cap, int64_t* pos) {
+  double s = 0.0;
+  for (int64_t t = threadIdx.x; t < n; t += kRedThreads) s += in[t];
+  const double tot = block_sum(s);
+  if (threadIdx.x == 0) {
+    const int64_t p = *pos;
+    log[p % cap] = 0.5 * tot;
+    *pos = p + 1;
+  }
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_sum(const double* in, int64_t n, double* out) {
   double s = 0.0;
   for (int64_t t = threadIdx.x; t < n; t += kRedThreads) s += in[t];
@@ -158,7 +172,7 @@ void timed(hopu_ctx* c, int family, F&& launch) {
 void free_all(hopu_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  void* ptrs[] = {c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
+  void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
                   c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -174,7 +188,7 @@ void convert(const std::vector<double>& src, std::vector<unsigned char>& dst, si
 }
 
 // Reorder the host FP64 tables into the kernel layouts (see hopu_internal.h).
-constexpr int kNumTables = 11;
+constexpr int kNumTables = 12;
 
 // Row stride of the point-major tables: an odd multiple of 16 bytes (matches
 // row_stride<T> in kernels.cuh).
@@ -199,6 +213,7 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
   auto& DinvT = out[8];
   auto& DT = out[9];
   auto& Dinv = out[10];
+  auto& Drow = out[11];
   Bt.assign((size_t)nq * nbq, 0.0);  // point-major [q][nbq]
   for (int q = 0; q < nq; ++q)
     for (int i = 0; i < nb; ++i) Bt[(size_t)q * nbq + i] = R.phi[(size_t)q * nb + i];
@@ -237,6 +252,11 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
       DT[(size_t)s * nlp + r] = R.D[(size_t)r * nl + s];
       Dinv[(size_t)s * nlp + r] = R.Dinv[(size_t)s * nl + r];
     }
+  // row-major D with an odd-multiple-of-16-byte row stride (fused back-projection)
+  const int nlr = point_row_stride(nl, fp64);
+  Drow.assign((size_t)nl * nlr, 0.0);
+  for (int r = 0; r < nl; ++r)
+    for (int s = 0; s < nl; ++s) Drow[(size_t)r * nlr + s] = R.D[(size_t)r * nl + s];
 }
 
 void enqueue_v2l(hopu_ctx* c, const void* uV, void* uL) {
@@ -255,6 +275,33 @@ hopu_status enqueue_stage_apply(hopu_ctx* c, const void* uL, const void* wL, int
   return check_launch(c, "apply kernels");
 }
 
+// STAGE wind, after u_L = E u_V: facet flux, volume term with the element part of the
+// back-projection fused in (when the kernel family has it), facet averaging R.
+hopu_status enqueue_stage_fused(hopu_ctx* c, Combine cmb, void* outV) {
+  timed(c, HOPU_K_FACET, [&] { c->ops->facet(c->dm, c->dt, c->d_uL, c->d_uL, c->l, nullptr, c->d_gam, nullptr, c->stream); });
+  if (c->ops->has_fused()) {
+    timed(c, HOPU_K_VOLUME, [&] { c->ops->volume_l2v(c->dm, c->dt, c->d_uL, c->d_gam, c->d_lf, cmb, outV, c->stream); });
+  } else {
+    Combine plain;
+    timed(c, HOPU_K_VOLUME, [&] { c->ops->volume(c->dm, c->dt, c->d_uL, c->d_uL, c->d_gam, plain, c->d_yL, c->stream); });
+    timed(c, HOPU_K_L2V_ELEM, [&] { c->ops->l2v_elem(c->dm, c->dt, c->d_yL, false, c->d_lf, cmb, outV, c->stream); });
+  }
+  timed(c, HOPU_K_L2V_FACET, [&] { c->ops->l2v_facet(c->dm, c->d_lf, false, cmb, outV, c->stream); });
+  return check_launch(c, "stage kernels");
+}
+
+hopu_status energy_log(hopu_ctx* c, const void* uL) {
+  const int G = geo_stride(c->dim);
+  if (c->fp64)
+    k_weighted_dot<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const double*)uL, (const double*)uL, c->d_red);
+  else
+    k_weighted_dot<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
+        c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const float*)uL, (const float*)uL, c->d_red);
+  k_sum_log<<<1, kRedThreads, 0, c->stream>>>(c->d_red, c->red_blocks, c->elog, c->elog_cap, c->d_elog_pos);
+  return check_launch(c, "energy log kernels");
+}
+
 // One SSP-RK3 (Shu-Osher) substep on the context stream.
 hopu_status enqueue_substep(hopu_ctx* c, void* state, double dt) {
   const Combine st[3] = {
@@ -265,12 +312,21 @@ hopu_status enqueue_substep(hopu_ctx* c, void* state, double dt) {
   const void* in[3] = {state, c->d_s1, c->d_s2};
   void* out[3] = {c->d_s1, c->d_s2, state};
   for (int s = 0; s < 3; ++s) {
+    if (s == 0 && c->elog) {  // a8: kinetic energy of the state at the start of the substep
+      if (c->wind == HOPU_WIND_STAGE) enqueue_v2l(c, in[0], c->d_uL);
+      const void* uL0 = (c->wind == HOPU_WIND_STAGE) ? c->d_uL : in[0];
+      hopu_status r = energy_log(c, uL0);
+      if (r != HOPU_OK) return r;
+      if (c->wind == HOPU_WIND_STAGE) {
+        r = enqueue_stage_fused(c, st[s], out[s]);
+        if (r != HOPU_OK) return r;
+        continue;
+      }
+    }
     if (c->wind == HOPU_WIND_STAGE) {
       enqueue_v2l(c, in[s], c->d_uL);
-      Combine plain;
-      hopu_status r = enqueue_stage_apply(c, c->d_uL, c->d_uL, c->l, nullptr, nullptr, plain, c->d_yL);
+      hopu_status r = enqueue_stage_fused(c, st[s], out[s]);
       if (r != HOPU_OK) return r;
-      enqueue_l2v(c, c->d_yL, false, st[s], out[s]);
     } else {
       hopu_status r = enqueue_stage_apply(c, in[s], c->d_wfz, c->l, nullptr, nullptr, st[s], out[s]);
       if (r != HOPU_OK) return r;
@@ -395,7 +451,7 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   unsigned char* tb = static_cast<unsigned char*>(c->d_tabs);
   const void** slots[kNumTables] = {&c->dt.Bt,   &c->dt.Wq,  &c->dt.Dm,    &c->dt.TrM,
                                     &c->dt.TrP,  &c->dt.Psi, &c->dt.WPsi,  &c->dt.Wf,
-                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv};
+                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow};
   for (int i = 0; i < kNumTables; ++i) *slots[i] = tb + offs[i];
 
   // scratch
@@ -411,6 +467,8 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   HOPU_CUDA(c, cudaMalloc(&c->d_s2, ts * nstate));
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_diss, sizeof(double) * NF));
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_red, sizeof(double) * (c->red_blocks + 8)));
+  HOPU_CUDA(c, cudaMalloc((void**)&c->d_elog_pos, sizeof(int64_t)));
+  HOPU_CUDA(c, cudaMemset(c->d_elog_pos, 0, sizeof(int64_t)));
   return HOPU_OK;
 }
 }  // namespace
@@ -614,6 +672,20 @@ hopu_status hopu_interpolate(hopu_ctx* c, const double* fvals, const double* vva
   else convert<float>(h, buf, 0);
   HOPU_CUDA(c, cudaMemcpyAsync(u_hdiv, buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
   HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOPU_OK;
+}
+
+hopu_status hopu_set_energy_log(hopu_ctx* c, double* dev_log, int64_t capacity) {
+  HOPU_PRECHECK(c);
+  if ((dev_log == nullptr) != (capacity == 0) || capacity < 0)
+    return fail(c, HOPU_EINVAL, "set_energy_log: log and capacity must be both set or both empty");
+  if (c->gexec) {  // the captured substep changes
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->elog = dev_log;
+  c->elog_cap = capacity;
+  HOPU_CUDA(c, cudaMemsetAsync(c->d_elog_pos, 0, sizeof(int64_t), c->stream));
   return HOPU_OK;
 }
 

@@ -43,6 +43,11 @@ struct hopu_ctx {
   double* d_diss = nullptr; // [NF]
   double* d_red = nullptr;  // partial sums + 4 scalars
   bool have_frozen = false;
+  // per-substep kinetic-energy log (device ring buffer owned by the caller)
+  double* elog = nullptr;
+  int64_t elog_cap = 0;
+  int64_t elog_next = 0;     // host-side counter of logged substeps
+  int64_t* d_elog_pos = nullptr;  // device-side counter (graph replays advance it)
   // cached CUDA graph of one substep
   cudaGraphExec_t gexec = nullptr;
   void* g_state = nullptr;

@@ -33,6 +33,8 @@ struct DevTabs {
   const void* DinvT = nullptr;  // [nloc][nlp]     DinvT[s][r] = Dinv[r][s]  (nlp = nloc rounded up to 4)
   const void* DT = nullptr;     // [nloc][nlp]     DT[s][r]    = D[r][s]
   const void* Dinv = nullptr;   // [nloc][nlp]     Dinv[s][r]
+  const void* Drow = nullptr;   // [nloc][nlr]     D[r][s] row-major, rows padded to nlr (an odd
+                                //                 multiple of 16 bytes), zero padding
 };
 
 // out = a0*x0 + a1*x1 + a2*v  (x0 / x1 may be null; out may alias x0 or x1)
@@ -63,6 +65,13 @@ class Ops {
   // volume term + facet lift + inverse mass, combined into out.  wL == uL means w = u.
   virtual int volume(const DevMesh&, const DevTabs&, const void* uL, const void* wL,
                      const void* gam, Combine c, void* out, cudaStream_t) = 0;
+  // volume kernel with the element part of R E^{-1} fused into its epilogue (w = u
+  // only): writes the combined interior V_h dofs into outV and the local facet
+  // functionals into lf.  Returns 0 (nothing launched) when this family has no fused
+  // variant; the caller then runs volume + l2v_elem.
+  virtual int volume_l2v(const DevMesh&, const DevTabs&, const void* uL, const void* gam, void* lf,
+                         Combine c, void* outV, cudaStream_t) = 0;
+  virtual bool has_fused() const = 0;
   // R E^{-1} (dual = false) or E^T (dual = true), combined into outV, in two launches:
   // the element part writes interior dofs and the local facet functionals lf
   // [E][d+1][nf]; the facet part averages (or sums) the two copies into the facet dofs.

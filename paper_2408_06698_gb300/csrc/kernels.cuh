@@ -641,18 +641,28 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
 // the only per-point table is phi_i(q).  Every per-element input (coefficients, the
 // element's signed facet moments, geometry) is one contiguous record; a warp prefetches
 // the next element's records with cp.async while it computes the current one.
-template <int D, int K, typename T, bool WSEP, bool STAB>
+template <int D, int K, typename T>
+struct FuseCfg {  // row-major D table (local functionals) staged for the fused back-projection
+  using S = Shape<D, K>;
+  static constexpr int NLR = row_stride<T>(S::nloc);
+  static constexpr int TAB = S::nloc * NLR;
+  static constexpr bool OK = size_t(TAB) * sizeof(T) <= 40 * 1024;
+};
+
+template <int D, int K, typename T, bool WSEP, bool STAB, bool FUSE>
 __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(DevMesh m, DevTabs tb, const T* __restrict__ uL,
                                                            const T* __restrict__ wL, const T* __restrict__ gam,
-                                                           T* out, Combine cmb) {
+                                                           T* out, Combine cmb, T* __restrict__ lf) {
   using S = Shape<D, K>;
   constexpr int NB = S::nb, NB1 = cnbasis(D, K - 1), NF = S::nf, NL = S::nloc, NQ = S::nq;
   constexpr int NVP = S::nvp, CPL = NVP / 32, GEO = S::gt;
   constexpr int NBP = r4i(NB), NB1P = r4i(NB1);
   constexpr int NBQ = row_stride<T>(NB);
   constexpr int BT = NQ * NBQ, DM = D * NB1 * NB, TRM = (D + 1) * NF * NB;
-  constexpr int TABN = r4i(BT + NQ + DM + TRM);
+  constexpr int FT = FUSE ? FuseCfg<D, K, T>::TAB : 0, NLR = FuseCfg<D, K, T>::NLR;
+  constexpr int TABN = r4i(BT + NQ + DM + TRM) + r4i(FT);
   constexpr int NG = (D + 1) * NF * D;
+  static_assert(!FUSE || (STAB && FuseCfg<D, K, T>::OK), "fused back-projection needs staged tables");
   // per-warp layout: two staging buffers (u record, w record, facet moments, geometry),
   // then the working arrays
   constexpr int STU = r4i(NL), STG = r4i(NG), STGEO = r4i(GEO);
@@ -675,6 +685,11 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     Dm = sbase + BT + NQ;
     TrM = sbase + BT + NQ + DM;
     sw = sbase + TABN;
+  }
+  T* Drow = sbase + r4i(BT + NQ + DM + TRM);  // [NL][NLR] row-major D (FUSE)
+  if (FUSE) {
+    const T* Dg = static_cast<const T*>(tb.Drow);
+    for (int t = threadIdx.x; t < FT; t += blockDim.x) Drow[t] = Dg[t];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -781,15 +796,53 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
       }
     }
     reduce_scatter<NVP>(acc, lane);
+    if (!FUSE) {
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      const int idx = lane * CPL + j;
-      if (idx < NL) {
-        const int a = idx / NB, i = idx - a * NB;
-        T r = acc[j];
+      for (int j = 0; j < CPL; ++j) {
+        const int idx = lane * CPL + j;
+        if (idx < NL) {
+          const int a = idx / NB, i = idx - a * NB;
+          T r = acc[j];
 #pragma unroll 4
-        for (int fm = 0; fm < (D + 1) * NF; ++fm) r = fma(TrM[fm * NB + i], gl[fm * D + a], r);
-        out[e * NL + idx] = combine_at<T>(cmb, r * invabs, e * NL + idx);
+          for (int fm = 0; fm < (D + 1) * NF; ++fm) r = fma(TrM[fm * NB + i], gl[fm * D + a], r);
+          out[e * NL + idx] = combine_at<T>(cmb, r * invabs, e * NL + idx);
+        }
+      }
+    } else {
+      // fused a7 (element part): y -> chat = det J Jinv y -> ell = D chat; interior rows
+      // combined into the V_h output, facet rows to lf with the sign sigma
+      T* sY = sC;  // [D][NBP], u coefficients are no longer needed
+      T* sCh = sG; // [NL (padded to 4)]
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int idx = lane * CPL + j;
+        if (idx < NL) {
+          const int a = idx / NB, i = idx - a * NB;
+          T r = acc[j];
+#pragma unroll 4
+          for (int fm = 0; fm < (D + 1) * NF; ++fm) r = fma(TrM[fm * NB + i], gl[fm * D + a], r);
+          sY[a * NBP + i] = r * invabs;
+        }
+      }
+      __syncwarp();
+      for (int idx = lane; idx < NL; idx += 32) {
+        const int bb = idx / NB, i = idx - bb * NB;
+        T c2 = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) c2 = fma(g[D * D + bb * D + a], sY[a * NBP + i], c2);
+        sCh[idx] = c2;
+      }
+      if (lane < r4i(NL) - NL) sCh[NL + lane] = T(0);
+      __syncwarp();
+      for (int r = lane; r < NL; r += 32) {
+        const T v = dot_ss<r4i(NL)>(Drow + r * NLR, sCh);
+        if (r < (D + 1) * NF) {
+          const int code = m.efc[e * (D + 1) + r / NF];
+          lf[e * (D + 1) * NF + r] = (code & 2) ? -v : v;
+        } else {
+          const int64_t idx = m.NF * NF + e * S::nint + (r - (D + 1) * NF);
+          out[idx] = combine_at<T>(cmb, v, idx);
+        }
       }
     }
     __syncwarp();

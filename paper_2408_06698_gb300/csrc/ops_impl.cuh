@@ -40,6 +40,11 @@ class OpsImpl final : public Ops {
   }
   static constexpr bool kVolumeTab = kVolTab + kWarps * volume_warp(true) <= kLimit;
   static constexpr size_t volume_smem(bool wsep) { return (kVolumeTab ? kVolTab : 0) + kWarps * volume_warp(wsep); }
+  using FC = FuseCfg<D, K, T>;
+  static constexpr size_t kFuseTab = r4(size_t(FC::TAB)) * sz;
+  static constexpr bool kFuse = kVolumeTab && FC::OK && kVolTab + kFuseTab + kWarps * volume_warp(false) <= kLimit;
+  static constexpr size_t kFuseSmem = kVolTab + kFuseTab + kWarps * volume_warp(false);
+  int g_fuse_ = 1;
 
   int nsm_ = 1;
   int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
@@ -74,8 +79,11 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_v2l<D, K, T>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, false, kFacetTab>, facet_smem(false), th, &g_fac_[0])) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, true, kFacetTab>, facet_smem(true), th, &g_fac_[1])) != cudaSuccess) return err;
-    if ((err = setup(k_volume<D, K, T, false, kVolumeTab>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
-    if ((err = setup(k_volume<D, K, T, true, kVolumeTab>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
+    if ((err = setup(k_volume<D, K, T, false, kVolumeTab, false>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
+    if ((err = setup(k_volume<D, K, T, true, kVolumeTab, false>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
+    if constexpr (kFuse) {
+      if ((err = setup(k_volume<D, K, T, false, true, true>, kFuseSmem, th, &g_fuse_)) != cudaSuccess) return err;
+    }
     if ((err = setup(k_l2v_elem<D, K, T, false>, kProjSmem, kProjThreads, &g_elem_[0])) != cudaSuccess) return err;
     if ((err = setup(k_l2v_elem<D, K, T, true>, kProjSmem, kProjThreads, &g_elem_[1])) != cudaSuccess) return err;
     if ((err = setup(k_l2v_facet<D, K, T, false>, 0, 256, &g_fsum_)) != cudaSuccess) return err;
@@ -107,14 +115,29 @@ class OpsImpl final : public Ops {
     const bool wsep = (wL != nullptr && wL != uL);
     const int g = clamp_grid(g_vol_[wsep ? 1 : 0], m.E, kWarps);
     if (wsep)
-      k_volume<D, K, T, true, kVolumeTab><<<g, 32 * kWarps, volume_smem(true), st>>>(
+      k_volume<D, K, T, true, kVolumeTab, false><<<g, 32 * kWarps, volume_smem(true), st>>>(
           m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(gam),
-          static_cast<T*>(out), c);
+          static_cast<T*>(out), c, nullptr);
     else
-      k_volume<D, K, T, false, kVolumeTab><<<g, 32 * kWarps, volume_smem(false), st>>>(
+      k_volume<D, K, T, false, kVolumeTab, false><<<g, 32 * kWarps, volume_smem(false), st>>>(
           m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
-          static_cast<T*>(out), c);
+          static_cast<T*>(out), c, nullptr);
     return 1;
+  }
+
+  bool has_fused() const override { return kFuse; }
+
+  int volume_l2v(const DevMesh& m, const DevTabs& t, const void* uL, const void* gam, void* lf, Combine c,
+                 void* outV, cudaStream_t st) override {
+    if constexpr (kFuse) {
+      const int g = clamp_grid(g_fuse_, m.E, kWarps);
+      k_volume<D, K, T, false, true, true><<<g, 32 * kWarps, kFuseSmem, st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
+          static_cast<T*>(outV), c, static_cast<T*>(lf));
+      return 1;
+    } else {
+      return 0;
+    }
   }
 
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,

@@ -105,6 +105,19 @@ class Hopu:
         self._check(self.lib.hopu_set_frozen_wind(self.ctx, self._vec(w_hdiv, self.n_hdiv, "w_hdiv")),
                     "hopu_set_frozen_wind")
 
+    def set_energy_log(self, log: torch.Tensor | None):
+        """Log 1/2 int |u|^2 at the start of every later substep into a float64 device tensor."""
+        if log is None:
+            self._check(self.lib.hopu_set_energy_log(self.ctx, None, 0), "hopu_set_energy_log")
+            self._elog = None
+            return
+        if log.dtype != torch.float64 or log.device != self.device or not log.is_contiguous():
+            raise ValueError("energy log must be a contiguous float64 tensor on the context's device")
+        self._sync_stream()
+        self._check(self.lib.hopu_set_energy_log(self.ctx, c_void_p(log.data_ptr()), log.numel()),
+                    "hopu_set_energy_log")
+        self._elog = log
+
     def rk_substep(self, state: torch.Tensor, dt: float, n_substeps: int = 1) -> torch.Tensor:
         n = self.n_hdiv if self.wind == "stage" else self.n_l2
         self._sync_stream()
@@ -170,7 +183,8 @@ class Hopu:
 
     # substep launch counts (kernels per call), for the bench's launch accounting
     def launches_per_substep(self) -> int:
-        return 15 if self.wind == "stage" else 6
+        n = 15 if self.wind == "stage" else 6
+        return n + (2 if getattr(self, "_elog", None) is not None else 0)
 
 
 def selftest(dim: int, k: int):

@@ -139,6 +139,30 @@ def test_rk_substep_stage(dim, n, k, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_energy_log_records_every_substep(prec):
+    """a8 inside the substep graph: E(u^n) at the start of each substep, on the device."""
+    dim, n, k = 3, 3, 3
+    g, sp = _mk(dim, n, k, prec, l=k - 1)
+    uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
+    log = torch.zeros(6, dtype=torch.float64, device=g.device)
+    stream = torch.cuda.Stream(device=g.device)
+    with torch.cuda.stream(stream):
+        s = _dev(g, uV)
+        g.set_energy_log(log)
+        g.rk_substep(s, 1e-2, 1)          # direct launch of the first capture
+        g.rk_substep(s, 1e-2, 3)          # graph replays
+        g.set_energy_log(None)
+    stream.synchronize()
+    got = log.cpu().numpy()
+    u = uV.copy()
+    for i in range(4):
+        ref = C.kinetic_energy(sp.topo, sp.to_l2(u))
+        assert abs(got[i] - ref) < (1e-13 if prec == "f64" else 3e-7) * ref, (i, got[i], ref)
+        u = rk.substeps_stage(sp, u, 1e-2, 1, k - 1)
+    assert got[4] == 0.0 and got[5] == 0.0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_rk_substep_frozen(prec):
     dim, n, k = 3, 3, 3
     g, sp = _mk(dim, n, k, prec, l=k - 1, wind="frozen")
