@@ -179,6 +179,48 @@ hopu_status hopu_points(hopu_ctx* ctx, int which, double* host_out, int64_t* cou
 hopu_status hopu_interpolate(hopu_ctx* ctx, const double* fvals, const double* vvals,
                              void* u_hdiv);
 
+/* ------------------------------------------------------------------ batches of meshes
+ * Many independent meshes of uneven size and order k advanced together.  The meshes of
+ * one order are merged into one context (their disjoint union: no facet is shared
+ * across meshes), so each kernel family runs once per order class and a substep of the
+ * whole batch is one CUDA-graph replay.  Inside a class vector every mesh owns
+ * contiguous ranges: its facet dofs, its interior dofs (V_h) and its element blocks
+ * (L2); hopu_batch_layout gives the offsets, so per-mesh views need no copies.        */
+typedef struct hopu_batch hopu_batch;
+
+/* meshes[i] with order k[i] (1..5 in 3D, 1..4 in 2D; one dimension for the whole
+ * batch).  opts->k is ignored; opts->l >= -1 is used as min(l, k_i); opts->l < -1 means
+ * l = k_i + 1 + opts->l per mesh (-2: k_i - 1).  prec and wind_mode apply to all.      */
+hopu_status hopu_batch_create(const hopu_mesh_desc* meshes, const int* k, int n_meshes,
+                              const hopu_options* opts, void* cuda_stream, hopu_batch** out);
+hopu_status hopu_batch_destroy(hopu_batch* batch);
+
+/* Number of order classes; per class (arrays of n_classes entries, each may be NULL)
+ * its order, V_h length and L2 length.                                                */
+hopu_status hopu_batch_classes(const hopu_batch* batch, int* n_classes, int* class_k,
+                               int64_t* class_n_hdiv, int64_t* class_n_l2);
+
+/* The context of class c (owned by the batch: do not destroy it); hopu_points,
+ * hopu_interpolate, hopu_project, hopu_energy, ... act on the merged class mesh.       */
+hopu_status hopu_batch_context(hopu_batch* batch, int c, hopu_ctx** ctx);
+
+/* Where mesh i lives: its class, and offset/length of its facet dofs, interior dofs
+ * (both inside the class V_h vector) and L2 coefficients (inside the class L2 vector).
+ * out7 = {class, facet_off, facet_len, interior_off, interior_len, l2_off, l2_len}.   */
+hopu_status hopu_batch_layout(const hopu_batch* batch, int mesh, int64_t* out7);
+
+/* n_substeps SSP-RK3 substeps of every mesh: class_states[c] is the state vector of
+ * class c (V_h for STAGE wind, L2 for FROZEN; FROZEN winds are set per class context
+ * with hopu_set_frozen_wind).  The substeps of all classes are captured once per
+ * (states, dt) as one CUDA graph and replayed (direct launches on the legacy default
+ * stream).                                                                            */
+hopu_status hopu_batch_rk_substep(hopu_batch* batch, void* const* class_states, double dt,
+                                  int n_substeps);
+
+/* Text of the batch's first error, else of the first failing class context ("" when
+ * none).  With batch == NULL: the last failed hopu_batch_create on this thread.        */
+const char* hopu_batch_last_error(const hopu_batch* batch);
+
 /* Text of the sticky error ("" when none).  Valid until the next call on ctx.
  * With ctx == NULL: the text of the last failed hopu_create on this thread.          */
 const char* hopu_last_error(const hopu_ctx* ctx);

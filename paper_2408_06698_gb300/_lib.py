@@ -53,6 +53,13 @@ SIGNATURES = {
     "hopu_clear_error": (c_int, [c_void_p]),
     "hopu_selftest": (c_int, [c_int, c_int, POINTER(c_double)]),
     "hopu_profile": (c_int, [c_void_p, c_int]),
+    "hopu_batch_create": (c_int, [c_void_p, c_void_p, c_int, POINTER(Options), c_void_p, POINTER(c_void_p)]),
+    "hopu_batch_destroy": (c_int, [c_void_p]),
+    "hopu_batch_classes": (c_int, [c_void_p, POINTER(c_int), c_void_p, c_void_p, c_void_p]),
+    "hopu_batch_context": (c_int, [c_void_p, c_int, POINTER(c_void_p)]),
+    "hopu_batch_layout": (c_int, [c_void_p, c_int, c_void_p]),
+    "hopu_batch_rk_substep": (c_int, [c_void_p, c_void_p, c_double, c_int]),
+    "hopu_batch_last_error": (c_char_p, [c_void_p]),
     "hopu_apply_convection_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -729,6 +731,194 @@ hopu_status hopu_profile_read(hopu_ctx* c, double* ms, int64_t* launches) {
   c->prof_direct.clear();
   c->graph_replayed = false;
   return HOPU_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+struct hopu_batch {
+  int dim = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<hopu_ctx*> cls;          // one merged context per order class
+  std::vector<int> cls_k;
+  std::vector<std::array<int64_t, 7>> layout;  // per mesh
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<void*> g_states;
+  double g_dt = 0.0;
+  std::string err;
+};
+
+namespace {
+hopu_status batch_fail(hopu_batch* b, int code, const std::string& msg) {
+  if (b && b->err.empty()) b->err = msg;
+  return (hopu_status)code;
+}
+}  // namespace
+
+extern "C" {
+
+hopu_status hopu_batch_destroy(hopu_batch* b) {
+  if (!b) return HOPU_OK;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (hopu_ctx* c : b->cls) hopu_destroy(c);
+  delete b;
+  return HOPU_OK;
+}
+
+hopu_status hopu_batch_create(const hopu_mesh_desc* meshes, const int* k, int n, const hopu_options* opts,
+                              void* cuda_stream, hopu_batch** out) {
+  if (!out) return HOPU_EINVAL;
+  *out = nullptr;
+  if (!meshes || !k || n <= 0 || !opts) return HOPU_EINVAL;
+  const int dim = meshes[0].dim;
+  for (int i = 0; i < n; ++i) {
+    if (meshes[i].dim != dim || !meshes[i].coords || !meshes[i].elem_vertices) return HOPU_EINVAL;
+    if (k[i] < 1 || k[i] > (dim == 2 ? 4 : 5)) return HOPU_ENOTSUP;
+  }
+  hopu_batch* b = new (std::nothrow) hopu_batch();
+  if (!b) return HOPU_ENOMEM;
+  b->dim = dim;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->layout.assign(n, {0, 0, 0, 0, 0, 0, 0});
+  std::vector<int> ks(k, k + n);
+  std::sort(ks.begin(), ks.end());
+  ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+  for (int kk : ks) {
+    // disjoint union of the meshes of order kk: vertex and representative ids offset
+    std::vector<int> members;
+    for (int i = 0; i < n; ++i)
+      if (k[i] == kk) members.push_back(i);
+    int64_t nv = 0, ne = 0;
+    for (int i : members) {
+      nv += meshes[i].n_vertices;
+      ne += meshes[i].n_elems;
+    }
+    std::vector<double> coords((size_t)nv * dim);
+    std::vector<int64_t> ev((size_t)ne * (dim + 1)), rep((size_t)nv);
+    int64_t vo = 0, eo = 0;
+    std::vector<int64_t> elem_start;
+    for (int i : members) {
+      const hopu_mesh_desc& m = meshes[i];
+      std::memcpy(&coords[(size_t)vo * dim], m.coords, sizeof(double) * m.n_vertices * dim);
+      for (int64_t v = 0; v < m.n_vertices; ++v) rep[vo + v] = vo + (m.vertex_rep ? m.vertex_rep[v] : v);
+      for (int64_t t = 0; t < m.n_elems * (dim + 1); ++t) ev[(size_t)eo * (dim + 1) + t] = vo + m.elem_vertices[t];
+      elem_start.push_back(eo);
+      vo += m.n_vertices;
+      eo += m.n_elems;
+    }
+    elem_start.push_back(eo);
+    hopu_mesh_desc md{dim, nv, coords.data(), ne, ev.data(), rep.data()};
+    hopu_options o = *opts;
+    o.k = kk;
+    o.l = opts->l < -1 ? std::max(-1, kk + 1 + opts->l) : std::min(opts->l, kk);
+    hopu_ctx* c = nullptr;
+    hopu_status r = hopu_create(&md, &o, cuda_stream, &c);
+    if (r != HOPU_OK) {
+      const std::string msg = std::string("batch class k=") + std::to_string(kk) + ": " + g_create_error;
+      hopu_batch_destroy(b);
+      g_create_error = msg;
+      return r;
+    }
+    const int cidx = (int)b->cls.size();
+    b->cls.push_back(c);
+    b->cls_k.push_back(kk);
+    // per-mesh ranges: facets of a mesh are contiguous (sorted by offset representative ids)
+    const int64_t NF = c->topo.n_facets;
+    std::vector<int64_t> fcount(members.size(), 0);
+    std::vector<int64_t> fmin(members.size(), INT64_MAX);
+    for (int64_t F = 0; F < NF; ++F) {
+      const int64_t e = c->topo.fa[F] >> 2;
+      const size_t mi = std::upper_bound(elem_start.begin(), elem_start.end(), e) - elem_start.begin() - 1;
+      fcount[mi] += 1;
+      fmin[mi] = std::min(fmin[mi], F);
+    }
+    for (size_t j = 0; j < members.size(); ++j) {
+      const int64_t e0 = elem_start[j], e1 = elem_start[j + 1];
+      b->layout[members[j]] = {cidx, fmin[j] * c->ref.nf, fcount[j] * c->ref.nf,
+                               NF * c->ref.nf + e0 * c->ref.nint, (e1 - e0) * c->ref.nint,
+                               e0 * c->ref.nloc, (e1 - e0) * c->ref.nloc};
+    }
+  }
+  *out = b;
+  return HOPU_OK;
+}
+
+hopu_status hopu_batch_classes(const hopu_batch* b, int* n_classes, int* class_k, int64_t* class_n_hdiv,
+                               int64_t* class_n_l2) {
+  if (!b) return HOPU_EINVAL;
+  if (n_classes) *n_classes = (int)b->cls.size();
+  for (size_t c = 0; c < b->cls.size(); ++c) {
+    if (class_k) class_k[c] = b->cls_k[c];
+    if (class_n_hdiv) class_n_hdiv[c] = b->cls[c]->n_hdiv;
+    if (class_n_l2) class_n_l2[c] = b->cls[c]->n_l2;
+  }
+  return HOPU_OK;
+}
+
+hopu_status hopu_batch_context(hopu_batch* b, int c, hopu_ctx** ctx) {
+  if (!b || !ctx || c < 0 || c >= (int)b->cls.size()) return HOPU_EINVAL;
+  *ctx = b->cls[c];
+  return HOPU_OK;
+}
+
+hopu_status hopu_batch_layout(const hopu_batch* b, int mesh, int64_t* out7) {
+  if (!b || !out7 || mesh < 0 || mesh >= (int)b->layout.size()) return HOPU_EINVAL;
+  for (int i = 0; i < 7; ++i) out7[i] = b->layout[mesh][i];
+  return HOPU_OK;
+}
+
+hopu_status hopu_batch_rk_substep(hopu_batch* b, void* const* states, double dt, int n_substeps) {
+  if (!b || !states || n_substeps < 0 || !std::isfinite(dt)) return HOPU_EINVAL;
+  for (size_t c = 0; c < b->cls.size(); ++c) {
+    if (!states[c] || !aligned16(states[c])) return batch_fail(b, HOPU_EINVAL, "batch_rk_substep: bad state pointer");
+    if (b->cls[c]->status != HOPU_OK) return (hopu_status)b->cls[c]->status;
+    b->cls[c]->stream = b->stream;
+  }
+  if (n_substeps == 0) return HOPU_OK;
+  if (b->stream == nullptr) {  // legacy default stream cannot be captured
+    for (int s = 0; s < n_substeps; ++s)
+      for (size_t c = 0; c < b->cls.size(); ++c) {
+        hopu_status r = enqueue_substep(b->cls[c], states[c], dt);
+        if (r != HOPU_OK) return r;
+      }
+    return HOPU_OK;
+  }
+  std::vector<void*> key(states, states + b->cls.size());
+  if (!b->gexec || b->g_states != key || b->g_dt != dt) {
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, HOPU_ECUDA, cudaGetErrorString(e));
+    hopu_status r = HOPU_OK;
+    for (size_t c = 0; c < b->cls.size() && r == HOPU_OK; ++c) r = enqueue_substep(b->cls[c], states[c], dt);
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (r != HOPU_OK) return r;
+    if (e != cudaSuccess) return batch_fail(b, HOPU_ECUDA, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->gexec = nullptr;
+      return batch_fail(b, HOPU_ECUDA, cudaGetErrorString(e));
+    }
+    b->g_states = key;
+    b->g_dt = dt;
+  }
+  for (int s = 0; s < n_substeps; ++s) {
+    cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, HOPU_ECUDA, cudaGetErrorString(e));
+  }
+  return HOPU_OK;
+}
+
+const char* hopu_batch_last_error(const hopu_batch* b) {
+  if (!b) return g_create_error.c_str();
+  if (!b->err.empty()) return b->err.c_str();
+  for (const hopu_ctx* c : b->cls)
+    if (c->status != HOPU_OK) return c->err.c_str();
+  return "";
 }
 
 const char* hopu_last_error(const hopu_ctx* c) {

@@ -187,6 +187,110 @@ class Hopu:
         return n + (2 if getattr(self, "_elog", None) is not None else 0)
 
 
+class _ClassView(Hopu):
+    """A non-owning Hopu view of one order class of a batch (the batch owns the context)."""
+
+    def __init__(self, batch: "HopuBatch", ctx: c_void_p, k: int, n_hdiv: int, n_l2: int):
+        self.lib = batch.lib
+        self.device, self.dtype, self.prec = batch.device, batch.dtype, batch.prec
+        self.k, self.l, self.wind, self.dim = k, None, batch.wind, batch.dim
+        self.ctx = ctx
+        self.n_hdiv, self.n_l2 = n_hdiv, n_l2
+        nh, nl, nf = c_int64(), c_int64(), c_int64()
+        self.lib.hopu_sizes(self.ctx, byref(nh), byref(nl), byref(nf))
+        self.n_facets = nf.value
+        self.n_elems = n_l2 // (self.dim * _nbasis(self.dim, k))
+
+    def close(self):  # owned by the batch
+        self.ctx = c_void_p()
+
+
+def _nbasis(d, k):
+    from math import comb
+    return comb(k + d, d)
+
+
+class HopuBatch:
+    """Many meshes of uneven size and order, advanced together (mirrors hopu_batch)."""
+
+    def __init__(self, meshes, ks, l: int = -2, prec: str = "f32", wind: str = "stage",
+                 device: str | torch.device = "cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhopu needs a CUDA device")
+        self.lib = L.load()
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float64 if prec == "f64" else torch.float32
+        self.prec, self.wind = prec, wind
+        self._keep = []
+        descs = (L.MeshDesc * len(meshes))()
+        for i, (coords, elems, rep) in enumerate(meshes):
+            c = np.ascontiguousarray(coords, dtype=np.float64)
+            e = np.ascontiguousarray(elems, dtype=np.int64)
+            r = None if rep is None else np.ascontiguousarray(rep, dtype=np.int64)
+            self._keep += [c, e, r]
+            descs[i] = L.MeshDesc(c.shape[1], c.shape[0], c.ctypes.data, e.shape[0], e.ctypes.data,
+                                  None if r is None else r.ctypes.data)
+        self.dim = int(descs[0].dim)
+        karr = (ctypes.c_int * len(ks))(*[int(x) for x in ks])
+        opts = L.Options(0, l, _PREC[prec], _WIND[wind], 0)
+        self.b = c_void_p()
+        self.stream = torch.cuda.Stream(device=self.device)
+        with torch.cuda.device(self.device):
+            st = self.lib.hopu_batch_create(descs, karr, len(meshes), byref(opts), c_void_p(self.stream.cuda_stream),
+                                            byref(self.b))
+        if st != L.HOPU_OK:
+            raise L.HopuError(st, "hopu_batch_create", self.lib.hopu_batch_last_error(None).decode())
+        nc = ctypes.c_int()
+        self.lib.hopu_batch_classes(self.b, byref(nc), None, None, None)
+        n = nc.value
+        ck, nh, nl = (ctypes.c_int * n)(), (c_int64 * n)(), (c_int64 * n)()
+        self.lib.hopu_batch_classes(self.b, byref(nc), ck, nh, nl)
+        self.classes = []
+        for c in range(n):
+            ctx = c_void_p()
+            self.lib.hopu_batch_context(self.b, c, byref(ctx))
+            self.classes.append(_ClassView(self, ctx, ck[c], nh[c], nl[c]))
+        self.layout = []
+        for i in range(len(meshes)):
+            o = (c_int64 * 7)()
+            self.lib.hopu_batch_layout(self.b, i, o)
+            self.layout.append(tuple(int(x) for x in o))
+
+    def mesh_views(self, i: int, class_state: torch.Tensor, space: str = "hdiv"):
+        """(facet dofs, interior dofs) views of mesh i in a V_h class vector, or its L2 block."""
+        c, fo, fl, io, il, lo, ll = self.layout[i]
+        if space == "hdiv":
+            return class_state[fo:fo + fl], class_state[io:io + il]
+        return class_state[lo:lo + ll]
+
+    def rk_substep(self, class_states, dt: float, n_substeps: int = 1):
+        ptrs = (c_void_p * len(self.classes))()
+        for c, (v, t) in enumerate(zip(self.classes, class_states)):
+            n = v.n_hdiv if self.wind == "stage" else v.n_l2
+            ptrs[c] = v._vec(t, n, f"class_states[{c}]")
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)             # inputs produced on the caller's stream
+        st = self.lib.hopu_batch_rk_substep(self.b, ptrs, float(dt), int(n_substeps))
+        cur.wait_stream(self.stream)             # results visible on the caller's stream
+        if st != L.HOPU_OK:
+            raise L.HopuError(st, "hopu_batch_rk_substep", self.lib.hopu_batch_last_error(self.b).decode())
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            for v in self.classes:
+                v.close()
+            self.lib.hopu_batch_destroy(self.b)
+            self.b = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def selftest(dim: int, k: int):
     """Host-only check of the library's reference tables (no GPU needed)."""
     lib = L.load()
