@@ -91,6 +91,22 @@ class HDiv:
         fac = acc / cnt[:, None]
         return np.concatenate([fac.reshape(-1), ell[:, (r.dim + 1) * nf:].reshape(-1)])
 
+    # -------------------------------------------------------------- (R E_T^{-1})^T
+    def from_l2_transpose(self, vV: np.ndarray) -> np.ndarray:
+        """Transpose of ``from_l2``: distribute each facet value to its copies with the
+        averaging weight (1/2 on interior facets) and the sign sigma, copy interior
+        values, then apply (D Piola^{-1})^T per element."""
+        t, r = self.topo, self.ref
+        nf = r.nf
+        cnt = np.zeros(t.n_facets)
+        np.add.at(cnt, t.elem_facet.reshape(-1), 1.0)
+        fac = vV[: self.n_facet_dofs].reshape(t.n_facets, nf) / cnt[:, None]
+        loc_f = t.sigma[:, :, None] * fac[t.elem_facet]
+        inter = vV[self.n_facet_dofs:].reshape(t.n_elems, r.nint)
+        ell = np.concatenate([loc_f.reshape(t.n_elems, -1), inter], axis=1)
+        chat = (ell @ self.D).reshape(t.n_elems, r.dim, r.nb)
+        return t.detJ[:, None, None] * np.einsum("eba,ebi->eai", t.Jinv, chat)
+
     # -------------------------------------------------------------- E^T
     def dual(self, rL: np.ndarray) -> np.ndarray:
         t, r = self.topo, self.ref
