@@ -119,8 +119,12 @@ def rollout_loss(space: HDiv, u0V, dt, n, l):
     return C.kinetic_energy(space.topo, space.to_l2(u)), u
 
 
-def rollout_vjp(space: HDiv, u0V, dt, n, l):
-    """(loss, d loss / d u0) by the discrete adjoint of the SSP-RK3 substeps."""
+def rollout_vjp(space: HDiv, u0V, dt, n, l, seed=None):
+    """(loss, d loss / d u0) by the discrete adjoint of the SSP-RK3 substeps.
+
+    With ``seed`` (a V_h cotangent of u_n) the adjoint starts from it instead of the
+    gradient of the loss, and the result is the cotangent of u0 (the loss is still
+    returned)."""
     states = []
     u = u0V.copy()
     for _ in range(n):
@@ -130,7 +134,7 @@ def rollout_vjp(space: HDiv, u0V, dt, n, l):
         u = u / 3.0 + 2.0 / 3.0 * (u2 - dt * _stage_rhs(space, u2, l))
     uL = space.to_l2(u)
     loss = C.kinetic_energy(space.topo, uL)
-    ubar = space.dual(space.topo.absdet[:, None, None] * uL)  # E^T M u_L
+    ubar = space.dual(space.topo.absdet[:, None, None] * uL) if seed is None else np.array(seed, dtype=float)
     for (u0, u1, u2) in reversed(states):
         b2 = 2.0 / 3.0 * (ubar - dt * _rhs_vjp(space, u2, ubar, l))
         b1 = 0.25 * (b2 - dt * _rhs_vjp(space, u1, b2, l))

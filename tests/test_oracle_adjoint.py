@@ -71,3 +71,17 @@ def test_rollout_adjoint_matches_finite_differences():
         h = 1e-5
         fd = (A.rollout_loss(sp, u0 + h * d, dt, n, 1)[0] - A.rollout_loss(sp, u0 - h * d, dt, n, 1)[0]) / (2 * h)
         assert abs(fd - np.dot(g, d)) < 1e-7 * max(abs(fd), np.abs(g).max())
+
+
+def test_seeded_rollout_adjoint_matches_finite_differences():
+    """With a cotangent seed s of u_n, the result g satisfies <s, (d u_n / d u0) d> = <g, d>
+    (the Jacobian-vector product by central differences of the rollout's final state)."""
+    sp = _space(3, 3, 2)
+    u0 = sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-2, 24)
+    dt, n = 2e-2, 3
+    s = np.random.default_rng(25).standard_normal(sp.n_hdiv)
+    _, g = A.rollout_vjp(sp, u0, dt, n, 1, seed=s)
+    for d in W.normal_vectors(3, sp.n_hdiv, seed=2):
+        h = 1e-5
+        jd = (A.rollout_loss(sp, u0 + h * d, dt, n, 1)[1] - A.rollout_loss(sp, u0 - h * d, dt, n, 1)[1]) / (2 * h)
+        assert abs(np.dot(s, jd) - np.dot(g, d)) < 1e-7 * np.linalg.norm(s) * max(np.linalg.norm(jd), 1.0)
