@@ -75,7 +75,13 @@ typedef enum {
   HOPU_ENOTSUP = -6   /* valid request this build does not support (e.g. boundary)  */
 } hopu_status;
 
-typedef enum { HOPU_FP64 = 0, HOPU_FP32 = 1 } hopu_prec;
+typedef enum {
+  HOPU_FP64 = 0,     /* FP64 coefficients and arithmetic                                     */
+  HOPU_FP32 = 1,     /* FP32 coefficients, FP32 FMA arithmetic                               */
+  HOPU_FP32_TC = 2,  /* FP32 coefficients; the batched projection GEMMs on tensor cores in
+                        3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation), FP32 FMA elsewhere */
+  HOPU_TF32 = 3      /* as HOPU_FP32_TC with one TF32 product (about 1e-3 relative)          */
+} hopu_prec;
 
 typedef enum {
   HOPU_HDIV_TO_L2 = 0,      /* E      : V_h -> L2 (gather, reference change of basis, Piola) */
@@ -121,6 +127,12 @@ hopu_status hopu_destroy(hopu_ctx* ctx);
 /* Replace the stream later calls enqueue on. */
 hopu_status hopu_set_stream(hopu_ctx* ctx, void* cuda_stream);
 
+/* Synchronise the context stream and report device-side failures: ETIMEOUT when a
+ * tensor-core kernel (HOPU_FP32_TC / HOPU_TF32) gave up waiting for its MMAs (its
+ * output is then incomplete).  hopu_energy performs the same check.  No paper
+ * counterpart: error reporting of the asynchronous calls.                             */
+hopu_status hopu_sync(hopu_ctx* ctx);
+
 /* Sizes of the coefficient vectors: V_h length, L2 length (n_elems*dim*nb), facets. */
 hopu_status hopu_sizes(const hopu_ctx* ctx, int64_t* n_hdiv, int64_t* n_l2, int64_t* n_facets);
 
@@ -165,6 +177,33 @@ hopu_status hopu_set_frozen_wind(hopu_ctx* ctx, const void* w_hdiv);
  *   host_out[2] = sum_F int 1/2 |w.n| |(I-Pi^l)[[u]]|^2     (facet dissipation; 0 if NULL)
  * For divergence-free normal-continuous w, host_out[1] == host_out[2] >= 0.            */
 hopu_status hopu_energy(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, double* host_out);
+
+/* Reverse-mode derivative (vector-Jacobian product) of y = hopu_apply_convection(w, u)
+ * with the context's l.  The apply is linear in u and, on facets, depends on w through
+ * w.n and |w.n| (Section 3.2, eq. "hopudefinition", conservative form); with
+ * z = M^{-1} ybar:
+ *   ubar_l2   = c(w; phi_j, z) for every L2 basis function phi_j (the transposed form);
+ *   wbar_hdiv = E^T of d/dw c(w; u, z) tested with phi_j (E: V_h -> L2 of HOPU_HDIV_TO_L2),
+ *               with d|s|/ds taken as 0 at s = w.n = 0.
+ * Either output may be NULL (not both); outputs may not alias inputs or each other.
+ * Layouts and working precision as hopu_apply_convection; asynchronous on the stream.  */
+hopu_status hopu_vjp_apply(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, const void* ybar_l2,
+                           void* wbar_hdiv, void* ubar_l2);
+
+/* Gradient through n_substeps STAGE SSP-RK3 substeps (hopu_rk_substep) started at u0_hdiv
+ * (not modified), by the discrete adjoint of the Shu-Osher stages:
+ *   b2 = 2/3 (ubar - dt J(u2)^T ubar),  b1 = 1/4 (b2 - dt J(u1)^T b2),
+ *   ubar <- 1/3 ubar + 3/4 b2 + b1 - dt J(u)^T b1,
+ * where J is the Jacobian of the STAGE right-hand side u -> R E^{-1} y(Eu, Eu).
+ * loss != NULL: the seed is the gradient of loss = 1/2 int |E u_N|^2 (FP64, written to
+ * *loss, the call then synchronises the stream) and u0bar_hdiv receives d loss / d u0.
+ * loss == NULL: u0bar_hdiv holds on entry the cotangent of u_N and on return that of u0.
+ * States are checkpointed every ckpt_every substeps (>= 1) and each segment is recomputed
+ * once, so device memory of (n_substeps/ckpt_every + 3 ckpt_every + 3) V_h vectors is
+ * allocated by the call and kept by the context.  STAGE wind only (ENOTSUP otherwise);
+ * not capturable into a CUDA graph; no energy-log entries are written.               */
+hopu_status hopu_vjp_rollout(hopu_ctx* ctx, const void* u0_hdiv, double dt, int n_substeps,
+                             int ckpt_every, void* u0bar_hdiv, double* loss);
 
 /* Physical quadrature points (host output, FP64):
  *   which = 0: facet points [n_facets][nqf][dim], taken from side A;
@@ -235,7 +274,9 @@ typedef enum {
   HOPU_K_VOLUME = 2,     /* volume term + facet lift + inverse mass (+ RK combination) */
   HOPU_K_L2V_ELEM = 3,   /* L2 -> V_h, element-local functionals                       */
   HOPU_K_L2V_FACET = 4,  /* L2 -> V_h, averaging R of the facet functionals            */
-  HOPU_K_COUNT = 5
+  HOPU_K_FACET_ADJ = 5,  /* VJP: facet moments of the two cotangents                   */
+  HOPU_K_VOLUME_ADJ = 6, /* VJP: volume part + lift of the facet moments               */
+  HOPU_K_COUNT = 7
 } hopu_kernel_family;
 
 /* Profiling: with enable != 0 every later kernel launch of the context is bracketed by

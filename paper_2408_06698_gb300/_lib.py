@@ -14,10 +14,10 @@ LIB_PATH = os.path.join(PKG, "libhopu.so")
 
 HOPU_OK, HOPU_EINVAL, HOPU_ENOMEM, HOPU_ECUDA, HOPU_EMESH, HOPU_ETIMEOUT, HOPU_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EMESH", -5: "ETIMEOUT", -6: "ENOTSUP"}
-HOPU_FP64, HOPU_FP32 = 0, 1
+HOPU_FP64, HOPU_FP32, HOPU_FP32_TC, HOPU_TF32 = 0, 1, 2, 3
 HOPU_HDIV_TO_L2, HOPU_L2_TO_HDIV, HOPU_L2_TO_HDIV_DUAL = 0, 1, 2
 HOPU_WIND_STAGE, HOPU_WIND_FROZEN = 0, 1
-KERNEL_FAMILIES = ["v2l", "facet", "volume", "l2v_elem", "l2v_facet"]
+KERNEL_FAMILIES = ["v2l", "facet", "volume", "l2v_elem", "l2v_facet", "facet_adj", "volume_adj"]
 
 
 class MeshDesc(Structure):
@@ -62,6 +62,9 @@ SIGNATURES = {
     "hopu_batch_last_error": (c_char_p, [c_void_p]),
     "hopu_apply_convection_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
+    "hopu_sync": (c_int, [c_void_p]),
+    "hopu_vjp_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hopu_vjp_rollout": (c_int, [c_void_p, c_void_p, c_double, c_int, c_int, c_void_p, POINTER(c_double)]),
 }
 
 _lib = None

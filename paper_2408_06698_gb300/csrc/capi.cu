@@ -20,33 +20,33 @@
 #include "reftables.h"
 
 namespace hopu {
-Ops* make_ops_2_1(bool);
-Ops* make_ops_2_2(bool);
-Ops* make_ops_2_3(bool);
-Ops* make_ops_2_4(bool);
-Ops* make_ops_3_1(bool);
-Ops* make_ops_3_2(bool);
-Ops* make_ops_3_3(bool);
-Ops* make_ops_3_4(bool);
-Ops* make_ops_3_5(bool);
+Ops* make_ops_2_1(bool, int);
+Ops* make_ops_2_2(bool, int);
+Ops* make_ops_2_3(bool, int);
+Ops* make_ops_2_4(bool, int);
+Ops* make_ops_3_1(bool, int);
+Ops* make_ops_3_2(bool, int);
+Ops* make_ops_3_3(bool, int);
+Ops* make_ops_3_4(bool, int);
+Ops* make_ops_3_5(bool, int);
 
-Ops* make_ops(int dim, int k, bool fp64) {
+Ops* make_ops(int dim, int k, bool fp64, int tc) {
   if (dim == 2) {
     switch (k) {
-      case 1: return make_ops_2_1(fp64);
-      case 2: return make_ops_2_2(fp64);
-      case 3: return make_ops_2_3(fp64);
-      case 4: return make_ops_2_4(fp64);
+      case 1: return make_ops_2_1(fp64, tc);
+      case 2: return make_ops_2_2(fp64, tc);
+      case 3: return make_ops_2_3(fp64, tc);
+      case 4: return make_ops_2_4(fp64, tc);
       default: return nullptr;
     }
   }
   if (dim == 3) {
     switch (k) {
-      case 1: return make_ops_3_1(fp64);
-      case 2: return make_ops_3_2(fp64);
-      case 3: return make_ops_3_3(fp64);
-      case 4: return make_ops_3_4(fp64);
-      case 5: return make_ops_3_5(fp64);
+      case 1: return make_ops_3_1(fp64, tc);
+      case 2: return make_ops_3_2(fp64, tc);
+      case 3: return make_ops_3_3(fp64, tc);
+      case 4: return make_ops_3_4(fp64, tc);
+      case 5: return make_ops_3_5(fp64, tc);
       default: return nullptr;
     }
   }
@@ -93,6 +93,22 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_log(const double* in, int64
     log[p % cap] = 0.5 * tot;
     *pos = p + 1;
   }
+}
+
+// x = a x + b y (n entries)
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpby(int64_t n, Combine w, T* x, const T* y) {
+  for (int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256)
+    if constexpr (sizeof(T) == 8) x[t] = fma(T(w.a0), x[t], T(w.a2) * y[t]);  // w = {a, x, 0, null, b}
+    else x[t] = fmaf(w.h2, y[t], fmaf(w.h0, x[t], fmaf(w.l2, y[t], w.l0 * x[t])));
+}
+
+// y = M x for an L2 field (M = |det J| I per element): the gradient of 1/2 int |x|^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_mass(int64_t E, int NL, int G, const double* geo, const T* x, T* y) {
+  const int64_t n = E * NL;
+  for (int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256)
+    y[t] = T(geo[(t / NL) * G + G - 1]) * x[t];
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_sum(const double* in, int64_t n, double* out) {
@@ -143,6 +159,18 @@ hopu_status check_launch(hopu_ctx* c, const char* where) {
   return HOPU_OK;
 }
 
+// Read the device error word (the stream must have been synchronised): ETIMEOUT when a
+// tensor-core kernel gave up waiting for its MMAs.
+hopu_status device_status(hopu_ctx* c) {
+  int e = 0;
+  HOPU_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e & 1) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return fail(c, HOPU_ETIMEOUT, "a tensor-core completion wait gave up");
+  }
+  return HOPU_OK;
+}
+
 constexpr int kProfPairs = 64;
 
 // Run launch() on the context stream, bracketed by a pair of timing events when
@@ -175,7 +203,7 @@ void free_all(hopu_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
-                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red};
+                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c->ops;
@@ -190,7 +218,7 @@ void convert(const std::vector<double>& src, std::vector<unsigned char>& dst, si
 }
 
 // Reorder the host FP64 tables into the kernel layouts (see hopu_internal.h).
-constexpr int kNumTables = 12;
+constexpr int kNumTables = 13;
 
 // Row stride of the point-major tables: an odd multiple of 16 bytes (matches
 // row_stride<T> in kernels.cuh).
@@ -216,6 +244,7 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
   auto& DT = out[9];
   auto& Dinv = out[10];
   auto& Drow = out[11];
+  auto& Dn = out[12];
   Bt.assign((size_t)nq * nbq, 0.0);  // point-major [q][nbq]
   for (int q = 0; q < nq; ++q)
     for (int i = 0; i < nb; ++i) Bt[(size_t)q * nbq + i] = R.phi[(size_t)q * nb + i];
@@ -254,6 +283,9 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
       DT[(size_t)s * nlp + r] = R.D[(size_t)r * nl + s];
       Dinv[(size_t)s * nlp + r] = R.Dinv[(size_t)s * nl + r];
     }
+  Dn.assign((size_t)nl * nlp, 0.0);  // Dn[s][r] = D[s][r] (transposed back-projection)
+  for (int r = 0; r < nl; ++r)
+    for (int s = 0; s < nl; ++s) Dn[(size_t)s * nlp + r] = R.D[(size_t)s * nl + r];
   // row-major D with an odd-multiple-of-16-byte row stride (fused back-projection)
   const int nlr = point_row_stride(nl, fp64);
   Drow.assign((size_t)nl * nlr, 0.0);
@@ -337,6 +369,73 @@ hopu_status enqueue_substep(hopu_ctx* c, void* state, double dt) {
   return check_launch(c, "substep kernels");
 }
 
+// ---------------------------------------------------------------- derivatives
+// facet-moment scratch of the wind cotangent (the apply's own d_gam holds the other set)
+hopu_status ensure_gamW(hopu_ctx* c) {
+  if (c->d_gamW) return HOPU_OK;
+  const size_t n = (size_t)c->topo.n_elems * (c->dim + 1) * c->ref.nf * c->dim;
+  HOPU_CUDA(c, cudaMalloc(&c->d_gamW, n * c->tsize));
+  return HOPU_OK;
+}
+
+// VJP of the apply y = M^{-1} c(w; u, .) for the L2 wind wL: facet moments, then volume
+// part + lift.  wL == uL means w = u (ubar then receives ubar + wbar, wbarL unused).
+void enqueue_apply_vjp(hopu_ctx* c, const void* uL, const void* wL, const void* ybar, void* ubar, void* wbarL) {
+  timed(c, HOPU_K_FACET_ADJ, [&] {
+    c->ops->facet_adj(c->dm, c->dt, uL, wL, ybar, c->l, nullptr, c->d_gam, c->d_gamW, c->stream);
+  });
+  timed(c, HOPU_K_VOLUME_ADJ, [&] {
+    c->ops->volume_adj(c->dm, c->dt, uL, wL, ybar, c->d_gam, c->d_gamW, ubar, wbarL, c->stream);
+  });
+}
+
+// out = cmb(J_F(u)^T vbar) with F(u) = R E^{-1} y(Eu, Eu), the STAGE right-hand side:
+// J_F^T vbar = E^T J_y^T(Eu) (R E^{-1})^T vbar.
+hopu_status enqueue_rhs_vjp(hopu_ctx* c, const void* uV, const void* vbar, Combine cmb, void* out) {
+  enqueue_v2l(c, uV, c->d_uL);
+  timed(c, HOPU_K_V2L, [&] { c->ops->v2l_pt(c->dm, c->dt, vbar, c->d_yL, c->stream); });
+  enqueue_apply_vjp(c, c->d_uL, c->d_uL, c->d_yL, c->d_wL, nullptr);
+  enqueue_l2v(c, c->d_wL, true, cmb, out);
+  return check_launch(c, "rhs vjp kernels");
+}
+
+void enqueue_axpby(hopu_ctx* c, int64_t n, double a, void* x, double b, const void* y) {
+  const int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8);
+  const Combine w{a, x, 0.0, nullptr, b};
+  if (c->fp64) k_axpby<double><<<g, 256, 0, c->stream>>>(n, w, (double*)x, (const double*)y);
+  else k_axpby<float><<<g, 256, 0, c->stream>>>(n, w, (float*)x, (const float*)y);
+}
+
+void enqueue_mass(hopu_ctx* c, const void* x, void* y) {
+  const int64_t n = c->n_l2;
+  const int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8);
+  const int G = geo_stride(c->dim);
+  if (c->fp64) k_mass<double><<<g, 256, 0, c->stream>>>(c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const double*)x, (double*)y);
+  else k_mass<float><<<g, 256, 0, c->stream>>>(c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const float*)x, (float*)y);
+}
+
+// cnt STAGE substeps of `work` in place, keeping the substep states (u, u1, u2) of
+// substep j in seg[3j], seg[3j+1], seg[3j+2] (each `slot` bytes apart).
+hopu_status stored_substeps(hopu_ctx* c, void* work, double dt, int cnt, unsigned char* seg, size_t slot) {
+  void* s1 = c->d_s1;
+  void* s2 = c->d_s2;
+  hopu_status r = HOPU_OK;
+  for (int j = 0; j < cnt && r == HOPU_OK; ++j) {
+    unsigned char* b = seg + 3 * (size_t)j * slot;
+    cudaError_t e = cudaMemcpyAsync(b, work, c->n_hdiv * c->tsize, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) {
+      r = cuda_fail(c, e, "vjp_rollout: checkpoint copy");
+      break;
+    }
+    c->d_s1 = b + slot;
+    c->d_s2 = b + 2 * slot;
+    r = enqueue_substep(c, work, dt);
+  }
+  c->d_s1 = s1;
+  c->d_s2 = s2;
+  return r;
+}
+
 hopu_status weighted_dot(hopu_ctx* c, const void* a, const void* b, int slot) {
   const int G = geo_stride(c->dim);
   if (c->fp64)
@@ -356,7 +455,8 @@ thread_local std::string g_create_error;
 
 hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, void* cuda_stream, hopu_ctx** out) {
   if (!mesh || !opts) return HOPU_EINVAL;
-  if (opts->prec != HOPU_FP64 && opts->prec != HOPU_FP32) return HOPU_EINVAL;
+  if (opts->prec != HOPU_FP64 && opts->prec != HOPU_FP32 && opts->prec != HOPU_FP32_TC && opts->prec != HOPU_TF32)
+    return HOPU_EINVAL;
   if (opts->wind_mode != HOPU_WIND_STAGE && opts->wind_mode != HOPU_WIND_FROZEN) return HOPU_EINVAL;
   if (mesh->dim != 2 && mesh->dim != 3) return HOPU_EINVAL;
   if (opts->k < 1 || opts->k > (mesh->dim == 2 ? 4 : 5)) return HOPU_ENOTSUP;
@@ -381,7 +481,7 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   const int64_t E = c->topo.n_elems, NF = c->topo.n_facets;
   c->n_l2 = E * R.nloc;
   c->n_hdiv = NF * R.nf + E * R.nint;
-  c->ops = make_ops(c->dim, c->k, c->fp64);
+  c->ops = make_ops(c->dim, c->k, c->fp64, c->prec == HOPU_FP32_TC ? 3 : (c->prec == HOPU_TF32 ? 1 : 0));
   if (!c->ops) return fail(c, HOPU_ENOTSUP, "no kernel family for this (dim, k)");
   cudaError_t ce = c->ops->prepare();
   if (ce != cudaSuccess) return cuda_fail(c, ce, "kernel setup");
@@ -453,7 +553,7 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   unsigned char* tb = static_cast<unsigned char*>(c->d_tabs);
   const void** slots[kNumTables] = {&c->dt.Bt,   &c->dt.Wq,  &c->dt.Dm,    &c->dt.TrM,
                                     &c->dt.TrP,  &c->dt.Psi, &c->dt.WPsi,  &c->dt.Wf,
-                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow};
+                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow, &c->dt.Dn};
   for (int i = 0; i < kNumTables; ++i) *slots[i] = tb + offs[i];
 
   // scratch
@@ -469,6 +569,9 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   HOPU_CUDA(c, cudaMalloc(&c->d_s2, ts * nstate));
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_diss, sizeof(double) * NF));
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_red, sizeof(double) * (c->red_blocks + 8)));
+  HOPU_CUDA(c, cudaMalloc((void**)&c->d_err, sizeof(int)));
+  HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
+  c->dm.err = c->d_err;
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_elog_pos, sizeof(int64_t)));
   HOPU_CUDA(c, cudaMemset(c->d_elog_pos, 0, sizeof(int64_t)));
   return HOPU_OK;
@@ -503,6 +606,12 @@ hopu_status hopu_set_stream(hopu_ctx* c, void* cuda_stream) {
   HOPU_PRECHECK(c);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   return HOPU_OK;
+}
+
+hopu_status hopu_sync(hopu_ctx* c) {
+  HOPU_PRECHECK(c);
+  HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  return device_status(c);
 }
 
 hopu_status hopu_sizes(const hopu_ctx* c, int64_t* n_hdiv, int64_t* n_l2, int64_t* n_facets) {
@@ -614,10 +723,129 @@ hopu_status hopu_energy(hopu_ctx* c, const void* w_hdiv, const void* u_l2, doubl
   HOPU_CUDA(c, cudaMemcpyAsync(vals, c->d_red + c->red_blocks, sizeof(double) * (w_hdiv ? 3 : 1),
                                cudaMemcpyDeviceToHost, c->stream));
   HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  r = device_status(c);
+  if (r != HOPU_OK) return r;
   host_out[0] = 0.5 * vals[0];
   host_out[1] = w_hdiv ? vals[1] : 0.0;
   host_out[2] = w_hdiv ? vals[2] : 0.0;
   return HOPU_OK;
+}
+
+hopu_status hopu_vjp_apply(hopu_ctx* c, const void* w_hdiv, const void* u_l2, const void* ybar_l2, void* wbar_hdiv,
+                           void* ubar_l2) {
+  HOPU_PRECHECK(c);
+  if (!w_hdiv || !u_l2 || !ybar_l2 || (!wbar_hdiv && !ubar_l2))
+    return fail(c, HOPU_EINVAL, "vjp_apply: NULL input or no output");
+  const void* ins[3] = {w_hdiv, u_l2, ybar_l2};
+  for (const void* p : ins)
+    if (p == wbar_hdiv || p == ubar_l2) return fail(c, HOPU_EINVAL, "vjp_apply: an output aliases an input");
+  if (wbar_hdiv && wbar_hdiv == ubar_l2) return fail(c, HOPU_EINVAL, "vjp_apply: aliased outputs");
+  if (!aligned16(w_hdiv) || !aligned16(u_l2) || !aligned16(ybar_l2) || (wbar_hdiv && !aligned16(wbar_hdiv)) ||
+      (ubar_l2 && !aligned16(ubar_l2)))
+    return fail(c, HOPU_EINVAL, "vjp_apply: vectors must be 16-byte aligned");
+  hopu_status r = ensure_gamW(c);
+  if (r != HOPU_OK) return r;
+  enqueue_v2l(c, w_hdiv, c->d_wL);
+  enqueue_apply_vjp(c, u_l2, c->d_wL, ybar_l2, ubar_l2 ? ubar_l2 : c->d_uL, c->d_yL);
+  if (wbar_hdiv) {
+    Combine plain;
+    enqueue_l2v(c, c->d_yL, true, plain, wbar_hdiv);
+  }
+  return check_launch(c, "vjp_apply kernels");
+}
+
+hopu_status hopu_vjp_rollout(hopu_ctx* c, const void* u0_hdiv, double dt, int n_substeps, int ckpt_every,
+                             void* u0bar_hdiv, double* loss) {
+  HOPU_PRECHECK(c);
+  if (!u0_hdiv || !u0bar_hdiv || u0_hdiv == u0bar_hdiv || n_substeps < 0 || ckpt_every < 1 || !std::isfinite(dt))
+    return fail(c, HOPU_EINVAL, "vjp_rollout: bad arguments");
+  if (!aligned16(u0_hdiv) || !aligned16(u0bar_hdiv))
+    return fail(c, HOPU_EINVAL, "vjp_rollout: vectors must be 16-byte aligned");
+  if (c->wind != HOPU_WIND_STAGE) return fail(c, HOPU_ENOTSUP, "vjp_rollout: only the STAGE wind rule");
+  hopu_status r = ensure_gamW(c);
+  if (r != HOPU_OK) return r;
+  const int n = n_substeps;
+  const int C = n > 0 ? std::min(ckpt_every, n) : 1;
+  const int nseg = n > 0 ? (n + C - 1) / C : 0;
+  // one slot per V_h vector, 256-byte aligned: checkpoints, 3C stage states, work, b2, b1
+  const size_t slot = (c->n_hdiv * c->tsize + 255) / 256 * 256;
+  const size_t need = slot * ((size_t)std::max(nseg - 1, 0) + 3 * (size_t)C + 3);
+  if (need > c->adj_bytes) {
+    if (c->d_adj) {
+      HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+      cudaFree(c->d_adj);
+      c->d_adj = nullptr;
+      c->adj_bytes = 0;
+    }
+    HOPU_CUDA(c, cudaMalloc(&c->d_adj, need));
+    c->adj_bytes = need;
+  }
+  unsigned char* base = static_cast<unsigned char*>(c->d_adj);
+  void* work = base;
+  void* b2 = base + slot;
+  void* b1 = base + 2 * slot;
+  unsigned char* seg = base + 3 * slot;
+  unsigned char* ckpt = seg + 3 * (size_t)C * slot;
+  const size_t vbytes = c->n_hdiv * c->tsize;
+  double* elog = c->elog;  // no energy logging inside the rollout
+  c->elog = nullptr;
+  auto body = [&]() -> hopu_status {
+    HOPU_CUDA(c, cudaMemcpyAsync(work, u0_hdiv, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+    // forward: checkpoints at segment starts, stage states of the last segment
+    for (int g = 0; g < nseg; ++g) {
+      const int cnt = std::min(C, n - g * C);
+      if (g < nseg - 1) {
+        HOPU_CUDA(c, cudaMemcpyAsync(ckpt + (size_t)g * slot, work, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+        for (int j = 0; j < cnt; ++j) {
+          hopu_status q = enqueue_substep(c, work, dt);
+          if (q != HOPU_OK) return q;
+        }
+      } else {
+        hopu_status q = stored_substeps(c, work, dt, cnt, seg, slot);
+        if (q != HOPU_OK) return q;
+      }
+    }
+    // seed: the cotangent of u_N, or the gradient E^T M E u_N of 1/2 int |E u_N|^2
+    if (loss) {
+      enqueue_v2l(c, work, c->d_uL);
+      hopu_status q = weighted_dot(c, c->d_uL, c->d_uL, 3);
+      if (q != HOPU_OK) return q;
+      enqueue_mass(c, c->d_uL, c->d_yL);
+      Combine plain;
+      enqueue_l2v(c, c->d_yL, true, plain, u0bar_hdiv);
+    }
+    // backward over the segments, recomputing the stage states from the checkpoints
+    for (int g = nseg - 1; g >= 0; --g) {
+      const int cnt = std::min(C, n - g * C);
+      if (g < nseg - 1) {
+        HOPU_CUDA(c, cudaMemcpyAsync(work, ckpt + (size_t)g * slot, vbytes, cudaMemcpyDeviceToDevice, c->stream));
+        hopu_status q = stored_substeps(c, work, dt, cnt, seg, slot);
+        if (q != HOPU_OK) return q;
+      }
+      for (int j = cnt - 1; j >= 0; --j) {
+        const unsigned char* st = seg + 3 * (size_t)j * slot;
+        void* ub = u0bar_hdiv;
+        // b2 = 2/3 (ub - dt J(u2)^T ub); b1 = 1/4 (b2 - dt J(u1)^T b2);
+        // ub = 1/3 ub + 3/4 b2 + b1 - dt J(u)^T b1
+        hopu_status q = enqueue_rhs_vjp(c, st + 2 * slot, ub, Combine{2.0 / 3.0, ub, 0.0, nullptr, -2.0 / 3.0 * dt}, b2);
+        if (q == HOPU_OK) q = enqueue_rhs_vjp(c, st + slot, b2, Combine{0.25, b2, 0.0, nullptr, -0.25 * dt}, b1);
+        if (q != HOPU_OK) return q;
+        enqueue_axpby(c, c->n_hdiv, 1.0 / 3.0, ub, 0.75, b2);
+        q = enqueue_rhs_vjp(c, st, b1, Combine{1.0, ub, 1.0, b1, -dt}, ub);
+        if (q != HOPU_OK) return q;
+      }
+    }
+    if (loss) {
+      double v = 0.0;
+      HOPU_CUDA(c, cudaMemcpyAsync(&v, c->d_red + c->red_blocks + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+      *loss = 0.5 * v;
+    }
+    return check_launch(c, "vjp_rollout kernels");
+  };
+  r = body();
+  c->elog = elog;
+  return r;
 }
 
 hopu_status hopu_points(hopu_ctx* c, int which, double* host_out, int64_t* count_out) {

@@ -40,8 +40,12 @@ struct hopu_ctx {
   void* d_wfz = nullptr;    // L2 frozen wind
   void* d_s1 = nullptr;     // RK stage vectors (max of V_h and L2 lengths)
   void* d_s2 = nullptr;
+  void* d_gamW = nullptr;   // VJP: facet moments of the wind cotangent (first VJP call)
+  void* d_adj = nullptr;    // VJP rollout: checkpoints, stage states, cotangent stages
+  size_t adj_bytes = 0;
   double* d_diss = nullptr; // [NF]
   double* d_red = nullptr;  // partial sums + 4 scalars
+  int* d_err = nullptr;     // device error word (DevMesh::err)
   bool have_frozen = false;
   // per-substep kinetic-energy log (device ring buffer owned by the caller)
   double* elog = nullptr;

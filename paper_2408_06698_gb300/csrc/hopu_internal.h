@@ -17,6 +17,7 @@ struct DevMesh {
   const int32_t* fa = nullptr;   // [NF]: element*4 + local facet of side A
   const int32_t* fb = nullptr;   // [NF]: same for side B
   const double* fgeo = nullptr;  // [NF][d+1]: canonical unit normal n_F, a_F = |F|/|param|
+  int* err = nullptr;            // device error word (bit 0: a tensor-core completion wait gave up)
 };
 
 // Device reference tables in working precision (all element-type T, 16-byte aligned).
@@ -33,17 +34,25 @@ struct DevTabs {
   const void* DinvT = nullptr;  // [nloc][nlp]     DinvT[s][r] = Dinv[r][s]  (nlp = nloc rounded up to 4)
   const void* DT = nullptr;     // [nloc][nlp]     DT[s][r]    = D[r][s]
   const void* Dinv = nullptr;   // [nloc][nlp]     Dinv[s][r]
+  const void* Dn = nullptr;     // [nloc][nlp]     Dn[s][r] = D[s][r]
   const void* Drow = nullptr;   // [nloc][nlr]     D[r][s] row-major, rows padded to nlr (an odd
                                 //                 multiple of 16 bytes), zero padding
 };
 
-// out = a0*x0 + a1*x1 + a2*v  (x0 / x1 may be null; out may alias x0 or x1)
+// out = a0*x0 + a1*x1 + a2*v  (x0 / x1 may be null; out may alias x0 or x1).
+// In FP32 every coefficient is applied as the sum of two floats (hi = float(a),
+// lo = float(a - hi)), so the combination weights keep FP64 accuracy: with plain
+// float weights the SSP-RK3 weights float(1/3) + float(2/3) = 1 + 3e-8 would scale the
+// state by that factor in every substep.
 struct Combine {
   double a0 = 0.0;
   const void* x0 = nullptr;
   double a1 = 0.0;
   const void* x1 = nullptr;
   double a2 = 1.0;
+  float h0 = float(a0), l0 = float(a0 - double(float(a0)));
+  float h1 = float(a1), l1 = float(a1 - double(float(a1)));
+  float h2 = float(a2), l2 = float(a2 - double(float(a2)));
 };
 
 // layout of the working-precision geometry record (offsets in elements)
@@ -72,6 +81,15 @@ class Ops {
   virtual int volume_l2v(const DevMesh&, const DevTabs&, const void* uL, const void* gam, void* lf,
                          Combine c, void* outV, cudaStream_t) = 0;
   virtual bool has_fused() const = 0;
+  virtual bool tensor_cores() const = 0;  // the V_h -> L2 projection runs on tensor cores
+  // adjoint kernels: (R E_T^{-1})^T, the facet and the volume parts of the VJP of the
+  // apply (ybar = cotangent of y; wL == uL means w = u and the cotangents are summed
+  // into ubar, wbar unused); gamU / gamW are element-major facet-moment scratch.
+  virtual int v2l_pt(const DevMesh&, const DevTabs&, const void* vV, void* yL, cudaStream_t) = 0;
+  virtual int facet_adj(const DevMesh&, const DevTabs&, const void* uL, const void* wL, const void* ybar,
+                        int l, const int8_t* facet_l, void* gamU, void* gamW, cudaStream_t) = 0;
+  virtual int volume_adj(const DevMesh&, const DevTabs&, const void* uL, const void* wL, const void* ybar,
+                         const void* gamU, const void* gamW, void* ubar, void* wbar, cudaStream_t) = 0;
   // R E^{-1} (dual = false) or E^T (dual = true), combined into outV, in two launches:
   // the element part writes interior dofs and the local facet functionals lf
   // [E][d+1][nf]; the facet part averages (or sums) the two copies into the facet dofs.

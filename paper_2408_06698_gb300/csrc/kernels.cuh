@@ -76,10 +76,19 @@ __device__ __forceinline__ void allreduce(T (&v)[N]) {
 
 template <typename T>
 __device__ __forceinline__ T combine_at(const Combine& c, T v, int64_t idx) {
-  T o = T(c.a2) * v;
-  if (c.x0) o += T(c.a0) * static_cast<const T*>(c.x0)[idx];
-  if (c.x1) o += T(c.a1) * static_cast<const T*>(c.x1)[idx];
-  return o;
+  if constexpr (sizeof(T) == 8) {
+    T o = T(c.a2) * v;
+    if (c.x0) o = fma(T(c.a0), static_cast<const T*>(c.x0)[idx], o);
+    if (c.x1) o = fma(T(c.a1), static_cast<const T*>(c.x1)[idx], o);
+    return o;
+  } else {
+    const float x0 = c.x0 ? static_cast<const float*>(c.x0)[idx] : 0.0f;
+    const float x1 = c.x1 ? static_cast<const float*>(c.x1)[idx] : 0.0f;
+    float o = fmaf(c.l2, v, fmaf(c.l0, x0, c.l1 * x1));  // the small parts first
+    o = fmaf(c.h1, x1, o);
+    o = fmaf(c.h0, x0, o);
+    return fmaf(c.h2, v, o);
+  }
 }
 
 // Vector views of shared memory: 16-byte loads of 4 floats or 2 doubles.
@@ -187,7 +196,10 @@ __device__ __forceinline__ const T* proj_setup(unsigned char* smem, const T* tab
 // a1: V_h -> L2.  Per element: gather the (d+1) facet blocks with the sign sigma and the
 // interior block, reference change of basis Dinv, contravariant Piola map J / det J.
 // tab = Dinv^T with rows padded to NLP: tab[s][r] = Dinv[r][s].
-template <int D, int K, typename T>
+// PT = true computes instead the transpose of the back-projection R E_T^{-1}: each facet
+// value goes to both copies with the averaging weight 1/2 and the sign sigma, interior
+// values are copied, then (D Piola^{-1})^T: tab[s][r] = D[s][r], Piola^{-1}^T = Pi^T.
+template <int D, int K, typename T, bool PT>
 __global__ void __launch_bounds__(kProjThreads) k_v2l(DevMesh m, const T* __restrict__ tab,
                                                       const T* __restrict__ uV, T* __restrict__ uL) {
   using S = Shape<D, K>;
@@ -232,6 +244,7 @@ __global__ void __launch_bounds__(kProjThreads) k_v2l(DevMesh m, const T* __rest
           const int code = sCode[k * (D + 1) + f];
           v = uV[(int64_t)(code >> 2) * NF + mm];
           if (code & 2) v = -v;
+          if (PT) v *= T(0.5);
         } else {
           v = uV[m.NF * NF + e * NINT + (s2 - (D + 1) * NF)];
         }
@@ -243,11 +256,12 @@ __global__ void __launch_bounds__(kProjThreads) k_v2l(DevMesh m, const T* __rest
     for (int t = tid; t < TE * NL; t += kProjThreads) {
       const int k = t / NL, idx = t - k * NL;
       if (e0 + k >= m.E) continue;
-      const T* g = sGeo + k * GEO;  // Pf = J / det J
+      const T* g = sGeo + k * GEO;  // Pf = J / det J   (PT: Pi^T, Pi = det J Jinv)
       const int a = idx / NB, i = idx - a * NB;
       T acc1 = T(0);
 #pragma unroll
-      for (int b = 0; b < D; ++b) acc1 = fma(g[a * D + b], sX[k * NLQ + b * NB + i], acc1);
+      for (int b = 0; b < D; ++b)
+        acc1 = fma(PT ? g[D * D + b * D + a] : g[a * D + b], sX[k * NLQ + b * NB + i], acc1);
       uL[e0 * NL + t] = acc1;
     }
     __syncthreads();

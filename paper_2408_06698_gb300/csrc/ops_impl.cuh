@@ -1,8 +1,11 @@
 // Launch wrappers of one kernel family (dimension D, order K, precision T).
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
+#include "kernels_adj.cuh"
+#include "kernels_tc.cuh"
 
 namespace hopu {
 
@@ -46,7 +49,20 @@ class OpsImpl final : public Ops {
   static constexpr size_t kFuseSmem = kVolTab + kFuseTab + kWarps * volume_warp(false);
   int g_fuse_ = 1;
 
+  // adjoint kernels (layouts of k_facet_adj / k_volume_adj)
+  static constexpr size_t facet_adj_warp(bool wsep) {
+    return (size_t(wsep ? 6 : 4) * D * r4(S::nb) + 3 * S::nqf * 4 + 7 * S::nf * 4) * sz;
+  }
+  static constexpr size_t facet_adj_smem(bool wsep) { return kFacTab + kWarps * facet_adj_warp(wsep); }
+  static constexpr size_t volume_adj_smem(bool wsep) {
+    return kWarps * (2 * size_t(D) * r4(S::nb) + size_t(D) * D * r4(kNB1) + (wsep ? size_t(D) * r4(S::nb) : 0) +
+                     2 * r4(size_t(D + 1) * S::nf * D)) * sz;
+  }
+  int g_fadj_ = 1, g_vadj_ = 1;
   int nsm_ = 1;
+  int tc_ = 0;  // FP32 only: 0 = FMA, 3 = 3xTF32 tensor cores, 1 = 1xTF32 tensor cores
+  int g_v2l_tc_ = 1;
+  static constexpr bool kTcV2l = std::is_same<T, float>::value && V2lTc<D, K>::OK;
   int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
 
   template <typename Kern>
@@ -69,6 +85,9 @@ class OpsImpl final : public Ops {
   }
 
  public:
+  explicit OpsImpl(int tc = 0) : tc_(std::is_same<T, float>::value ? tc : 0) {}
+  bool tensor_cores() const override { return tc_ != 0 && kTcV2l; }
+
   cudaError_t prepare() override {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
@@ -76,7 +95,19 @@ class OpsImpl final : public Ops {
     err = cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     const int th = 32 * kWarps;
-    if ((err = setup(k_v2l<D, K, T>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
+    if ((err = setup(k_v2l<D, K, T, false>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
+    if ((err = setup(k_v2l<D, K, T, true>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
+    if constexpr (kTcV2l) {
+      if (tc_) {
+        if (tc_ == 3) err = setup(k_v2l_tc<D, K, true>, V2lTc<D, K>::SMEM, 128, &g_v2l_tc_);
+        else err = setup(k_v2l_tc<D, K, false>, V2lTc<D, K>::SMEM, 128, &g_v2l_tc_);
+        if (err != cudaSuccess) return err;
+      }
+    }
+    if ((err = setup(k_facet_adj<D, K, T, false>, facet_adj_smem(false), th, &g_fadj_)) != cudaSuccess) return err;
+    if ((err = setup(k_facet_adj<D, K, T, true>, facet_adj_smem(true), th, &g_fadj_)) != cudaSuccess) return err;
+    if ((err = setup(k_volume_adj<D, K, T, false>, volume_adj_smem(false), th, &g_vadj_)) != cudaSuccess) return err;
+    if ((err = setup(k_volume_adj<D, K, T, true>, volume_adj_smem(true), th, &g_vadj_)) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, false, kFacetTab>, facet_smem(false), th, &g_fac_[0])) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, true, kFacetTab>, facet_smem(true), th, &g_fac_[1])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, false, kVolumeTab, false>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
@@ -91,8 +122,21 @@ class OpsImpl final : public Ops {
   }
 
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
+    if constexpr (kTcV2l) {
+      if (tc_) {
+        const int g = clamp_grid(g_v2l_tc_, m.E, V2lTc<D, K>::TM);
+        const int nlp = (S::nloc + 3) / 4 * 4;
+        if (tc_ == 3)
+          k_v2l_tc<D, K, true><<<g, 128, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
+                                                                  static_cast<const float*>(uV), static_cast<float*>(uL));
+        else
+          k_v2l_tc<D, K, false><<<g, 128, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
+                                                                   static_cast<const float*>(uV), static_cast<float*>(uL));
+        return 1;
+      }
+    }
     const int g = clamp_grid(g_v2l_, m.E, PC::TE);
-    k_v2l<D, K, T><<<g, kProjThreads, kProjSmem, st>>>(
+    k_v2l<D, K, T, false><<<g, kProjThreads, kProjSmem, st>>>(
         m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
     return 1;
   }
@@ -126,6 +170,43 @@ class OpsImpl final : public Ops {
   }
 
   bool has_fused() const override { return kFuse; }
+
+  int v2l_pt(const DevMesh& m, const DevTabs& t, const void* vV, void* yL, cudaStream_t st) override {
+    const int g = clamp_grid(g_v2l_, m.E, PC::TE);
+    k_v2l<D, K, T, true><<<g, kProjThreads, kProjSmem, st>>>(
+        m, static_cast<const T*>(t.Dn), static_cast<const T*>(vV), static_cast<T*>(yL));
+    return 1;
+  }
+
+  int facet_adj(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* ybar, int l,
+                const int8_t* facet_l, void* gamU, void* gamW, cudaStream_t st) override {
+    const bool wsep = (wL != nullptr && wL != uL);
+    const int g = clamp_grid(g_fadj_, m.NF, kWarps);
+    if (wsep)
+      k_facet_adj<D, K, T, true><<<g, 32 * kWarps, facet_adj_smem(true), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(ybar), l, facet_l,
+          static_cast<T*>(gamU), static_cast<T*>(gamW));
+    else
+      k_facet_adj<D, K, T, false><<<g, 32 * kWarps, facet_adj_smem(false), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(ybar), l, facet_l,
+          static_cast<T*>(gamU), static_cast<T*>(gamW));
+    return 1;
+  }
+
+  int volume_adj(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* ybar,
+                 const void* gamU, const void* gamW, void* ubar, void* wbar, cudaStream_t st) override {
+    const bool wsep = (wL != nullptr && wL != uL);
+    const int g = clamp_grid(g_vadj_, m.E, kWarps);
+    if (wsep)
+      k_volume_adj<D, K, T, true><<<g, 32 * kWarps, volume_adj_smem(true), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(ybar),
+          static_cast<const T*>(gamU), static_cast<const T*>(gamW), static_cast<T*>(ubar), static_cast<T*>(wbar));
+    else
+      k_volume_adj<D, K, T, false><<<g, 32 * kWarps, volume_adj_smem(false), st>>>(
+          m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(ybar),
+          static_cast<const T*>(gamU), static_cast<const T*>(gamW), static_cast<T*>(ubar), nullptr);
+    return 1;
+  }
 
   int volume_l2v(const DevMesh& m, const DevTabs& t, const void* uL, const void* gam, void* lf, Combine c,
                  void* outV, cudaStream_t st) override {
@@ -166,8 +247,8 @@ class OpsImpl final : public Ops {
 
 #define HOPU_DEFINE_OPS(D, K)                                               \
   namespace hopu {                                                          \
-  Ops* make_ops_##D##_##K(bool fp64) {                                      \
+  Ops* make_ops_##D##_##K(bool fp64, int tc) {                              \
     if (fp64) return new OpsImpl<D, K, double>();                           \
-    return new OpsImpl<D, K, float>();                                      \
+    return new OpsImpl<D, K, float>(tc);                                    \
   }                                                                         \
   }

@@ -14,7 +14,7 @@ import torch
 
 from . import _lib as L
 
-_PREC = {"f64": L.HOPU_FP64, "f32": L.HOPU_FP32}
+_PREC = {"f64": L.HOPU_FP64, "f32": L.HOPU_FP32, "f32_tc": L.HOPU_FP32_TC, "tf32": L.HOPU_TF32}
 _WIND = {"stage": L.HOPU_WIND_STAGE, "frozen": L.HOPU_WIND_FROZEN}
 _DIR = {"hdiv_to_l2": L.HOPU_HDIV_TO_L2, "l2_to_hdiv": L.HOPU_L2_TO_HDIV, "l2_to_hdiv_dual": L.HOPU_L2_TO_HDIV_DUAL}
 
@@ -33,6 +33,8 @@ class Hopu:
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
+        if prec not in _PREC:
+            raise ValueError(f"prec must be one of {sorted(_PREC)}")
         self.dtype = torch.float64 if prec == "f64" else torch.float32
         self.prec, self.k, self.l, self.wind = prec, k, l, wind
         self._coords = np.ascontiguousarray(coords, dtype=np.float64)
@@ -99,6 +101,34 @@ class Hopu:
                                                    self._vec(u_l2, self.n_l2, "u_l2"),
                                                    self._vec(out, self.n_l2, "y_l2"), fl), "hopu_apply_convection")
         return out
+
+    def vjp_apply(self, w_hdiv, u_l2, ybar_l2, need_w: bool = True, need_u: bool = True):
+        """(wbar_hdiv, ubar_l2) = cotangents of apply_convection(w, u) for ybar (None if not needed)."""
+        wbar = self.new("hdiv") if need_w else None
+        ubar = self.new("l2") if need_u else None
+        self._sync_stream()
+        self._check(self.lib.hopu_vjp_apply(self.ctx, self._vec(w_hdiv, self.n_hdiv, "w_hdiv"),
+                                            self._vec(u_l2, self.n_l2, "u_l2"), self._vec(ybar_l2, self.n_l2, "ybar_l2"),
+                                            None if wbar is None else wbar.data_ptr(),
+                                            None if ubar is None else ubar.data_ptr()), "hopu_vjp_apply")
+        return wbar, ubar
+
+    def vjp_rollout(self, u0_hdiv, dt: float, n_substeps: int, ckpt_every: int = 1, seed=None):
+        """Gradient through n STAGE substeps from u0.  seed None: (loss, d loss/d u0) for
+        loss = 1/2 int |E u_n|^2; else (None, cotangent of u0) for the cotangent seed of u_n."""
+        out = self.new("hdiv")
+        loss = c_double(0.0)
+        if seed is not None:
+            out.copy_(seed)
+        self._sync_stream()
+        self._check(self.lib.hopu_vjp_rollout(self.ctx, self._vec(u0_hdiv, self.n_hdiv, "u0_hdiv"), float(dt),
+                                              int(n_substeps), int(ckpt_every), out.data_ptr(),
+                                              byref(loss) if seed is None else None), "hopu_vjp_rollout")
+        return (float(loss.value) if seed is None else None), out
+
+    def sync(self):
+        """Synchronise the context stream; raises on a device-side failure (ETIMEOUT)."""
+        self._check(self.lib.hopu_sync(self.ctx), "hopu_sync")
 
     def set_frozen_wind(self, w_hdiv: torch.Tensor):
         self._sync_stream()
@@ -187,6 +217,41 @@ class Hopu:
         return n + (2 if getattr(self, "_elog", None) is not None else 0)
 
 
+class ConvectionApply(torch.autograd.Function):
+    """y = apply_convection(w, u) as an autograd node; the backward is hopu_vjp_apply."""
+
+    @staticmethod
+    def forward(ctx, hopu: Hopu, w_hdiv, u_l2):
+        ctx.hopu = hopu
+        ctx.save_for_backward(w_hdiv, u_l2)
+        return hopu.apply_convection(w_hdiv.detach().contiguous(), u_l2.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, ybar):
+        w, u = ctx.saved_tensors
+        wbar, ubar = ctx.hopu.vjp_apply(w.detach(), u.detach(), ybar.contiguous(),
+                                        need_w=ctx.needs_input_grad[1], need_u=ctx.needs_input_grad[2])
+        return None, wbar, ubar
+
+
+class Rollout(torch.autograd.Function):
+    """u_n = n STAGE SSP-RK3 substeps of u0 as an autograd node; the backward is
+    hopu_vjp_rollout with the incoming cotangent as seed."""
+
+    @staticmethod
+    def forward(ctx, hopu: Hopu, u0_hdiv, dt: float, n_substeps: int, ckpt_every: int = 1):
+        ctx.hopu, ctx.dt, ctx.n, ctx.ck = hopu, dt, n_substeps, ckpt_every
+        ctx.save_for_backward(u0_hdiv)
+        u = u0_hdiv.detach().clone()
+        return hopu.rk_substep(u, dt, n_substeps)
+
+    @staticmethod
+    def backward(ctx, ubar):
+        (u0,) = ctx.saved_tensors
+        _, g = ctx.hopu.vjp_rollout(u0.detach(), ctx.dt, ctx.n, ctx.ck, seed=ubar.contiguous())
+        return None, g, None, None, None
+
+
 class _ClassView(Hopu):
     """A non-owning Hopu view of one order class of a batch (the batch owns the context)."""
 
@@ -221,6 +286,8 @@ class HopuBatch:
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
+        if prec not in _PREC:
+            raise ValueError(f"prec must be one of {sorted(_PREC)}")
         self.dtype = torch.float64 if prec == "f64" else torch.float32
         self.prec, self.wind = prec, wind
         self._keep = []

@@ -1,0 +1,99 @@
+"""GPU parity of the tensor-core precision modes against the FP64 oracle.
+
+HOPU_FP32_TC runs the batched V_h -> L2 projection GEMM on the tensor cores (tcgen05
+kind::tf32) in 3xTF32; HOPU_TF32 uses one TF32 product.  Tolerances (relative to the
+largest reference entry): 3xTF32 keeps about 2^-21 per product, so the projections are
+held to 4e-6 (FP32 FMA: 2e-6) and the apply / substep to the FP32 bounds; one TF32
+product (2^-11) is held to 1e-2 and its error is printed.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import convection as C
+from oracle import fe, hdiv, mesh, rk
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(2, 4, 1), (2, 8, 2), (2, 4, 4), (3, 3, 1), (3, 3, 2), (3, 5, 3), (3, 3, 4), (3, 3, 5)]
+PTOL = {"f32_tc": 4e-6, "tf32": 1e-2}
+
+
+def _mk(dim, n, k, prec, l=-1, wind="stage"):
+    from paper_2408_06698_gb300 import Hopu
+    m = W.periodic_box_mesh(dim, n)
+    g = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec=prec, wind=wind)
+    topo = mesh.MeshTopo(m.coords, m.elems, m.rep)
+    sp = hdiv.HDiv(topo, fe.ref_element(dim, k))
+    return g, sp
+
+
+def _dev(g, x):
+    return torch.as_tensor(np.ascontiguousarray(x).reshape(-1), dtype=g.dtype, device=g.device)
+
+
+def _host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _rounded(g, x):
+    return _host(_dev(g, x)).reshape(np.shape(x))
+
+
+def _rel(got, ref):
+    return float(np.abs(np.asarray(got).reshape(-1) - np.asarray(ref).reshape(-1)).max() / np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec", ["f32_tc", "tf32"])
+@pytest.mark.parametrize("dim,n,k", CASES)
+def test_tc_projection(dim, n, k, prec):
+    g, sp = _mk(dim, n, k, prec)
+    rng = np.random.default_rng(700 + 10 * dim + k)
+    uV = _rounded(g, rng.standard_normal(sp.n_hdiv))
+    got = _host(g.project("hdiv_to_l2", _dev(g, uV)))
+    g.sync()
+    err = _rel(got, sp.to_l2(uV))
+    print(f"{prec} d={dim} k={k} E={sp.topo.n_elems}: V_h -> L2 error {err:.2e}")
+    assert err < PTOL[prec]
+    # the other projections are unchanged by the mode
+    uL = _rounded(g, rng.standard_normal((sp.topo.n_elems, dim, sp.ref.nb)))
+    assert _rel(_host(g.project("l2_to_hdiv", _dev(g, uL))), sp.from_l2(uL)) < 2e-6
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 4, 3), (3, 3, 4)])
+def test_tc_apply_and_substep(dim, n, k):
+    g, sp = _mk(dim, n, k, "f32_tc", l=k - 1)
+    rng = np.random.default_rng(800 + k)
+    wV = _rounded(g, rng.standard_normal(sp.n_hdiv))
+    uL = _rounded(g, rng.standard_normal((sp.topo.n_elems, dim, sp.ref.nb)))
+    y = _host(g.apply_convection(_dev(g, wV), _dev(g, uL)))
+    ref = C.apply(sp.topo, sp.ref, sp.to_l2(wV), uL, k - 1)
+    err = _rel(y, ref)
+    print(f"f32_tc apply d={dim} k={k}: {err:.2e}")
+    assert err < 2e-6
+    u0 = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
+    x = _dev(g, u0)
+    g.rk_substep(x, 5e-3, 1)
+    g.sync()
+    ref = rk.substeps_stage(sp, u0, 5e-3, 1, k - 1)
+    err = _rel(_host(x), ref)
+    print(f"f32_tc substep d={dim} k={k}: {err:.2e}")
+    assert err < 2e-6
+
+
+def test_tc_full_size_projection():
+    """16^3 x 6 tetrahedra, k = 3: the tensor-core projection against the FP32 FMA one on
+    the same input (both at FP32 parity with the oracle on the small meshes)."""
+    from paper_2408_06698_gb300 import Hopu
+    m = W.periodic_box_mesh(3, 16)
+    a = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32_tc")
+    b = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32")
+    u = a.interpolate_function(W.taylor_green)
+    u += torch.as_tensor(W.uniform_noise(a.n_hdiv, 1e-3, 0), device=a.device).float()
+    ya = a.project("hdiv_to_l2", u)
+    yb = b.project("hdiv_to_l2", u)
+    a.sync()
+    err = float((ya - yb).abs().max() / yb.abs().max())
+    print(f"full size V_h -> L2, 3xTF32 vs FP32 FMA: {err:.2e}")
+    assert err < 4e-6

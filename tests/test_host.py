@@ -170,3 +170,10 @@ def test_reference_arm_prints_on_rank0_only(tmp_path):
     assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     assert outs[1][0].strip() == ""
+
+
+def test_bench_profiles_every_kernel_family():
+    import bench
+    from paper_2408_06698_gb300 import _lib as L
+    assert bench.ALL_FAMILIES == L.KERNEL_FAMILIES
+    assert set(bench.FAMILIES) <= set(bench.ALL_FAMILIES)
