@@ -359,6 +359,41 @@ def our_arm(args, rank, world):
     fp64 = {"value": whole_job_value(dofs * K64, world, d64 / 1e3), "unit": UNIT, "steps": K64,
             "ms_per_step": d64 / K64}
 
+    # ---------------- FP32 with the tensor-core (3xTF32) projection GEMM
+    gtc, stc = make("f32_tc")
+    Ktc = min(K, 500)
+    dtc, _, acctc, _, _ = timed_steps(gtc, stc, Ktc, Wm, profile=True)
+    dtc = max_over_ranks(dtc, world)
+    fp32_tc = {"value": whole_job_value(dofs * Ktc, world, dtc / 1e3), "unit": UNIT, "steps": Ktc,
+               "ms_per_step": dtc / Ktc,
+               "kernels": {f: {"avg_us": 1e3 * acctc[f][0] / max(1, acctc[f][1]), "launches": acctc[f][1]}
+                           for f in FAMILIES}}
+    del gtc, stc
+
+    # ---------------- differentiation: 24^3 x 6, k = 3, 200-substep rollout, VJP with
+    # checkpoints every 20 substeps (FP32)
+    vjp = None
+    if not args.no_vjp:
+        mv = W.periodic_box_mesh(3, 24)
+        gv = Hopu(mv.coords, mv.elems, mv.rep, k=3, l=2, prec="f32", device=dev)
+        uv = gv.interpolate_function(W.taylor_green)
+        uv += torch.as_tensor(W.uniform_noise(gv.n_hdiv, 1e-3, 0), device=dev).float()
+        with torch.cuda.stream(stream):
+            gv.vjp_rollout(uv, dt, 20, 20)            # warm-up: allocations, first launches
+            stream.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            loss_v, _ = gv.vjp_rollout(uv, dt, 200, 20)
+            t1.record(stream)
+        stream.synchronize()
+        vms = max_over_ranks(t0.elapsed_time(t1), world)
+        vjp = {"workload": "24^3 x 6 tets (82,944 elements), k=3, l=2, FP32, 200 STAGE substeps dt=5e-4, "
+                           "loss = final kinetic energy, checkpoints every 20 substeps",
+               "ms_rollout_and_adjoint": vms, "loss": loss_v,
+               "dof_updates_per_s_forward_equivalent": gv.n_l2 * APPLIES_PER_STEP * 200 / (vms / 1e3)}
+        del gv, uv
+
     # ---------------- roofline of the dominant kernel (FP32 run, live CUDA events)
     alg = algorithmic(dim, k, g32.n_elems, g32.n_facets, 4)
     dom = max(FAMILIES, key=lambda f: acc[f][0])
@@ -400,6 +435,7 @@ def our_arm(args, rank, world):
                    "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "fp64": fp64,
+        "fp32_tc": fp32_tc, "vjp": vjp,
         "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernels,
         "kernels_f64": {f: {"avg_us": 1e3 * acc64[f][0] / max(1, acc64[f][1]), "launches": acc64[f][1]}
                         for f in FAMILIES},
@@ -419,7 +455,7 @@ def our_arm(args, rank, world):
                                           "16^3 x 6 k=3 workload, numpy FP64, 1 BLAS thread",
                                 "seconds": res["seconds"]}
         errs = {}
-        for prec in ("f32", "f64"):
+        for prec in ("f32", "f32_tc", "f64"):
             g, s = make(prec)
             with torch.cuda.stream(stream):
                 g.rk_substep(s, dt, 1)
@@ -439,6 +475,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-vjp", action="store_true", help="skip the rollout-adjoint measurement")
     ap.add_argument("--ref-budget-s", type=float, default=150.0,
                     help="seconds of oracle work the reference arm aims for (sizes its per-step sample)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)

@@ -66,15 +66,32 @@ class OpsImpl final : public Ops {
   int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
 
   template <typename Kern>
-  cudaError_t setup(Kern kern, size_t smem, int threads, int* grid) {
+  cudaError_t setup(Kern kern, size_t smem, int threads, int* grid, bool max_carveout = false) {
     cudaError_t err = cudaSuccess;
     if (smem > 48 * 1024) {
       err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
     }
+    if (max_carveout) {  // the largest shared-memory carveout, so that it does not cut occupancy
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if (err != cudaSuccess) return err;
+    }
     int occ = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (err != cudaSuccess) return err;
+    if (max_carveout) {  // resident blocks by shared memory, threads and registers
+      int dev = 0, sm_smem = 0, reserved = 0;
+      cudaFuncAttributes fa{};
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+          cudaFuncGetAttributes(&fa, kern) == cudaSuccess) {
+        const int by_smem = sm_smem / (int)(smem + fa.sharedSizeBytes + reserved);
+        const int by_threads = 2048 / threads;
+        const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * threads) : by_threads;
+        occ = std::max(occ, std::min(by_smem, std::min(by_threads, by_regs)));
+      }
+    }
     *grid = nsm_ * std::max(occ, 1);
     return cudaSuccess;
   }
@@ -99,8 +116,8 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_v2l<D, K, T, true>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
     if constexpr (kTcV2l) {
       if (tc_) {
-        if (tc_ == 3) err = setup(k_v2l_tc<D, K, true>, V2lTc<D, K>::SMEM, 128, &g_v2l_tc_);
-        else err = setup(k_v2l_tc<D, K, false>, V2lTc<D, K>::SMEM, 128, &g_v2l_tc_);
+        if (tc_ == 3) err = setup(k_v2l_tc<D, K, true>, V2lTc<D, K>::SMEM, V2lTc<D, K>::THREADS, &g_v2l_tc_, true);
+        else err = setup(k_v2l_tc<D, K, false>, V2lTc<D, K>::SMEM, V2lTc<D, K>::THREADS, &g_v2l_tc_, true);
         if (err != cudaSuccess) return err;
       }
     }
@@ -127,10 +144,10 @@ class OpsImpl final : public Ops {
         const int g = clamp_grid(g_v2l_tc_, m.E, V2lTc<D, K>::TM);
         const int nlp = (S::nloc + 3) / 4 * 4;
         if (tc_ == 3)
-          k_v2l_tc<D, K, true><<<g, 128, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
+          k_v2l_tc<D, K, true><<<g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
                                                                   static_cast<const float*>(uV), static_cast<float*>(uL));
         else
-          k_v2l_tc<D, K, false><<<g, 128, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
+          k_v2l_tc<D, K, false><<<g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
                                                                    static_cast<const float*>(uV), static_cast<float*>(uL));
         return 1;
       }
