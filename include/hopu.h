@@ -151,6 +151,7 @@ hopu_status hopu_project(hopu_ctx* ctx, int dir, const void* in, void* out);
  * (int8 device array of n_facets entries in -1..k), NULL = opts.l for every facet.     */
 hopu_status hopu_apply_convection(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2,
                                   void* y_l2, const int8_t* facet_l);
+/* (facet_l NULL: the orders of hopu_set_facet_l when set, else the context's l.) */
 
 /* n_substeps explicit SSP-RK3 substeps (Shu-Osher) of du/dt = -y(u) with step dt.
  * STAGE wind: state is a V_h vector, updated in place, w = u at every stage.
@@ -177,6 +178,24 @@ hopu_status hopu_set_frozen_wind(hopu_ctx* ctx, const void* w_hdiv);
  *   host_out[2] = sum_F int 1/2 |w.n| |(I-Pi^l)[[u]]|^2     (facet dissipation; 0 if NULL)
  * For divergence-free normal-continuous w, host_out[1] == host_out[2] >= 0.            */
 hopu_status hopu_energy(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, double* host_out);
+
+/* Per-facet HOPU orders (device int8 [n_facets], values -1..k, caller-owned, read at every
+ * later launch) used by hopu_rk_substep, hopu_vjp_apply, hopu_vjp_rollout, hopu_energy
+ * and by hopu_apply_convection* when their facet_l is NULL.  NULL restores the
+ * context's uniform l.  Not itself asynchronous: the cached substep graph is dropped. */
+hopu_status hopu_set_facet_l(hopu_ctx* ctx, const int8_t* facet_l);
+
+/* Adaptive HOPU (Section 3.2): for every facet the average absolute jump
+ *   eta = int_F |(I - Pi^l)[[u]]| ds / int_F |<u>| ds
+ * of the L2 field u_l2, with l the facet's current order in facet_l (device int8
+ * [n_facets], in/out); then the new order: l = i for eta_i < eta <= eta_{i+1}, -1 for
+ * eta <= eta_0, k for eta > eta_k (eta_{k+1} = 1 and eta > 1 both give k; a zero
+ * average with a non-zero jump counts as eta = +inf), written back to facet_l.
+ * thresholds: host, k+1 increasing values in (0, 1) (EINVAL otherwise).  eta_out:
+ * device FP64 [n_facets] or NULL.  Sums and the decision in FP64.  The paper repeats
+ * this every 10th time step (the caller's loop; see the Python binding).           */
+hopu_status hopu_adapt_l(hopu_ctx* ctx, const void* u_l2, const double* thresholds, int8_t* facet_l,
+                         double* eta_out);
 
 /* Reverse-mode derivative (vector-Jacobian product) of y = hopu_apply_convection(w, u)
  * with the context's l.  The apply is linear in u and, on facets, depends on w through

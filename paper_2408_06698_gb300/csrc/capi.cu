@@ -312,7 +312,7 @@ hopu_status enqueue_stage_apply(hopu_ctx* c, const void* uL, const void* wL, int
 // STAGE wind, after u_L = E u_V: facet flux, volume term with the element part of the
 // back-projection fused in (when the kernel family has it), facet averaging R.
 hopu_status enqueue_stage_fused(hopu_ctx* c, Combine cmb, void* outV) {
-  timed(c, HOPU_K_FACET, [&] { c->ops->facet(c->dm, c->dt, c->d_uL, c->d_uL, c->l, nullptr, c->d_gam, nullptr, c->stream); });
+  timed(c, HOPU_K_FACET, [&] { c->ops->facet(c->dm, c->dt, c->d_uL, c->d_uL, c->l, c->facet_l, c->d_gam, nullptr, c->stream); });
   if (c->ops->has_fused()) {
     timed(c, HOPU_K_VOLUME, [&] { c->ops->volume_l2v(c->dm, c->dt, c->d_uL, c->d_gam, c->d_lf, cmb, outV, c->stream); });
   } else {
@@ -362,7 +362,7 @@ hopu_status enqueue_substep(hopu_ctx* c, void* state, double dt) {
       hopu_status r = enqueue_stage_fused(c, st[s], out[s]);
       if (r != HOPU_OK) return r;
     } else {
-      hopu_status r = enqueue_stage_apply(c, in[s], c->d_wfz, c->l, nullptr, nullptr, st[s], out[s]);
+      hopu_status r = enqueue_stage_apply(c, in[s], c->d_wfz, c->l, c->facet_l, nullptr, st[s], out[s]);
       if (r != HOPU_OK) return r;
     }
   }
@@ -382,7 +382,7 @@ hopu_status ensure_gamW(hopu_ctx* c) {
 // part + lift.  wL == uL means w = u (ubar then receives ubar + wbar, wbarL unused).
 void enqueue_apply_vjp(hopu_ctx* c, const void* uL, const void* wL, const void* ybar, void* ubar, void* wbarL) {
   timed(c, HOPU_K_FACET_ADJ, [&] {
-    c->ops->facet_adj(c->dm, c->dt, uL, wL, ybar, c->l, nullptr, c->d_gam, c->d_gamW, c->stream);
+    c->ops->facet_adj(c->dm, c->dt, uL, wL, ybar, c->l, c->facet_l, c->d_gam, c->d_gamW, c->stream);
   });
   timed(c, HOPU_K_VOLUME_ADJ, [&] {
     c->ops->volume_adj(c->dm, c->dt, uL, wL, ybar, c->d_gam, c->d_gamW, ubar, wbarL, c->stream);
@@ -645,7 +645,7 @@ hopu_status hopu_apply_convection(hopu_ctx* c, const void* w_hdiv, const void* u
     return fail(c, HOPU_EINVAL, "apply_convection: vectors must be 16-byte aligned");
   enqueue_v2l(c, w_hdiv, c->d_wL);
   Combine plain;
-  return enqueue_stage_apply(c, u_l2, c->d_wL, c->l, facet_l, nullptr, plain, y_l2);
+  return enqueue_stage_apply(c, u_l2, c->d_wL, c->l, facet_l ? facet_l : c->facet_l, nullptr, plain, y_l2);
 }
 
 hopu_status hopu_set_frozen_wind(hopu_ctx* c, const void* w_hdiv) {
@@ -711,7 +711,7 @@ hopu_status hopu_energy(hopu_ctx* c, const void* w_hdiv, const void* u_l2, doubl
   if (w_hdiv) {
     enqueue_v2l(c, w_hdiv, c->d_wL);
     Combine plain;
-    r = enqueue_stage_apply(c, u_l2, c->d_wL, c->l, nullptr, c->d_diss, plain, c->d_yL);
+    r = enqueue_stage_apply(c, u_l2, c->d_wL, c->l, c->facet_l, c->d_diss, plain, c->d_yL);
     if (r != HOPU_OK) return r;
     // c(w;u,u) = sum_T |det J| u . y  (y = M^{-1} r, M = |det J| I)
     r = weighted_dot(c, u_l2, c->d_yL, 1);
@@ -846,6 +846,31 @@ hopu_status hopu_vjp_rollout(hopu_ctx* c, const void* u0_hdiv, double dt, int n_
   r = body();
   c->elog = elog;
   return r;
+}
+
+hopu_status hopu_set_facet_l(hopu_ctx* c, const int8_t* facet_l) {
+  HOPU_PRECHECK(c);
+  if (c->facet_l != facet_l && c->gexec) {  // the cached substep graph holds the old pointer
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->facet_l = facet_l;
+  return HOPU_OK;
+}
+
+hopu_status hopu_adapt_l(hopu_ctx* c, const void* u_l2, const double* thresholds, int8_t* facet_l,
+                         double* eta_out) {
+  HOPU_PRECHECK(c);
+  if (!u_l2 || !thresholds || !facet_l) return fail(c, HOPU_EINVAL, "adapt_l: NULL pointer");
+  if (!aligned16(u_l2)) return fail(c, HOPU_EINVAL, "adapt_l: u must be 16-byte aligned");
+  hopu::EtaThresholds th{};
+  for (int i = 0; i <= c->k; ++i) {
+    th.t[i] = thresholds[i];
+    if (!(thresholds[i] > (i ? thresholds[i - 1] : 0.0)) || !(thresholds[i] < 1.0))
+      return fail(c, HOPU_EINVAL, "adapt_l: need k+1 increasing thresholds in (0, 1)");
+  }
+  c->ops->eta(c->dm, c->dt, u_l2, c->l, facet_l, th, eta_out, c->stream);
+  return check_launch(c, "adapt_l kernel");
 }
 
 hopu_status hopu_points(hopu_ctx* c, int which, double* host_out, int64_t* count_out) {

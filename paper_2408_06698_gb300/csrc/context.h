@@ -47,6 +47,7 @@ struct hopu_ctx {
   double* d_red = nullptr;  // partial sums + 4 scalars
   int* d_err = nullptr;     // device error word (DevMesh::err)
   bool have_frozen = false;
+  const int8_t* facet_l = nullptr;  // per-facet HOPU orders (hopu_set_facet_l), or NULL
   // per-substep kinetic-energy log (device ring buffer owned by the caller)
   double* elog = nullptr;
   int64_t elog_cap = 0;

@@ -55,6 +55,11 @@ struct Combine {
   float h2 = float(a2), l2 = float(a2 - double(float(a2)));
 };
 
+// thresholds eta_0 < ... < eta_k of the adaptive HOPU order rule (k + 1 <= 6 values)
+struct EtaThresholds {
+  double t[6];
+};
+
 // layout of the working-precision geometry record (offsets in elements)
 inline constexpr int geoT_stride(int d) { return ((3 * d * d + 1 + 3) / 4) * 4; }
 
@@ -85,6 +90,9 @@ class Ops {
   // adjoint kernels: (R E_T^{-1})^T, the facet and the volume parts of the VJP of the
   // apply (ybar = cotangent of y; wL == uL means w = u and the cotangents are summed
   // into ubar, wbar unused); gamU / gamW are element-major facet-moment scratch.
+  // adaptive HOPU: eta per facet with the current orders, new orders written in place
+  virtual int eta(const DevMesh&, const DevTabs&, const void* uL, int l, int8_t* facet_l,
+                  const EtaThresholds& th, double* eta_out, cudaStream_t) = 0;
   virtual int v2l_pt(const DevMesh&, const DevTabs&, const void* vV, void* yL, cudaStream_t) = 0;
   virtual int facet_adj(const DevMesh&, const DevTabs&, const void* uL, const void* wL, const void* ybar,
                         int l, const int8_t* facet_l, void* gamU, void* gamW, cudaStream_t) = 0;

@@ -93,7 +93,7 @@ extern "C" hopu_status hopu_apply_convection_noalloc(hopu_ctx* c, const void* w_
 
   hopu::Combine plain;
   c->ops->v2l(c->dm, c->dt, w_hdiv, wl, c->stream);
-  c->ops->facet(c->dm, c->dt, u_l2, wl, c->l, facet_l, gam, nullptr, c->stream);
+  c->ops->facet(c->dm, c->dt, u_l2, wl, c->l, facet_l ? facet_l : c->facet_l, gam, nullptr, c->stream);
   c->ops->volume(c->dm, c->dt, u_l2, wl, gam, plain, y_l2, c->stream);
   e = cudaGetLastError();
   if (e != cudaSuccess)

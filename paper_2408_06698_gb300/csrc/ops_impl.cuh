@@ -6,6 +6,7 @@
 #include "kernels.cuh"
 #include "kernels_adj.cuh"
 #include "kernels_tc.cuh"
+#include "kernels_adapt.cuh"
 
 namespace hopu {
 
@@ -58,7 +59,11 @@ class OpsImpl final : public Ops {
     return kWarps * (2 * size_t(D) * r4(S::nb) + size_t(D) * D * r4(kNB1) + (wsep ? size_t(D) * r4(S::nb) : 0) +
                      2 * r4(size_t(D + 1) * S::nf * D)) * sz;
   }
-  int g_fadj_ = 1, g_vadj_ = 1;
+  int g_fadj_ = 1, g_vadj_ = 1, g_eta_ = 1;
+  static constexpr size_t eta_smem() {
+    return (r4(size_t(D + 1) * S::nf * r4(S::nb) + S::nf * S::nqf + S::nqf) +
+            kWarps * (2 * size_t(D) * r4(S::nb) + 2 * S::nf * 4)) * sz;
+  }
   int nsm_ = 1;
   int tc_ = 0;  // FP32 only: 0 = FMA, 3 = 3xTF32 tensor cores, 1 = 1xTF32 tensor cores
   int g_v2l_tc_ = 1;
@@ -121,6 +126,7 @@ class OpsImpl final : public Ops {
         if (err != cudaSuccess) return err;
       }
     }
+    if ((err = setup(k_eta<D, K, T>, eta_smem(), th, &g_eta_)) != cudaSuccess) return err;
     if ((err = setup(k_facet_adj<D, K, T, false>, facet_adj_smem(false), th, &g_fadj_)) != cudaSuccess) return err;
     if ((err = setup(k_facet_adj<D, K, T, true>, facet_adj_smem(true), th, &g_fadj_)) != cudaSuccess) return err;
     if ((err = setup(k_volume_adj<D, K, T, false>, volume_adj_smem(false), th, &g_vadj_)) != cudaSuccess) return err;
@@ -187,6 +193,13 @@ class OpsImpl final : public Ops {
   }
 
   bool has_fused() const override { return kFuse; }
+
+  int eta(const DevMesh& m, const DevTabs& t, const void* uL, int l, int8_t* facet_l, const EtaThresholds& th,
+          double* eta_out, cudaStream_t st) override {
+    const int g = clamp_grid(g_eta_, m.NF, kWarps);
+    k_eta<D, K, T><<<g, 32 * kWarps, eta_smem(), st>>>(m, t, static_cast<const T*>(uL), l, facet_l, th, eta_out);
+    return 1;
+  }
 
   int v2l_pt(const DevMesh& m, const DevTabs& t, const void* vV, void* yL, cudaStream_t st) override {
     const int g = clamp_grid(g_v2l_, m.E, PC::TE);

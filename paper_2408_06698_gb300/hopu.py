@@ -126,6 +126,52 @@ class Hopu:
                                               byref(loss) if seed is None else None), "hopu_vjp_rollout")
         return (float(loss.value) if seed is None else None), out
 
+    def set_facet_l(self, facet_l: torch.Tensor | None):
+        """Per-facet HOPU orders (int8 device tensor, kept referenced) for later calls; None = uniform l."""
+        if facet_l is None:
+            self._check(self.lib.hopu_set_facet_l(self.ctx, None), "hopu_set_facet_l")
+            self._facet_l = None
+            return
+        if facet_l.dtype != torch.int8 or facet_l.numel() != self.n_facets or facet_l.device != self.device \
+                or not facet_l.is_contiguous():
+            raise ValueError("facet_l must be a contiguous int8 device tensor with one entry per facet")
+        self._check(self.lib.hopu_set_facet_l(self.ctx, c_void_p(facet_l.data_ptr())), "hopu_set_facet_l")
+        self._facet_l = facet_l
+
+    def adapt_l(self, u_l2: torch.Tensor, thresholds, facet_l: torch.Tensor, eta_out: torch.Tensor | None = None):
+        """Adaptive HOPU: eta per facet with the current orders in facet_l, new orders written back."""
+        th = (c_double * (self.k + 1))(*[float(x) for x in thresholds])
+        if len(thresholds) != self.k + 1:
+            raise ValueError(f"need k+1 = {self.k + 1} thresholds")
+        if facet_l.dtype != torch.int8 or facet_l.numel() != self.n_facets or facet_l.device != self.device:
+            raise ValueError("facet_l must be an int8 device tensor with one entry per facet")
+        ep = None
+        if eta_out is not None:
+            if eta_out.dtype != torch.float64 or eta_out.numel() != self.n_facets or eta_out.device != self.device:
+                raise ValueError("eta_out must be a float64 device tensor with one entry per facet")
+            ep = c_void_p(eta_out.data_ptr())
+        self._sync_stream()
+        self._check(self.lib.hopu_adapt_l(self.ctx, self._vec(u_l2, self.n_l2, "u_l2"), th,
+                                          c_void_p(facet_l.data_ptr()), ep), "hopu_adapt_l")
+        return facet_l
+
+    def adaptive_substeps(self, state: torch.Tensor, dt: float, n_substeps: int, thresholds,
+                          facet_l: torch.Tensor, period: int = 10) -> torch.Tensor:
+        """STAGE substeps with adaptive HOPU orders: before every period-th substep (the
+        first included) the orders are re-determined from the current state."""
+        if self.wind != "stage":
+            raise ValueError("adaptive_substeps runs the STAGE wind rule")
+        self.set_facet_l(facet_l)
+        uL = self.new("l2")
+        done = 0
+        while done < n_substeps:
+            self.project("hdiv_to_l2", state, out=uL)
+            self.adapt_l(uL, thresholds, facet_l)
+            m = min(period, n_substeps - done)
+            self.rk_substep(state, dt, m)
+            done += m
+        return state
+
     def sync(self):
         """Synchronise the context stream; raises on a device-side failure (ETIMEOUT)."""
         self._check(self.lib.hopu_sync(self.ctx), "hopu_sync")
