@@ -256,6 +256,96 @@ def traffic_from_profiles(kernel: str):
     return ent.get("dram_bytes_per_launch_full_size")
 
 
+def _events_ms(stream, fn, K):
+    """Device time (ms) of K calls of fn on stream, bracketed by CUDA events."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        stream.synchronize()
+        a.record(stream)
+        for _ in range(K):
+            fn()
+        b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b)
+
+
+def other_configs(dev, stream, world):
+    """2D k=2 FP64 (8x8x2 triangles), the 32^3 x 6 k=4 precision comparison and the
+    512-mesh batch: throughput in the headline's unit plus the stated errors."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2408_06698_gb300 import Hopu, HopuBatch
+    out = {}
+    # 2D periodic square, Taylor-Green (canonical interpolant), 1 apply + 100 substeps dt=1e-3
+    m = W.periodic_box_mesh(2, 8)
+    g = Hopu(m.coords, m.elems, m.rep, k=2, l=1, prec="f64", device=dev)
+    u = g.interpolate_function(W.taylor_green)
+    uL = g.project("hdiv_to_l2", u)
+    y = g.new("l2")
+    g.apply_convection(u, uL, out=y)
+    ms = _events_ms(stream, lambda: g.rk_substep(u, 1e-3, 1), 100)
+    out["square_8x8x2_k2_f64"] = {"elements": g.n_elems, "substeps": 100, "ms_per_substep": ms / 100,
+                                  "value": g.n_l2 * APPLIES_PER_STEP * 100 / (ms / 1e3), "unit": UNIT}
+    del g
+    # 32^3 x 6, k = 4: one apply in every precision against the FP64 GPU result (itself at
+    # oracle parity on small meshes), 10 substeps each with the per-substep energy drift
+    m = W.periodic_box_mesh(3, 32)
+    prec_rows = {}
+    ref_y = None
+    u64 = None
+    for prec in ("f64", "f32", "f32_tc", "tf32"):
+        g = Hopu(m.coords, m.elems, m.rep, k=4, l=3, prec=prec, device=dev)
+        if u64 is None:                          # one interpolant, rounded per precision
+            u64 = g.interpolate_function(W.taylor_green)
+            u64 += torch.as_tensor(W.uniform_noise(g.n_hdiv, 1e-3, 0), device=dev)
+        u = u64.to(g.dtype).clone()
+        with torch.cuda.stream(stream):
+            uL = g.project("hdiv_to_l2", u)
+            yv = g.apply_convection(u, uL)
+        stream.synchronize()
+        yd = yv.double()
+        if prec == "f64":
+            ref_y = yd
+        err = float((yd - ref_y).abs().max() / ref_y.abs().max())
+        log = torch.zeros(12, dtype=torch.float64, device=dev)
+        g.set_energy_log(log)
+        ms = _events_ms(stream, lambda: g.rk_substep(u, 5e-4, 1), 10)
+        g.set_energy_log(None)
+        e = log[:10].cpu().numpy()
+        prec_rows[prec] = {"ms_per_substep": ms / 10, "value": g.n_l2 * APPLIES_PER_STEP * 10 / (ms / 1e3),
+                           "unit": UNIT, "apply_max_rel_err_vs_gpu_f64": err,
+                           "energy_drift_per_substep": float(np.mean(np.diff(e)) / e[0])}
+        del g, u, uL, yv
+    out["box_32cubed_k4_precisions"] = {"elements": 6 * 32 ** 3, "substeps": 10, "by_precision": prec_rows}
+    # 512 meshes, n ~ U{4..12}, k ~ U{2..5} (seed 1), FP32, one graph replay per substep
+    draws = W.batch_draws(512, seed=1)
+    meshes = [W.periodic_box_mesh(3, n) for n, _ in draws]
+    b = HopuBatch([(mm.coords, mm.elems, mm.rep) for mm in meshes], [k for _, k in draws], l=-2, prec="f32",
+                  device=dev)
+    states = []
+    for c, v in enumerate(b.classes):
+        states.append(torch.as_tensor(W.uniform_noise(v.n_hdiv, 1.0, 1000 + c), device=dev).float())
+    b.rk_substep(states, 5e-4, 3)
+    K = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record()
+    for _ in range(K):
+        b.rk_substep(states, 5e-4, 1)
+    a1.record()
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    l2 = sum(v.n_l2 for v in b.classes)
+    out["batch_512_meshes_f32"] = {"meshes": 512, "elements": sum(mm.n_elems for mm in meshes),
+                                   "order_classes": len(b.classes), "substeps": K, "ms_per_substep": ms / K,
+                                   "value": l2 * APPLIES_PER_STEP * K / (ms / 1e3), "unit": UNIT}
+    b.close()
+    return out
+
+
 def our_arm(args, rank, world):
     import numpy as np
     import torch
@@ -365,7 +455,7 @@ def our_arm(args, rank, world):
     dtc, _, acctc, _, _ = timed_steps(gtc, stc, Ktc, Wm, profile=True)
     dtc = max_over_ranks(dtc, world)
     fp32_tc = {"value": whole_job_value(dofs * Ktc, world, dtc / 1e3), "unit": UNIT, "steps": Ktc,
-               "ms_per_step": dtc / Ktc,
+               "ms_per_step": dtc / Ktc, "autotuned_variants": gtc.tuning(),
                "kernels": {f: {"avg_us": 1e3 * acctc[f][0] / max(1, acctc[f][1]), "launches": acctc[f][1]}
                            for f in FAMILIES}}
     del gtc, stc
@@ -393,6 +483,9 @@ def our_arm(args, rank, world):
                "ms_rollout_and_adjoint": vms, "loss": loss_v,
                "dof_updates_per_s_forward_equivalent": gv.n_l2 * APPLIES_PER_STEP * 200 / (vms / 1e3)}
         del gv, uv
+
+    # ---------------- the other configurations (extra keys; the headline is 16^3 x 6)
+    others = None if args.quick else other_configs(dev, stream, world)
 
     # ---------------- roofline of the dominant kernel (FP32 run, live CUDA events)
     alg = algorithmic(dim, k, g32.n_elems, g32.n_facets, 4)
@@ -435,7 +528,7 @@ def our_arm(args, rank, world):
                    "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "fp64": fp64,
-        "fp32_tc": fp32_tc, "vjp": vjp,
+        "fp32_tc": fp32_tc, "vjp": vjp, "other_configs": others,
         "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernels,
         "kernels_f64": {f: {"avg_us": 1e3 * acc64[f][0] / max(1, acc64[f][1]), "launches": acc64[f][1]}
                         for f in FAMILIES},
@@ -476,6 +569,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-vjp", action="store_true", help="skip the rollout-adjoint measurement")
+    ap.add_argument("--quick", action="store_true", help="skip the 2D, 32^3 and batch configurations")
     ap.add_argument("--ref-budget-s", type=float, default=150.0,
                     help="seconds of oracle work the reference arm aims for (sizes its per-step sample)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)

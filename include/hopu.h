@@ -110,7 +110,9 @@ typedef struct {
                      0..k = Pi^l of Section 3.2 (l = k: central flux)                      */
   int prec;       /* hopu_prec                                                            */
   int wind_mode;  /* hopu_wind, used by hopu_rk_substep                                    */
-  int tile_hint;  /* 0 = library default; reserved for launch-shape tuning                 */
+  int tile_hint;  /* kernel variants in the tensor-core modes: 0 = autotune (time the FP32
+                     FMA and the tensor-core kernel of each family on this mesh at create
+                     and keep the faster), 1 = FMA kernels, 2 = tensor-core kernels      */
 } hopu_options;
 
 /* Build a context: validate and copy the mesh, compute FP64 geometry (Jacobians, Piola
@@ -126,6 +128,11 @@ hopu_status hopu_destroy(hopu_ctx* ctx);
 
 /* Replace the stream later calls enqueue on. */
 hopu_status hopu_set_stream(hopu_ctx* ctx, void* cuda_stream);
+
+/* Kernel variants in use: out2[0] for the V_h -> L2 projection, out2[1] for the fused
+ * STAGE volume kernel; 0 = FP32 FMA kernel, 1 = tensor-core kernel.  No paper
+ * counterpart (launch tuning).                                                        */
+hopu_status hopu_tuning(const hopu_ctx* ctx, int* out2);
 
 /* Synchronise the context stream and report device-side failures: ETIMEOUT when a
  * tensor-core kernel (HOPU_FP32_TC / HOPU_TF32) gave up waiting for its MMAs (its

@@ -203,7 +203,7 @@ void free_all(hopu_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
-                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err};
+                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err, c->d_tcvol};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c->ops;
@@ -291,6 +291,39 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
   Drow.assign((size_t)nl * nlr, 0.0);
   for (int r = 0; r < nl; ++r)
     for (int s = 0; s < nl; ++s) Drow[(size_t)r * nlr + s] = R.D[(size_t)r * nl + s];
+}
+
+// Round an FP32 value to TF32 (10 mantissa bits), to nearest with ties away from zero.
+float tf32_round(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// Tables of the tensor-core volume kernel, FP32, in the blocked K-major operand layout of
+// the tensor cores (core matrices of 8 rows x 4 values, 128 bytes each):
+//   phiA[q][i] = phi_i(x_q)  (128 x KP1, KP1 = nb rounded up to 8)   hi part, then lo part
+//   phiB[i][q] = phi_i(x_q)  (N2 x 128, N2 = nb rounded up to 16)     hi part, then lo part
+// hi = tf32(phi), lo = tf32(phi - hi); zero outside the points and the basis.
+void tensor_core_volume_table(const RefTables& R, std::vector<float>& out) {
+  const int nb = R.nb, nq = R.nq, KP1 = (nb + 7) / 8 * 8, N2 = (nb + 15) / 16 * 16, K2 = 128;
+  const size_t PA = (size_t)128 * KP1, PB = (size_t)N2 * K2;
+  out.assign(2 * PA + 2 * PB, 0.0f);
+  auto off = [](int row, int col, int kp) {
+    return (size_t)(((row >> 3) * (kp >> 2) + (col >> 2)) * 32 + (row & 7) * 4 + (col & 3));
+  };
+  for (int q = 0; q < nq && q < 128; ++q)
+    for (int i = 0; i < nb; ++i) {
+      const float v = (float)R.phi[(size_t)q * nb + i];
+      const float h = tf32_round(v), l = tf32_round(v - h);
+      out[off(q, i, KP1)] = h;
+      out[PA + off(q, i, KP1)] = l;
+      out[2 * PA + off(i, q, K2)] = h;
+      out[2 * PA + PB + off(i, q, K2)] = l;
+    }
 }
 
 void enqueue_v2l(hopu_ctx* c, const void* uV, void* uL) {
@@ -453,6 +486,66 @@ hopu_status weighted_dot(hopu_ctx* c, const void* a, const void* b, int slot) {
 namespace {
 thread_local std::string g_create_error;
 
+// Autotuner of the kernel variants.  In the tensor-core precision modes each kernel
+// family that has both an FP32 FMA and a tensor-core kernel is timed on this context's
+// mesh (zero-filled scratch; one warm-up launch, then three launches between CUDA
+// events on the context stream) and the faster variant is kept.  tile_hint 1 keeps the
+// FMA kernels, 2 the tensor-core kernels.  The choice is reported by hopu_tuning.
+hopu_status autotune(hopu_ctx* c, int hint) {
+  Ops* o = c->ops;
+  if (!o->tensor_cores() && !o->tensor_core_volume()) return HOPU_OK;
+  if (hint == 1 || hint == 2) {
+    o->select(hint == 2, hint == 2);
+    return HOPU_OK;
+  }
+  const int64_t nstate = std::max(c->n_hdiv, c->n_l2);
+  HOPU_CUDA(c, cudaMemsetAsync(c->d_s1, 0, c->tsize * nstate, c->stream));
+  HOPU_CUDA(c, cudaMemsetAsync(c->d_uL, 0, c->tsize * c->n_l2, c->stream));
+  HOPU_CUDA(c, cudaMemsetAsync(c->d_gam, 0, c->tsize * c->topo.n_elems * (c->dim + 1) * c->ref.nf * c->dim,
+                               c->stream));
+  cudaEvent_t a = nullptr, b = nullptr;
+  HOPU_CUDA(c, cudaEventCreate(&a));
+  HOPU_CUDA(c, cudaEventCreate(&b));
+  auto timed_ms = [&](auto&& launch) -> float {
+    launch();
+    cudaEventRecord(a, c->stream);
+    for (int i = 0; i < 3; ++i) launch();
+    cudaEventRecord(b, c->stream);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 1e30f;
+    return ms;
+  };
+  Combine plain;
+  // the element part of a STAGE stage after the facet kernel: fused volume + back-projection
+  // when the family has it, else the volume kernel and the element back-projection
+  auto stage_volume = [&]() {
+    if (!o->volume_l2v(c->dm, c->dt, c->d_uL, c->d_gam, c->d_lf, plain, c->d_s2, c->stream)) {
+      o->volume(c->dm, c->dt, c->d_uL, c->d_uL, c->d_gam, plain, c->d_yL, c->stream);
+      o->l2v_elem(c->dm, c->dt, c->d_yL, false, c->d_lf, plain, c->d_s2, c->stream);
+    }
+  };
+  int v2l = 0, vol = 0;
+  if (o->tensor_cores()) {
+    o->select(0, 0);
+    const float t0 = timed_ms([&] { o->v2l(c->dm, c->dt, c->d_s1, c->d_uL, c->stream); });
+    o->select(1, 0);
+    const float t1 = timed_ms([&] { o->v2l(c->dm, c->dt, c->d_s1, c->d_uL, c->stream); });
+    v2l = t1 < t0;
+  }
+  if (o->tensor_core_volume()) {
+    o->select(v2l, 0);
+    const float t0 = timed_ms(stage_volume);
+    o->select(v2l, 1);
+    const float t1 = timed_ms(stage_volume);
+    vol = t1 < t0;
+  }
+  o->select(v2l, vol);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
+  return device_status(c);
+}
+
 hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, void* cuda_stream, hopu_ctx** out) {
   if (!mesh || !opts) return HOPU_EINVAL;
   if (opts->prec != HOPU_FP64 && opts->prec != HOPU_FP32 && opts->prec != HOPU_FP32_TC && opts->prec != HOPU_TF32)
@@ -461,6 +554,7 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   if (mesh->dim != 2 && mesh->dim != 3) return HOPU_EINVAL;
   if (opts->k < 1 || opts->k > (mesh->dim == 2 ? 4 : 5)) return HOPU_ENOTSUP;
   if (opts->l < -1 || opts->l > opts->k) return HOPU_EINVAL;
+  if (opts->tile_hint < 0 || opts->tile_hint > 2) return HOPU_EINVAL;
   hopu_ctx* c = new (std::nothrow) hopu_ctx();
   if (!c) return HOPU_ENOMEM;
   c->dim = mesh->dim;
@@ -555,6 +649,13 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
                                     &c->dt.TrP,  &c->dt.Psi, &c->dt.WPsi,  &c->dt.Wf,
                                     &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow, &c->dt.Dn};
   for (int i = 0; i < kNumTables; ++i) *slots[i] = tb + offs[i];
+  if (c->ops->tensor_core_volume()) {
+    std::vector<float> tv;
+    tensor_core_volume_table(R, tv);
+    HOPU_CUDA(c, cudaMalloc(&c->d_tcvol, tv.size() * sizeof(float)));
+    HOPU_CUDA(c, cudaMemcpy(c->d_tcvol, tv.data(), tv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->dt.tcvol = c->d_tcvol;
+  }
 
   // scratch
   const size_t ts = c->tsize;
@@ -574,7 +675,7 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   c->dm.err = c->d_err;
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_elog_pos, sizeof(int64_t)));
   HOPU_CUDA(c, cudaMemset(c->d_elog_pos, 0, sizeof(int64_t)));
-  return HOPU_OK;
+  return autotune(c, opts->tile_hint);
 }
 }  // namespace
 
@@ -605,6 +706,13 @@ hopu_status hopu_destroy(hopu_ctx* c) {
 hopu_status hopu_set_stream(hopu_ctx* c, void* cuda_stream) {
   HOPU_PRECHECK(c);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return HOPU_OK;
+}
+
+hopu_status hopu_tuning(const hopu_ctx* c, int* out2) {
+  if (!c || !out2) return HOPU_EINVAL;
+  out2[0] = c->ops ? c->ops->selected_v2l() : 0;
+  out2[1] = c->ops ? c->ops->selected_volume() : 0;
   return HOPU_OK;
 }
 

@@ -32,6 +32,7 @@ struct hopu_ctx {
   void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
   void* d_geoT = nullptr;   // working-precision geometry factors
   void* d_tabs = nullptr;   // every reference table
+  void* d_tcvol = nullptr;  // tensor-core volume tables (FP32 tensor-core modes)
   void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major
   void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals
   void* d_uL = nullptr;     // L2 stage field

@@ -35,6 +35,8 @@ struct DevTabs {
   const void* DT = nullptr;     // [nloc][nlp]     DT[s][r]    = D[r][s]
   const void* Dinv = nullptr;   // [nloc][nlp]     Dinv[s][r]
   const void* Dn = nullptr;     // [nloc][nlp]     Dn[s][r] = D[s][r]
+  const void* tcvol = nullptr;  // FP32 tensor-core volume tables (phi in the two operand layouts,
+                                //   TF32 hi and lo parts), or NULL
   const void* Drow = nullptr;   // [nloc][nlr]     D[r][s] row-major, rows padded to nlr (an odd
                                 //                 multiple of 16 bytes), zero padding
 };
@@ -87,6 +89,11 @@ class Ops {
                          Combine c, void* outV, cudaStream_t) = 0;
   virtual bool has_fused() const = 0;
   virtual bool tensor_cores() const = 0;  // the V_h -> L2 projection runs on tensor cores
+  virtual bool tensor_core_volume() const = 0;  // a tensor-core fused STAGE volume kernel exists
+  // variant choice per kernel family (autotuner): 0 = FP32 FMA kernel, 1 = tensor-core kernel
+  virtual void select(int v2l_tc, int volume_tc) = 0;
+  virtual int selected_v2l() const = 0;
+  virtual int selected_volume() const = 0;
   // adjoint kernels: (R E_T^{-1})^T, the facet and the volume parts of the VJP of the
   // apply (ybar = cotangent of y; wL == uL means w = u and the cotangents are summed
   // into ubar, wbar unused); gamU / gamW are element-major facet-moment scratch.

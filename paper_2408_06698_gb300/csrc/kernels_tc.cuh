@@ -199,4 +199,304 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
   }
 }
 
+// ------------------------------------------------------------------------------------
+// a3 + a5 + fused a7 (element part), STAGE wind (w = u), on the tensor cores.
+//
+// Per CTA, super-chunks of EB = 40 elements, processed in chunks of EC = 8:
+//   X (B operand, 96 rows = 8 elements x 12 quantities, K = basis index padded to 24):
+//     the coefficients of u_a (3 rows) and of the modal reference gradients
+//     d^_c u_a = sum_j (Dm_c u_a)_j phi_j (9 rows, j < dim P^{k-1});
+//   GEMM1: D1[q][n] = sum_i phi_i(x_q) X[n][i]   (M = 128 quadrature points, N = 96)
+//     -> every thread (one quadrature point) reads u, grad^ u of 4 elements from TMEM,
+//        forms W = |det J| J^-1 u, div^ W and f_a = w_q (div^W u_a + W . grad^ u_a);
+//   F (A operand, rows (element, a) of the super-chunk, K = quadrature point);
+//   GEMM2: D2[(e,a)][i] = sum_q F[(e,a)][q] phi_i(x_q)   (M = 128 rows, 120 used, N = 32);
+//   epilogue: facet lift sum_fm TrM[fm][i] gam[e][fm][a], inverse mass 1/|det J|, the
+//     contravariant pull-back det J J^-1 and the local functionals D (back-projection),
+//     interior rows combined into the V_h output, facet rows to lf with the sign sigma.
+// Tables (phi in both operand layouts, hi and lo TF32 parts) arrive by one bulk copy.
+template <int D, int K>
+struct VolTc {
+  using S = Shape<D, K>;
+  static constexpr int NB = S::nb, NB1 = cnbasis(D, K - 1), NQ = S::nq, NL = S::nloc;
+  static constexpr int KP1 = (NB + 7) / 8 * 8;          // GEMM1 K (basis index)
+  static constexpr int QTY = D + D * D;                 // u_a and d^_c u_a
+  static constexpr int EC = 8;                          // elements per GEMM1
+  static constexpr int N1 = QTY * EC;                   // GEMM1 N
+  static constexpr int NCH = 5;                         // chunks per super-chunk
+  static constexpr int EB = EC * NCH;                   // elements per GEMM2
+  static constexpr int K2 = 128;                        // GEMM2 K (quadrature points)
+  static constexpr int N2 = (NB + 15) / 16 * 16;        // GEMM2 N (basis index)
+  static constexpr int THREADS = 512;                   // 16 warps: lane quarter w % 4, element group w / 4
+  static constexpr int GT = S::gt;
+  // bytes
+  static constexpr size_t PA = size_t(128) * KP1 * 4;   // phi, GEMM1 A operand (one part)
+  static constexpr size_t PB = size_t(N2) * K2 * 4;     // phi, GEMM2 B operand (one part)
+  static constexpr size_t TAB = 2 * PA + 2 * PB;        // the bulk-copied table
+  static constexpr size_t FB = size_t(128) * K2 * 4;    // F (one part)
+  static constexpr size_t XB = size_t(N1) * KP1 * 4;    // X (one part)
+  static constexpr size_t O_F = TAB, O_X = O_F + 2 * FB, O_U = O_X + 2 * XB;
+  static constexpr size_t O_GEO = O_U + size_t(EC) * NL * 4;
+  static constexpr size_t O_WQ = O_GEO + size_t(EB) * GT * 4;
+  static constexpr size_t O_DM = O_WQ + 128 * 4;
+  static constexpr size_t O_TRM = O_DM + size_t(D) * NB1 * NB * 4;
+  static constexpr size_t O_BAR = (O_TRM + size_t(D + 1) * S::nf * NB * 4 + 15) / 16 * 16;
+  static constexpr size_t SMEM = O_BAR + 32;
+  // the epilogue keeps y in the X region and the pulled-back coefficients in the lo part
+  // of F ahead of its last row group (rows 120..127, which must stay zero)
+  static constexpr int ZR = D * EB;                      // F rows from ZR on stay zero
+  static constexpr bool OK = (NQ <= 128) && N1 <= 256 && ZR <= 120 && ZR % 8 == 0 && SMEM <= 227 * 1024 &&
+                             size_t(EB) * NL * 4 <= 2 * XB && size_t(EB) * NL * 4 <= size_t(ZR / 8) * (K2 / 4) * 128;
+  static constexpr uint32_t TCOLS = 256;                // D1 at column 0, D2 at column 128
+};
+
+template <int D, int K>
+__global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __restrict__ tctab,
+                                                      const float* __restrict__ Dm_g, const float* __restrict__ Wq_g,
+                                                      const float* __restrict__ TrM_g, const float* __restrict__ Drow_g,
+                                                      int nlr, const float* __restrict__ uL,
+                                                      const float* __restrict__ gam, float* out, Combine cmb,
+                                                      float* __restrict__ lf) {
+  using C = VolTc<D, K>;
+  using S = Shape<D, K>;
+  constexpr int NB = C::NB, NB1 = C::NB1, NL = C::NL, NF = S::nf, NINT = S::nint, GT = C::GT;
+  constexpr int KP1 = C::KP1, QTY = C::QTY, EC = C::EC, N1 = C::N1, EB = C::EB, K2 = C::K2, N2 = C::N2;
+  constexpr int NT = C::THREADS, NG = (D + 1) * NF * D;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* sPAh = smem_raw;
+  unsigned char* sPAl = smem_raw + C::PA;
+  unsigned char* sPBh = smem_raw + 2 * C::PA;
+  unsigned char* sPBl = sPBh + C::PB;
+  unsigned char* sFh = smem_raw + C::O_F;
+  unsigned char* sFl = sFh + C::FB;
+  unsigned char* sXh = smem_raw + C::O_X;
+  unsigned char* sXl = sXh + C::XB;
+  float* sU = reinterpret_cast<float*>(smem_raw + C::O_U);     // [EC][NL]
+  float* sGeo = reinterpret_cast<float*>(smem_raw + C::O_GEO); // [EB][GT]
+  float* sWq = reinterpret_cast<float*>(smem_raw + C::O_WQ);   // [128]
+  float* sDm = reinterpret_cast<float*>(smem_raw + C::O_DM);   // [D][NB1][NB]
+  float* sTrM = reinterpret_cast<float*>(smem_raw + C::O_TRM); // [(D+1) NF][NB]
+  uint64_t* mb_tab = reinterpret_cast<uint64_t*>(smem_raw + C::O_BAR);
+  uint64_t* mb_mma = mb_tab + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mb_tab + 2);
+  float* sY = reinterpret_cast<float*>(sXh);                   // [EB][NL] (epilogue, X is free)
+  float* sCh = reinterpret_cast<float*>(sFl);                  // [EB][NL] (epilogue, F is free)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* geoT = static_cast<const float*>(m.geoT);
+
+  if (warp == 0) tc::tmem_alloc(tslot, C::TCOLS);
+  if (tid == 0) {
+    tc::mbar_init(mb_tab, 1);
+    tc::mbar_init(mb_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    tc::mbar_expect_tx(mb_tab, (uint32_t)C::TAB);
+    tc::bulk_g2s(smem_raw, tctab, (uint32_t)C::TAB, mb_tab);
+  }
+  for (int t = tid; t < 128; t += NT) sWq[t] = t < S::nq ? Wq_g[t] : 0.0f;
+  for (int t = tid; t < D * NB1 * NB; t += NT) sDm[t] = Dm_g[t];
+  for (int t = tid; t < (D + 1) * NF * NB; t += NT) sTrM[t] = TrM_g[t];
+  // rows ZR .. 127 of F stay zero
+  for (int t = tid; t < (128 - C::ZR) * K2; t += NT) {
+    const int row = C::ZR + t / K2, q = t % K2;
+    *reinterpret_cast<float*>(sFh + tc::blk_off(row, q, K2)) = 0.0f;
+    *reinterpret_cast<float*>(sFl + tc::blk_off(row, q, K2)) = 0.0f;
+  }
+  bool ok = __syncthreads_and(tc::mbar_wait(mb_tab, 0)) != 0;
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t id1 = tc::idesc_tf32(128, N1), id2 = tc::idesc_tf32(128, N2);
+  uint32_t phase = 0;
+  const int64_t nsc = (m.E + EB - 1) / EB;
+  const int qrow = (warp & 3) * 32 + lane;              // TMEM lane of this thread
+  const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+  for (int64_t sc = blockIdx.x; ok && sc < nsc; sc += gridDim.x) {
+    const int64_t e0 = sc * EB;
+    for (int t = tid; t < EB * GT; t += NT) {
+      const int64_t e = e0 + t / GT;
+      sGeo[t] = e < m.E ? geoT[e0 * GT + t] : 0.0f;
+    }
+#pragma unroll 1
+    for (int c = 0; c < C::NCH && ok; ++c) {
+      const int64_t ec = e0 + c * EC;
+      for (int t = tid; t < EC * NL; t += NT) sU[t] = (ec + t / NL < m.E) ? uL[ec * NL + t] : 0.0f;
+      __syncthreads();
+      // X rows (element el, quantity qq): qq < D -> u_a, else grad^ of u_a in direction cc
+      for (int t = tid; t < N1 * KP1; t += NT) {
+        const int n = t / KP1, j = t - n * KP1;
+        const int el = n / QTY, qq = n - el * QTY;
+        float v = 0.0f;
+        if (qq < D) {
+          if (j < NB) v = sU[el * NL + qq * NB + j];
+        } else if (j < NB1) {
+          const int a = (qq - D) / D, cc = (qq - D) - a * D;
+          const float* dm = sDm + (cc * NB1 + j) * NB;
+          const float* uu = sU + el * NL + a * NB;
+          float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+          for (int i = 0; i < NB; ++i) p[i & 3] = fmaf(dm[i], uu[i], p[i & 3]);
+          v = (p[0] + p[1]) + (p[2] + p[3]);
+        }
+        float h, l;
+        tc::split_tf32(v, h, l, true);
+        *reinterpret_cast<float*>(sXh + tc::blk_off(n, j, KP1)) = h;
+        *reinterpret_cast<float*>(sXl + tc::blk_off(n, j, KP1)) = l;
+      }
+      tc::fence_smem_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        constexpr uint32_t SBA = (KP1 / 4) * 128;
+        const uint32_t aH = tc::smem_u32(sPAh), aL = tc::smem_u32(sPAl);
+        const uint32_t bH = tc::smem_u32(sXh), bL = tc::smem_u32(sXl);
+#pragma unroll 1
+        for (int ks = 0; ks < KP1 / 8; ++ks) {
+          const uint32_t off = ks * 256;
+          tc::mma_tf32(tbase, tc::sdesc(aH + off, 128, SBA), tc::sdesc(bH + off, 128, SBA), id1, ks > 0);
+          tc::mma_tf32(tbase, tc::sdesc(aH + off, 128, SBA), tc::sdesc(bL + off, 128, SBA), id1, 1);
+          tc::mma_tf32(tbase, tc::sdesc(aL + off, 128, SBA), tc::sdesc(bH + off, 128, SBA), id1, 1);
+        }
+        tc::commit(mb_mma);
+      }
+      ok = __syncthreads_and(tc::mbar_wait(mb_mma, phase)) != 0;
+      phase ^= 1u;
+      tc::fence_after_sync();
+      if (!ok) break;
+      // pointwise: quadrature point qrow, elements 4 (warp / 4) .. +3 of the chunk
+      const float wq = sWq[qrow];
+#pragma unroll 1
+      for (int el = (warp >> 2) * (EC / 4); el < (warp >> 2) * (EC / 4) + EC / 4; ++el) {
+        float v[16];
+        tc::ld16(tbase + tlane + (uint32_t)(el * QTY), v);
+        const float* g = sGeo + (c * EC + el) * GT;
+        float u[D], G[D][D], W[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          u[a] = v[a];
+#pragma unroll
+          for (int cc = 0; cc < D; ++cc) G[a][cc] = v[D + a * D + cc];
+        }
+        float dv = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) {
+          float s = 0.0f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            const float Mcb = g[2 * D * D + cc * D + b];
+            s = fmaf(Mcb, u[b], s);
+            dv = fmaf(Mcb, G[b][cc], dv);
+          }
+          W[cc] = s;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float f = dv * u[a];
+#pragma unroll
+          for (int cc = 0; cc < D; ++cc) f = fmaf(W[cc], G[a][cc], f);
+          f *= wq;
+          float h, l;
+          tc::split_tf32(f, h, l, true);
+          const int row = (c * EC + el) * D + a;
+          *reinterpret_cast<float*>(sFh + tc::blk_off(row, qrow, K2)) = h;
+          *reinterpret_cast<float*>(sFl + tc::blk_off(row, qrow, K2)) = l;
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+    if (!ok) break;
+    // GEMM2: D2[(e,a)][i] = sum_q F[(e,a)][q] phi_i(x_q)
+    tc::fence_smem_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      constexpr uint32_t SB2 = (K2 / 4) * 128;
+      const uint32_t aH = tc::smem_u32(sFh), aL = tc::smem_u32(sFl);
+      const uint32_t bH = tc::smem_u32(sPBh), bL = tc::smem_u32(sPBl);
+#pragma unroll 1
+      for (int ks = 0; ks < K2 / 8; ++ks) {
+        const uint32_t off = ks * 256;
+        tc::mma_tf32(tbase + 128, tc::sdesc(aH + off, 128, SB2), tc::sdesc(bH + off, 128, SB2), id2, ks > 0);
+        tc::mma_tf32(tbase + 128, tc::sdesc(aH + off, 128, SB2), tc::sdesc(bL + off, 128, SB2), id2, 1);
+        tc::mma_tf32(tbase + 128, tc::sdesc(aL + off, 128, SB2), tc::sdesc(bH + off, 128, SB2), id2, 1);
+      }
+      tc::commit(mb_mma);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(mb_mma, phase)) != 0;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok) break;
+    // epilogue 1: row (e, a) = qrow; warps w and w + 4 split the basis index range
+    {
+      float r[N2];
+#pragma unroll
+      for (int c0 = 0; c0 < N2; c0 += 16) tc::ld16(tbase + tlane + 128u + (uint32_t)c0, r + c0);
+      tc::fence_before_sync();
+      const int el = qrow / D, a = qrow - el * D;
+      const int64_t e = e0 + el;
+      if (qrow < D * EB && e < m.E) {
+        constexpr int PART = (NB + 3) / 4;
+        const int i0 = (warp >> 2) * PART, i1 = i0 + PART < NB ? i0 + PART : NB;
+        const float invabs = sGeo[el * GT + 3 * D * D];
+        const float* gl = gam + e * NG;
+        float gv[(D + 1) * NF];
+#pragma unroll
+        for (int fm = 0; fm < (D + 1) * NF; ++fm) gv[fm] = __ldg(gl + fm * D + a);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i < i0 || i >= i1) continue;
+          float p[4] = {r[i], 0.0f, 0.0f, 0.0f};
+#pragma unroll
+          for (int fm = 0; fm < (D + 1) * NF; ++fm) p[fm & 3] = fmaf(sTrM[fm * NB + i], gv[fm], p[fm & 3]);
+          sY[el * NL + a * NB + i] = ((p[0] + p[1]) + (p[2] + p[3])) * invabs;
+        }
+      }
+    }
+    __syncthreads();
+    // epilogue 2: chat = det J Jinv y, then ell = D chat, combined into the outputs
+    for (int t = tid; t < EB * NL; t += NT) {
+      const int el = t / NL, s2 = t - el * NL;
+      const int b = s2 / NB, i = s2 - b * NB;
+      const float* g = sGeo + el * GT;
+      float acc = 0.0f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc = fmaf(g[D * D + b * D + a], sY[el * NL + a * NB + i], acc);
+      sCh[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < EB * NL; t += NT) {
+      const int el = t / NL, rr = t - el * NL;
+      const int64_t e = e0 + el;
+      if (e >= m.E) continue;
+      const float* drow = Drow_g + rr * nlr;
+      const float* ch = sCh + el * NL;
+      float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int s2 = 0; s2 < NL; ++s2) p[s2 & 3] = fmaf(__ldg(drow + s2), ch[s2], p[s2 & 3]);
+      const float v = (p[0] + p[1]) + (p[2] + p[3]);
+      if (rr < (D + 1) * NF) {
+        const int code = m.efc[e * (D + 1) + rr / NF];
+        lf[e * (D + 1) * NF + rr] = (code & 2) ? -v : v;
+      } else {
+        const int64_t idx = m.NF * NF + e * NINT + (rr - (D + 1) * NF);
+        out[idx] = combine_at<float>(cmb, v, idx);
+      }
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(m.err, kErrTcTimeout);
+    tc::mbar_wait(mb_tab, 0);          // bounded: the table copy and the MMAs in flight drain
+    tc::mbar_wait(mb_mma, phase ^ 1u);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, C::TCOLS);
+  }
+}
+
 }  // namespace hopu

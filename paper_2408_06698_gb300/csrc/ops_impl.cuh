@@ -68,6 +68,9 @@ class OpsImpl final : public Ops {
   int tc_ = 0;  // FP32 only: 0 = FMA, 3 = 3xTF32 tensor cores, 1 = 1xTF32 tensor cores
   int g_v2l_tc_ = 1;
   static constexpr bool kTcV2l = std::is_same<T, float>::value && V2lTc<D, K>::OK;
+  static constexpr bool kTcVol = std::is_same<T, float>::value && VolTc<D, K>::OK;
+  int g_vol_tc_ = 1;
+  bool use_tc_v2l_ = true, use_tc_vol_ = true;  // autotuner choices (tensor-core modes)
   int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
 
   template <typename Kern>
@@ -109,6 +112,13 @@ class OpsImpl final : public Ops {
  public:
   explicit OpsImpl(int tc = 0) : tc_(std::is_same<T, float>::value ? tc : 0) {}
   bool tensor_cores() const override { return tc_ != 0 && kTcV2l; }
+  bool tensor_core_volume() const override { return tc_ != 0 && kTcVol; }
+  void select(int v2l_tc, int volume_tc) override {
+    use_tc_v2l_ = v2l_tc != 0 && tensor_cores();
+    use_tc_vol_ = volume_tc != 0 && tensor_core_volume();
+  }
+  int selected_v2l() const override { return (use_tc_v2l_ && tensor_cores()) ? 1 : 0; }
+  int selected_volume() const override { return (use_tc_vol_ && tensor_core_volume()) ? 1 : 0; }
 
   cudaError_t prepare() override {
     int dev = 0;
@@ -119,6 +129,11 @@ class OpsImpl final : public Ops {
     const int th = 32 * kWarps;
     if ((err = setup(k_v2l<D, K, T, false>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
     if ((err = setup(k_v2l<D, K, T, true>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
+    if constexpr (kTcVol) {
+      if (tc_ && (err = setup(k_volume_tc<D, K>, VolTc<D, K>::SMEM, VolTc<D, K>::THREADS, &g_vol_tc_, true)) !=
+                     cudaSuccess)
+        return err;
+    }
     if constexpr (kTcV2l) {
       if (tc_) {
         if (tc_ == 3) err = setup(k_v2l_tc<D, K, true>, V2lTc<D, K>::SMEM, V2lTc<D, K>::THREADS, &g_v2l_tc_, true);
@@ -146,7 +161,7 @@ class OpsImpl final : public Ops {
 
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
     if constexpr (kTcV2l) {
-      if (tc_) {
+      if (tc_ && use_tc_v2l_) {
         const int g = clamp_grid(g_v2l_tc_, m.E, V2lTc<D, K>::TM);
         const int nlp = (S::nloc + 3) / 4 * 4;
         if (tc_ == 3)
@@ -192,7 +207,7 @@ class OpsImpl final : public Ops {
     return 1;
   }
 
-  bool has_fused() const override { return kFuse; }
+  bool has_fused() const override { return kFuse || (tc_ != 0 && kTcVol && use_tc_vol_); }
 
   int eta(const DevMesh& m, const DevTabs& t, const void* uL, int l, int8_t* facet_l, const EtaThresholds& th,
           double* eta_out, cudaStream_t st) override {
@@ -240,6 +255,17 @@ class OpsImpl final : public Ops {
 
   int volume_l2v(const DevMesh& m, const DevTabs& t, const void* uL, const void* gam, void* lf, Combine c,
                  void* outV, cudaStream_t st) override {
+    if constexpr (kTcVol) {
+      if (tc_ && use_tc_vol_ && t.tcvol) {
+        const int g = clamp_grid(g_vol_tc_, m.E, VolTc<D, K>::EB);
+        const int nlr = row_stride<float>(S::nloc);
+        k_volume_tc<D, K><<<g, VolTc<D, K>::THREADS, VolTc<D, K>::SMEM, st>>>(
+            m, static_cast<const float*>(t.tcvol), static_cast<const float*>(t.Dm), static_cast<const float*>(t.Wq),
+            static_cast<const float*>(t.TrM), static_cast<const float*>(t.Drow), nlr, static_cast<const float*>(uL),
+            static_cast<const float*>(gam), static_cast<float*>(outV), c, static_cast<float*>(lf));
+        return 1;
+      }
+    }
     if constexpr (kFuse) {
       const int g = clamp_grid(g_fuse_, m.E, kWarps);
       k_volume<D, K, T, false, true, true><<<g, 32 * kWarps, kFuseSmem, st>>>(

@@ -26,7 +26,7 @@ class Hopu:
     """
 
     def __init__(self, coords, elems, rep=None, k: int = 3, l: int = -1, prec: str = "f64",
-                 wind: str = "stage", device: str | torch.device = "cuda"):
+                 wind: str = "stage", device: str | torch.device = "cuda", tile_hint: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("libhopu needs a CUDA device")
         self.lib = L.load()
@@ -43,7 +43,7 @@ class Hopu:
         self.dim = int(self._coords.shape[1])
         desc = L.MeshDesc(self.dim, self._coords.shape[0], self._coords.ctypes.data, self._elems.shape[0],
                           self._elems.ctypes.data, None if self._rep is None else self._rep.ctypes.data)
-        opts = L.Options(k, l, _PREC[prec], _WIND[wind], 0)
+        opts = L.Options(k, l, _PREC[prec], _WIND[wind], int(tile_hint))
         self.ctx = c_void_p()
         with torch.cuda.device(self.device):
             st = self.lib.hopu_create(byref(desc), byref(opts), c_void_p(self._stream()), byref(self.ctx))
@@ -171,6 +171,12 @@ class Hopu:
             self.rk_substep(state, dt, m)
             done += m
         return state
+
+    def tuning(self) -> dict:
+        """Kernel variants the autotuner kept: {'v2l': 'fma'|'tc', 'volume': 'fma'|'tc'}."""
+        out = (ctypes.c_int * 2)()
+        self._check(self.lib.hopu_tuning(self.ctx, out), "hopu_tuning")
+        return {"v2l": "tc" if out[0] else "fma", "volume": "tc" if out[1] else "fma"}
 
     def sync(self):
         """Synchronise the context stream; raises on a device-side failure (ETIMEOUT)."""

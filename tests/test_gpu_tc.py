@@ -20,10 +20,11 @@ CASES = [(2, 4, 1), (2, 8, 2), (2, 4, 4), (3, 3, 1), (3, 3, 2), (3, 5, 3), (3, 3
 PTOL = {"f32_tc": 4e-6, "tf32": 1e-2}
 
 
-def _mk(dim, n, k, prec, l=-1, wind="stage"):
+def _mk(dim, n, k, prec, l=-1, wind="stage", tile_hint=2):
+    """tile_hint 2 forces the tensor-core kernels (the autotuner may prefer others)."""
     from paper_2408_06698_gb300 import Hopu
     m = W.periodic_box_mesh(dim, n)
-    g = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec=prec, wind=wind)
+    g = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec=prec, wind=wind, tile_hint=tile_hint)
     topo = mesh.MeshTopo(m.coords, m.elems, m.rep)
     sp = hdiv.HDiv(topo, fe.ref_element(dim, k))
     return g, sp
@@ -61,7 +62,7 @@ def test_tc_projection(dim, n, k, prec):
     assert _rel(_host(g.project("l2_to_hdiv", _dev(g, uL))), sp.from_l2(uL)) < 2e-6
 
 
-@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 4, 3), (3, 3, 4)])
+@pytest.mark.parametrize("dim,n,k", [(2, 8, 1), (2, 8, 2), (2, 6, 4), (3, 3, 1), (3, 3, 2), (3, 4, 3), (3, 3, 4)])
 def test_tc_apply_and_substep(dim, n, k):
     g, sp = _mk(dim, n, k, "f32_tc", l=k - 1)
     rng = np.random.default_rng(800 + k)
@@ -87,7 +88,7 @@ def test_tc_full_size_projection():
     the same input (both at FP32 parity with the oracle on the small meshes)."""
     from paper_2408_06698_gb300 import Hopu
     m = W.periodic_box_mesh(3, 16)
-    a = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32_tc")
+    a = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32_tc", tile_hint=2)
     b = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32")
     u = a.interpolate_function(W.taylor_green)
     u += torch.as_tensor(W.uniform_noise(a.n_hdiv, 1e-3, 0), device=a.device).float()
@@ -97,3 +98,51 @@ def test_tc_full_size_projection():
     err = float((ya - yb).abs().max() / yb.abs().max())
     print(f"full size V_h -> L2, 3xTF32 vs FP32 FMA: {err:.2e}")
     assert err < 4e-6
+
+
+def test_tc_full_size_substep():
+    """16^3 x 6 tetrahedra, k = 3: one STAGE substep with the tensor-core projection and
+    volume kernels against the FP32 FMA kernels on the same state (both at FP32 parity
+    with the oracle on the small meshes), and against the FP64 path."""
+    from paper_2408_06698_gb300 import Hopu
+    m = W.periodic_box_mesh(3, 16)
+    a = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32_tc", tile_hint=2)
+    b = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32")
+    c = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f64")
+    assert a.tuning() == {"v2l": "tc", "volume": "tc"}
+    u = c.interpolate_function(W.taylor_green)
+    u += torch.as_tensor(W.uniform_noise(c.n_hdiv, 1e-3, 0), device=c.device)
+    xa, xb, xc = u.float().clone(), u.float().clone(), u.float().double().clone()
+    a.rk_substep(xa, 5e-4, 1)
+    b.rk_substep(xb, 5e-4, 1)
+    c.rk_substep(xc, 5e-4, 1)
+    a.sync()
+    ea = float((xa.double() - xc).abs().max() / xc.abs().max())
+    eb = float((xb.double() - xc).abs().max() / xc.abs().max())
+    print(f"full size substep vs FP64: 3xTF32 tensor cores {ea:.2e}, FP32 FMA {eb:.2e}")
+    assert ea < 4e-7 and eb < 4e-7
+
+
+def test_autotuner_choices():
+    """tile_hint 0 times both variants of each family on the mesh and keeps one; 1 and 2
+    force them; every choice gives the same substep to FP32 accuracy."""
+    from paper_2408_06698_gb300 import Hopu
+    m = W.periodic_box_mesh(3, 8)
+    got = {}
+    for hint in (0, 1, 2):
+        g = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32_tc", tile_hint=hint)
+        t = g.tuning()
+        if hint == 1:
+            assert t == {"v2l": "fma", "volume": "fma"}
+        if hint == 2:
+            assert t == {"v2l": "tc", "volume": "tc"}
+        assert set(t.values()) <= {"fma", "tc"}
+        u = g.interpolate_function(W.taylor_green)
+        g.rk_substep(u, 5e-4, 2)
+        g.sync()
+        got[hint] = u.double().cpu().numpy()
+        print(f"tile_hint {hint}: {t}")
+    for hint in (0, 2):
+        assert np.abs(got[hint] - got[1]).max() < 1e-6 * np.abs(got[1]).max()
+    g = Hopu(m.coords, m.elems, m.rep, k=3, l=2, prec="f32")
+    assert g.tuning() == {"v2l": "fma", "volume": "fma"}
