@@ -224,3 +224,70 @@ def test_stage_substep_conserves_momentum_and_is_consistent():
     m0 = np.sum(sp.topo.absdet[:, None] * sp.to_l2(uV)[:, :, 0], axis=0)
     m1 = np.sum(sp.topo.absdet[:, None] * sp.to_l2(u1)[:, :, 0], axis=0)
     assert np.abs(m1 - m0).max() < 1e-12
+
+
+def _locate(topo, x):
+    """(element, reference point) of physical points x [P, d] inside the periodic box
+    (unwrapped element coordinates cover [0, 2pi]^d): barycentric search over all elements."""
+    d = topo.dim
+    ref = np.einsum("ecj,epj->epc", topo.Jinv, x[None, :, :] - topo.X[:, None, 0, :])   # [E, P, d]
+    lam = np.concatenate([1.0 - ref.sum(-1, keepdims=True), ref], axis=-1)
+    inside = np.all(lam > -1e-12, axis=-1)
+    e = np.argmax(inside, axis=0)
+    assert np.all(inside[e, np.arange(x.shape[0])]), "a point lies in no element"
+    return e, ref[e, np.arange(x.shape[0])]
+
+
+def _values(sp, uL, e, xref):
+    v, _ = fe.dubiner(sp.ref.dim, sp.ref.k, xref)                  # [P, nb]
+    return np.einsum("pi,pai->pa", v, uL[e])
+
+
+def _shifted(sp, vL, shift):
+    """Exact L2 coefficients of x -> v(x + shift) for an element-wise polynomial field v
+    of degree k: each element's polynomial is sampled through the element containing the
+    shifted points and projected with the volume rule (exact for degree 2k <= 3k - 1)."""
+    t, ref = sp.topo, sp.ref
+    x = t.volume_points(ref.xq).reshape(-1, ref.dim)
+    e1, xr1 = _locate(t, np.mod(x + shift, 2.0 * np.pi))
+    vals = _values(sp, vL, e1, xr1).reshape(t.n_elems, -1, ref.dim)
+    return np.einsum("q,qi,eqa->eai", ref.wq, ref.phi, vals)
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 4, 2), (3, 3, 2)])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_P10_translation_by_one_cube(dim, n, k, axis):
+    """The periodic Kuhn mesh is invariant under a shift by one cube, so the operator
+    commutes with it: y[w(. + h e), u(. + h e)](x) = y[w, u](x + h e).  Elements at the
+    periodic seam see their vertices in another order than their interior neighbours, so
+    a mistake in the orientation signs, the facet pairing or the trace permutations breaks
+    the identity.  Element-wise polynomial (L2) inputs are shifted exactly; compared point
+    by point at every volume quadrature point.  The wind is a constant plus a small
+    polynomial perturbation, so that w.n keeps its sign on every facet: |w.n| is then a
+    polynomial there and the facet rule integrates it exactly whatever the order of the
+    facet's points (the collapsed facet rule is not symmetric under relabelling the
+    vertices of a triangle, so with sign changes inside a facet the identity would only
+    hold up to the rule's error)."""
+    sp = _space(dim, n, k)
+    t = sp.topo
+    h = 2.0 * np.pi / n
+    shift = np.zeros(dim)
+    shift[axis] = h
+    rng = np.random.default_rng(50 + axis)
+    wL = 0.002 * rng.standard_normal((t.n_elems, dim, sp.ref.nb))
+    wL[:, :, 0] += np.array([1.0, 0.55, 0.2][:dim]) * np.sqrt(float(np.sum(sp.ref.wq)))   # constant part
+    uL = rng.standard_normal((t.n_elems, dim, sp.ref.nb))
+    wn = C.facet_quantities(t, sp.ref, wL, uL, -1)[0]
+    assert not np.any(np.any(wn > 0, axis=1) & np.any(wn < 0, axis=1))   # the precondition
+    wS, uS = _shifted(sp, wL, shift), _shifted(sp, uL, shift)
+    x = t.volume_points(sp.ref.xq).reshape(-1, dim)
+    e0 = np.repeat(np.arange(t.n_elems), sp.ref.xq.shape[0])
+    xr0 = np.tile(sp.ref.xq, (t.n_elems, 1))
+    e1, xr1 = _locate(t, np.mod(x + shift, 2.0 * np.pi))
+    assert np.abs(_values(sp, uS, e0, xr0) - _values(sp, uL, e1, xr1)).max() < 1e-12 * np.abs(uL).max()
+    for l in (-1, k - 1, k):
+        y = C.apply(t, sp.ref, wL, uL, l)
+        ys = C.apply(t, sp.ref, wS, uS, l)
+        lhs = _values(sp, ys, e0, xr0)
+        rhs = _values(sp, y, e1, xr1)
+        assert np.abs(lhs - rhs).max() < 1e-11 * np.abs(rhs).max(), l
