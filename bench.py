@@ -426,10 +426,17 @@ def our_arm(args, rank, world):
     except Exception:
         pass
     clocks = Clocks(uuid)
-    dev_ms, wall, acc, ck, energies = timed_steps(g32, s32, K, Wm, profile=True, clocks=clocks)
+    # the headline runs without per-kernel events (they would split the substep graph's
+    # programmatic launch overlap and add their own cost); a second, profiled pass of the
+    # same workload gives the per-kernel times
+    dev_ms, wall, _, ck, energies = timed_steps(g32, s32, K, Wm, profile=False, clocks=clocks)
     tmax_ms = max_over_ranks(dev_ms, world)
     dofs = g32.n_l2 * APPLIES_PER_STEP
     value = whole_job_value(dofs * K, world, tmax_ms / 1e3)
+    g32p, s32p = make("f32")
+    Kp = min(K, 300)
+    prof_ms, _, acc, _, _ = timed_steps(g32p, s32p, Kp, Wm, profile=True)
+    del g32p, s32p
 
     # ---------------- e2e through host buffers (pinned), same metric
     g32e, s32e = make("f32")
@@ -444,16 +451,18 @@ def our_arm(args, rank, world):
     # ---------------- FP64 path (same workload, fewer steps)
     g64, s64 = make("f64")
     K64 = min(K, 100)
-    d64, _, acc64, _, _ = timed_steps(g64, s64, K64, min(Wm, 3), profile=True)
+    d64, _, _, _, _ = timed_steps(g64, s64, K64, min(Wm, 3))
     d64 = max_over_ranks(d64, world)
+    _, _, acc64, _, _ = timed_steps(g64, s64, min(K64, 30), 1, profile=True)
     fp64 = {"value": whole_job_value(dofs * K64, world, d64 / 1e3), "unit": UNIT, "steps": K64,
             "ms_per_step": d64 / K64}
 
     # ---------------- FP32 with the tensor-core (3xTF32) projection GEMM
     gtc, stc = make("f32_tc")
     Ktc = min(K, 500)
-    dtc, _, acctc, _, _ = timed_steps(gtc, stc, Ktc, Wm, profile=True)
+    dtc, _, _, _, _ = timed_steps(gtc, stc, Ktc, Wm)
     dtc = max_over_ranks(dtc, world)
+    _, _, acctc, _, _ = timed_steps(gtc, stc, min(Ktc, 100), 1, profile=True)
     fp32_tc = {"value": whole_job_value(dofs * Ktc, world, dtc / 1e3), "unit": UNIT, "steps": Ktc,
                "ms_per_step": dtc / Ktc, "autotuned_variants": gtc.tuning(),
                "kernels": {f: {"avg_us": 1e3 * acctc[f][0] / max(1, acctc[f][1]), "launches": acctc[f][1]}
@@ -515,9 +524,9 @@ def our_arm(args, rank, world):
                    "avg_us": 1e3 * acc[f][0] / max(1, acc[f][1]),
                    "gflops": alg[f][0] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9,
                    "gbs": alg[f][1] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9} for f in FAMILIES}
-    step_bytes = sum(alg[f][1] * (acc[f][1] / max(1, K)) for f in FAMILIES)
+    step_bytes = sum(alg[f][1] * (acc[f][1] / max(1, Kp)) for f in FAMILIES)
     hbm_step_frac = step_bytes / (dev_ms / K / 1e3) / 1e9 / hbm_peak
-    launches = sum(acc[f][1] for f in FAMILIES) + 2 * K   # + the two energy-log kernels per substep
+    launches = round(sum(acc[f][1] for f in FAMILIES) * K / Kp) + 2 * K   # + the two energy-log kernels per substep
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
@@ -530,6 +539,8 @@ def our_arm(args, rank, world):
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "fp64": fp64,
         "fp32_tc": fp32_tc, "vjp": vjp, "other_configs": others,
         "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernels,
+        "profiled_pass": {"steps": Kp, "ms_per_step": prof_ms / Kp,
+                          "note": "per-kernel CUDA events around every launch (roofline, kernels_f32)"},
         "kernels_f64": {f: {"avg_us": 1e3 * acc64[f][0] / max(1, acc64[f][1]), "launches": acc64[f][1]}
                         for f in FAMILIES},
         "energy_drift_per_step": (energies[-1] - energies[0]) / max(1, len(energies) - 1) / energies[0],

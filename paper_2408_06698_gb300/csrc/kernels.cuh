@@ -41,6 +41,14 @@ struct Shape {
 constexpr int kWarps = 4;  // warps per CTA of the warp-per-item kernels
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch: every kernel lets the next kernel of the stream be
+// scheduled as soon as all of its own CTAs have started (pdl_trigger), and waits for the
+// previous kernel to complete, with its memory visible (pdl_wait), only after its
+// prologue, which reads nothing but constant tables and mesh data and writes only shared
+// memory.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Butterfly reduce-scatter of N (multiple of 32) per-lane values: afterwards lane L holds
 // the warp totals of indices [L*N/32, (L+1)*N/32) in v[0 .. N/32).
 template <int O, int S, int N, typename T>
@@ -207,11 +215,13 @@ __global__ void __launch_bounds__(kProjThreads) k_v2l(DevMesh m, const T* __rest
   constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
   constexpr int NLP = C::NLP, NLQ = C::NLQ, TE = C::TE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
   const T* geoT = static_cast<const T*>(m.geoT);
   T* sX = reinterpret_cast<T*>(smem_raw + C::TABS);         // [TE][NLQ]
   T* sGeo = reinterpret_cast<T*>(smem_raw + C::TABS + ((size_t(TE) * NLQ * sizeof(T) + 15) / 16) * 16);
   int* sCode = reinterpret_cast<int*>(sGeo + TE * GEO);      // [TE][D+1]
+  pdl_wait();
   __syncthreads();
   const int tid = threadIdx.x;
   const int64_t ntiles = (m.E + TE - 1) / TE;
@@ -281,10 +291,12 @@ __global__ void __launch_bounds__(kProjThreads) k_l2v_elem(DevMesh m, const T* _
   constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
   constexpr int NLP = C::NLP, NLQ = C::NLQ, TE = C::TE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
   const T* geoT = static_cast<const T*>(m.geoT);
   T* sX = reinterpret_cast<T*>(smem_raw + C::TABS);
   T* sGeo = reinterpret_cast<T*>(smem_raw + C::TABS + ((size_t(TE) * NLQ * sizeof(T) + 15) / 16) * 16);
+  pdl_wait();
   __syncthreads();
   const int tid = threadIdx.x;
   const int64_t ntiles = (m.E + TE - 1) / TE;
@@ -494,6 +506,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
   constexpr int SV = NQF * 4;
   constexpr int PER_WARP = (WSEP ? 4 : 2) * CW + 2 * SV + 2 * NF * 4 + 2 * NF * 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   T* sbase = reinterpret_cast<T*>(smem_raw);
   {
     const T* TrMg = static_cast<const T*>(tb.TrM);
@@ -515,6 +528,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
   const T* WPsi = sbase + TRM + PSI;
   const T* Wf = sbase + TRM + 2 * PSI;
   T* sw = sbase + TABN;
+  pdl_wait();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* cA = sw + warp * PER_WARP;
@@ -683,6 +697,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   constexpr int STAGE = STU + (WSEP ? STU : 0) + STG + STGEO;
   constexpr int PER_WARP = 2 * STAGE + D * NBP + D * D * NB1P + (WSEP ? D * NBP + NB1P : 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   T* sbase = reinterpret_cast<T*>(smem_raw);
   const T* Bt = static_cast<const T*>(tb.Bt);
   const T* Wq = static_cast<const T*>(tb.Wq);
@@ -705,6 +720,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     const T* Dg = static_cast<const T*>(tb.Drow);
     for (int t = threadIdx.x; t < FT; t += blockDim.x) Drow[t] = Dg[t];
   }
+  pdl_wait();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* wbase = sw + warp * PER_WARP;
@@ -872,6 +888,8 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
 template <int D, int K, typename T, bool DUAL>
 __global__ void __launch_bounds__(256) k_l2v_facet(DevMesh m, const T* __restrict__ lf, T* outV, Combine cmb) {
   constexpr int NF = Shape<D, K>::nf;
+  pdl_trigger();
+  pdl_wait();
   const int64_t total = m.NF * NF;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t F = t / NF;

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_eta(DevMesh m, DevTabs tb, cons
   constexpr int CW = D * NBP;
   constexpr int PER_WARP = 2 * CW + 2 * NF * 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   T* sbase = reinterpret_cast<T*>(smem_raw);
   {
     const T* TrMg = static_cast<const T*>(tb.TrM);
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_eta(DevMesh m, DevTabs tb, cons
   const T* TrM = sbase;
   const T* Psi = sbase + TRM;
   const T* Wf = sbase + TRM + PSI;
+  pdl_wait();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* cuA = sbase + TABN + warp * PER_WARP;

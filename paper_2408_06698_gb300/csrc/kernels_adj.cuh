@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet_adj(DevMesh m, DevTabs tb
   constexpr int CW = D * NBP, SV = NQF * 4, GT = S::gt;
   constexpr int PER_WARP = (WSEP ? 6 : 4) * CW + 3 * SV + 4 * NF * 4 + 3 * NF * 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   T* sbase = reinterpret_cast<T*>(smem_raw);
   {
     const T* TrMg = static_cast<const T*>(tb.TrM);
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet_adj(DevMesh m, DevTabs tb
   const T* Psi = sbase + TRM;
   const T* WPsi = sbase + TRM + PSI;
   const T* geoT = static_cast<const T*>(m.geoT);
+  pdl_wait();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* cuA = sbase + TABN + warp * PER_WARP;
@@ -208,6 +210,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_volume_adj(DevMesh m, DevTabs t
   const T* TrM = static_cast<const T*>(tb.TrM);
   const T* geoT = static_cast<const T*>(m.geoT);
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
+  pdl_wait();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* sC = reinterpret_cast<T*>(smem_raw) + warp * PER_WARP;  // [D][NBP] u
   T* sZ = sC + D * NBP;                                     // [D][NBP] z = ybar / |det J|

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const float* geoT = static_cast<const float*>(m.geoT);
+  pdl_trigger();
 
   // B operand (once per CTA) and the zero padding columns of A
   for (int t = tid; t < NP * KP; t += NT) {
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
   uint32_t phase = 0;
   bool ok = true;
   const int64_t ntiles = (m.E + TM - 1) / TM;
+  pdl_wait();
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * TM;
     for (int t = tid; t < TM * (D + 1); t += NT)
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
   float* sCh = reinterpret_cast<float*>(sFl);                  // [EB][NL] (epilogue, F is free)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const float* geoT = static_cast<const float*>(m.geoT);
+  pdl_trigger();
 
   if (warp == 0) tc::tmem_alloc(tslot, C::TCOLS);
   if (tid == 0) {
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
   const int64_t nsc = (m.E + EB - 1) / EB;
   const int qrow = (warp & 3) * 32 + lane;              // TMEM lane of this thread
   const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+  pdl_wait();
   for (int64_t sc = blockIdx.x; ok && sc < nsc; sc += gridDim.x) {
     const int64_t e0 = sc * EB;
     for (int t = tid; t < EB * GT; t += NT) {

@@ -2,6 +2,7 @@
 #pragma once
 #include <algorithm>
 #include <type_traits>
+#include <utility>
 
 #include "kernels.cuh"
 #include "kernels_adj.cuh"
@@ -104,6 +105,23 @@ class OpsImpl final : public Ops {
     return cudaSuccess;
   }
 
+  // Every launch of the family carries the programmatic-stream-serialization attribute
+  // (the kernels wait for their predecessor after their prologue, see pdl_wait).
+  template <typename... KArgs, typename... Args>
+  static void launch(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  }
+
   static int clamp_grid(int g, int64_t items, int per_block) {
     const int64_t need = (items + per_block - 1) / per_block;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, need));
@@ -165,16 +183,16 @@ class OpsImpl final : public Ops {
         const int g = clamp_grid(g_v2l_tc_, m.E, V2lTc<D, K>::TM);
         const int nlp = (S::nloc + 3) / 4 * 4;
         if (tc_ == 3)
-          k_v2l_tc<D, K, true><<<g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
+          launch(k_v2l_tc<D, K, true>, g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st, m, static_cast<const float*>(t.Dinv), nlp,
                                                                   static_cast<const float*>(uV), static_cast<float*>(uL));
         else
-          k_v2l_tc<D, K, false><<<g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st>>>(m, static_cast<const float*>(t.Dinv), nlp,
+          launch(k_v2l_tc<D, K, false>, g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st, m, static_cast<const float*>(t.Dinv), nlp,
                                                                    static_cast<const float*>(uV), static_cast<float*>(uL));
         return 1;
       }
     }
     const int g = clamp_grid(g_v2l_, m.E, PC::TE);
-    k_v2l<D, K, T, false><<<g, kProjThreads, kProjSmem, st>>>(
+    launch(k_v2l<D, K, T, false>, g, kProjThreads, kProjSmem, st, 
         m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
     return 1;
   }
@@ -184,10 +202,10 @@ class OpsImpl final : public Ops {
     const bool wsep = (wL != nullptr && wL != uL);
     const int g = clamp_grid(g_fac_[wsep ? 1 : 0], m.NF, kWarps);
     if (wsep)
-      k_facet<D, K, T, true, kFacetTab><<<g, 32 * kWarps, facet_smem(true), st>>>(
+      launch(k_facet<D, K, T, true, kFacetTab>, g, 32 * kWarps, facet_smem(true), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), l, facet_l, static_cast<T*>(gam), diss);
     else
-      k_facet<D, K, T, false, kFacetTab><<<g, 32 * kWarps, facet_smem(false), st>>>(
+      launch(k_facet<D, K, T, false, kFacetTab>, g, 32 * kWarps, facet_smem(false), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), l, facet_l, static_cast<T*>(gam), diss);
     return 1;
   }
@@ -197,11 +215,11 @@ class OpsImpl final : public Ops {
     const bool wsep = (wL != nullptr && wL != uL);
     const int g = clamp_grid(g_vol_[wsep ? 1 : 0], m.E, kWarps);
     if (wsep)
-      k_volume<D, K, T, true, kVolumeTab, false><<<g, 32 * kWarps, volume_smem(true), st>>>(
+      launch(k_volume<D, K, T, true, kVolumeTab, false>, g, 32 * kWarps, volume_smem(true), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(gam),
           static_cast<T*>(out), c, nullptr);
     else
-      k_volume<D, K, T, false, kVolumeTab, false><<<g, 32 * kWarps, volume_smem(false), st>>>(
+      launch(k_volume<D, K, T, false, kVolumeTab, false>, g, 32 * kWarps, volume_smem(false), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
           static_cast<T*>(out), c, nullptr);
     return 1;
@@ -212,13 +230,13 @@ class OpsImpl final : public Ops {
   int eta(const DevMesh& m, const DevTabs& t, const void* uL, int l, int8_t* facet_l, const EtaThresholds& th,
           double* eta_out, cudaStream_t st) override {
     const int g = clamp_grid(g_eta_, m.NF, kWarps);
-    k_eta<D, K, T><<<g, 32 * kWarps, eta_smem(), st>>>(m, t, static_cast<const T*>(uL), l, facet_l, th, eta_out);
+    launch(k_eta<D, K, T>, g, 32 * kWarps, eta_smem(), st, m, t, static_cast<const T*>(uL), l, facet_l, th, eta_out);
     return 1;
   }
 
   int v2l_pt(const DevMesh& m, const DevTabs& t, const void* vV, void* yL, cudaStream_t st) override {
     const int g = clamp_grid(g_v2l_, m.E, PC::TE);
-    k_v2l<D, K, T, true><<<g, kProjThreads, kProjSmem, st>>>(
+    launch(k_v2l<D, K, T, true>, g, kProjThreads, kProjSmem, st, 
         m, static_cast<const T*>(t.Dn), static_cast<const T*>(vV), static_cast<T*>(yL));
     return 1;
   }
@@ -228,11 +246,11 @@ class OpsImpl final : public Ops {
     const bool wsep = (wL != nullptr && wL != uL);
     const int g = clamp_grid(g_fadj_, m.NF, kWarps);
     if (wsep)
-      k_facet_adj<D, K, T, true><<<g, 32 * kWarps, facet_adj_smem(true), st>>>(
+      launch(k_facet_adj<D, K, T, true>, g, 32 * kWarps, facet_adj_smem(true), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(ybar), l, facet_l,
           static_cast<T*>(gamU), static_cast<T*>(gamW));
     else
-      k_facet_adj<D, K, T, false><<<g, 32 * kWarps, facet_adj_smem(false), st>>>(
+      launch(k_facet_adj<D, K, T, false>, g, 32 * kWarps, facet_adj_smem(false), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(ybar), l, facet_l,
           static_cast<T*>(gamU), static_cast<T*>(gamW));
     return 1;
@@ -243,11 +261,11 @@ class OpsImpl final : public Ops {
     const bool wsep = (wL != nullptr && wL != uL);
     const int g = clamp_grid(g_vadj_, m.E, kWarps);
     if (wsep)
-      k_volume_adj<D, K, T, true><<<g, 32 * kWarps, volume_adj_smem(true), st>>>(
+      launch(k_volume_adj<D, K, T, true>, g, 32 * kWarps, volume_adj_smem(true), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(wL), static_cast<const T*>(ybar),
           static_cast<const T*>(gamU), static_cast<const T*>(gamW), static_cast<T*>(ubar), static_cast<T*>(wbar));
     else
-      k_volume_adj<D, K, T, false><<<g, 32 * kWarps, volume_adj_smem(false), st>>>(
+      launch(k_volume_adj<D, K, T, false>, g, 32 * kWarps, volume_adj_smem(false), st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(ybar),
           static_cast<const T*>(gamU), static_cast<const T*>(gamW), static_cast<T*>(ubar), nullptr);
     return 1;
@@ -259,7 +277,7 @@ class OpsImpl final : public Ops {
       if (tc_ && use_tc_vol_ && t.tcvol) {
         const int g = clamp_grid(g_vol_tc_, m.E, VolTc<D, K>::EB);
         const int nlr = row_stride<float>(S::nloc);
-        k_volume_tc<D, K><<<g, VolTc<D, K>::THREADS, VolTc<D, K>::SMEM, st>>>(
+        launch(k_volume_tc<D, K>, g, VolTc<D, K>::THREADS, VolTc<D, K>::SMEM, st, 
             m, static_cast<const float*>(t.tcvol), static_cast<const float*>(t.Dm), static_cast<const float*>(t.Wq),
             static_cast<const float*>(t.TrM), static_cast<const float*>(t.Drow), nlr, static_cast<const float*>(uL),
             static_cast<const float*>(gam), static_cast<float*>(outV), c, static_cast<float*>(lf));
@@ -268,7 +286,7 @@ class OpsImpl final : public Ops {
     }
     if constexpr (kFuse) {
       const int g = clamp_grid(g_fuse_, m.E, kWarps);
-      k_volume<D, K, T, false, true, true><<<g, 32 * kWarps, kFuseSmem, st>>>(
+      launch(k_volume<D, K, T, false, true, true>, g, 32 * kWarps, kFuseSmem, st, 
           m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
           static_cast<T*>(outV), c, static_cast<T*>(lf));
       return 1;
@@ -281,10 +299,10 @@ class OpsImpl final : public Ops {
                void* outV, cudaStream_t st) override {
     const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, PC::TE);
     if (dual)
-      k_l2v_elem<D, K, T, true><<<g, kProjThreads, kProjSmem, st>>>(
+      launch(k_l2v_elem<D, K, T, true>, g, kProjThreads, kProjSmem, st, 
           m, static_cast<const T*>(t.Dinv), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
     else
-      k_l2v_elem<D, K, T, false><<<g, kProjThreads, kProjSmem, st>>>(
+      launch(k_l2v_elem<D, K, T, false>, g, kProjThreads, kProjSmem, st, 
           m, static_cast<const T*>(t.DT), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
     return 1;
   }
@@ -292,9 +310,9 @@ class OpsImpl final : public Ops {
   int l2v_facet(const DevMesh& m, const void* lf, bool dual, Combine c, void* outV, cudaStream_t st) override {
     const int gf = clamp_grid(g_fsum_, m.NF * S::nf, 256);
     if (dual)
-      k_l2v_facet<D, K, T, true><<<gf, 256, 0, st>>>(m, static_cast<const T*>(lf), static_cast<T*>(outV), c);
+      launch(k_l2v_facet<D, K, T, true>, gf, 256, 0, st, m, static_cast<const T*>(lf), static_cast<T*>(outV), c);
     else
-      k_l2v_facet<D, K, T, false><<<gf, 256, 0, st>>>(m, static_cast<const T*>(lf), static_cast<T*>(outV), c);
+      launch(k_l2v_facet<D, K, T, false>, gf, 256, 0, st, m, static_cast<const T*>(lf), static_cast<T*>(outV), c);
     return 1;
   }
 };
