@@ -239,8 +239,18 @@ def reference_arm(args, rank):
 
 
 # ------------------------------------------------------------------ our arm
+def kernel_sources_sha() -> str:
+    """sha256[:16] of every kernel header of the library (sorted by name, concatenated)."""
+    d = os.path.join(ROOT, "paper_2408_06698_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(f for f in os.listdir(d) if f.endswith(".cuh")):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel: str):
-    """DRAM bytes per launch from the committed ncu capture, if the kernel is unchanged."""
+    """DRAM bytes per launch from the committed ncu capture, if the kernels are unchanged."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -249,9 +259,7 @@ def traffic_from_profiles(kernel: str):
     ent = t.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_2408_06698_gb300", "csrc", "kernels.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if ent.get("kernels_cuh_sha") != sha:
+    if ent.get("kernel_sources_sha") != kernel_sources_sha():
         return None
     return ent.get("dram_bytes_per_launch_full_size")
 

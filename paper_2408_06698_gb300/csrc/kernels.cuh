@@ -404,6 +404,25 @@ __device__ __forceinline__ T dot_row_v(const T* x, const T* s) {
   return acc;
 }
 
+// the same row against two point vectors: every 16-byte shared load feeds both sums
+template <int N, typename T>
+__device__ __forceinline__ void dot2_row_v(const T* x0, const T* x1, const T* s, T& a0, T& a1) {
+  constexpr int W = Pack<T>::W;
+  a0 = T(0);
+  a1 = T(0);
+#pragma unroll
+  for (int i = 0; i < N; i += W) {
+    T o[W];
+    lds_v(s + i, o);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (i + w < N) {
+        a0 = fma(x0[i + w], o[w], a0);
+        a1 = fma(x1[i + w], o[w], a1);
+      }
+  }
+}
+
 template <int N, typename T>
 __device__ __forceinline__ T dot_row(const T* x, const T* s) {
   constexpr int W = Pack<T>::W;
@@ -690,6 +709,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   constexpr int FT = FUSE ? FuseCfg<D, K, T>::TAB : 0, NLR = FuseCfg<D, K, T>::NLR;
   constexpr int TABN = r4i(BT + NQ + DM + TRM) + r4i(FT);
   constexpr int NG = (D + 1) * NF * D;
+  constexpr int QB = (sizeof(T) == 4 && NQ > 32) ? 2 : 1;  // quadrature points per lane and pass
   static_assert(!FUSE || (STAB && FuseCfg<D, K, T>::OK), "fused back-projection needs staged tables");
   // per-warp layout: two staging buffers (u record, w record, facet moments, geometry),
   // then the working arrays
@@ -787,6 +807,58 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     T acc[NVP];
 #pragma unroll
     for (int j = 0; j < NVP; ++j) acc[j] = T(0);
+    if constexpr (QB == 2) {
+      // two points per lane (q and q + 32): every coefficient row loaded from shared
+      // memory feeds both points
+      for (int q = lane; q < NQ; q += 64) {
+        const int q1 = q + 32;
+        const bool v1 = q1 < NQ;
+        T ph0[NB], ph1[NB];
+        load_row<NB>(Bt + q * NBQ, ph0);
+        load_row<NB>(Bt + (v1 ? q1 : q) * NBQ, ph1);
+        T u0[D], u1[D], G0[D][D], G1[D][D], W0[D], W1[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          dot2_row_v<NB>(ph0, ph1, sC + a * NBP, u0[a], u1[a]);
+#pragma unroll
+          for (int c = 0; c < D; ++c) dot2_row_v<NB1>(ph0, ph1, sG + (a * D + c) * NB1P, G0[a][c], G1[a][c]);
+        }
+        T dv0 = T(0), dv1 = T(0);
+        if (WSEP) {
+#pragma unroll
+          for (int c = 0; c < D; ++c) dot2_row_v<NB>(ph0, ph1, sW + c * NBP, W0[c], W1[c]);
+          dot2_row_v<NB1>(ph0, ph1, sDv, dv0, dv1);
+        } else {
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            T s0 = T(0), s1 = T(0);
+#pragma unroll
+            for (int bb = 0; bb < D; ++bb) {
+              s0 = fma(M[c][bb], u0[bb], s0);
+              s1 = fma(M[c][bb], u1[bb], s1);
+              dv0 = fma(M[c][bb], G0[bb][c], dv0);
+              dv1 = fma(M[c][bb], G1[bb][c], dv1);
+            }
+            W0[c] = s0;
+            W1[c] = s1;
+          }
+        }
+        const T wq0 = Wq[q], wq1 = v1 ? Wq[q1] : T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          T f0 = dv0 * u0[a], f1 = dv1 * u1[a];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            f0 = fma(W0[c], G0[a][c], f0);
+            f1 = fma(W1[c], G1[a][c], f1);
+          }
+          f0 *= wq0;
+          f1 *= wq1;
+#pragma unroll
+          for (int i = 0; i < NB; ++i) acc[a * NB + i] = fma(f1, ph1[i], fma(f0, ph0[i], acc[a * NB + i]));
+        }
+      }
+    } else
     for (int q = lane; q < NQ; q += 32) {
       T ph[NB];
       load_row<NB>(Bt + q * NBQ, ph);
