@@ -82,21 +82,28 @@ def complement_projection(ref: RefElement, l_F: np.ndarray, nF: np.ndarray,
     return out
 
 
-def facet_quantities(topo, ref, wL, uL, l, exterior=None):
+def facet_quantities(topo, ref, wL, uL, l, exterior=None, inlet=None):
     """Per facet point: w.n, [[u]], <u>, (I-Pi)[[u]] and (I-Pi)[1/2|w.n|(I-Pi)[[u]]].
 
-    exterior: optional (u_ext, w_ext) arrays [F, nqf, d] used as the side-B trace
-    on boundary facets (the inlet rule of Section 2.2: the exterior trace is the
-    given boundary data).
+    Boundary facets (Section 2.1: F^I holds interior, periodic and inlet facets; wall
+    and outlet facets carry no term in the paper's form):
+    * inlet facets take the given exterior traces as side B (Section 2.2: the jump and
+      the average use u_I); exterior = (u_ext, w_ext) arrays [F, nqf, d]; inlet is a
+      boolean mask [F] (None: every boundary facet is an inlet when exterior is given);
+    * the other boundary facets (walls, outlets) take side A's own trace as side B:
+      the jump vanishes, so the paper's form has no term there, and the conservative
+      form keeps the flux (w.n) u . v that its element-wise integration by parts needs
+      to equal the paper's form (reading A12).
     """
     l_F = _as_facet_l(topo, l)
     uA, wA = facet_trace(topo, ref, uL, "A"), facet_trace(topo, ref, wL, "A")
     uB, wB = facet_trace(topo, ref, uL, "B"), facet_trace(topo, ref, wL, "B")
     if np.any(topo.boundary):
-        if exterior is None:
-            raise ValueError("mesh has boundary facets but no exterior data was given")
         b = topo.boundary
-        uB[b], wB[b] = exterior[0][b], exterior[1][b]
+        uB[b], wB[b] = uA[b], wA[b]
+        if exterior is not None:
+            bi = b if inlet is None else (b & np.asarray(inlet, dtype=bool))
+            uB[bi], wB[bi] = exterior[0][bi], exterior[1][bi]
     wn = 0.5 * np.einsum("Fqa,Fa->Fq", wA + wB, topo.nF)
     jump = uA - uB
     avg = 0.5 * (uA + uB)
@@ -115,37 +122,37 @@ def _test_facets(topo, ref, r, g, side):
             np.add.at(r, ef[m, 0], contrib)
 
 
-def residual_conservative(topo, ref, wL, uL, l, exterior=None) -> np.ndarray:
+def residual_conservative(topo, ref, wL, uL, l, exterior=None, inlet=None) -> np.ndarray:
     """r[e, a, i] = c(w; u, phi_i e_a) in the conservative reading."""
     U = np.einsum("qi,eai->eqa", ref.phi, uL)
     W = np.einsum("qi,eai->eqa", ref.phi, wL)
     Wt = np.einsum("e,ecb,eqb->eqc", topo.absdet, topo.Jinv, W)       # |det J| J^{-1} w
     r = -np.einsum("q,eqa,qic,eqc->eai", ref.wq, U, ref.dphi, Wt)
-    wn, jump, avg, PJ, Ph = facet_quantities(topo, ref, wL, uL, l, exterior)
+    wn, jump, avg, PJ, Ph = facet_quantities(topo, ref, wL, uL, l, exterior, inlet)
     g = wn[..., None] * avg + Ph
     _test_facets(topo, ref, r, g, "A")
     _test_facets(topo, ref, r, -g, "B")
     return r
 
 
-def residual_nonconservative(topo, ref, wL, uL, l, exterior=None) -> np.ndarray:
+def residual_nonconservative(topo, ref, wL, uL, l, exterior=None, inlet=None) -> np.ndarray:
     """r[e, a, i] = c(w; u, phi_i e_a) in the paper's form (eq. "hopudefinition")."""
     W = np.einsum("qi,eai->eqa", ref.phi, wL)
     gref = np.einsum("qic,eai->eqac", ref.dphi, uL)                     # reference gradient
     grad = np.einsum("ecb,eqac->eqab", topo.Jinv, gref)                 # d u_a / d x_b
     adv = np.einsum("eqab,eqb->eqa", grad, W)                           # (grad u) w
     r = np.einsum("q,e,eqa,qi->eai", ref.wq, topo.absdet, adv, ref.phi)
-    wn, jump, avg, PJ, Ph = facet_quantities(topo, ref, wL, uL, l, exterior)
+    wn, jump, avg, PJ, Ph = facet_quantities(topo, ref, wL, uL, l, exterior, inlet)
     central = -0.5 * wn[..., None] * jump                               # -(w.n)[[u]].<v>
     _test_facets(topo, ref, r, central + Ph, "A")                       # [[v]] = v^A
     _test_facets(topo, ref, r, central - Ph, "B")                       # [[v]] = -v^B
     return r
 
 
-def apply(topo, ref, wL, uL, l, form="conservative", exterior=None) -> np.ndarray:
+def apply(topo, ref, wL, uL, l, form="conservative", exterior=None, inlet=None) -> np.ndarray:
     """y = M_L^{-1} c(w; u, .) (orthonormal basis: M_T = |det J| I)."""
     fn = residual_conservative if form == "conservative" else residual_nonconservative
-    return fn(topo, ref, wL, uL, l, exterior) / topo.absdet[:, None, None]
+    return fn(topo, ref, wL, uL, l, exterior, inlet) / topo.absdet[:, None, None]
 
 
 # ------------------------------------------------------------------ functionals

@@ -291,3 +291,71 @@ def test_P10_translation_by_one_cube(dim, n, k, axis):
         lhs = _values(sp, ys, e0, xr0)
         rhs = _values(sp, y, e1, xr1)
         assert np.abs(lhs - rhs).max() < 1e-11 * np.abs(rhs).max(), l
+
+
+def _box(dim, n, k):
+    """The box of the periodic tests without the identification: every face a boundary."""
+    m = W.periodic_box_mesh(dim, n)
+    topo = mesh.MeshTopo(m.coords, m.elems)
+    return hdiv.HDiv(topo, fe.ref_element(dim, k))
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 3, 2), (3, 3, 2)])
+def test_P2_with_wall_and_outlet_boundaries(dim, n, k):
+    """Non-periodic box, every boundary facet a wall or outlet (no term in the paper's
+    form): for a divergence-free normal-continuous wind the conservative form, which keeps
+    (w.n) u . v there, equals the paper's form; w.n does not vanish on the boundary."""
+    sp = _box(dim, n, k)
+    t = sp.topo
+    assert np.any(t.boundary)
+    wL = _divfree(sp, seed=5)
+    wn = C.facet_quantities(t, sp.ref, wL, wL, -1)[0]
+    assert np.abs(wn[t.boundary]).max() > 1e-2
+    uL = np.random.default_rng(60).standard_normal(wL.shape)
+    for l in _ls(k):
+        r1 = C.residual_conservative(t, sp.ref, wL, uL, l)
+        r2 = C.residual_nonconservative(t, sp.ref, wL, uL, l)
+        assert np.abs(r1 - r2).max() < 1e-11 * np.abs(r1).max(), l
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 3, 2), (3, 3, 2)])
+def test_inlet_with_the_interior_trace_equals_the_wall_rule(dim, n, k):
+    """An inlet whose data equal the interior trace has no jump: the result must not
+    depend on which boundary facets are declared inlets; with other data it must."""
+    sp = _box(dim, n, k)
+    t = sp.topo
+    rng = np.random.default_rng(61)
+    wL, uL = rng.standard_normal((2, t.n_elems, dim, sp.ref.nb))
+    ext = (C.facet_trace(t, sp.ref, uL, "A"), C.facet_trace(t, sp.ref, wL, "A"))
+    inlet = t.boundary & (rng.random(t.n_facets) < 0.5)
+    y0 = C.apply(t, sp.ref, wL, uL, 1)
+    y1 = C.apply(t, sp.ref, wL, uL, 1, exterior=ext, inlet=inlet)
+    assert np.abs(y1 - y0).max() < 1e-13 * np.abs(y0).max()
+    ext2 = (ext[0] + 0.5, ext[1])
+    y2 = C.apply(t, sp.ref, wL, uL, 1, exterior=ext2, inlet=inlet)
+    assert np.abs(y2 - y0).max() > 1e-3 * np.abs(y0).max()
+
+
+@pytest.mark.parametrize("dim,k", [(2, 2), (3, 2)])
+def test_energy_identity_with_walls(dim, k):
+    """P3 on a non-periodic box whose wind is tangential on the boundary (a stream
+    function / vector potential vanishing there): c(w; u, u) = sum_F int 1/2 |w.n|
+    |(I - Pi^l)[[u]]|^2 over the interior facets, the walls contributing nothing."""
+    sp = _box(dim, 3, k)
+    t = sp.topo
+    L = 2.0 * np.pi
+    if dim == 2:
+        pot = lambda x: np.sin(x[..., 0] / 2) ** 2 * np.sin(x[..., 1] / 2) ** 2 * np.cos(x[..., 0] - x[..., 1])
+    else:
+        def pot(x):
+            b = (np.sin(x[..., 0] / 2) * np.sin(x[..., 1] / 2) * np.sin(x[..., 2] / 2)) ** 2
+            return np.stack([b * np.cos(x[..., 1]), b * np.sin(x[..., 2]), b * np.cos(x[..., 0] + 1.0)], axis=-1)
+    wL = fields.curl_field(t, dim, k, pot)
+    wn = C.facet_quantities(t, sp.ref, wL, wL, -1)[0]
+    assert np.abs(wn[t.boundary]).max() < 1e-12 * np.abs(wn).max()   # tangential on the walls
+    uL = np.random.default_rng(62).standard_normal(wL.shape)
+    for l in _ls(k):
+        cval = C.form_value(t, sp.ref, wL, uL, l)
+        diss = C.facet_dissipation(t, sp.ref, wL, uL, l)
+        assert abs(cval - diss) < 1e-11 * abs(diss), l
+    del L
