@@ -186,6 +186,24 @@ hopu_status hopu_set_frozen_wind(hopu_ctx* ctx, const void* w_hdiv);
  * For divergence-free normal-continuous w, host_out[1] == host_out[2] >= 0.            */
 hopu_status hopu_energy(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, double* host_out);
 
+/* Boundary facets (meshes that are not closed; Section 2.1: F^I holds interior, periodic
+ * and inlet facets, walls and outlets carry no convection term).  A facet with a single
+ * element is a boundary facet: its normal n_F points out of the domain and by default it
+ * is a wall / outlet facet, whose exterior trace is the element's own (no jump; the
+ * conservative form keeps the flux (w.n) u.v that makes it equal to the paper's form).
+ * hopu_boundary_facets lists their ids in ascending order (out may be NULL to query the
+ * count).                                                                             */
+hopu_status hopu_boundary_facets(const hopu_ctx* ctx, int64_t* out, int64_t* count);
+
+/* Declare n boundary facets inlets (Section 2.2: jump and average use the inlet data
+ * u_I) and give u_I at their facet quadrature points (the points of hopu_points, facet
+ * order of `facets`): values host FP64 [n][nqf][dim].  The data enter through their
+ * L2 projection onto P^k of the facet (exact for polynomial data of degree <= k) and
+ * also serve as the exterior wind.  Replaces the previous inlet set; n = 0 makes every
+ * boundary facet a wall / outlet again.  EINVAL for a facet that is not a boundary
+ * facet or is listed twice.  Synchronises the stream; drops the cached substep graph. */
+hopu_status hopu_set_inlet(hopu_ctx* ctx, const int64_t* facets, int64_t n, const double* values);
+
 /* Per-facet HOPU orders (device int8 [n_facets], values -1..k, caller-owned, read at every
  * later launch) used by hopu_rk_substep, hopu_vjp_apply, hopu_vjp_rollout, hopu_energy
  * and by hopu_apply_convection* when their facet_l is NULL.  NULL restores the
@@ -215,6 +233,7 @@ hopu_status hopu_adapt_l(hopu_ctx* ctx, const void* u_l2, const double* threshol
  * Layouts and working precision as hopu_apply_convection; asynchronous on the stream.  */
 hopu_status hopu_vjp_apply(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, const void* ybar_l2,
                            void* wbar_hdiv, void* ubar_l2);
+/* (hopu_vjp_apply and hopu_vjp_rollout: ENOTSUP on meshes with boundary facets.)       */
 
 /* Gradient through n_substeps STAGE SSP-RK3 substeps (hopu_rk_substep) started at u0_hdiv
  * (not modified), by the discrete adjoint of the Shu-Osher stages:

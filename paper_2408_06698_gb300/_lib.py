@@ -63,6 +63,8 @@ SIGNATURES = {
     "hopu_apply_convection_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "hopu_sync": (c_int, [c_void_p]),
+    "hopu_boundary_facets": (c_int, [c_void_p, c_void_p, POINTER(c_int64)]),
+    "hopu_set_inlet": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "hopu_tuning": (c_int, [c_void_p, POINTER(c_int)]),
     "hopu_set_facet_l": (c_int, [c_void_p, c_void_p]),
     "hopu_adapt_l": (c_int, [c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p]),

@@ -203,7 +203,8 @@ void free_all(hopu_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
-                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err, c->d_tcvol};
+                  c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err, c->d_tcvol,
+                  c->d_inlet, c->d_inlet_modes};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c->ops;
@@ -851,6 +852,7 @@ hopu_status hopu_vjp_apply(hopu_ctx* c, const void* w_hdiv, const void* u_l2, co
   if (!aligned16(w_hdiv) || !aligned16(u_l2) || !aligned16(ybar_l2) || (wbar_hdiv && !aligned16(wbar_hdiv)) ||
       (ubar_l2 && !aligned16(ubar_l2)))
     return fail(c, HOPU_EINVAL, "vjp_apply: vectors must be 16-byte aligned");
+  if (!c->topo.boundary.empty()) return fail(c, HOPU_ENOTSUP, "vjp_apply: meshes with boundary facets");
   hopu_status r = ensure_gamW(c);
   if (r != HOPU_OK) return r;
   enqueue_v2l(c, w_hdiv, c->d_wL);
@@ -870,6 +872,7 @@ hopu_status hopu_vjp_rollout(hopu_ctx* c, const void* u0_hdiv, double dt, int n_
   if (!aligned16(u0_hdiv) || !aligned16(u0bar_hdiv))
     return fail(c, HOPU_EINVAL, "vjp_rollout: vectors must be 16-byte aligned");
   if (c->wind != HOPU_WIND_STAGE) return fail(c, HOPU_ENOTSUP, "vjp_rollout: only the STAGE wind rule");
+  if (!c->topo.boundary.empty()) return fail(c, HOPU_ENOTSUP, "vjp_rollout: meshes with boundary facets");
   hopu_status r = ensure_gamW(c);
   if (r != HOPU_OK) return r;
   const int n = n_substeps;
@@ -954,6 +957,61 @@ hopu_status hopu_vjp_rollout(hopu_ctx* c, const void* u0_hdiv, double dt, int n_
   r = body();
   c->elog = elog;
   return r;
+}
+
+hopu_status hopu_boundary_facets(const hopu_ctx* c, int64_t* out, int64_t* count) {
+  if (!c) return HOPU_EINVAL;
+  if (count) *count = (int64_t)c->topo.boundary.size();
+  if (out) std::copy(c->topo.boundary.begin(), c->topo.boundary.end(), out);
+  return HOPU_OK;
+}
+
+hopu_status hopu_set_inlet(hopu_ctx* c, const int64_t* facets, int64_t n, const double* values) {
+  HOPU_PRECHECK(c);
+  if (n < 0 || (n > 0 && (!facets || !values))) return fail(c, HOPU_EINVAL, "set_inlet: bad arguments");
+  const RefTables& R = c->ref;
+  const int d = c->dim, nf = R.nf, nqf = R.nqf;
+  const int64_t NF = c->topo.n_facets;
+  std::vector<int32_t> row((size_t)NF, -1);
+  std::vector<double> modes((size_t)n * nf * d, 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t F = facets[r];
+    if (F < 0 || F >= NF || !std::binary_search(c->topo.boundary.begin(), c->topo.boundary.end(), F))
+      return fail(c, HOPU_EINVAL, "set_inlet: facet " + std::to_string(F) + " is not a boundary facet");
+    if (row[(size_t)F] >= 0) return fail(c, HOPU_EINVAL, "set_inlet: facet listed twice");
+    row[(size_t)F] = (int32_t)r;
+    // modal exterior trace: the facet-rule moments against the orthonormal facet basis
+    for (int m = 0; m < nf; ++m)
+      for (int a = 0; a < d; ++a) {
+        double acc = 0.0;
+        for (int q = 0; q < nqf; ++q)
+          acc += R.wf[q] * R.psi[(size_t)q * nf + m] * values[((size_t)r * nqf + q) * d + a];
+        modes[((size_t)r * nf + m) * d + a] = acc;
+      }
+  }
+  HOPU_CUDA(c, cudaStreamSynchronize(c->stream));  // kernels in flight may read the old data
+  if (c->d_inlet) cudaFree(c->d_inlet);
+  if (c->d_inlet_modes) cudaFree(c->d_inlet_modes);
+  c->d_inlet = nullptr;
+  c->d_inlet_modes = nullptr;
+  c->dm.inlet = nullptr;
+  c->dm.inlet_modes = nullptr;
+  c->n_inlet = n;
+  if (c->gexec) {  // the cached substep graph holds the old mesh view
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  if (n == 0) return HOPU_OK;
+  std::vector<unsigned char> hm(c->tsize * modes.size());
+  if (c->fp64) convert<double>(modes, hm, 0);
+  else convert<float>(modes, hm, 0);
+  HOPU_CUDA(c, cudaMalloc((void**)&c->d_inlet, sizeof(int32_t) * NF));
+  HOPU_CUDA(c, cudaMemcpy(c->d_inlet, row.data(), sizeof(int32_t) * NF, cudaMemcpyHostToDevice));
+  HOPU_CUDA(c, cudaMalloc(&c->d_inlet_modes, hm.size()));
+  HOPU_CUDA(c, cudaMemcpy(c->d_inlet_modes, hm.data(), hm.size(), cudaMemcpyHostToDevice));
+  c->dm.inlet = c->d_inlet;
+  c->dm.inlet_modes = c->d_inlet_modes;
+  return HOPU_OK;
 }
 
 hopu_status hopu_set_facet_l(hopu_ctx* c, const int8_t* facet_l) {

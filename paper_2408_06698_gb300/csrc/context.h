@@ -49,6 +49,9 @@ struct hopu_ctx {
   int* d_err = nullptr;     // device error word (DevMesh::err)
   bool have_frozen = false;
   const int8_t* facet_l = nullptr;  // per-facet HOPU orders (hopu_set_facet_l), or NULL
+  int32_t* d_inlet = nullptr;       // [NF] inlet row or -1 (hopu_set_inlet)
+  void* d_inlet_modes = nullptr;    // [n_inlet][nf][d] modal exterior traces
+  int64_t n_inlet = 0;
   // per-substep kinetic-energy log (device ring buffer owned by the caller)
   double* elog = nullptr;
   int64_t elog_cap = 0;

@@ -18,6 +18,10 @@ struct DevMesh {
   const int32_t* fb = nullptr;   // [NF]: same for side B
   const double* fgeo = nullptr;  // [NF][d+1]: canonical unit normal n_F, a_F = |F|/|param|
   int* err = nullptr;            // device error word (bit 0: a tensor-core completion wait gave up)
+  // boundary facets have fb[F] == fa[F] (wall / outlet rule: the exterior trace is the
+  // interior one); inlet facets also have inlet[F] >= 0, the row of their exterior data
+  const int32_t* inlet = nullptr;  // [NF] or NULL (no inlets)
+  const void* inlet_modes = nullptr;  // [n_inlet][nf][d] modal exterior trace, working precision
 };
 
 // Device reference tables in working precision (all element-type T, 16-byte aligned).

@@ -580,14 +580,17 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       }
     }
     __syncwarp();
-    // modal traces: jump and average wind
+    // modal traces: jump and average wind (an inlet facet's side B is its given data)
+    const int inl = m.inlet ? m.inlet[F] : -1;
+    const T* ext = inl >= 0 ? static_cast<const T*>(m.inlet_modes) + (int64_t)inl * NF * D : nullptr;
     for (int v = lane; v < NF * D; v += 32) {
       const int mm = v / D, a = v - mm * D;
       const T* ra = TrM + (fa * NF + mm) * NBP;
       const T* rb = TrM + (fb * NF + mm) * NBP;
-      const T ta = dot_ss<NB>(ra, cA + a * NBP), tbv = dot_ss<NB>(rb, cB + a * NBP);
+      const T ta = dot_ss<NB>(ra, cA + a * NBP);
+      const T tbv = ext ? ext[mm * D + a] : dot_ss<NB>(rb, cB + a * NBP);
       const T wa = WSEP ? dot_ss<NB>(ra, wA + a * NBP) : ta;
-      const T wb = WSEP ? dot_ss<NB>(rb, wB + a * NBP) : tbv;
+      const T wb = ext ? ext[mm * D + a] : (WSEP ? dot_ss<NB>(rb, wB + a * NBP) : tbv);
       sJ[mm * 4 + a] = ta - tbv;
       sWv[mm * 4 + a] = T(0.5) * (wa + wb);
     }
@@ -659,8 +662,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       for (int a = 0; a < D; ++a) sOut[(which * NF + mm) * 4 + a] = aF * acc[a];
     }
     __syncwarp();
-    // element-major output: side A's slot gets alpha + beta, side B's alpha - beta
-    for (int v = lane; v < 2 * NF * D; v += 32) {
+    // element-major output: side A's slot gets alpha + beta, side B's alpha - beta (a
+    // boundary facet has no side B: fb == fa)
+    for (int v = lane; v < (pb == pa ? 1 : 2) * NF * D; v += 32) {
       const int side = v / (NF * D), rest = v - side * (NF * D);
       const int mm = rest / D, a = rest - mm * D;
       const T al = sOut[mm * 4 + a], be = sOut[(NF + mm) * 4 + a];
@@ -967,8 +971,11 @@ __global__ void __launch_bounds__(256) k_l2v_facet(DevMesh m, const T* __restric
     const int64_t F = t / NF;
     const int mm = (int)(t - F * NF);
     const int pa = m.fa[F], pb = m.fb[F];
-    T v = lf[((int64_t)(pa >> 2) * (D + 1) + (pa & 3)) * NF + mm] + lf[((int64_t)(pb >> 2) * (D + 1) + (pb & 3)) * NF + mm];
-    if (!DUAL) v *= T(0.5);
+    T v = lf[((int64_t)(pa >> 2) * (D + 1) + (pa & 3)) * NF + mm];
+    if (pb != pa) {  // an interior facet: average (R) or sum (transpose) of the two copies
+      v += lf[((int64_t)(pb >> 2) * (D + 1) + (pb & 3)) * NF + mm];
+      if (!DUAL) v *= T(0.5);
+    }
     outV[t] = combine_at<T>(cmb, v, t);
   }
 }

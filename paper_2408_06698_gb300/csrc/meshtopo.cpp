@@ -133,6 +133,7 @@ int build_mesh_topo(int d, int64_t nv, const double* coords, int64_t ne, const i
   m.efc.assign((size_t)nef, 0);
   m.fa.clear();
   m.fb.clear();
+  m.boundary.clear();
   m.fgeo.clear();
   int64_t i = 0;
   while (i < nef) {
@@ -148,7 +149,7 @@ int build_mesh_topo(int d, int64_t nv, const double* coords, int64_t ne, const i
     }
     const int64_t cnt = j - i;
     if (cnt > 2) { err = "mesh: non-manifold facet (more than two neighbours)"; return HOPU_EMESH; }
-    if (cnt < 2) { err = "mesh: boundary facet (only closed/periodic meshes are supported)"; return HOPU_ENOTSUP; }
+    const bool bnd = (cnt == 1);  // boundary facet: its single element is side A
     const int64_t F = (int64_t)m.fa.size();
     int side_a = -1;
     double nA[3] = {0, 0, 0}, aA = 0.0;
@@ -172,6 +173,12 @@ int build_mesh_topo(int d, int64_t nv, const double* coords, int64_t ne, const i
         }
         dot += o * cr[b];
       }
+      // a boundary facet whose element points against the canonical normal is flipped
+      const bool flip = bnd && !(dot > 0.0);
+      if (flip) {
+        for (int c = 0; c < d; ++c) cr[c] = -cr[c];
+        dot = -dot;
+      }
       const bool is_a = dot > 0.0;
       const double det = m.geo[(size_t)e * G + 2 * d * d];
       const bool sigma_neg = ((dot > 0.0) != (det > 0.0));
@@ -185,8 +192,13 @@ int build_mesh_topo(int d, int64_t nv, const double* coords, int64_t ne, const i
       }
     }
     if (side_a < 0) { err = "mesh: both neighbours of a facet lie on the same side"; return HOPU_EMESH; }
-    const int64_t idb = order[i + (side_a == 0 ? 1 : 0)];
-    m.fb.push_back((int32_t)((idb / nvl) * 4 + (idb % nvl)));
+    if (bnd) {
+      m.fb.push_back(m.fa.back());  // side B = side A: the wall / outlet rule (no jump)
+      m.boundary.push_back(F);
+    } else {
+      const int64_t idb = order[i + (side_a == 0 ? 1 : 0)];
+      m.fb.push_back((int32_t)((idb / nvl) * 4 + (idb % nvl)));
+    }
     for (int c = 0; c < d; ++c) m.fgeo.push_back(nA[c]);
     m.fgeo.push_back(aA);
     i = j;

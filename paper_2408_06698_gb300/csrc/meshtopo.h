@@ -17,12 +17,15 @@ struct MeshTopo {
   // per facet
   std::vector<int32_t> fa, fb;  // packed element*4 + local facet of side A / side B
   std::vector<double> fgeo;     // [F][dim+1]: n_F (unit, canonical), a_F = |F| / |param|
+  // boundary facets (one neighbour, side B = side A, n_F outward), ascending
+  std::vector<int64_t> boundary;
 };
 
 inline int geo_stride(int dim) { return 2 * dim * dim + 2; }
 
 // Build topology and geometry.  Returns 0 on success, otherwise a hopu_status code with
-// a message in err (EMESH for invalid meshes, ENOTSUP for boundary facets).
+// a message in err (EMESH for invalid meshes).  Facets with one neighbour are boundary
+// facets: that element is side A (n_F flipped outward if needed) and also side B.
 int build_mesh_topo(int dim, int64_t nv, const double* coords, int64_t ne, const int64_t* ev,
                     const int64_t* rep, MeshTopo& out, std::string& err);
 

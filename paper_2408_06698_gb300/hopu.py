@@ -126,6 +126,28 @@ class Hopu:
                                               byref(loss) if seed is None else None), "hopu_vjp_rollout")
         return (float(loss.value) if seed is None else None), out
 
+    def boundary_facets(self) -> np.ndarray:
+        """Ids of the facets with a single element (walls / outlets unless declared inlets)."""
+        cnt = c_int64()
+        self._check(self.lib.hopu_boundary_facets(self.ctx, None, byref(cnt)), "hopu_boundary_facets")
+        out = np.empty(cnt.value, dtype=np.int64)
+        if cnt.value:
+            self._check(self.lib.hopu_boundary_facets(self.ctx, out.ctypes.data, None), "hopu_boundary_facets")
+        return out
+
+    def set_inlet(self, facets, values=None, fun=None):
+        """Declare boundary facets inlets with data u_I given at their facet quadrature
+        points (values [n, nqf, dim]) or as a callable of points; no facets clears them."""
+        f = np.ascontiguousarray(np.asarray(facets, dtype=np.int64).reshape(-1))
+        if f.size == 0:
+            self._check(self.lib.hopu_set_inlet(self.ctx, None, 0, None), "hopu_set_inlet")
+            return
+        if values is None:
+            pts = self.points("facet").reshape(self.n_facets, -1, self.dim)[f]
+            values = fun(pts)
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self._check(self.lib.hopu_set_inlet(self.ctx, f.ctypes.data, f.size, v.ctypes.data), "hopu_set_inlet")
+
     def set_facet_l(self, facet_l: torch.Tensor | None):
         """Per-facet HOPU orders (int8 device tensor, kept referenced) for later calls; None = uniform l."""
         if facet_l is None:
