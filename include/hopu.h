@@ -195,11 +195,12 @@ hopu_status hopu_energy(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2, dou
  * count).                                                                             */
 hopu_status hopu_boundary_facets(const hopu_ctx* ctx, int64_t* out, int64_t* count);
 
-/* Declare n boundary facets inlets (Section 2.2: jump and average use the inlet data
- * u_I) and give u_I at their facet quadrature points (the points of hopu_points, facet
- * order of `facets`): values host FP64 [n][nqf][dim].  The data enter through their
- * L2 projection onto P^k of the facet (exact for polynomial data of degree <= k) and
- * also serve as the exterior wind.  Replaces the previous inlet set; n = 0 makes every
+/* Declare n boundary facets inlets (Section 2.2: jump and average of the convected
+ * velocity use the inlet data u_I) and give u_I at their facet quadrature points (the
+ * points of hopu_points, facet order of `facets`): values host FP64 [n][nqf][dim].  The
+ * data enter through their L2 projection onto P^k of the facet (exact for polynomial
+ * data of degree <= k); the wind keeps its own normal component there (w.n of a V_h
+ * field is single-valued).  Replaces the previous inlet set; n = 0 makes every
  * boundary facet a wall / outlet again.  EINVAL for a facet that is not a boundary
  * facet or is listed twice.  Synchronises the stream; drops the cached substep graph. */
 hopu_status hopu_set_inlet(hopu_ctx* ctx, const int64_t* facets, int64_t n, const double* values);

@@ -89,7 +89,9 @@ def facet_quantities(topo, ref, wL, uL, l, exterior=None, inlet=None):
     and outlet facets carry no term in the paper's form):
     * inlet facets take the given exterior traces as side B (Section 2.2: the jump and
       the average use u_I); exterior = (u_ext, w_ext) arrays [F, nqf, d]; inlet is a
-      boolean mask [F] (None: every boundary facet is an inlet when exterior is given);
+      boolean mask [F] (None: every boundary facet is an inlet when exterior is given).
+      The wind of a V_h field has a single-valued normal component, so callers give
+      w_ext = the wind's own trace (reading A12); a different w_ext is also accepted;
     * the other boundary facets (walls, outlets) take side A's own trace as side B:
       the jump vanishes, so the paper's form has no term there, and the conservative
       form keeps the flux (w.n) u . v that its element-wise integration by parts needs

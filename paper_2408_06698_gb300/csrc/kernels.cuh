@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       }
     }
     __syncwarp();
-    // modal traces: jump and average wind (an inlet facet's side B is its given data)
+    // modal traces: jump and average wind (an inlet facet's side B of u is its given data)
     const int inl = m.inlet ? m.inlet[F] : -1;
     const T* ext = inl >= 0 ? static_cast<const T*>(m.inlet_modes) + (int64_t)inl * NF * D : nullptr;
     for (int v = lane; v < NF * D; v += 32) {
@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       const T ta = dot_ss<NB>(ra, cA + a * NBP);
       const T tbv = ext ? ext[mm * D + a] : dot_ss<NB>(rb, cB + a * NBP);
       const T wa = WSEP ? dot_ss<NB>(ra, wA + a * NBP) : ta;
-      const T wb = ext ? ext[mm * D + a] : (WSEP ? dot_ss<NB>(rb, wB + a * NBP) : tbv);
+      const T wb = ext ? wa : (WSEP ? dot_ss<NB>(rb, wB + a * NBP) : tbv);  // an inlet keeps the wind's own w.n
       sJ[mm * 4 + a] = ta - tbv;
       sWv[mm * 4 + a] = T(0.5) * (wa + wb);
     }

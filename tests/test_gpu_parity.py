@@ -198,8 +198,8 @@ def test_invalid_arguments_are_reported():
     bad[0, 1] = bad[0, 0]
     with pytest.raises(HopuError, match="EMESH"):
         Hopu(m.coords, bad, m.rep, k=2)
-    with pytest.raises(HopuError, match="ENOTSUP"):   # a non-periodic mesh has boundary facets
-        Hopu(m.coords, m.elems, None, k=2)
+    with pytest.raises(HopuError, match="EMESH"):     # a facet with three neighbours
+        Hopu(m.coords, np.concatenate([m.elems, m.elems[:1]]), m.rep, k=2)
     g = Hopu(m.coords, m.elems, m.rep, k=2)
     x = g.new("hdiv")
     with pytest.raises(ValueError):
