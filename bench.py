@@ -152,7 +152,14 @@ def oracle_worker(args):
     sp = hdiv.HDiv(mesh.MeshTopo(m.coords, m.elems, m.rep), fe.ref_element(dim, k))
     u = sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, WORKLOAD["noise"], WORKLOAD["seed"])
     res = {"n": n, "n_l2": sp.n_l2, "elements": sp.topo.n_elems}
-    if cfg["mode"] == "sample":
+    if cfg["mode"] == "vjp_sample":
+        from oracle import adjoint as A
+        t0 = time.perf_counter()
+        loss, _ = A.rollout_vjp(sp, u, dt, cfg["steps"], l)
+        res["seconds"] = time.perf_counter() - t0
+        res["steps"] = cfg["steps"]
+        res["loss"] = float(loss)
+    elif cfg["mode"] == "sample":
         t0 = time.perf_counter()
         u1 = rk.substeps_stage(sp, u, dt, 1, l)
         res["seconds"] = time.perf_counter() - t0
@@ -576,6 +583,14 @@ def our_arm(args, rank, world):
             errs[prec] = {"max_rel": float(np.abs(got - u1).max() / np.abs(u1).max()),
                           "l2_rel": float(np.linalg.norm(got - u1) / np.linalg.norm(u1))}
         line["error_vs_oracle_one_substep"] = errs
+        if line.get("vjp"):
+            rv = run_oracle({"mode": "vjp_sample", "n": 6, "steps": 2, "out": os.path.join(tmp, "v")})
+            line["vjp"]["cpu_baseline"] = {
+                "value": rv["n_l2"] * APPLIES_PER_STEP * rv["steps"] / rv["seconds"], "unit": UNIT,
+                "cores": 1, "kind": "oracle",
+                "sample": "FP64 oracle rollout + adjoint, 2 STAGE substeps of the 6^3 x 6 k=3 box "
+                          "(same recipe), forward-equivalent DOF-updates/s, 1 BLAS thread",
+                "seconds": rv["seconds"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
