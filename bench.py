@@ -333,7 +333,10 @@ def other_configs(dev, stream, world):
                 y64r = g64.apply_convection(ur, g64.project("hdiv_to_l2", ur))
             stream.synchronize()
             err_same = float((yd - y64r).abs().max() / y64r.abs().max())
+            l2_same = float(torch.linalg.vector_norm(yd - y64r) / torch.linalg.vector_norm(y64r))
         err = float((yd - ref_y).abs().max() / ref_y.abs().max())
+        if prec == "f64":
+            l2_same = 0.0
         log = torch.zeros(12, dtype=torch.float64, device=dev)
         g.set_energy_log(log)
         ms = _events_ms(stream, lambda: g.rk_substep(u, 5e-4, 1), 10)
@@ -342,6 +345,7 @@ def other_configs(dev, stream, world):
         prec_rows[prec] = {"ms_per_substep": ms / 10, "value": g.n_l2 * APPLIES_PER_STEP * 10 / (ms / 1e3),
                            "unit": UNIT, "apply_max_rel_err_vs_gpu_f64": err,
                            "apply_max_rel_err_vs_gpu_f64_same_rounded_input": err_same,
+                           "apply_l2_rel_err_vs_gpu_f64_same_rounded_input": l2_same,
                            "energy_drift_per_substep": float(np.mean(np.diff(e)) / e[0])}
         if prec != "f64":
             del g

@@ -6,6 +6,7 @@
 // grids are persistent (a multiple of the SM count), so every CTA loads them once.
 // Geometry is stored in FP64 and rounded to T at use.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -711,7 +712,8 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   constexpr int NBQ = row_stride<T>(NB);
   constexpr int BT = NQ * NBQ, DM = D * NB1 * NB, TRM = (D + 1) * NF * NB;
   constexpr int FT = FUSE ? FuseCfg<D, K, T>::TAB : 0, NLR = FuseCfg<D, K, T>::NLR;
-  constexpr int TABN = r4i(BT + NQ + DM + TRM) + r4i(FT);
+  constexpr int OTRM = r4i(BT + NQ + DM);  // TrM 16-byte aligned (paired loads in the lift)
+  constexpr int TABN = r4i(OTRM + TRM) + r4i(FT);
   constexpr int NG = (D + 1) * NF * D;
   constexpr int QB = (sizeof(T) == 4 && NQ > 32) ? 2 : 1;  // quadrature points per lane and pass
   static_assert(!FUSE || (STAB && FuseCfg<D, K, T>::OK), "fused back-projection needs staged tables");
@@ -732,14 +734,14 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     for (int t = threadIdx.x; t < BT; t += blockDim.x) sbase[t] = Bt[t];
     for (int t = threadIdx.x; t < NQ; t += blockDim.x) sbase[BT + t] = Wq[t];
     for (int t = threadIdx.x; t < DM; t += blockDim.x) sbase[BT + NQ + t] = Dm[t];
-    for (int t = threadIdx.x; t < TRM; t += blockDim.x) sbase[BT + NQ + DM + t] = TrM[t];
+    for (int t = threadIdx.x; t < TRM; t += blockDim.x) sbase[OTRM + t] = TrM[t];
     Bt = sbase;
     Wq = sbase + BT;
     Dm = sbase + BT + NQ;
-    TrM = sbase + BT + NQ + DM;
+    TrM = sbase + OTRM;
     sw = sbase + TABN;
   }
-  T* Drow = sbase + r4i(BT + NQ + DM + TRM);  // [NL][NLR] row-major D (FUSE)
+  T* Drow = sbase + r4i(OTRM + TRM);  // [NL][NLR] row-major D (FUSE)
   if (FUSE) {
     const T* Dg = static_cast<const T*>(tb.Drow);
     for (int t = threadIdx.x; t < FT; t += blockDim.x) Drow[t] = Dg[t];
@@ -761,6 +763,35 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     if (WSEP) warp_copy_async<NL * (int)sizeof(T)>(st_w(b), wL + e * NL, lane);
     warp_copy_async<NG * (int)sizeof(T)>(st_g(b), gam + e * NG, lane);
     warp_copy_async<GEO * (int)sizeof(T)>(st_geo(b), static_cast<const T*>(m.geoT) + e * GEO, lane);
+  };
+  // facet lift of this lane's outputs: acc[j] += sum_fm TrM[fm][i] gl[fm][a]; with two
+  // outputs per lane of one component and consecutive basis indices (NB even) every
+  // paired TrM load and every moment load feed two FMAs
+  auto lift = [&](T* accv, const T* gl) {
+    if constexpr (CPL == 2 && NB % 2 == 0) {
+      const int idx = lane * 2;
+      if (idx < NL) {
+        const int a = idx / NB, i = idx - a * NB;
+#pragma unroll 4
+        for (int fm = 0; fm < (D + 1) * NF; ++fm) {
+          using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+          const T gv = gl[fm * D + a];
+          const P2 tp = *reinterpret_cast<const P2*>(TrM + fm * NB + i);  // i even: aligned pair
+          accv[0] = fma(tp.x, gv, accv[0]);
+          accv[1] = fma(tp.y, gv, accv[1]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const int idx = lane * CPL + j;
+        if (idx < NL) {
+          const int a = idx / NB, i = idx - a * NB;
+#pragma unroll 4
+          for (int fm = 0; fm < (D + 1) * NF; ++fm) accv[j] = fma(TrM[fm * NB + i], gl[fm * D + a], accv[j]);
+        }
+      }
+    }
   };
   const int64_t stride = (int64_t)gridDim.x * kWarps;
   int64_t e = (int64_t)blockIdx.x * kWarps + warp;
@@ -903,31 +934,24 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     }
     reduce_scatter<NVP>(acc, lane);
     if (!FUSE) {
+      lift(acc, gl);
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
         const int idx = lane * CPL + j;
-        if (idx < NL) {
-          const int a = idx / NB, i = idx - a * NB;
-          T r = acc[j];
-#pragma unroll 4
-          for (int fm = 0; fm < (D + 1) * NF; ++fm) r = fma(TrM[fm * NB + i], gl[fm * D + a], r);
-          out[e * NL + idx] = combine_at<T>(cmb, r * invabs, e * NL + idx);
-        }
+        if (idx < NL) out[e * NL + idx] = combine_at<T>(cmb, acc[j] * invabs, e * NL + idx);
       }
     } else {
       // fused a7 (element part): y -> chat = det J Jinv y -> ell = D chat; interior rows
       // combined into the V_h output, facet rows to lf with the sign sigma
       T* sY = sC;  // [D][NBP], u coefficients are no longer needed
       T* sCh = sG; // [NL (padded to 4)]
+      lift(acc, gl);
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
         const int idx = lane * CPL + j;
         if (idx < NL) {
           const int a = idx / NB, i = idx - a * NB;
-          T r = acc[j];
-#pragma unroll 4
-          for (int fm = 0; fm < (D + 1) * NF; ++fm) r = fma(TrM[fm * NB + i], gl[fm * D + a], r);
-          sY[a * NBP + i] = r * invabs;
+          sY[a * NBP + i] = acc[j] * invabs;
         }
       }
       __syncwarp();
