@@ -73,9 +73,13 @@ __global__ void __launch_bounds__(kRedThreads) k_weighted_dot(int64_t E, int NL,
                                                               const T* a, const T* b, double* partial) {
   double s = 0.0;
   const int64_t n = E * NL;
-  for (int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; t < n; t += (int64_t)gridDim.x * kRedThreads) {
-    const int64_t e = t / NL;
-    s += geo[e * G + G - 1] * double(a[t]) * double(b[t]);
+  if (n < (int64_t(1) << 31)) {  // 32-bit index arithmetic (a 64-bit division per entry is slow)
+    const int n32 = (int)n, stride = (int)gridDim.x * kRedThreads;
+    for (int t = (int)blockIdx.x * kRedThreads + (int)threadIdx.x; t < n32; t += stride)
+      s += geo[(int64_t)(t / NL) * G + G - 1] * (double(a[t]) * double(b[t]));
+  } else {
+    for (int64_t t = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; t < n; t += (int64_t)gridDim.x * kRedThreads)
+      s += geo[(t / NL) * G + G - 1] * (double(a[t]) * double(b[t]));
   }
   const double tot = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
