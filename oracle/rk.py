@@ -9,8 +9,10 @@ explicit substep, so the Shu-Osher SSP-RK3 scheme is used:
 Wind rules (reading of the paper's silence on the wind inside substeps):
 
 * STAGE  (default): the state lives in V_h; at every stage w = u = E u_V and
-  A(u_V) = R E_T^{-1} M_L^{-1} c(E u_V; E u_V, .).  Parity unpinned beyond
-  GPU-vs-oracle agreement (no closed form for the nonlinear stage map).
+  A(u_V) = R E_T^{-1} M_L^{-1} c(E u_V; E u_V, .).  No closed form for the
+  nonlinear stage map; pinned by the scheme's third order in dt (with the central
+  flux the map is smooth and the error at a fixed time falls by 2^3 per halving),
+  momentum conservation and first-order consistency (tests).
 * FROZEN: the wind w = E w_V is fixed; the state lives in L2 and
   A(u_L) = M_L^{-1} c(w; u_L, .), which is linear in u_L.  Pinned: one substep
   equals u - dt A u + dt^2/2 A^2 u - dt^3/6 A^3 u (tests).

@@ -359,3 +359,17 @@ def test_energy_identity_with_walls(dim, k):
         diss = C.facet_dissipation(t, sp.ref, wL, uL, l)
         assert abs(cval - diss) < 1e-11 * abs(diss), l
     del L
+
+
+def test_stage_substeps_are_third_order_in_time():
+    """SSP-RK3 (Shu-Osher) is third order: with the central flux (l = k, no |w.n| factor,
+    so the STAGE right-hand side is a smooth quadratic map of the V_h state) the error at
+    a fixed time falls by 2^3 when the substep halves.  A wrong stage weight or a stage
+    evaluated at the wrong state drops the order."""
+    sp = _space(2, 4, 2)
+    u0 = sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-2, 7)
+    T = 0.4
+    ref = rk.substeps_stage(sp, u0, T / 256, 256, 2)
+    errs = [np.abs(rk.substeps_stage(sp, u0, T / n, n, 2) - ref).max() for n in (8, 16, 32)]
+    rates = [np.log2(a / b) for a, b in zip(errs, errs[1:])]
+    assert all(2.8 < r < 3.3 for r in rates), (errs, rates)
