@@ -558,7 +558,7 @@ def our_arm(args, rank, world):
                    "gbs": alg[f][1] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9} for f in FAMILIES}
     step_bytes = sum(alg[f][1] * (acc[f][1] / max(1, Kp)) for f in FAMILIES)
     hbm_step_frac = step_bytes / (dev_ms / K / 1e3) / 1e9 / hbm_peak
-    launches = round(sum(acc[f][1] for f in FAMILIES) * K / Kp) + 2 * K   # + the two energy-log kernels per substep
+    launches = round(sum(acc[f][1] for f in FAMILIES) * K / Kp) + K   # + the energy-log kernel of every substep
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,

@@ -85,18 +85,110 @@ __global__ void __launch_bounds__(kRedThreads) k_weighted_dot(int64_t E, int NL,
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// Sum the block partials and append 1/2 * total to a ring buffer at the device-side
-// position *pos (advanced by one), so replayed graphs log every substep.
-__global__ void __launch_bounds__(kRedThreads) k_sum_log(const double* in, int64_t n, double* log,
-                                                         int64_t cap, int64_t* pos) {
-  double s = 0.0;
-  for (int64_t t = threadIdx.x; t < n; t += kRedThreads) s += in[t];
-  const double tot = block_sum(s);
-  if (threadIdx.x == 0) {
-    const int64_t p = *pos;
-    log[p % cap] = 0.5 * tot;
-    *pos = p + 1;
+// sum_t u_t^2 over one element's NL entries.  FP32: every square split exactly into
+// p + e (p = fl(u*u), e = fma(u, u, -p)) and the p summed with TwoSum (Knuth), so the pair
+// hi + lo carries the element sum to about NL * 2^-48 relative; FP64: fused multiply-adds.
+// GB300 issues FP64 at a small fraction of its FP32 rate: this keeps FP64 arithmetic to a
+// few operations per element.  Up to 16 float4 loads are issued before the first is used.
+__device__ __forceinline__ void two_sum_sq(float x, float& hi, float& lo) {
+  const float p = __fmul_rn(x, x), e = __fmaf_rn(x, x, -p);
+  const float s = __fadd_rn(hi, p), bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+  hi = s;
+}
+__device__ __forceinline__ double elem_sq(const float* u, int NL) {
+  float hi = 0.f, lo = 0.f;
+  if ((NL & 3) == 0 && (reinterpret_cast<uintptr_t>(u) & 15) == 0) {
+    const float4* v = reinterpret_cast<const float4*>(u);
+    const int n4 = NL / 4;
+    for (int i = 0; i < n4; i += 16) {
+      float4 q[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (i + j < n4) q[j] = __ldg(v + i + j);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (i + j < n4)
+          two_sum_sq(q[j].x, hi, lo), two_sum_sq(q[j].y, hi, lo), two_sum_sq(q[j].z, hi, lo), two_sum_sq(q[j].w, hi, lo);
+    }
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < NL; ++i) two_sum_sq(__ldg(u + i), hi, lo);
   }
+  return double(hi) + double(lo);
+}
+__device__ __forceinline__ double elem_sq(const double* u, int NL) {
+  double s = 0.0;
+#pragma unroll 8
+  for (int i = 0; i < NL; ++i) s = fma(__ldg(u + i), __ldg(u + i), s);
+  return s;
+}
+
+// butterfly sum over the warp (the same order, and result, in every lane)
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Kinetic energy of the state into the device log in one kernel: one thread per element
+// (strided), |det J_e| sum_t u_t^2 accumulated in FP64; every block writes its partial to
+// partial[block]; the block that arrives last (ticket) sums the partials in block order
+// (deterministic), writes 1/2 * total to log[*pos % cap], advances *pos and resets the
+// ticket, so replayed graphs log every substep.  Small blocks spread the elements over
+// every SM.  Launched as a programmatic dependent of the projection before it.
+constexpr int kElogThreads = 64;
+template <typename T>
+__global__ void __launch_bounds__(kElogThreads) k_energy_log(int64_t E, int NL, int G, const double* geo,
+                                                             const T* u, double* partial, unsigned* ticket,
+                                                             double* log, int64_t cap, int64_t* pos) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  constexpr int NW = kElogThreads / 32;
+  __shared__ double ws[NW];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * kElogThreads + threadIdx.x; e < E; e += (int64_t)gridDim.x * kElogThreads)
+    s = fma(__ldg(geo + e * G + G - 1), elem_sq(u + e * NL, NL), s);
+  s = warp_sum(s);
+  if (lane == 0) ws[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < NW; ++w) tot += ws[w];
+    partial[blockIdx.x] = tot;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s2 = 0.0;
+  for (int t0 = threadIdx.x; t0 < (int)gridDim.x; t0 += 8 * kElogThreads) {  // 8 loads in flight
+    double q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q[j] = (t0 + j * kElogThreads < (int)gridDim.x) ? __ldcg(partial + t0 + j * kElogThreads) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s2 += q[j];
+  }
+  s2 = warp_sum(s2);
+  if (lane == 0) ws[warp] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double total = 0.0;
+    for (int w = 0; w < NW; ++w) total += ws[w];
+    const int64_t p = *pos;
+    log[p % cap] = 0.5 * total;
+    *pos = p + 1;
+    *ticket = 0u;
+  }
+}
+
+// blocks of the energy-log kernel: one thread per element, at most 8 blocks per SM
+int64_t elog_blocks(int64_t n_elems, int nsm) {
+  const int64_t need = (n_elems + kElogThreads - 1) / kElogThreads;
+  return std::max<int64_t>(1, std::min<int64_t>(need, 8 * (int64_t)nsm));
 }
 
 // x = a x + b y (n entries)
@@ -364,14 +456,24 @@ hopu_status enqueue_stage_fused(hopu_ctx* c, Combine cmb, void* outV) {
 
 hopu_status energy_log(hopu_ctx* c, const void* uL) {
   const int G = geo_stride(c->dim);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)elog_blocks(c->topo.n_elems, c->nsm));
+  cfg.blockDim = dim3(kElogThreads);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  unsigned* ticket = reinterpret_cast<unsigned*>(c->d_elog_pos + 1);
+  double* partial = reinterpret_cast<double*>(c->d_elog_pos + 2);
   if (c->fp64)
-    k_weighted_dot<double><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-        c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const double*)uL, (const double*)uL, c->d_red);
+    cudaLaunchKernelEx(&cfg, k_energy_log<double>, (int64_t)c->topo.n_elems, (int)c->ref.nloc, G, c->dm.geo,
+                       (const double*)uL, partial, ticket, c->elog, c->elog_cap, c->d_elog_pos);
   else
-    k_weighted_dot<float><<<c->red_blocks, kRedThreads, 0, c->stream>>>(
-        c->topo.n_elems, c->ref.nloc, G, c->dm.geo, (const float*)uL, (const float*)uL, c->d_red);
-  k_sum_log<<<1, kRedThreads, 0, c->stream>>>(c->d_red, c->red_blocks, c->elog, c->elog_cap, c->d_elog_pos);
-  return check_launch(c, "energy log kernels");
+    cudaLaunchKernelEx(&cfg, k_energy_log<float>, (int64_t)c->topo.n_elems, (int)c->ref.nloc, G, c->dm.geo,
+                       (const float*)uL, partial, ticket, c->elog, c->elog_cap, c->d_elog_pos);
+  return check_launch(c, "energy log kernel");
 }
 
 // One SSP-RK3 (Shu-Osher) substep on the context stream.
@@ -678,8 +780,10 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_err, sizeof(int)));
   HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
   c->dm.err = c->d_err;
-  HOPU_CUDA(c, cudaMalloc((void**)&c->d_elog_pos, sizeof(int64_t)));
-  HOPU_CUDA(c, cudaMemset(c->d_elog_pos, 0, sizeof(int64_t)));
+  // position, ticket, then the per-block partials of the energy-log kernel
+  const size_t elog_bytes = sizeof(int64_t) * (2 + elog_blocks(c->topo.n_elems, c->nsm));
+  HOPU_CUDA(c, cudaMalloc((void**)&c->d_elog_pos, elog_bytes));
+  HOPU_CUDA(c, cudaMemset(c->d_elog_pos, 0, elog_bytes));
   return autotune(c, opts->tile_hint);
 }
 }  // namespace

@@ -288,7 +288,7 @@ class Hopu:
     # substep launch counts (kernels per call), for the bench's launch accounting
     def launches_per_substep(self) -> int:
         n = 15 if self.wind == "stage" else 6
-        return n + (2 if getattr(self, "_elog", None) is not None else 0)
+        return n + (1 if getattr(self, "_elog", None) is not None else 0)
 
 
 class ConvectionApply(torch.autograd.Function):

@@ -139,9 +139,10 @@ def test_rk_substep_stage(dim, n, k, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_energy_log_records_every_substep(prec):
-    """a8 inside the substep graph: E(u^n) at the start of each substep, on the device."""
-    dim, n, k = 3, 3, 3
+@pytest.mark.parametrize("dim,n,k", [(3, 3, 3), (2, 4, 1)])
+def test_energy_log_records_every_substep(dim, n, k, prec):
+    """a8 inside the substep graph: E(u^n) at the start of each substep, on the device
+    (d = 3, k = 3: 60 entries per element, read as float4; d = 2, k = 1: 6, read one by one)."""
     g, sp = _mk(dim, n, k, prec, l=k - 1)
     uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
     log = torch.zeros(6, dtype=torch.float64, device=g.device)
