@@ -202,80 +202,127 @@ __device__ __forceinline__ const T* proj_setup(unsigned char* smem, const T* tab
   return sT;
 }
 
-// a1: V_h -> L2.  Per element: gather the (d+1) facet blocks with the sign sigma and the
-// interior block, reference change of basis Dinv, contravariant Piola map J / det J.
+// a1: V_h -> L2 in warp tiles.  A warp takes EW = 8 elements at a time and needs no
+// block-wide barrier, so the warps of an SM overlap one another's gathers and products.
+// Per tile: one connectivity code per lane ((d+1) x 8 <= 32; code = facet << 2 | sign),
+// the gather of the (d+1) facet blocks with the sign sigma and the interior block into
+// X[s][k] (lane-consecutive addresses), the reference change of basis Dinv as a
+// register-blocked product (four rows x four elements per lane; both operands one 16-byte
+// load), and the contravariant Piola map J / det J on the way out (coalesced stores).
 // tab = Dinv^T with rows padded to NLP: tab[s][r] = Dinv[r][s].
 // PT = true computes instead the transpose of the back-projection R E_T^{-1}: each facet
 // value goes to both copies with the averaging weight 1/2 and the sign sigma, interior
 // values are copied, then (D Piola^{-1})^T: tab[s][r] = D[s][r], Piola^{-1}^T = Pi^T.
-template <int D, int K, typename T, bool PT>
-__global__ void __launch_bounds__(kProjThreads) k_v2l(DevMesh m, const T* __restrict__ tab,
-                                                      const T* __restrict__ uV, T* __restrict__ uL) {
+template <int D, int K, typename T>
+struct ProjWCfg {
   using S = Shape<D, K>;
   using C = ProjCfg<D, K, T>;
+  static constexpr int EW = 8;  // elements per warp tile
+  static constexpr int NL = S::nloc, RG = C::RG, NLP = C::NLP, NLQ = C::NLQ, DD = D * D;
+  static constexpr int NTASK = RG * (EW / 4);  // four rows x four elements per task
+  static constexpr int NPASS = (NTASK + 31) / 32;
+  static constexpr int XW = ((NL * EW > EW * NLQ ? NL * EW : EW * NLQ) + 3) / 4 * 4;  // X, then Y
+  static constexpr int PER_WARP = XW + (EW * DD + 3) / 4 * 4;
+  static constexpr int WARPS = 8;
+  static constexpr size_t SMEM = C::TABS + size_t(WARPS) * PER_WARP * sizeof(T);
+  static_assert((D + 1) * EW <= 32, "one connectivity code per lane");
+  static_assert(SMEM <= 227 * 1024, "projection tile exceeds shared memory");
+};
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* o) {  // 4 consecutive values, 16-byte aligned
+  Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p), o);
+  if constexpr (Pack<T>::W == 2) Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p + 2), o + 2);
+}
+
+template <int D, int K, typename T, bool PT>
+__global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_v2l(DevMesh m, const T* __restrict__ tab,
+                                                                       const T* __restrict__ uV, T* __restrict__ uL) {
+  using S = Shape<D, K>;
+  using W = ProjWCfg<D, K, T>;
   constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
-  constexpr int NLP = C::NLP, NLQ = C::NLQ, TE = C::TE;
+  constexpr int NLP = W::NLP, NLQ = W::NLQ, EW = W::EW, DD = W::DD, NC = (D + 1) * EW;
+  constexpr int NIT = (NL * EW + 31) / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_trigger();
   const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
   const T* geoT = static_cast<const T*>(m.geoT);
-  T* sX = reinterpret_cast<T*>(smem_raw + C::TABS);         // [TE][NLQ]
-  T* sGeo = reinterpret_cast<T*>(smem_raw + C::TABS + ((size_t(TE) * NLQ * sizeof(T) + 15) / 16) * 16);
-  int* sCode = reinterpret_cast<int*>(sGeo + TE * GEO);      // [TE][D+1]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* sX = reinterpret_cast<T*>(smem_raw + ProjCfg<D, K, T>::TABS) + warp * W::PER_WARP;  // X [NL][EW], Y [EW][NLQ]
+  T* sP = sX + W::XW;                                                                   // [EW][D*D]
   pdl_wait();
   __syncthreads();
-  const int tid = threadIdx.x;
-  const int64_t ntiles = (m.E + TE - 1) / TE;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e0 = tile * TE;
-    constexpr int IG = (TE * GEO + kProjThreads - 1) / kProjThreads;
-#pragma unroll
-    for (int it = 0; it < IG; ++it) {
-      const int t = tid + it * kProjThreads;
-      if (t < TE * GEO) sGeo[t] = (e0 + t / GEO < m.E) ? geoT[e0 * GEO + t] : T(0);
+  const int64_t ngroups = (m.E + EW - 1) / EW;
+  for (int64_t grp = (int64_t)blockIdx.x * W::WARPS + warp; grp < ngroups; grp += (int64_t)gridDim.x * W::WARPS) {
+    const int64_t e0 = grp * EW;
+    const int ne = (m.E - e0 < EW) ? (int)(m.E - e0) : EW;
+    const int code = (lane < NC && lane / (D + 1) < ne) ? m.efc[e0 * (D + 1) + lane] : 0;
+    for (int t = lane; t < EW * DD; t += 32) {  // Pf = J / det J   (PT: Pi^T, Pi = det J Jinv)
+      const int k = t / DD, r = t - k * DD, a = r / D, b = r - a * D;
+      sP[t] = (k < ne) ? geoT[(e0 + k) * GEO + (PT ? DD + b * D + a : a * D + b)] : T(0);
     }
-    constexpr int IC = (TE * (D + 1) + kProjThreads - 1) / kProjThreads;
-#pragma unroll
-    for (int it = 0; it < IC; ++it) {
-      const int t = tid + it * kProjThreads;
-      if (t < TE * (D + 1)) sCode[t] = (e0 + t / (D + 1) < m.E) ? m.efc[e0 * (D + 1) + t] : 0;
-    }
-    __syncthreads();
-    constexpr int IX = (TE * NL + kProjThreads - 1) / kProjThreads;
-#pragma unroll
-    for (int it = 0; it < IX; ++it) {
-      const int t = tid + it * kProjThreads;
-      if (t >= TE * NL) break;
-      const int k = t / NL, s2 = t - k * NL;
-      const int64_t e = e0 + k;
+#pragma unroll 5
+    for (int it = 0; it < NIT; ++it) {
+      const int t = lane + 32 * it;
+      const int k = t % EW, s2 = t / EW;
+      const int f = min(s2 / NF, D);
+      const int c = __shfl_sync(kFull, code, k * (D + 1) + f);
       T v = T(0);
-      if (e < m.E) {
+      if (t < NL * EW && k < ne) {
         if (s2 < (D + 1) * NF) {
-          const int f = s2 / NF, mm = s2 - f * NF;
-          const int code = sCode[k * (D + 1) + f];
-          v = uV[(int64_t)(code >> 2) * NF + mm];
-          if (code & 2) v = -v;
+          v = uV[(int64_t)(c >> 2) * NF + (s2 - f * NF)];
+          if (c & 2) v = -v;
           if (PT) v *= T(0.5);
         } else {
-          v = uV[m.NF * NF + e * NINT + (s2 - (D + 1) * NF)];
+          v = uV[(int64_t)m.NF * NF + (e0 + k) * NINT + (s2 - (D + 1) * NF)];
         }
       }
-      sX[k * NLQ + s2] = v;
+      if (t < NL * EW) sX[t] = v;  // t = s2 * EW + k
     }
-    __syncthreads();
-    tile_apply<NL, NLP, NLQ, TE, T>(Tb, sX);
-    for (int t = tid; t < TE * NL; t += kProjThreads) {
+    __syncwarp();
+    T keep[W::NPASS][4][4];
+#pragma unroll
+    for (int p = 0; p < W::NPASS; ++p) {
+      const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) keep[p][i][j] = T(0);
+      if (task < W::NTASK) {
+#pragma unroll 4
+        for (int s2 = 0; s2 < NL; ++s2) {
+          T tv[4], xv[4];
+          ld4(Tb + s2 * NLP + rg * 4, tv);
+          ld4(sX + s2 * EW + eg * 4, xv);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) keep[p][i][j] = fma(tv[i], xv[j], keep[p][i][j]);
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < W::NPASS; ++p) {
+      const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
+      if (task < W::NTASK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (rg * 4 + i < NL)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sX[(eg * 4 + j) * NLQ + rg * 4 + i] = keep[p][i][j];
+      }
+    }
+    __syncwarp();
+    for (int t = lane; t < ne * NL; t += 32) {
       const int k = t / NL, idx = t - k * NL;
-      if (e0 + k >= m.E) continue;
-      const T* g = sGeo + k * GEO;  // Pf = J / det J   (PT: Pi^T, Pi = det J Jinv)
       const int a = idx / NB, i = idx - a * NB;
       T acc1 = T(0);
 #pragma unroll
-      for (int b = 0; b < D; ++b)
-        acc1 = fma(PT ? g[D * D + b * D + a] : g[a * D + b], sX[k * NLQ + b * NB + i], acc1);
+      for (int b = 0; b < D; ++b) acc1 = fma(sP[k * DD + a * D + b], sX[k * NLQ + b * NB + i], acc1);
       uL[e0 * NL + t] = acc1;
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 

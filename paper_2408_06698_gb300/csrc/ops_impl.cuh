@@ -20,6 +20,7 @@ class OpsImpl final : public Ops {
 
   using PC = ProjCfg<D, K, T>;
   static constexpr size_t kProjSmem = PC::SMEM;
+  using PW = ProjWCfg<D, K, T>;
 
   // facet kernel: padded modal trace matrices, Psi, WPsi, Wf; per warp: coefficient
   // blocks, two [nqf][4] point buffers, modal jump / wind, moments (layout of k_facet)
@@ -145,8 +146,8 @@ class OpsImpl final : public Ops {
     err = cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     const int th = 32 * kWarps;
-    if ((err = setup(k_v2l<D, K, T, false>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
-    if ((err = setup(k_v2l<D, K, T, true>, kProjSmem, kProjThreads, &g_v2l_)) != cudaSuccess) return err;
+    if ((err = setup(k_v2l<D, K, T, false>, PW::SMEM, 32 * PW::WARPS, &g_v2l_)) != cudaSuccess) return err;
+    if ((err = setup(k_v2l<D, K, T, true>, PW::SMEM, 32 * PW::WARPS, &g_v2l_)) != cudaSuccess) return err;
     if constexpr (kTcVol) {
       if (tc_ && (err = setup(k_volume_tc<D, K>, VolTc<D, K>::SMEM, VolTc<D, K>::THREADS, &g_vol_tc_, true)) !=
                      cudaSuccess)
@@ -191,8 +192,8 @@ class OpsImpl final : public Ops {
         return 1;
       }
     }
-    const int g = clamp_grid(g_v2l_, m.E, PC::TE);
-    launch(k_v2l<D, K, T, false>, g, kProjThreads, kProjSmem, st, 
+    const int g = clamp_grid(g_v2l_, (m.E + PW::EW - 1) / PW::EW, PW::WARPS);
+    launch(k_v2l<D, K, T, false>, g, 32 * PW::WARPS, PW::SMEM, st, 
         m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
     return 1;
   }
@@ -235,8 +236,8 @@ class OpsImpl final : public Ops {
   }
 
   int v2l_pt(const DevMesh& m, const DevTabs& t, const void* vV, void* yL, cudaStream_t st) override {
-    const int g = clamp_grid(g_v2l_, m.E, PC::TE);
-    launch(k_v2l<D, K, T, true>, g, kProjThreads, kProjSmem, st, 
+    const int g = clamp_grid(g_v2l_, (m.E + PW::EW - 1) / PW::EW, PW::WARPS);
+    launch(k_v2l<D, K, T, true>, g, 32 * PW::WARPS, PW::SMEM, st, 
         m, static_cast<const T*>(t.Dn), static_cast<const T*>(vV), static_cast<T*>(yL));
     return 1;
   }
