@@ -114,14 +114,9 @@ template <> struct Pack<double> {
 };
 
 // ------------------------------------------------------------------------------------
-// Projections (a1, a7) as CTA-tiled GEMMs.  A CTA of kProjThreads threads takes a tile
-// of TE elements: it gathers their local vectors into shared memory ([element][NLQ],
-// NLQ odd so that column reads are bank-conflict free), multiplies by the n_loc x n_loc
-// reference matrix (staged once per CTA, [s][NLP] so that four rows are one 16-byte
-// load) with a 4 x 4 register tile per thread (four consecutive rows x four elements
-// strided by TE/4), and finishes with the per-element Piola / scatter step.
-constexpr int kProjThreads = 256;
-
+// Projections (a1, a7) as products of the n_loc x n_loc reference matrix with the local
+// vectors of tiles of elements.  The matrix is staged once per CTA ([s][NLP], so that four
+// rows are one 16-byte load) when it fits in shared memory; the tiles are per warp (below).
 template <int D, int K, typename T>
 struct ProjCfg {
   using S = Shape<D, K>;
@@ -131,67 +126,8 @@ struct ProjCfg {
   static constexpr int NLQ = (NL % 2) ? NL : NL + 1;  // odd stride of the element rows
   static constexpr size_t TAB = size_t(NL) * NLP * sizeof(T);
   static constexpr bool STAB = TAB <= 120 * 1024;
-  static constexpr size_t tile_bytes(int te) {  // element rows, geometry, connectivity codes
-    return ((size_t(te) * NLQ * sizeof(T) + 15) / 16) * 16 + size_t(te) * S::gt * sizeof(T) + size_t(te) * (D + 1) * 4;
-  }
-  static constexpr int TE = ((STAB ? TAB : 0) + tile_bytes(64) <= 200 * 1024) ? 64 : 32;
-  static constexpr int EG = TE / 4;          // element groups
   static constexpr size_t TABS = STAB ? ((TAB + 15) / 16) * 16 : 0;
-  static constexpr size_t SMEM = TABS + ((tile_bytes(TE) + 15) / 16) * 16;
 };
-
-// acc[i][j] = sum_s tab[s][r0 + i] * X[k_j][s],  k_j = eg + j * EG.
-template <int NL, int NLP, int NLQ, int EG, typename T>
-__device__ __forceinline__ void tile_gemm(const T* tab, const T* X, int r0, int eg, T (&acc)[4][4]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-#pragma unroll 4
-  for (int s2 = 0; s2 < NL; ++s2) {
-    T t[4];
-    Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(tab + s2 * NLP + r0), t);
-    if constexpr (Pack<T>::W == 2)
-      Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(tab + s2 * NLP + r0 + 2), t + 2);
-    T x[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = X[(eg + j * EG) * NLQ + s2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(t[i], x[j], acc[i][j]);
-  }
-}
-
-// The GEMM step shared by both projections: X[k][s] (k < TE, s < NL) is replaced by
-// sum_s tab[s][r] X[k][s].  The result stays in registers until every thread has read X.
-template <int NL, int NLP, int NLQ, int TE, typename T>
-__device__ __forceinline__ void tile_apply(const T* tab, T* X) {
-  constexpr int EG = TE / 4, RG = (NL + 3) / 4, STEP = kProjThreads / EG;
-  constexpr int NPASS = (RG + STEP - 1) / STEP;
-  const int tid = threadIdx.x, eg = tid % EG;
-  T keep[NPASS][4][4];
-#pragma unroll
-  for (int p = 0; p < NPASS; ++p) {
-    const int rg = tid / EG + p * STEP;
-    if (rg < RG) tile_gemm<NL, NLP, NLQ, EG, T>(tab, X, rg * 4, eg, keep[p]);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int p = 0; p < NPASS; ++p) {
-    const int rg = tid / EG + p * STEP;
-    if (rg < RG) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = rg * 4 + i;
-        if (r < NL)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) X[(eg + j * EG) * NLQ + r] = keep[p][i][j];
-      }
-    }
-  }
-  __syncthreads();
-}
 
 template <int D, int K, typename T>
 __device__ __forceinline__ const T* proj_setup(unsigned char* smem, const T* tab) {
@@ -233,6 +169,49 @@ template <typename T>
 __device__ __forceinline__ void ld4(const T* p, T* o) {  // 4 consecutive values, 16-byte aligned
   Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p), o);
   if constexpr (Pack<T>::W == 2) Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p + 2), o + 2);
+}
+
+// The product of a warp tile: X[s][k] (s < NL, k < EW, in sX) is replaced by
+// Y[k][r] = sum_s tab[s][r] X[s][k] (at sX[k * NLQ + r]).  Lanes own four rows x four
+// elements; the tile stays in registers until every lane has read X.
+template <int D, int K, typename T>
+__device__ __forceinline__ void warp_tile_gemm(const T* Tb, T* sX, int lane) {
+  using W = ProjWCfg<D, K, T>;
+  constexpr int NL = W::NL, NLP = W::NLP, NLQ = W::NLQ, EW = W::EW;
+  T keep[W::NPASS][4][4];
+#pragma unroll
+  for (int p = 0; p < W::NPASS; ++p) {
+    const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) keep[p][i][j] = T(0);
+    if (task < W::NTASK) {
+#pragma unroll 4
+      for (int s2 = 0; s2 < NL; ++s2) {
+        T tv[4], xv[4];
+        ld4(Tb + s2 * NLP + rg * 4, tv);
+        ld4(sX + s2 * EW + eg * 4, xv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) keep[p][i][j] = fma(tv[i], xv[j], keep[p][i][j]);
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < W::NPASS; ++p) {
+    const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
+    if (task < W::NTASK) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (rg * 4 + i < NL)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sX[(eg * 4 + j) * NLQ + rg * 4 + i] = keep[p][i][j];
+    }
+  }
+  __syncwarp();
 }
 
 template <int D, int K, typename T, bool PT>
@@ -280,40 +259,7 @@ __global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_v2l(DevMesh m
       if (t < NL * EW) sX[t] = v;  // t = s2 * EW + k
     }
     __syncwarp();
-    T keep[W::NPASS][4][4];
-#pragma unroll
-    for (int p = 0; p < W::NPASS; ++p) {
-      const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) keep[p][i][j] = T(0);
-      if (task < W::NTASK) {
-#pragma unroll 4
-        for (int s2 = 0; s2 < NL; ++s2) {
-          T tv[4], xv[4];
-          ld4(Tb + s2 * NLP + rg * 4, tv);
-          ld4(sX + s2 * EW + eg * 4, xv);
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) keep[p][i][j] = fma(tv[i], xv[j], keep[p][i][j]);
-        }
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int p = 0; p < W::NPASS; ++p) {
-      const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
-      if (task < W::NTASK) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (rg * 4 + i < NL)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) sX[(eg * 4 + j) * NLQ + rg * 4 + i] = keep[p][i][j];
-      }
-    }
-    __syncwarp();
+    warp_tile_gemm<D, K, T>(Tb, sX, lane);
     for (int t = lane; t < ne * NL; t += 32) {
       const int k = t / NL, idx = t - k * NL;
       const int a = idx / NB, i = idx - a * NB;
@@ -326,74 +272,68 @@ __global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_v2l(DevMesh m
   }
 }
 
-// a7 (element part): local functionals of an L2 field.  Not dual: ell = D (det J Jinv y);
-// dual (the transpose E^T): ell = Dinv^T (J^T y / det J).  Interior rows are combined
-// into the V_h output; facet rows go to lf[e][f][m] with the sign sigma.
-// tab[s][r] (rows padded to NLP) = D[r][s] (not dual) or Dinv[s][r] (dual).
+// a7 (element part): local functionals of an L2 field, in the warp tiles of k_v2l.
+// Not dual: ell = D (det J Jinv y); dual (the transpose E^T): ell = Dinv^T (J^T y / det J).
+// Interior rows are combined into the V_h output; facet rows go to lf[e][f][m] with the
+// sign sigma.  tab[s][r] (rows padded to NLP) = D[r][s] (not dual) or Dinv[s][r] (dual).
 template <int D, int K, typename T, bool DUAL>
-__global__ void __launch_bounds__(kProjThreads) k_l2v_elem(DevMesh m, const T* __restrict__ tab,
-                                                           const T* __restrict__ yL, T* __restrict__ lf,
-                                                           T* outV, Combine cmb) {
+__global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_l2v_elem(DevMesh m, const T* __restrict__ tab,
+                                                                            const T* __restrict__ yL, T* __restrict__ lf,
+                                                                            T* outV, Combine cmb) {
   using S = Shape<D, K>;
-  using C = ProjCfg<D, K, T>;
+  using W = ProjWCfg<D, K, T>;
   constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
-  constexpr int NLP = C::NLP, NLQ = C::NLQ, TE = C::TE;
+  constexpr int NLQ = W::NLQ, EW = W::EW, DD = W::DD, NC = (D + 1) * EW;
+  constexpr int NIT = (NL * EW + 31) / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_trigger();
   const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
   const T* geoT = static_cast<const T*>(m.geoT);
-  T* sX = reinterpret_cast<T*>(smem_raw + C::TABS);
-  T* sGeo = reinterpret_cast<T*>(smem_raw + C::TABS + ((size_t(TE) * NLQ * sizeof(T) + 15) / 16) * 16);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* sX = reinterpret_cast<T*>(smem_raw + ProjCfg<D, K, T>::TABS) + warp * W::PER_WARP;  // X [NL][EW], Y [EW][NLQ]
+  T* sP = sX + W::XW;                                                                   // [EW][D*D]
   pdl_wait();
   __syncthreads();
-  const int tid = threadIdx.x;
-  const int64_t ntiles = (m.E + TE - 1) / TE;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e0 = tile * TE;
-    constexpr int IG = (TE * GEO + kProjThreads - 1) / kProjThreads;
-#pragma unroll
-    for (int it = 0; it < IG; ++it) {
-      const int t = tid + it * kProjThreads;
-      if (t < TE * GEO) sGeo[t] = (e0 + t / GEO < m.E) ? geoT[e0 * GEO + t] : T(0);
+  const int64_t ngroups = (m.E + EW - 1) / EW;
+  for (int64_t grp = (int64_t)blockIdx.x * W::WARPS + warp; grp < ngroups; grp += (int64_t)gridDim.x * W::WARPS) {
+    const int64_t e0 = grp * EW;
+    const int ne = (m.E - e0 < EW) ? (int)(m.E - e0) : EW;
+    const int code = (lane < NC && lane / (D + 1) < ne) ? m.efc[e0 * (D + 1) + lane] : 0;
+    for (int t = lane; t < EW * DD; t += 32) {  // F[b][a]: Pi[b][a] = (det J Jinv)[b][a], or Pf^T[b][a]
+      const int k = t / DD, r = t - k * DD, b = r / D, a = r - b * D;
+      sP[t] = (k < ne) ? geoT[(e0 + k) * GEO + (DUAL ? a * D + b : DD + b * D + a)] : T(0);
     }
-    __syncthreads();
-    constexpr int IX = (TE * NL + kProjThreads - 1) / kProjThreads;
-#pragma unroll
-    for (int it = 0; it < IX; ++it) {
-      const int t = tid + it * kProjThreads;
-      if (t >= TE * NL) break;
-      const int k = t / NL, s2 = t - k * NL;
+    __syncwarp();
+    for (int t = lane; t < NL * EW; t += 32) {  // X[s][k] = sum_a F_k[b][a] y_k[a][i],  s = b NB + i
+      const int k = t % EW, s2 = t / EW;
       T acc1 = T(0);
-      if (e0 + k < m.E) {
-        const T* g = sGeo + k * GEO;
+      if (k < ne) {
         const int b = s2 / NB, i = s2 - b * NB;
-        const T* y = yL + (e0 + k) * NL;
-        if (!DUAL) {  // Pi = det J * Jinv
+        const T* y = yL + (e0 + k) * NL + i;
 #pragma unroll
-          for (int a = 0; a < D; ++a) acc1 = fma(g[D * D + b * D + a], y[a * NB + i], acc1);
-        } else {      // Pf^T = J^T / det J
-#pragma unroll
-          for (int a = 0; a < D; ++a) acc1 = fma(g[a * D + b], y[a * NB + i], acc1);
+        for (int a = 0; a < D; ++a) acc1 = fma(sP[k * DD + b * D + a], y[a * NB], acc1);
+      }
+      sX[t] = acc1;
+    }
+    __syncwarp();
+    warp_tile_gemm<D, K, T>(Tb, sX, lane);
+#pragma unroll 5
+    for (int it = 0; it < NIT; ++it) {
+      const int t = lane + 32 * it;
+      const int k = t / NL, r = t - k * NL;
+      const int c = __shfl_sync(kFull, code, min(k, EW - 1) * (D + 1) + min(r / NF, D));
+      if (t < ne * NL) {
+        const int64_t e = e0 + k;
+        const T v = sX[k * NLQ + r];
+        if (r < (D + 1) * NF) {
+          lf[e * (D + 1) * NF + r] = (c & 2) ? -v : v;
+        } else {
+          const int64_t idx = (int64_t)m.NF * NF + e * NINT + (r - (D + 1) * NF);
+          outV[idx] = combine_at<T>(cmb, v, idx);
         }
       }
-      sX[k * NLQ + s2] = acc1;
     }
-    __syncthreads();
-    tile_apply<NL, NLP, NLQ, TE, T>(Tb, sX);
-    for (int t = tid; t < TE * NL; t += kProjThreads) {
-      const int k = t / NL, r = t - k * NL;
-      const int64_t e = e0 + k;
-      if (e >= m.E) continue;
-      const T v = sX[k * NLQ + r];
-      if (r < (D + 1) * NF) {
-        const int code = m.efc[e * (D + 1) + r / NF];
-        lf[e * (D + 1) * NF + r] = (code & 2) ? -v : v;
-      } else {
-        const int64_t idx = m.NF * NF + e * NINT + (r - (D + 1) * NF);
-        outV[idx] = combine_at<T>(cmb, v, idx);
-      }
-    }
-    __syncthreads();
+    __syncwarp();
   }
 }
 

@@ -18,9 +18,7 @@ class OpsImpl final : public Ops {
   static constexpr size_t sz = sizeof(T);
   static constexpr size_t r4(size_t n) { return ((n + 3) / 4) * 4; }
 
-  using PC = ProjCfg<D, K, T>;
-  static constexpr size_t kProjSmem = PC::SMEM;
-  using PW = ProjWCfg<D, K, T>;
+  using PW = ProjWCfg<D, K, T>;  // warp tiles of the projections
 
   // facet kernel: padded modal trace matrices, Psi, WPsi, Wf; per warp: coefficient
   // blocks, two [nqf][4] point buffers, modal jump / wind, moments (layout of k_facet)
@@ -172,8 +170,8 @@ class OpsImpl final : public Ops {
     if constexpr (kFuse) {
       if ((err = setup(k_volume<D, K, T, false, true, true>, kFuseSmem, th, &g_fuse_)) != cudaSuccess) return err;
     }
-    if ((err = setup(k_l2v_elem<D, K, T, false>, kProjSmem, kProjThreads, &g_elem_[0])) != cudaSuccess) return err;
-    if ((err = setup(k_l2v_elem<D, K, T, true>, kProjSmem, kProjThreads, &g_elem_[1])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_elem<D, K, T, false>, PW::SMEM, 32 * PW::WARPS, &g_elem_[0])) != cudaSuccess) return err;
+    if ((err = setup(k_l2v_elem<D, K, T, true>, PW::SMEM, 32 * PW::WARPS, &g_elem_[1])) != cudaSuccess) return err;
     if ((err = setup(k_l2v_facet<D, K, T, false>, 0, 256, &g_fsum_)) != cudaSuccess) return err;
     return cudaSuccess;
   }
@@ -298,12 +296,12 @@ class OpsImpl final : public Ops {
 
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,
                void* outV, cudaStream_t st) override {
-    const int g = clamp_grid(g_elem_[dual ? 1 : 0], m.E, PC::TE);
+    const int g = clamp_grid(g_elem_[dual ? 1 : 0], (m.E + PW::EW - 1) / PW::EW, PW::WARPS);
     if (dual)
-      launch(k_l2v_elem<D, K, T, true>, g, kProjThreads, kProjSmem, st, 
+      launch(k_l2v_elem<D, K, T, true>, g, 32 * PW::WARPS, PW::SMEM, st, 
           m, static_cast<const T*>(t.Dinv), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
     else
-      launch(k_l2v_elem<D, K, T, false>, g, kProjThreads, kProjSmem, st, 
+      launch(k_l2v_elem<D, K, T, false>, g, 32 * PW::WARPS, PW::SMEM, st, 
           m, static_cast<const T*>(t.DT), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);
     return 1;
   }
