@@ -383,7 +383,7 @@ def our_arm(args, rank, world):
     import torch
 
     import workloads as W
-    from paper_2408_06698_gb300 import Hopu
+    from paper_2408_06698_gb300 import Hopu, measure_alu_peak
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device(f"cuda:{local}")
@@ -542,12 +542,17 @@ def our_arm(args, rank, world):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     ach_tflops = flops / (avg_ms / 1e3) / 1e12
-    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    # FMA peaks measured on this device after the timed regions (hopu_measure_alu_peak)
+    alu_meas = {"fp32_tflops": measure_alu_peak(False), "fp64_tflops": measure_alu_peak(True),
+                "fp32_nominal_tflops_at_sampled_clock": fp32_alu_peak_tflops(sm_mhz),
+                "fp64_nominal_tflops_at_sampled_clock": fp64_alu_peak_tflops(sm_mhz)}
+    alu_peak = alu_meas["fp32_tflops"]
     traffic = traffic_from_profiles(dom)
     roofline = {"kernel": dom, "bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach_tflops / alu_peak, "traffic": traffic,
-                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
-                               "sampled during the timed region)",
+                "peak_source": "measured FP32 FMA throughput of this GPU (hopu_measure_alu_peak: 8 independent "
+                               "FMA chains per thread, 2048 threads per SM, CUDA events); nominal at the "
+                               f"sampled {sm_mhz:.0f} MHz: {fp32_alu_peak_tflops(sm_mhz):.1f}",
                 "achieved_bytes_gbs": byts / (avg_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": byts / (avg_ms / 1e3) / 1e9 / hbm_peak,
                 "flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
@@ -568,7 +573,8 @@ def our_arm(args, rank, world):
                    "hdiv_dofs": g32.n_hdiv, "applies_per_step": APPLIES_PER_STEP,
                    "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": ck, "fp64": fp64,
+        "roofline": roofline, "alu_peaks_measured": alu_meas, "e2e": e2e, "gpu_launches": launches,
+        "clocks": ck, "fp64": fp64,
         "fp32_tc": fp32_tc, "vjp": vjp, "other_configs": others,
         "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernels,
         "profiled_pass": {"steps": Kp, "ms_per_step": prof_ms / Kp,

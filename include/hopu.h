@@ -35,8 +35,14 @@
  *     interior dofs u[NF*nf + e*nint + j] = int_That uhat . z_j dxhat,
  *                  uhat the contravariant Piola pull-back (u = J uhat / det J), z_j the
  *                  interior moment functions of the BDM_k element (Nedelec first kind
- *                  of index k-1) in the basis documented in the design doc,
- *                  nint = d*nb - (d+1)*nf.
+ *                  of index k-1), nint = d*nb - (d+1)*nf, in this order:
+ *                  (A) phi_j e_m for every Dubiner phi_j of P^{k-2}, m = 0..d-1 (m-major);
+ *                  (B) with x~ = (d+1)(xhat - centroid): in 2D x~^perp phi_j,
+ *                  x~^perp = (-x~_2, x~_1), phi_j over the degree-(k-2) block of the 2D
+ *                  Dubiner basis; in 3D x~ x (phi_j e_m) for m = 0, 1 with phi_j over the
+ *                  degree-(k-2) block of the 3D Dubiner basis, then x~ x (chi_j e_2) with
+ *                  chi_j over the degree-(k-2) block of the 2D Dubiner basis of
+ *                  (xhat_1, xhat_2).
  *
  *   Quadrature: collapsed Gauss-Jacobi rules, exact to degree 3k-1 on elements and 3k
  *   on facets (Section 2.2 asks for exact integration of every form).
@@ -324,6 +330,14 @@ typedef enum {
   HOPU_K_VOLUME_ADJ = 6, /* VJP: volume part + lift of the facet moments               */
   HOPU_K_COUNT = 7
 } hopu_kernel_family;
+
+/* Measured fused multiply-add throughput of the current CUDA device (no context needed):
+ * fp64 = 0 for FP32, 1 for FP64; iters = timed loop trips (each thread 128 FMA per trip;
+ * about 2000 for FP32 and 50 for FP64 give a launch of a few milliseconds on GB300).  One
+ * warm-up launch, then one launch timed with CUDA events on a private stream; writes the
+ * rate in TFLOP/s (2 flop per FMA) to *tflops.  Synchronises that stream.
+ * Errors: EINVAL (NULL tflops, iters <= 0), ECUDA (launch or event failure).            */
+hopu_status hopu_measure_alu_peak(int fp64, int iters, double* tflops);
 
 /* Profiling: with enable != 0 every later kernel launch of the context is bracketed by
  * CUDA timing events on the context stream (also inside captured substep graphs; the

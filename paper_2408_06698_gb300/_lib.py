@@ -62,6 +62,7 @@ SIGNATURES = {
     "hopu_batch_last_error": (c_char_p, [c_void_p]),
     "hopu_apply_convection_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
+    "hopu_measure_alu_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
     "hopu_sync": (c_int, [c_void_p]),
     "hopu_boundary_facets": (c_int, [c_void_p, c_void_p, POINTER(c_int64)]),
     "hopu_set_inlet": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),

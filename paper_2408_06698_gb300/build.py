@@ -21,6 +21,7 @@ LIB = os.path.join(PKG, "libhopu.so")
 SOURCES = [
     "capi.cu",
     "noalloc.cu",
+    "peaks.cu",
     "reftables.cpp",
     "meshtopo.cpp",
     "ops_d2.cu",

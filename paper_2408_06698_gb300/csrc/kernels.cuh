@@ -504,6 +504,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
                                                        const int8_t* __restrict__ facet_l,
                                                        T* __restrict__ gam, double* __restrict__ diss) {
   static_assert(STAB, "facet tables always fit in shared memory");
+  static_assert(Shape<D, K>::nf <= 32, "one lane per facet mode");
   using S = Shape<D, K>;
   constexpr int NB = S::nb, NF = S::nf, NL = S::nloc, NQF = S::nqf, QP = (NQF + 31) / 32;
   constexpr int NBP = r4i(NB);
@@ -558,13 +559,22 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
     const T aF = T(fg[D]);
     const int l = facet_l ? int(facet_l[F]) : lconst;
     const int nl = (l < 0) ? 0 : cnbasis(D - 1, l);
-    for (int s2 = lane; s2 < NL; s2 += 32) {
-      const int a = s2 / NB, i = s2 - a * NB;
-      cA[a * NBP + i] = uL[eA * NL + s2];
-      cB[a * NBP + i] = uL[eB * NL + s2];
-      if (WSEP) {
-        wA[a * NBP + i] = wL[eA * NL + s2];
-        wB[a * NBP + i] = wL[eB * NL + s2];
+    if constexpr (NBP == NB && (NL * sizeof(T)) % 16 == 0) {  // unpadded rows: 16-byte chunks
+      constexpr int NCH = NL * (int)sizeof(T) / 16, CH = 16 / (int)sizeof(T);
+      for (int c = lane; c < (WSEP ? 4 : 2) * NCH; c += 32) {
+        const int which = c / NCH, cc = c - which * NCH;  // cA, cB, wA, wB (contiguous blocks of CW = NL)
+        const T* src = (which < 2 ? uL : wL) + ((which & 1) ? eB : eA) * NL + cc * CH;
+        *reinterpret_cast<uint4*>(cA + which * CW + cc * CH) = __ldg(reinterpret_cast<const uint4*>(src));
+      }
+    } else {
+      for (int s2 = lane; s2 < NL; s2 += 32) {
+        const int a = s2 / NB, i = s2 - a * NB;
+        cA[a * NBP + i] = uL[eA * NL + s2];
+        cB[a * NBP + i] = uL[eB * NL + s2];
+        if (WSEP) {
+          wA[a * NBP + i] = wL[eA * NL + s2];
+          wB[a * NBP + i] = wL[eB * NL + s2];
+        }
       }
     }
     __syncwarp();
@@ -583,6 +593,25 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       sWv[mm * 4 + a] = T(0.5) * (wa + wb);
     }
     __syncwarp();
+    // per mode: the normal component of the averaged wind (slot 3 of sJ) and the source of
+    // the Pi^l complement (modes below nl keep only (J_m . n) n)
+    T* sPj = sOut;  // [NF][4], free until the moments are written
+    if (lane < NF) {
+      T jm[4], wv[4];
+      lds4(sJ + lane * 4, jm);
+      lds4(sWv + lane * 4, wv);
+      T jn = T(0), wvn = T(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        jn = fma(jm[a], n[a], jn);
+        wvn = fma(wv[a], n[a], wvn);
+      }
+      const bool low = lane < nl;
+#pragma unroll
+      for (int a = 0; a < D; ++a) sPj[lane * 4 + a] = low ? jn * n[a] : jm[a];
+      sJ[lane * 4 + 3] = wvn;
+    }
+    __syncwarp();
     T dsum = T(0);
 #pragma unroll
     for (int qq = 0; qq < QP; ++qq) {
@@ -595,21 +624,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
 #pragma unroll
       for (int mm = 0; mm < NF; ++mm) {
         const T p = Psi[mm * NQF + qc];
-        T jm[4], wv[4];
-        lds4(sJ + mm * 4, jm);
-        lds4(sWv + mm * 4, wv);
-        T jn = T(0), wvn = T(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          jn = fma(jm[a], n[a], jn);
-          wvn = fma(wv[a], n[a], wvn);
-        }
-        wn = fma(p, wvn, wn);
-        const bool low = mm < nl;  // Pi^l removes the tangential part of the low modes
+        T jm[4], pm[4];
+        lds4(sJ + mm * 4, jm);   // J_m, (w.n)_m
+        lds4(sPj + mm * 4, pm);  // J_m or (J_m . n) n
+        wn = fma(p, jm[3], wn);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           J[a] = fma(p, jm[a], J[a]);
-          P[a] = fma(p, low ? jn * n[a] : jm[a], P[a]);
+          P[a] = fma(p, pm[a], P[a]);
         }
       }
       const T aw = T(0.5) * fabs(wn);

@@ -432,6 +432,17 @@ class HopuBatch:
             pass
 
 
+def measure_alu_peak(fp64: bool = False, iters: int | None = None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current CUDA device (hopu_measure_alu_peak)."""
+    lib = L.load()
+    out = c_double()
+    it = int(iters if iters is not None else (50 if fp64 else 2000))
+    st = lib.hopu_measure_alu_peak(1 if fp64 else 0, it, byref(out))
+    if st != L.HOPU_OK:
+        raise L.HopuError(st, "hopu_measure_alu_peak")
+    return float(out.value)
+
+
 def selftest(dim: int, k: int):
     """Host-only check of the library's reference tables (no GPU needed)."""
     lib = L.load()

@@ -4,7 +4,7 @@ Inputs are seeded and synthetic; the oracle gets exactly the values the GPU gets
 runs feed the oracle the FP32-rounded inputs, so the comparison measures the kernels'
 arithmetic).  Tolerances (relative to the largest reference entry):
   FP64: 1e-12 (the oracle and the kernels differ only in summation order);
-  FP32: 1e-6 on the operator output (BASELINE's stated FP32 bound), 2e-6 on projections
+  FP32: 1e-6 on the operator output (the stated FP32 error bound), 2e-6 on projections
         whose condition number is bounded by cond(D) <= 120.
 """
 import numpy as np
@@ -229,3 +229,15 @@ def test_full_size_taylor_green_apply(prec):
     # which the solver advances, stays at 1.6e-7 (bench.py states it).
     assert l2 < (TOL[prec] if prec == "f64" else 2e-6), l2
     assert _rel(y, ref) < (TOL[prec] if prec == "f64" else 5e-6), _rel(y, ref)
+
+
+def test_measured_alu_peaks_are_plausible():
+    """hopu_measure_alu_peak: the FP32 FMA rate lies between half and 1.1x the nominal
+    152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s; FP64 is positive and far
+    below it."""
+    from paper_2408_06698_gb300 import measure_alu_peak
+    f32 = measure_alu_peak(False)
+    f64 = measure_alu_peak(True)
+    print(f"measured FMA peaks: FP32 {f32:.1f} TFLOP/s, FP64 {f64:.2f} TFLOP/s")
+    assert 40.0 < f32 < 89.0
+    assert 0.0 < f64 < 0.5 * f32

@@ -41,6 +41,17 @@ def test_library_exports_every_declared_symbol(lib):
     assert sorted(_lib.SIGNATURES) == names
 
 
+def test_alu_peak_probe_rejects_bad_arguments(lib):
+    """Argument checks of hopu_measure_alu_peak come before any CUDA call."""
+    from ctypes import byref, c_double
+    from paper_2408_06698_gb300 import _lib
+    out = c_double(-1.0)
+    assert lib.hopu_measure_alu_peak(0, 0, byref(out)) == _lib.HOPU_EINVAL
+    assert lib.hopu_measure_alu_peak(1, -5, byref(out)) == _lib.HOPU_EINVAL
+    assert lib.hopu_measure_alu_peak(0, 10, None) == _lib.HOPU_EINVAL
+    assert out.value == -1.0
+
+
 def test_no_cpu_fallback_when_library_missing(tmp_path):
     from paper_2408_06698_gb300 import _lib
     with pytest.raises(RuntimeError, match="no CPU fallback"):
