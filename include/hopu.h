@@ -368,9 +368,11 @@ hopu_status hopu_apply_convection_noalloc(hopu_ctx* ctx, const void* w_hdiv, con
                                           void* y_l2, const int8_t* facet_l);
 
 /* Host-only self check of the reference tables of (dim, k), no GPU needed:
- * report[0] = max relative error of the volume rule on monomials up to degree 3k-1,
+ * report[0] = max relative error of the volume rules (the collapsed Gauss-Jacobi rule of
+ *             hopu_points / hopu_interpolate and the compact rule of the volume kernels)
+ *             on monomials up to degree 3k-1,
  * report[1] = same for the facet rule up to degree 3k (closed form a!b!c!/(a+b+c+d)!),
- * report[2] = max |M - I| of the basis mass matrix (orthonormality),
+ * report[2] = max |M - I| of the basis mass matrix under both volume rules,
  * report[3] = max |D Dinv - I| of the degree-of-freedom matrix.                        */
 hopu_status hopu_selftest(int dim, int k, double* report);
 

@@ -325,7 +325,7 @@ int point_row_stride(int n, bool fp64) {
 }
 
 void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double>>& out) {
-  const int d = R.dim, nb = R.nb, nf = R.nf, nq = R.nq, nqf = R.nqf, nl = R.nloc;
+  const int d = R.dim, nb = R.nb, nf = R.nf, nq = R.nq, nqk = R.nqk, nqf = R.nqf, nl = R.nloc;
   const int nbq = point_row_stride(nb, fp64);
   const int nb1 = nbasis(d, R.k - 1);
   out.assign(kNumTables, {});
@@ -342,10 +342,10 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
   auto& Dinv = out[10];
   auto& Drow = out[11];
   auto& Dn = out[12];
-  Bt.assign((size_t)nq * nbq, 0.0);  // point-major [q][nbq]
-  for (int q = 0; q < nq; ++q)
-    for (int i = 0; i < nb; ++i) Bt[(size_t)q * nbq + i] = R.phi[(size_t)q * nb + i];
-  Wq = R.wq;
+  Bt.assign((size_t)nqk * nbq, 0.0);  // point-major [q][nbq], the volume kernels' rule
+  for (int q = 0; q < nqk; ++q)
+    for (int i = 0; i < nb; ++i) Bt[(size_t)q * nbq + i] = R.phik[(size_t)q * nb + i];
+  Wq = R.wk;
   // modal differentiation: d phi_i / d xhat_c = sum_{j < nb(k-1)} Dm[c][j][i] phi_j, with
   // Dm[c][j][i] = int (d phi_i / d xhat_c) phi_j (exact: degree 2k-2 <= 3k-1)
   Dm.assign((size_t)d * nb1 * nb, 0.0);
@@ -406,7 +406,7 @@ float tf32_round(float x) {
 //   phiB[i][q] = phi_i(x_q)  (N2 x 128, N2 = nb rounded up to 16)     hi part, then lo part
 // hi = tf32(phi), lo = tf32(phi - hi); zero outside the points and the basis.
 void tensor_core_volume_table(const RefTables& R, std::vector<float>& out) {
-  const int nb = R.nb, nq = R.nq, KP1 = (nb + 7) / 8 * 8, N2 = (nb + 15) / 16 * 16, K2 = 128;
+  const int nb = R.nb, nq = R.nqk, KP1 = (nb + 7) / 8 * 8, N2 = (nb + 15) / 16 * 16, K2 = 128;
   const size_t PA = (size_t)128 * KP1, PB = (size_t)N2 * K2;
   out.assign(2 * PA + 2 * PB, 0.0f);
   auto off = [](int row, int col, int kp) {
@@ -414,7 +414,7 @@ void tensor_core_volume_table(const RefTables& R, std::vector<float>& out) {
   };
   for (int q = 0; q < nq && q < 128; ++q)
     for (int i = 0; i < nb; ++i) {
-      const float v = (float)R.phi[(size_t)q * nb + i];
+      const float v = (float)R.phik[(size_t)q * nb + i];
       const float h = tf32_round(v), l = tf32_round(v - h);
       out[off(q, i, KP1)] = h;
       out[PA + off(q, i, KP1)] = l;

@@ -69,6 +69,12 @@ struct EtaThresholds {
 // layout of the working-precision geometry record (offsets in elements)
 inline constexpr int geoT_stride(int d) { return ((3 * d * d + 1 + 3) / 4) * 4; }
 
+// Points of the compact volume rule the volume kernels use (exact to degree 3k - 1; the
+// tables are in volume_rules.h), or 0 where they use the collapsed Gauss-Jacobi rule.
+inline constexpr int compact_volume_points(int d, int k) {
+  return d != 3 ? 0 : k == 3 ? 46 : k == 4 ? 100 : k == 5 ? 190 : 0;
+}
+
 // One family of kernels for a fixed (dim, k, precision).  Every call enqueues on the
 // given stream and returns the number of kernels it launched.
 class Ops {

@@ -32,7 +32,7 @@ struct Shape {
   static constexpr int nint = nloc - (D + 1) * nf;  // interior V_h dofs
   static constexpr int mv = (3 * K - 1 + 2) / 2;    // points per direction, degree 3K-1
   static constexpr int mf = (3 * K + 2) / 2;        // points per direction, degree 3K
-  static constexpr int nq = cpow(mv, D);
+  static constexpr int nq = compact_volume_points(D, K) ? compact_volume_points(D, K) : cpow(mv, D);  // kernel rule
   static constexpr int nqf = cpow(mf, D - 1);
   static constexpr int geo = 2 * D * D + 2;
   static constexpr int gt = geoT_stride(D);  // Pf [0, d^2), Pi [d^2, 2d^2), M [2d^2, 3d^2), 1/|det J|

@@ -12,6 +12,9 @@
 //   and interior moments against the Nedelec-first-kind space of index k-1.
 #include "reftables.h"
 
+#include "hopu_internal.h"
+#include "volume_rules.h"
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -286,6 +289,32 @@ bool build_ref_tables(int dim, int k, RefTables& T, std::string& err) {
   for (int q = 0; q < nq; ++q)
     dubiner(dim, k, &T.xq[(size_t)q * dim], &T.phi[(size_t)q * nb], &T.dphi[(size_t)q * nb * dim]);
 
+  // the volume kernels' rule
+  const double* tab = nullptr;
+  int ntab = 0;
+  if (dim == 3 && k == 3) tab = kTetRule3, ntab = kTetRule3N;
+  if (dim == 3 && k == 4) tab = kTetRule4, ntab = kTetRule4N;
+  if (dim == 3 && k == 5) tab = kTetRule5, ntab = kTetRule5N;
+  if (ntab != compact_volume_points(dim, k)) {
+    err = "reference tables: compact volume rule size mismatch";
+    return false;
+  }
+  if (tab) {
+    T.nqk = ntab;
+    T.xk.resize((size_t)ntab * 3);
+    T.wk.resize(ntab);
+    for (int q = 0; q < ntab; ++q) {
+      for (int c = 0; c < 3; ++c) T.xk[(size_t)q * 3 + c] = tab[q * 4 + c];
+      T.wk[q] = tab[q * 4 + 3];
+    }
+  } else {
+    T.nqk = nq;
+    T.xk = T.xq;
+    T.wk = T.wq;
+  }
+  T.phik.assign((size_t)T.nqk * nb, 0.0);
+  for (int q = 0; q < T.nqk; ++q) dubiner(dim, k, &T.xk[(size_t)q * dim], &T.phik[(size_t)q * nb], nullptr);
+
   T.psi.assign((size_t)nqf * nf, 0.0);
   for (int q = 0; q < nqf; ++q) dubiner(dim - 1, k, &T.sq[(size_t)q * (dim - 1)], &T.psi[(size_t)q * nf], nullptr);
 
@@ -348,13 +377,14 @@ bool selftest_ref_tables(int dim, int k, double report[4], std::string& err) {
   RefTables T;
   if (!build_ref_tables(dim, k, T, err)) return false;
   auto fact = [](int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; };
-  // (0) volume rule on monomials up to 3k-1 and (1) facet rule up to 3k
+  // (0) both volume rules (collapsed, kernels') on monomials up to 3k-1 and (1) the facet
+  // rule up to 3k
   double e0 = 0.0, e1 = 0.0;
-  for (int pass = 0; pass < 2; ++pass) {
-    const int d = pass == 0 ? dim : dim - 1;
-    const int deg = pass == 0 ? 3 * k - 1 : 3 * k;
-    const std::vector<double>& X = pass == 0 ? T.xq : T.sq;
-    const std::vector<double>& Wt = pass == 0 ? T.wq : T.wf;
+  for (int pass = 0; pass < 3; ++pass) {  // 0: collapsed volume, 1: facet, 2: kernel volume
+    const int d = pass == 1 ? dim - 1 : dim;
+    const int deg = pass == 1 ? 3 * k : 3 * k - 1;
+    const std::vector<double>& X = pass == 0 ? T.xq : pass == 1 ? T.sq : T.xk;
+    const std::vector<double>& Wt = pass == 0 ? T.wq : pass == 1 ? T.wf : T.wk;
     const int n = (int)Wt.size();
     for (int a = 0; a <= deg; ++a)
       for (int b = 0; b <= (d >= 2 ? deg - a : 0); ++b)
@@ -368,16 +398,17 @@ bool selftest_ref_tables(int dim, int k, double report[4], std::string& err) {
           }
           const double ex = fact(a) * fact(b) * fact(c) / fact(a + b + c + d);
           const double e = std::fabs(val - ex) / ex;
-          if (pass == 0) e0 = std::max(e0, e); else e1 = std::max(e1, e);
+          if (pass == 1) e1 = std::max(e1, e); else e0 = std::max(e0, e);
         }
   }
-  // (2) orthonormality of the basis under the volume rule (exact to 3k-1 >= 2k for k>=1)
+  // (2) orthonormality of the basis under both volume rules (exact to 3k-1 >= 2k for k>=1)
   double e2 = 0.0;
   for (int i = 0; i < T.nb; ++i)
     for (int j = 0; j < T.nb; ++j) {
-      double acc = 0.0;
+      double acc = 0.0, acck = 0.0;
       for (int q = 0; q < T.nq; ++q) acc += T.wq[q] * T.phi[(size_t)q * T.nb + i] * T.phi[(size_t)q * T.nb + j];
-      e2 = std::max(e2, std::fabs(acc - (i == j ? 1.0 : 0.0)));
+      for (int q = 0; q < T.nqk; ++q) acck += T.wk[q] * T.phik[(size_t)q * T.nb + i] * T.phik[(size_t)q * T.nb + j];
+      e2 = std::max(e2, std::max(std::fabs(acc - (i == j ? 1.0 : 0.0)), std::fabs(acck - (i == j ? 1.0 : 0.0))));
     }
   // (3) D * Dinv = I
   double e3 = 0.0;

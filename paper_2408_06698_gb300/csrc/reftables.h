@@ -27,6 +27,11 @@ struct RefTables {
   std::vector<double> trm;       // [dim+1][nf][nb]   modal trace <phi_i o xhat_f, psi_m>
   std::vector<double> z;         // [nint][nq][dim]   interior moment functions
   std::vector<double> D, Dinv;   // [nloc][nloc]      functionals x (component-major basis)
+  // the volume kernels' rule (exact to degree 3k-1; compact where one is tabulated, else
+  // the rule above) and the basis there
+  int nqk = 0;
+  std::vector<double> xk, wk;    // [nqk][dim], [nqk]
+  std::vector<double> phik;      // [nqk][nb]
 };
 
 // Gauss-Jacobi nodes t in (0,1) and weights for int_0^1 f(t) (1-t)^alpha dt.
