@@ -43,24 +43,31 @@ ALL_FAMILIES = FAMILIES + ["facet_adj", "volume_adj"]                   # every 
 
 
 # ------------------------------------------------------------------ roofline arithmetic
+# points of the compact volume rules the volume kernels integrate with (exact to degree
+# 3k - 1; elsewhere the collapsed Gauss-Jacobi rule with m^d points)
+COMPACT_VOLUME_POINTS = {(3, 3): 46, (3, 4): 100, (3, 5): 190}
+
+
 def shape(dim, k):
     from math import comb
     nb = comb(k + dim, dim)
     nf = comb(k + dim - 1, dim - 1)
     mv = (3 * k + 1) // 2
     mf = (3 * k + 2) // 2
-    return dict(nb=nb, nf=nf, nloc=dim * nb, nint=dim * nb - (dim + 1) * nf, nq=mv ** dim, nqf=mf ** (dim - 1))
+    return dict(nb=nb, nf=nf, nloc=dim * nb, nint=dim * nb - (dim + 1) * nf, nq=mv ** dim, nqf=mf ** (dim - 1),
+                nq_kernel=COMPACT_VOLUME_POINTS.get((dim, k), mv ** dim))
 
 
 def algorithmic(dim, k, E, NF, tsize):
     """Per-launch algorithmic flops and bytes of each kernel family (STAGE wind: w = u).
 
     Bytes count each input/output once (coefficients, the geometry actually read, facet
-    moments, connectivity); flops count the contractions the kernels perform.
+    moments, connectivity); flops count the contractions the kernels perform, the volume
+    term with the kernels' own quadrature rule (nq_kernel points).
     """
     from math import comb
     s = shape(dim, k)
-    nb, nf, nl, nq, nqf = s["nb"], s["nf"], s["nloc"], s["nq"], s["nqf"]
+    nb, nf, nl, nq, nqf = s["nb"], s["nf"], s["nloc"], s["nq_kernel"], s["nqf"]
     nb1 = comb(k - 1 + dim, dim)
     d = dim
     l = k - 1
@@ -247,10 +254,11 @@ def reference_arm(args, rank):
 
 # ------------------------------------------------------------------ our arm
 def kernel_sources_sha() -> str:
-    """sha256[:16] of every kernel header of the library (sorted by name, concatenated)."""
+    """sha256[:16] of every kernel and table header of the library (csrc/*.cuh and
+    csrc/*.h, sorted by name, concatenated)."""
     d = os.path.join(ROOT, "paper_2408_06698_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(f for f in os.listdir(d) if f.endswith(".cuh")):
+    for name in sorted(f for f in os.listdir(d) if f.endswith(".cuh") or f.endswith(".h")):
         with open(os.path.join(d, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

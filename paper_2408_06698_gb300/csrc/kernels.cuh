@@ -721,7 +721,8 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   constexpr int NBQ = row_stride<T>(NB);
   constexpr int BT = NQ * NBQ, DM = D * NB1 * NB, TRM = (D + 1) * NF * NB;
   constexpr int FT = FUSE ? FuseCfg<D, K, T>::TAB : 0, NLR = FuseCfg<D, K, T>::NLR;
-  constexpr int OTRM = r4i(BT + NQ + DM);  // TrM 16-byte aligned (paired loads in the lift)
+  constexpr int ODM = r4i(BT + NQ);          // staged Dm rows padded to NBP, 16-byte aligned
+  constexpr int OTRM = r4i(ODM + D * NB1 * NBP);  // TrM 16-byte aligned (paired loads in the lift)
   constexpr int TABN = r4i(OTRM + TRM) + r4i(FT);
   constexpr int NG = (D + 1) * NF * D;
   constexpr int QB = (sizeof(T) == 4 && NQ > 32) ? 2 : 1;  // quadrature points per lane and pass
@@ -742,11 +743,14 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   if (STAB) {
     for (int t = threadIdx.x; t < BT; t += blockDim.x) sbase[t] = Bt[t];
     for (int t = threadIdx.x; t < NQ; t += blockDim.x) sbase[BT + t] = Wq[t];
-    for (int t = threadIdx.x; t < DM; t += blockDim.x) sbase[BT + NQ + t] = Dm[t];
+    for (int t = threadIdx.x; t < D * NB1 * NBP; t += blockDim.x) {
+      const int row = t / NBP, i = t - row * NBP;
+      sbase[ODM + t] = i < NB ? Dm[row * NB + i] : T(0);
+    }
     for (int t = threadIdx.x; t < TRM; t += blockDim.x) sbase[OTRM + t] = TrM[t];
     Bt = sbase;
     Wq = sbase + BT;
-    Dm = sbase + BT + NQ;
+    Dm = sbase + ODM;
     TrM = sbase + OTRM;
     sw = sbase + TABN;
   }
@@ -759,8 +763,8 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* wbase = sw + warp * PER_WARP;
-  T* sC = wbase + 2 * STAGE;                // [D][NBP]       u coefficients
-  T* sG = sC + D * NBP;                     // [D][D][NB1P]   modal reference gradients of u
+  T* sCpad = wbase + 2 * STAGE;             // [D][NBP]       u coefficients (padded rows)
+  T* sG = sCpad + D * NBP;                  // [D][D][NB1P]   modal reference gradients of u
   T* sW = sG + D * D * NB1P;                // [D][NBP]       W coefficients (WSEP)
   T* sDv = sW + (WSEP ? D * NBP : 0);       // [NB1P]         modal div^ W (WSEP)
   auto st_u = [&](int b) { return wbase + b * STAGE; };
@@ -802,6 +806,8 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
       }
     }
   };
+  if constexpr (NBP != NB)  // the padding of the u rows meets zero Dm columns: keep it finite
+    for (int t = lane; t < D * NBP; t += 32) sCpad[t] = T(0);
   const int64_t stride = (int64_t)gridDim.x * kWarps;
   int64_t e = (int64_t)blockIdx.x * kWarps + warp;
   if (e < m.E) issue(e, 0);
@@ -820,9 +826,11 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
 #pragma unroll
       for (int c = 0; c < D; ++c) M[a][c] = g[2 * D * D + a * D + c];
     const T invabs = g[3 * D * D];
+    // u coefficients [D][NBP]: the staged record itself when its rows need no padding
+    T* sC = (NBP == NB) ? st_u(b) : sCpad;
     for (int s2 = lane; s2 < NL; s2 += 32) {
       const int a = s2 / NB, i = s2 - a * NB;
-      sC[a * NBP + i] = st_u(b)[s2];
+      if (NBP != NB) sC[a * NBP + i] = st_u(b)[s2];
       if (WSEP) {
         T acc = T(0);
 #pragma unroll
@@ -831,19 +839,43 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
       }
     }
     __syncwarp();
-    for (int v = lane; v < D * D * NB1; v += 32) {
-      const int a = v / (D * NB1), c = (v / NB1) % D, j = v % NB1;
-      T acc = T(0);
+    if constexpr (STAB) {  // lane (c, j): (Dm_c u_a)_j for every a; padded rows, 16-byte loads
+      for (int v = lane; v < D * NB1; v += 32) {
+        const int c = v / NB1, j = v - c * NB1;
+        const T* drow = Dm + (c * NB1 + j) * NBP;
+        T acc[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] = T(0);
+#pragma unroll
+        for (int i = 0; i < NBP; i += 4) {
+          T dv[4];
+          lds4(drow + i, dv);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            T cv[4];
+            lds4(sC + a * NBP + i, cv);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc[a] = fma(dv[t], cv[t], acc[a]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) sG[(a * D + c) * NB1P + j] = acc[a];
+      }
+    } else {
+      for (int v = lane; v < D * D * NB1; v += 32) {
+        const int a = v / (D * NB1), c = (v / NB1) % D, j = v % NB1;
+        T acc = T(0);
 #pragma unroll 4
-      for (int i = 0; i < NB; ++i) acc = fma(Dm[(c * NB1 + j) * NB + i], sC[a * NBP + i], acc);
-      sG[(a * D + c) * NB1P + j] = acc;
+        for (int i = 0; i < NB; ++i) acc = fma(Dm[(c * NB1 + j) * NB + i], sC[a * NBP + i], acc);
+        sG[(a * D + c) * NB1P + j] = acc;
+      }
     }
     if (WSEP) {
       for (int j = lane; j < NB1; j += 32) {
         T acc = T(0);
         for (int c = 0; c < D; ++c)
 #pragma unroll 4
-          for (int i = 0; i < NB; ++i) acc = fma(Dm[(c * NB1 + j) * NB + i], sW[c * NBP + i], acc);
+          for (int i = 0; i < NB; ++i) acc = fma(Dm[(c * NB1 + j) * (STAB ? NBP : NB) + i], sW[c * NBP + i], acc);
         sDv[j] = acc;
       }
     }

@@ -33,8 +33,8 @@ class OpsImpl final : public Ops {
   // volume kernel: Bt, Wq, Dm, TrM; per warp: coefficients, modal gradients, (W and its
   // divergence), signed facet moments (layout of k_volume)
   static constexpr int kNB1 = cnbasis(D, K - 1);
-  static constexpr size_t kVolTab =  // TrM starts 16-byte aligned (layout of k_volume)
-      r4(r4(size_t(S::nq) * kNBQ + S::nq + size_t(D) * kNB1 * S::nb) + size_t(D + 1) * S::nf * S::nb) * sz;
+  static constexpr size_t kVolTab =  // Dm rows padded, Dm and TrM 16-byte aligned (layout of k_volume)
+      r4(r4(r4(size_t(S::nq) * kNBQ + S::nq) + size_t(D) * kNB1 * r4(S::nb)) + size_t(D + 1) * S::nf * S::nb) * sz;
   static constexpr size_t volume_stage(bool wsep) {
     return r4(S::nloc) * (wsep ? 2 : 1) + r4(size_t(D + 1) * S::nf * D) + r4(S::gt);
   }
