@@ -554,13 +554,14 @@ def our_arm(args, rank, world):
     alu_meas = {"fp32_tflops": measure_alu_peak(False), "fp64_tflops": measure_alu_peak(True),
                 "fp32_nominal_tflops_at_sampled_clock": fp32_alu_peak_tflops(sm_mhz),
                 "fp64_nominal_tflops_at_sampled_clock": fp64_alu_peak_tflops(sm_mhz)}
-    alu_peak = alu_meas["fp32_tflops"]
+    alu_peak = fp32_alu_peak_tflops(sm_mhz)
     traffic = traffic_from_profiles(dom)
     roofline = {"kernel": dom, "bound": "alu", "achieved": ach_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach_tflops / alu_peak, "traffic": traffic,
-                "peak_source": "measured FP32 FMA throughput of this GPU (hopu_measure_alu_peak: 8 independent "
-                               "FMA chains per thread, 2048 threads per SM, CUDA events); nominal at the "
-                               f"sampled {sm_mhz:.0f} MHz: {fp32_alu_peak_tflops(sm_mhz):.1f}",
+                "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
+                               "sampled during the timed region)",
+                "peak_measured": alu_meas["fp32_tflops"],
+                "frac_of_measured": ach_tflops / alu_meas["fp32_tflops"],
                 "achieved_bytes_gbs": byts / (avg_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": byts / (avg_ms / 1e3) / 1e9 / hbm_peak,
                 "flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
