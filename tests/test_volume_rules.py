@@ -53,3 +53,17 @@ def test_compact_rule_weights_positive_points_interior(k):
     bary = np.column_stack([1.0 - X.sum(1), X])
     assert bary.min() > 1e-4
     assert abs(w.sum() - 1.0 / 6.0) < 1e-15
+
+
+def test_bench_flop_model_uses_the_kernels_rule_sizes():
+    """bench.py's algorithmic flop count of the volume kernel uses the point counts of the
+    committed rules (and of the header's compact_volume_points)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    internal = open(os.path.join(os.path.dirname(HEADER), "hopu_internal.h")).read()
+    for k in (3, 4, 5):
+        X, _ = _rule(k)
+        assert bench.COMPACT_VOLUME_POINTS[(3, k)] == X.shape[0]
+        assert f"k == {k} ? {X.shape[0]}" in internal
+        assert bench.shape(3, k)["nq_kernel"] == X.shape[0]
