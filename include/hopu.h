@@ -44,8 +44,13 @@
  *                  chi_j over the degree-(k-2) block of the 2D Dubiner basis of
  *                  (xhat_1, xhat_2).
  *
- *   Quadrature: collapsed Gauss-Jacobi rules, exact to degree 3k-1 on elements and 3k
- *   on facets (Section 2.2 asks for exact integration of every form).
+ *   Quadrature (Section 2.2 asks for exact integration of every form): facet rules are
+ *   collapsed Gauss-Jacobi rules exact to degree 3k; volume integrals of the operator use
+ *   rules exact to degree 3k-1 -- in 3D for k = 3, 4, 5 compact rules of 46, 100 and
+ *   190 points (the project's own, checked on every monomial), otherwise the
+ *   collapsed Gauss-Jacobi rule.  hopu_points / hopu_interpolate use the collapsed rules.
+ *   Every exact rule gives the same operator up to rounding (the integrand is a
+ *   polynomial of degree 3k-1 on an affine element).
  *
  * Conventions of every call:
  *   - Coefficient pointers are DEVICE pointers owned by the caller, in the working
@@ -76,17 +81,25 @@ typedef enum {
   HOPU_EINVAL = -1,   /* bad argument (NULL pointer, size, enum value)               */
   HOPU_ENOMEM = -2,   /* host or device allocation failed                            */
   HOPU_ECUDA = -3,    /* a CUDA runtime call failed (text in hopu_last_error)        */
-  HOPU_EMESH = -4,    /* mesh is not a valid closed simplicial mesh                  */
+  HOPU_EMESH = -4,    /* mesh is not a valid conforming simplicial mesh              */
   HOPU_ETIMEOUT = -5, /* a bounded device-side wait ran out                          */
-  HOPU_ENOTSUP = -6   /* valid request this build does not support (e.g. boundary)  */
+  HOPU_ENOTSUP = -6   /* valid request this build does not support (e.g. the VJP on
+                         a mesh with boundary facets)                                 */
 } hopu_status;
 
 typedef enum {
   HOPU_FP64 = 0,     /* FP64 coefficients and arithmetic                                     */
-  HOPU_FP32 = 1,     /* FP32 coefficients, FP32 FMA arithmetic                               */
-  HOPU_FP32_TC = 2,  /* FP32 coefficients; the batched projection GEMMs on tensor cores in
-                        3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation), FP32 FMA elsewhere */
-  HOPU_TF32 = 3      /* as HOPU_FP32_TC with one TF32 product (about 1e-3 relative)          */
+  HOPU_FP32 = 1,     /* FP32 coefficients, FP32 FMA arithmetic; the V_h -> L2 projection and
+                        the facet traces of the jump as compensated FP32 dot products (as if
+                        in twice the working precision), the geometry kept in FP64            */
+  HOPU_FP32_TC = 2,  /* as HOPU_FP32, with the volume contractions of the STAGE substep on the
+                        tensor cores in 3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation);
+                        the V_h -> L2 projection stays the compensated FP32 product (on the
+                        tensor cores its FP32 accumulation would lose the small high-degree
+                        coefficients of smooth fields)                                      */
+  HOPU_TF32 = 3      /* FP32 coefficients; the V_h -> L2 projection GEMM and the STAGE volume
+                        contractions on the tensor cores with one TF32 product (about 1e-3
+                        relative); FP32 FMA elsewhere                                       */
 } hopu_prec;
 
 typedef enum {
@@ -125,7 +138,10 @@ typedef struct {
  * maps, normals), facet pairing, reference tables, and allocate device scratch.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  On failure *out is NULL
  * and the status says why (EMESH: non-manifold facet, a facet whose two sides agree on
- * the normal, a degenerate element; ENOTSUP: boundary facets, k outside 1..5).        */
+ * the normal, a degenerate element; ENOTSUP: k outside 1..5 in 3D or 1..4 in 2D).
+ * Facets with one element are boundary facets (walls / outlets unless declared inlets,
+ * see hopu_boundary_facets).  The geometry (Jacobians, Piola maps, inverse mass) is
+ * computed and stored in FP64 in every precision mode.                                 */
 hopu_status hopu_create(const hopu_mesh_desc* mesh, const hopu_options* opts,
                         void* cuda_stream, hopu_ctx** out);
 
@@ -135,9 +151,9 @@ hopu_status hopu_destroy(hopu_ctx* ctx);
 /* Replace the stream later calls enqueue on. */
 hopu_status hopu_set_stream(hopu_ctx* ctx, void* cuda_stream);
 
-/* Kernel variants in use: out2[0] for the V_h -> L2 projection, out2[1] for the fused
- * STAGE volume kernel; 0 = FP32 FMA kernel, 1 = tensor-core kernel.  No paper
- * counterpart (launch tuning).                                                        */
+/* Kernel variants in use: out2[0] for the V_h -> L2 projection (a tensor-core variant
+ * exists in HOPU_TF32 only), out2[1] for the fused STAGE volume kernel; 0 = FP32 FMA
+ * kernel, 1 = tensor-core kernel.  No paper counterpart (launch tuning).               */
 hopu_status hopu_tuning(const hopu_ctx* ctx, int* out2);
 
 /* Synchronise the context stream and report device-side failures: ETIMEOUT when a
@@ -145,6 +161,17 @@ hopu_status hopu_tuning(const hopu_ctx* ctx, int* out2);
  * output is then incomplete).  hopu_energy performs the same check.  No paper
  * counterpart: error reporting of the asynchronous calls.                             */
 hopu_status hopu_sync(hopu_ctx* ctx);
+
+/* Poll limit of the tensor-core kernels' MMA completion waits (k_v2l_tc in HOPU_TF32,
+ * k_volume_tc in HOPU_FP32_TC / HOPU_TF32): polls >= 0 sets it (0 makes the first such
+ * wait give up at once), polls < 0 restores the default of 2^22 polls (~0.3 s).  A wait
+ * that gives up records ETIMEOUT in the device error word (hopu_sync / hopu_energy
+ * report it and name the kernel); the kernel then stops issuing work, waits with the
+ * default limit for its MMAs in flight, frees its tensor memory and returns, leaving
+ * that launch's outputs incomplete.  No paper counterpart: failure detection of the
+ * asynchronous calls, settable so that the time-out path can be exercised.  Drops the
+ * cached substep graph.  EINVAL for polls above 2^32 - 1.                             */
+hopu_status hopu_set_wait_limit(hopu_ctx* ctx, int64_t polls);
 
 /* Sizes of the coefficient vectors: V_h length, L2 length (n_elems*dim*nb), facets. */
 hopu_status hopu_sizes(const hopu_ctx* ctx, int64_t* n_hdiv, int64_t* n_l2, int64_t* n_facets);
@@ -359,10 +386,14 @@ hopu_status hopu_profile_read(hopu_ctx* ctx, double* ms, int64_t* launches);
  * 32 MiB that is part of the library image, so every GPU that loads libhopu holds it
  * until the process exits.  Meshes that need more scratch than that (n_l2 plus
  * n_elems*(dim+1)*nf*dim values in the working precision) are rejected with EINVAL.
- * The first call on a device looks up the buffer's device address (make that first
- * call before any stream capture).  Every call shares the buffer, which keeps the last
+ * Every call made outside a stream capture looks up the buffer's device address on the
+ * current device (so a device reset or a new primary context is picked up); a call made
+ * while the stream is being captured reuses the address of the last earlier call on that
+ * device, so make one call on each device before capturing (EINVAL otherwise), and do
+ * not capture across a device reset.  Every call shares the buffer, which keeps the last
  * call's contents (nothing in it needs to start at zero); calls that overlap on the GPU
- * (other streams, threads or contexts on the same device) race on it.  Arguments,
+ * (other streams, threads or contexts on the same device) race on it.  Profiling
+ * (hopu_profile) times its kernels like those of hopu_apply_convection.  Arguments,
  * result and errors as hopu_apply_convection.                                         */
 hopu_status hopu_apply_convection_noalloc(hopu_ctx* ctx, const void* w_hdiv, const void* u_l2,
                                           void* y_l2, const int8_t* facet_l);

@@ -17,6 +17,9 @@ simplices, written in FP64:
 * ``convection`` the HOPU convection form in conservative and in the paper's
                  non-conservative form, the inverse mass, energy functionals.
 * ``rk``         SSP-RK3 substeps (Shu-Osher) with the two wind rules.
+* ``sampled``    the apply on sampled elements of a large mesh, evaluated on the
+                 sub-mesh of their facet neighbourhood (pinned: equal to the full
+                 apply on the sampled elements, bit for bit).
 
 Parity status of every function is listed in its module docstring; functions
 without an independent pin say "parity unpinned".

@@ -64,6 +64,7 @@ SIGNATURES = {
     "hopu_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "hopu_measure_alu_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
     "hopu_sync": (c_int, [c_void_p]),
+    "hopu_set_wait_limit": (c_int, [c_void_p, c_int64]),
     "hopu_boundary_facets": (c_int, [c_void_p, c_void_p, POINTER(c_int64)]),
     "hopu_set_inlet": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "hopu_tuning": (c_int, [c_void_p, POINTER(c_int)]),

@@ -256,43 +256,19 @@ hopu_status check_launch(hopu_ctx* c, const char* where) {
 }
 
 // Read the device error word (the stream must have been synchronised): ETIMEOUT when a
-// tensor-core kernel gave up waiting for its MMAs.
+// tensor-core kernel gave up waiting for its MMAs (bit 0: k_v2l_tc, bit 1: k_volume_tc);
+// the word is cleared once read.
 hopu_status device_status(hopu_ctx* c) {
   int e = 0;
   HOPU_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (e & 1) {
-    cudaMemset(c->d_err, 0, sizeof(int));
-    return fail(c, HOPU_ETIMEOUT, "a tensor-core completion wait gave up");
+  if (e & 3) {
+    HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    std::string who = (e & 1) ? "k_v2l_tc (V_h -> L2 projection)" : "";
+    if (e & 2) who += std::string(who.empty() ? "" : " and ") + "k_volume_tc (volume term)";
+    return fail(c, HOPU_ETIMEOUT, "a tensor-core MMA completion wait gave up in " + who +
+                                      "; the outputs of that launch are incomplete");
   }
   return HOPU_OK;
-}
-
-constexpr int kProfPairs = 64;
-
-// Run launch() on the context stream, bracketed by a pair of timing events when
-// profiling is on.  Inside a graph capture the event records become graph nodes, so
-// every replay re-records them.
-template <class F>
-void timed(hopu_ctx* c, int family, F&& launch) {
-  if (!c->prof_on || c->ev.empty()) {
-    launch();
-    return;
-  }
-  int p;
-  if (c->capturing) {
-    p = (int)c->prof_graph.size() % kProfPairs;
-    c->prof_graph.push_back({p, family});
-  } else {
-    p = kProfPairs + c->prof_next_direct;
-    c->prof_next_direct = (c->prof_next_direct + 1) % kProfPairs;
-    if ((int)c->prof_direct.size() >= kProfPairs) c->prof_direct.erase(c->prof_direct.begin());
-    c->prof_direct.push_back({p, family});
-  }
-  // inside a capture only the External flag turns the record into a graph node
-  const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-  cudaEventRecordWithFlags(c->ev[2 * p], c->stream, flags);
-  launch();
-  cudaEventRecordWithFlags(c->ev[2 * p + 1], c->stream, flags);
 }
 
 void free_all(hopu_ctx* c) {
@@ -300,7 +276,7 @@ void free_all(hopu_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
                   c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err, c->d_tcvol,
-                  c->d_inlet, c->d_inlet_modes};
+                  c->d_inlet, c->d_inlet_modes, c->d_csr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c->ops;
@@ -388,6 +364,44 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
   Drow.assign((size_t)nl * nlr, 0.0);
   for (int r = 0; r < nl; ++r)
     for (int s = 0; s < nl; ++s) Drow[(size_t)r * nlr + s] = R.D[(size_t)r * nl + s];
+}
+
+// The nonzeros of the dof matrix D (row s = functional, column r = basis function b*nb + i)
+// for the residual of the refined FP32 projection: nloc row headers {s, first entry, count, 0}
+// (int32 bits) sorted by count, largest first, then one entry {r (int32 bits), hi, lo, 0}
+// per nonzero with hi = float(D[s][r]), lo = float(D[s][r] - hi).  Entries below 1e-13 of
+// max |D| are the exact zeros of the orthogonality relations, rounded by the quadrature.
+void dof_matrix_csr(const RefTables& R, std::vector<float>& out) {
+  const int nl = R.nloc;
+  double mx = 0.0;
+  for (double v : R.D) mx = std::max(mx, std::fabs(v));
+  std::vector<std::vector<std::pair<int, double>>> rows(nl);
+  for (int s = 0; s < nl; ++s)
+    for (int r = 0; r < nl; ++r) {
+      const double v = R.D[(size_t)s * nl + r];
+      if (std::fabs(v) > 1e-13 * mx) rows[s].push_back({r, v});
+    }
+  std::vector<int> order(nl);
+  for (int s = 0; s < nl; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a].size() > rows[b].size(); });
+  size_t nnz = 0;
+  for (const auto& r : rows) nnz += r.size();
+  out.assign(4 * (nl + nnz), 0.0f);
+  auto put_int = [&](size_t i, int v) { std::memcpy(&out[i], &v, 4); };
+  int next = nl;
+  for (int h = 0; h < nl; ++h) {
+    const int s = order[h];
+    put_int(4 * h, s);
+    put_int(4 * h + 1, next);
+    put_int(4 * h + 2, (int)rows[s].size());
+    for (const auto& e : rows[s]) {
+      const float hi = (float)e.second;
+      put_int(4 * (size_t)next, e.first);
+      out[4 * (size_t)next + 1] = hi;
+      out[4 * (size_t)next + 2] = (float)(e.second - (double)hi);
+      ++next;
+    }
+  }
 }
 
 // Round an FP32 value to TF32 (10 mantissa bits), to nearest with ties away from zero.
@@ -712,7 +726,7 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   c->dm.fb = reinterpret_cast<const int32_t*>(base + s_geo + s_efc + s_f);
   c->dm.fgeo = reinterpret_cast<const double*>(base + s_geo + s_efc + 2 * s_f);
 
-  // working-precision geometry factors, computed in FP64 and rounded once
+  // geometry factors, computed and kept in FP64 (the FP32 kernels round them at load)
   {
     const int d = c->dim, GT = geoT_stride(d);
     std::vector<double> gt((size_t)E * GT, 0.0);
@@ -727,12 +741,9 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
       }
       o[3 * d * d] = 1.0 / ad;
     }
-    std::vector<unsigned char> hg(c->tsize * gt.size());
-    if (c->fp64) convert<double>(gt, hg, 0);
-    else convert<float>(gt, hg, 0);
-    HOPU_CUDA(c, cudaMalloc(&c->d_geoT, hg.size()));
-    HOPU_CUDA(c, cudaMemcpy(c->d_geoT, hg.data(), hg.size(), cudaMemcpyHostToDevice));
-    c->dm.geoT = c->d_geoT;
+    HOPU_CUDA(c, cudaMalloc(&c->d_geoT, sizeof(double) * gt.size()));
+    HOPU_CUDA(c, cudaMemcpy(c->d_geoT, gt.data(), sizeof(double) * gt.size(), cudaMemcpyHostToDevice));
+    c->dm.geoT = static_cast<const double*>(c->d_geoT);
   }
 
   // tables upload, converted to the working precision
@@ -756,6 +767,14 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
                                     &c->dt.TrP,  &c->dt.Psi, &c->dt.WPsi,  &c->dt.Wf,
                                     &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow, &c->dt.Dn};
   for (int i = 0; i < kNumTables; ++i) *slots[i] = tb + offs[i];
+  if (!c->fp64) {
+    std::vector<float> csr;
+    dof_matrix_csr(R, csr);
+    HOPU_CUDA(c, cudaMalloc(&c->d_csr, csr.size() * sizeof(float)));
+    HOPU_CUDA(c, cudaMemcpy(c->d_csr, csr.data(), csr.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->dt.Dcsr = c->d_csr;
+    c->dt.csr_n = (int)(csr.size() / 4);
+  }
   if (c->ops->tensor_core_volume()) {
     std::vector<float> tv;
     tensor_core_volume_table(R, tv);
@@ -784,6 +803,8 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   const size_t elog_bytes = sizeof(int64_t) * (2 + elog_blocks(c->topo.n_elems, c->nsm));
   HOPU_CUDA(c, cudaMalloc((void**)&c->d_elog_pos, elog_bytes));
   HOPU_CUDA(c, cudaMemset(c->d_elog_pos, 0, elog_bytes));
+  ce = c->ops->configure(c->dt);
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "kernel configuration");
   return autotune(c, opts->tile_hint);
 }
 }  // namespace
@@ -829,6 +850,17 @@ hopu_status hopu_sync(hopu_ctx* c) {
   HOPU_PRECHECK(c);
   HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
   return device_status(c);
+}
+
+hopu_status hopu_set_wait_limit(hopu_ctx* c, int64_t polls) {
+  HOPU_PRECHECK(c);
+  if (polls > (int64_t)UINT32_MAX) return fail(c, HOPU_EINVAL, "set_wait_limit: more than 2^32 - 1 polls");
+  c->dm.tc_wait_limit = polls < 0 ? (1u << 22) : (uint32_t)polls;
+  if (c->gexec) {  // the captured substep holds the old limit in its kernel parameters
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return HOPU_OK;
 }
 
 hopu_status hopu_sizes(const hopu_ctx* c, int64_t* n_hdiv, int64_t* n_l2, int64_t* n_facets) {

@@ -33,6 +33,7 @@ struct hopu_ctx {
   void* d_geoT = nullptr;   // working-precision geometry factors
   void* d_tabs = nullptr;   // every reference table
   void* d_tcvol = nullptr;  // tensor-core volume tables (FP32 tensor-core modes)
+  void* d_csr = nullptr;    // FP32: nonzeros of the dof matrix D (refined projection)
   void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major
   void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals
   void* d_uL = nullptr;     // L2 stage field
@@ -73,3 +74,35 @@ struct hopu_ctx {
   int status = HOPU_OK;
   std::string err;
 };
+
+namespace hopu {
+
+constexpr int kProfPairs = 64;
+
+// Run launch() on the context stream, bracketed by a pair of timing events when
+// profiling is on (hopu_profile).  Inside a graph capture the event records become graph
+// nodes, so every replay re-records them.
+template <class F>
+void timed(hopu_ctx* c, int family, F&& launch) {
+  if (!c->prof_on || c->ev.empty()) {
+    launch();
+    return;
+  }
+  int p;
+  if (c->capturing) {
+    p = (int)c->prof_graph.size() % kProfPairs;
+    c->prof_graph.push_back({p, family});
+  } else {
+    p = kProfPairs + c->prof_next_direct;
+    c->prof_next_direct = (c->prof_next_direct + 1) % kProfPairs;
+    if ((int)c->prof_direct.size() >= kProfPairs) c->prof_direct.erase(c->prof_direct.begin());
+    c->prof_direct.push_back({p, family});
+  }
+  // inside a capture only the External flag turns the record into a graph node
+  const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaEventRecordWithFlags(c->ev[2 * p], c->stream, flags);
+  launch();
+  cudaEventRecordWithFlags(c->ev[2 * p + 1], c->stream, flags);
+}
+
+}  // namespace hopu

@@ -11,13 +11,16 @@ namespace hopu {
 struct DevMesh {
   int64_t E = 0, NF = 0;
   const double* geo = nullptr;   // [E][2d^2+2]: J (row-major), Jinv, det J, |det J| (FP64)
-  const void* geoT = nullptr;    // [E][geoT_stride(d)] in working precision, computed in FP64:
+  const double* geoT = nullptr;  // [E][geoT_stride(d)] FP64 in every precision mode (the FP32 kernels
+                                 // round each factor when they load it):
                                  //   Pf = J / det J, Pi = det J * Jinv, M = |det J| * Jinv, 1/|det J|
   const int32_t* efc = nullptr;  // [E][d+1]: F*4 + (sigma<0)*2 + (element is side B)
   const int32_t* fa = nullptr;   // [NF]: element*4 + local facet of side A
   const int32_t* fb = nullptr;   // [NF]: same for side B
   const double* fgeo = nullptr;  // [NF][d+1]: canonical unit normal n_F, a_F = |F|/|param|
-  int* err = nullptr;            // device error word (bit 0: a tensor-core completion wait gave up)
+  int* err = nullptr;            // device error word (bit 0 / bit 1: a completion wait of the
+                                 // tensor-core projection / volume kernel gave up)
+  uint32_t tc_wait_limit = 1u << 22;  // polls of the tensor-core MMA completion waits (hopu_set_wait_limit)
   // boundary facets have fb[F] == fa[F] (wall / outlet rule: the exterior trace is the
   // interior one); inlet facets also have inlet[F] >= 0, the row of their exterior data
   const int32_t* inlet = nullptr;  // [NF] or NULL (no inlets)
@@ -36,6 +39,9 @@ struct DevTabs {
   const void* WPsi = nullptr;   // [nf][nqf]       w_q psi_m(s_q)
   const void* Wf = nullptr;     // [nqf]           facet weights
   const void* DinvT = nullptr;  // [nloc][nlp]     DinvT[s][r] = Dinv[r][s]  (nlp = nloc rounded up to 4)
+  const void* Dcsr = nullptr;   // FP32: the nonzeros of D by rows, 16-byte entries (layout in
+                                //   k_v2l / warp_tile_residual); csr_n entries in all
+  int csr_n = 0;
   const void* DT = nullptr;     // [nloc][nlp]     DT[s][r]    = D[r][s]
   const void* Dinv = nullptr;   // [nloc][nlp]     Dinv[s][r]
   const void* Dn = nullptr;     // [nloc][nlp]     Dn[s][r] = D[s][r]
@@ -81,6 +87,8 @@ class Ops {
  public:
   virtual ~Ops() {}
   virtual cudaError_t prepare() = 0;
+  // launch configuration that depends on the uploaded tables (after prepare)
+  virtual cudaError_t configure(const DevTabs&) = 0;
   // E: V_h -> L2
   virtual int v2l(const DevMesh&, const DevTabs&, const void* uV, void* uL, cudaStream_t) = 0;
   // facet flux moments, element-major: gam[e][f][nf][d] for the element e that sees the

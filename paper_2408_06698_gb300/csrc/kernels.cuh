@@ -4,7 +4,7 @@
 // Work decomposition: one warp per element (projections, volume term) or per facet
 // (facet flux).  Reference tables are staged once per CTA in shared memory and the
 // grids are persistent (a multiple of the SM count), so every CTA loads them once.
-// Geometry is stored in FP64 and rounded to T at use.
+// Geometry is stored in FP64 (every precision mode) and rounded to T at use.
 #pragma once
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -100,6 +100,22 @@ __device__ __forceinline__ T combine_at(const Combine& c, T v, int64_t idx) {
   }
 }
 
+// Error-free transformations of FP32 arithmetic (compensated dot products, Ogita, Rump
+// and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005), Dot2): the
+// product a*x splits exactly into p + pe (pe by one FMA) and the running sum s + p into
+// t + se (Knuth's TwoSum); the rounding errors collect in c, so that s + c carries the dot
+// product as if it had been computed in twice the working precision and rounded once.
+// The intrinsics keep the compiler from contracting or reordering the steps.
+__device__ __forceinline__ void dot2_step(float& s, float& c, float a, float x) {
+  const float p = __fmul_rn(a, x);
+  const float pe = __fmaf_rn(a, x, -p);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(se, pe));
+}
+
 // Vector views of shared memory: 16-byte loads of 4 floats or 2 doubles.
 template <typename T> struct Pack;
 template <> struct Pack<float> {
@@ -165,6 +181,25 @@ struct ProjWCfg {
   static_assert(SMEM <= 227 * 1024, "projection tile exceeds shared memory");
 };
 
+// The refined FP32 V_h -> L2 projection (k_v2l, FP32): per warp tile X [NL][EW] (the
+// gathered local dofs, then the residual) and Y [EW][NLQ] (the coefficients) side by
+// side; the sparse rows of D (csr, 16-byte entries) and, when it fits, Dinv^T are staged
+// per CTA.  More warps per CTA where the per-CTA tables are large.
+template <int D, int K>
+struct ProjRCfg {
+  using W = ProjWCfg<D, K, float>;
+  using C = ProjCfg<D, K, float>;
+  static constexpr int NL = W::NL, EW = W::EW, NLQ = W::NLQ, DD = W::DD;
+  static constexpr int XS = (NL * EW + 3) / 4 * 4, YS = (EW * NLQ + 3) / 4 * 4, PS = (EW * DD + 3) / 4 * 4;
+  static constexpr int PER_WARP = XS + YS + PS;
+  static constexpr size_t CSR_MAX = size_t(NL + NL * NL) * 16;  // headers + every entry (upper bound)
+  static constexpr size_t TILE = size_t(PER_WARP) * 4;
+  static constexpr size_t TAB = C::TAB;                          // Dinv^T, FP32
+  static constexpr int fit_warps(size_t fixed) {
+    return fixed + 16 * TILE <= 220 * 1024 ? 16 : fixed + 12 * TILE <= 220 * 1024 ? 12 : fixed + 8 * TILE <= 220 * 1024 ? 8 : 4;
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ void ld4(const T* p, T* o) {  // 4 consecutive values, 16-byte aligned
   Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p), o);
@@ -214,31 +249,145 @@ __device__ __forceinline__ void warp_tile_gemm(const T* Tb, T* sX, int lane) {
   __syncwarp();
 }
 
+// The product of a warp tile into a separate buffer: Y[k][r] (=|+=) sum_s tab[s][r] X[s][k]
+// (X [s][EW] in sX, Y [EW][NLQ] in sY).
+template <int D, int K, bool ADD>
+__device__ __forceinline__ void warp_tile_gemm_to(const float* Tb, const float* sX, float* sY, int lane) {
+  using W = ProjWCfg<D, K, float>;
+  constexpr int NL = W::NL, NLP = W::NLP, NLQ = W::NLQ, EW = W::EW;
+  float keep[W::NPASS][4][4];
+#pragma unroll
+  for (int p = 0; p < W::NPASS; ++p) {
+    const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) keep[p][i][j] = 0.0f;
+    if (task < W::NTASK) {
+#pragma unroll 4
+      for (int s2 = 0; s2 < NL; ++s2) {
+        float tv[4], xv[4];
+        ld4(Tb + s2 * NLP + rg * 4, tv);
+        ld4(sX + s2 * EW + eg * 4, xv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) keep[p][i][j] = fmaf(tv[i], xv[j], keep[p][i][j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < W::NPASS; ++p) {
+    const int task = lane + 32 * p, rg = task / (EW / 4), eg = task - rg * (EW / 4);
+    if (task < W::NTASK) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (rg * 4 + i < NL)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float* y = sY + (eg * 4 + j) * NLQ + rg * 4 + i;
+            *y = ADD ? __fadd_rn(*y, keep[p][i][j]) : keep[p][i][j];
+          }
+    }
+  }
+  __syncwarp();
+}
+
+// Residual of the reference change of basis, in place: X[s][k] <- X[s][k] - sum_r D[s][r] Y[k][r]
+// in compensated FP32 (Dot2), so that it is accurate to the rounding of its own (small)
+// size.  csr: NL row headers {s, first entry, count, 0} sorted by count (the rows a warp
+// instruction serves have similar lengths), then entries {r, D_hi, D_lo, 0} with
+// D_hi = float(D[s][r]) and D_lo = float(D[s][r] - D_hi) (the nonzeros of D only).  A lane
+// takes one row for two of the tile's eight elements (eight rows per warp instruction: the
+// row lengths of D are skewed, and more rows per instruction would leave more lanes idle).
+template <int D, int K>
+__device__ __forceinline__ void warp_tile_residual(const float4* csr, float* sX, const float* sY, int lane) {
+  using W = ProjWCfg<D, K, float>;
+  constexpr int NL = W::NL, EW = W::EW, NLQ = W::NLQ;
+  static_assert(EW == 8, "four pairs of elements per row");
+  const int4* hdr = reinterpret_cast<const int4*>(csr);
+  for (int t = lane; t < NL * 4; t += 32) {
+    const int h = t >> 2, q = t & 3;  // row header h, elements q and q + 4
+    const int4 hd = hdr[h];
+    float a0 = sX[hd.x * EW + q], a1 = sX[hd.x * EW + q + 4], c0 = 0.0f, c1 = 0.0f;
+    const float* y0 = sY + q * NLQ;
+    const float* y1 = y0 + 4 * NLQ;
+    for (int j = hd.y; j < hd.y + hd.z; ++j) {
+      const float4 ent = csr[j];
+      const int r = __float_as_int(ent.x);
+      const float v0 = y0[r], v1 = y1[r];
+      dot2_step(a0, c0, -ent.y, v0);
+      dot2_step(a1, c1, -ent.y, v1);
+      c0 = __fmaf_rn(-ent.z, v0, c0);
+      c1 = __fmaf_rn(-ent.z, v1, c1);
+    }
+    sX[hd.x * EW + q] = __fadd_rn(a0, c0);
+    sX[hd.x * EW + q + 4] = __fadd_rn(a1, c1);
+  }
+  __syncwarp();
+}
+
+// FP32 (PT = false): the reference change of basis Dinv X is refined once, Y = Dinv X,
+// then Y += Dinv (X - D Y) with the residual in compensated FP32 (csr: the sparse rows of
+// D, see warp_tile_residual).  Reason: on smooth fields the reference coefficients of
+// degree >= 2 are small differences of O(|u|) local dofs, so the plain FP32 product loses
+// ~cond(D) ulps of |u| in them, and the convection operator, a first derivative,
+// amplifies that by ~k^2/h (3e-6 of max |y| on a 16^3, k = 3 Taylor-Green field); after
+// the refinement the projection is accurate to the rounding of its output.  nw: warps of
+// the CTA (blockDim.x / 32); tab_staged: stage tab in shared memory.
 template <int D, int K, typename T, bool PT>
-__global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_v2l(DevMesh m, const T* __restrict__ tab,
-                                                                       const T* __restrict__ uV, T* __restrict__ uL) {
+__global__ void __launch_bounds__((!PT && sizeof(T) == 4) ? 512 : 32 * ProjWCfg<D, K, T>::WARPS) k_v2l(DevMesh m, const T* __restrict__ tab, const float4* __restrict__ csr,
+                                             int csr_n, int tab_staged, const T* __restrict__ uV,
+                                             T* __restrict__ uL) {
   using S = Shape<D, K>;
   using W = ProjWCfg<D, K, T>;
   constexpr int NL = S::nloc, NF = S::nf, NB = S::nb, NINT = S::nint, GEO = S::gt;
   constexpr int NLP = W::NLP, NLQ = W::NLQ, EW = W::EW, DD = W::DD, NC = (D + 1) * EW;
   constexpr int NIT = (NL * EW + 31) / 32;
+  constexpr bool REF = !PT && sizeof(T) == 4;
+  using R = ProjRCfg<D, K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_trigger();
-  const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
-  const T* geoT = static_cast<const T*>(m.geoT);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* sX = reinterpret_cast<T*>(smem_raw + ProjCfg<D, K, T>::TABS) + warp * W::PER_WARP;  // X [NL][EW], Y [EW][NLQ]
-  T* sP = sX + W::XW;                                                                   // [EW][D*D]
+  const T* Tb = tab;
+  const float4* sCsr = csr;
+  T* sX;
+  T* sY;
+  T* sP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if constexpr (REF) {
+    // [csr (csr_n float4)][Dinv^T if staged][per-warp X | Y | P]
+    float4* c4 = reinterpret_cast<float4*>(smem_raw);
+    for (int t = threadIdx.x; t < csr_n; t += blockDim.x) c4[t] = csr[t];
+    sCsr = c4;
+    size_t off = size_t(csr_n) * 16;
+    if (tab_staged) {
+      T* sT = reinterpret_cast<T*>(smem_raw + off);
+      for (int t = threadIdx.x; t < NL * NLP; t += blockDim.x) sT[t] = tab[t];
+      Tb = sT;
+      off += (R::TAB + 15) / 16 * 16;
+    }
+    sX = reinterpret_cast<T*>(smem_raw + off) + warp * R::PER_WARP;
+    sY = sX + R::XS;
+    sP = sY + R::YS;
+  } else {
+    Tb = proj_setup<D, K, T>(smem_raw, tab);
+    sX = reinterpret_cast<T*>(smem_raw + ProjCfg<D, K, T>::TABS) + warp * W::PER_WARP;  // X [NL][EW], Y [EW][NLQ]
+    sY = sX;
+    sP = sX + W::XW;                                                                   // [EW][D*D]
+  }
+  const double* geoT = m.geoT;
   pdl_wait();
   __syncthreads();
+  // tiles interleaved over the CTAs (tile = warp * gridDim.x + block), so that every SM of
+  // the persistent grid gets the same number of tiles
   const int64_t ngroups = (m.E + EW - 1) / EW;
-  for (int64_t grp = (int64_t)blockIdx.x * W::WARPS + warp; grp < ngroups; grp += (int64_t)gridDim.x * W::WARPS) {
+  for (int64_t grp = (int64_t)warp * gridDim.x + blockIdx.x; grp < ngroups; grp += (int64_t)gridDim.x * nwarps) {
     const int64_t e0 = grp * EW;
     const int ne = (m.E - e0 < EW) ? (int)(m.E - e0) : EW;
     const int code = (lane < NC && lane / (D + 1) < ne) ? m.efc[e0 * (D + 1) + lane] : 0;
     for (int t = lane; t < EW * DD; t += 32) {  // Pf = J / det J   (PT: Pi^T, Pi = det J Jinv)
       const int k = t / DD, r = t - k * DD, a = r / D, b = r - a * D;
-      sP[t] = (k < ne) ? geoT[(e0 + k) * GEO + (PT ? DD + b * D + a : a * D + b)] : T(0);
+      sP[t] = (k < ne) ? T(geoT[(e0 + k) * GEO + (PT ? DD + b * D + a : a * D + b)]) : T(0);
     }
 #pragma unroll 5
     for (int it = 0; it < NIT; ++it) {
@@ -259,13 +408,22 @@ __global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_v2l(DevMesh m
       if (t < NL * EW) sX[t] = v;  // t = s2 * EW + k
     }
     __syncwarp();
-    warp_tile_gemm<D, K, T>(Tb, sX, lane);
+    if constexpr (REF) {
+      const float* Tf = reinterpret_cast<const float*>(Tb);
+      float* fX = reinterpret_cast<float*>(sX);
+      float* fY = reinterpret_cast<float*>(sY);
+      warp_tile_gemm_to<D, K, false>(Tf, fX, fY, lane);  // Y = Dinv X
+      warp_tile_residual<D, K>(sCsr, fX, fY, lane);       // X <- X - D Y (compensated)
+      warp_tile_gemm_to<D, K, true>(Tf, fX, fY, lane);   // Y += Dinv X
+    } else {
+      warp_tile_gemm<D, K, T>(Tb, sX, lane);
+    }
     for (int t = lane; t < ne * NL; t += 32) {
       const int k = t / NL, idx = t - k * NL;
       const int a = idx / NB, i = idx - a * NB;
       T acc1 = T(0);
 #pragma unroll
-      for (int b = 0; b < D; ++b) acc1 = fma(sP[k * DD + a * D + b], sX[k * NLQ + b * NB + i], acc1);
+      for (int b = 0; b < D; ++b) acc1 = fma(sP[k * DD + a * D + b], sY[k * NLQ + b * NB + i], acc1);
       uL[e0 * NL + t] = acc1;
     }
     __syncwarp();
@@ -288,20 +446,20 @@ __global__ void __launch_bounds__(32 * ProjWCfg<D, K, T>::WARPS) k_l2v_elem(DevM
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_trigger();
   const T* Tb = proj_setup<D, K, T>(smem_raw, tab);
-  const T* geoT = static_cast<const T*>(m.geoT);
+  const double* geoT = m.geoT;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* sX = reinterpret_cast<T*>(smem_raw + ProjCfg<D, K, T>::TABS) + warp * W::PER_WARP;  // X [NL][EW], Y [EW][NLQ]
   T* sP = sX + W::XW;                                                                   // [EW][D*D]
   pdl_wait();
   __syncthreads();
-  const int64_t ngroups = (m.E + EW - 1) / EW;
-  for (int64_t grp = (int64_t)blockIdx.x * W::WARPS + warp; grp < ngroups; grp += (int64_t)gridDim.x * W::WARPS) {
+  const int64_t ngroups = (m.E + EW - 1) / EW;  // tiles interleaved over the CTAs (see k_v2l)
+  for (int64_t grp = (int64_t)warp * gridDim.x + blockIdx.x; grp < ngroups; grp += (int64_t)gridDim.x * W::WARPS) {
     const int64_t e0 = grp * EW;
     const int ne = (m.E - e0 < EW) ? (int)(m.E - e0) : EW;
     const int code = (lane < NC && lane / (D + 1) < ne) ? m.efc[e0 * (D + 1) + lane] : 0;
     for (int t = lane; t < EW * DD; t += 32) {  // F[b][a]: Pi[b][a] = (det J Jinv)[b][a], or Pf^T[b][a]
       const int k = t / DD, r = t - k * DD, b = r / D, a = r - b * D;
-      sP[t] = (k < ne) ? geoT[(e0 + k) * GEO + (DUAL ? a * D + b : DD + b * D + a)] : T(0);
+      sP[t] = (k < ne) ? T(geoT[(e0 + k) * GEO + (DUAL ? a * D + b : DD + b * D + a)]) : T(0);
     }
     __syncwarp();
     for (int t = lane; t < NL * EW; t += 32) {  // X[s][k] = sum_a F_k[b][a] y_k[a][i],  s = b NB + i
@@ -492,6 +650,22 @@ __device__ __forceinline__ T dot_ss(const T* p, const T* q) {
   return acc;
 }
 
+// sum_i p[i] q[i] as the compensated pair s + c (Dot2, both rows 16-byte aligned)
+template <int N>
+__device__ __forceinline__ void dot2_ss(const float* p, const float* q, float& s, float& c) {
+  s = 0.0f;
+  c = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; i += 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p + i);
+    const float4 b = *reinterpret_cast<const float4*>(q + i);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+      if (i + w < N) dot2_step(s, c, av[w], bv[w]);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void lds4(const T* p, T* o) {  // 4 consecutive values, 16-byte aligned
   Pack<T>::unpack(*reinterpret_cast<const typename Pack<T>::V*>(p), o);
@@ -585,11 +759,26 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       const int mm = v / D, a = v - mm * D;
       const T* ra = TrM + (fa * NF + mm) * NBP;
       const T* rb = TrM + (fb * NF + mm) * NBP;
-      const T ta = dot_ss<NB>(ra, cA + a * NBP);
-      const T tbv = ext ? ext[mm * D + a] : dot_ss<NB>(rb, cB + a * NBP);
+      T ta, tbv, jump;
+      if constexpr (sizeof(T) == 4) {
+        // FP32: both traces as compensated pairs, so that the jump of a smooth field (a
+        // small difference of O(|u|) traces whose plain FP32 sums carry errors of several
+        // ulps of the largest partial sum) is accurate to the rounding of its own size
+        float sa, ca, sb = 0.0f, cb = 0.0f;
+        dot2_ss<NB>(ra, cA + a * NBP, sa, ca);
+        if (ext) sb = ext[mm * D + a];
+        else dot2_ss<NB>(rb, cB + a * NBP, sb, cb);
+        ta = __fadd_rn(sa, ca);
+        tbv = __fadd_rn(sb, cb);
+        jump = __fadd_rn(__fsub_rn(sa, sb), __fsub_rn(ca, cb));
+      } else {
+        ta = dot_ss<NB>(ra, cA + a * NBP);
+        tbv = ext ? ext[mm * D + a] : dot_ss<NB>(rb, cB + a * NBP);
+        jump = ta - tbv;
+      }
       const T wa = WSEP ? dot_ss<NB>(ra, wA + a * NBP) : ta;
       const T wb = ext ? wa : (WSEP ? dot_ss<NB>(rb, wB + a * NBP) : tbv);  // an inlet keeps the wind's own w.n
-      sJ[mm * 4 + a] = ta - tbv;
+      sJ[mm * 4 + a] = jump;
       sWv[mm * 4 + a] = T(0.5) * (wa + wb);
     }
     __syncwarp();
@@ -729,7 +918,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
   static_assert(!FUSE || (STAB && FuseCfg<D, K, T>::OK), "fused back-projection needs staged tables");
   // per-warp layout: two staging buffers (u record, w record, facet moments, geometry),
   // then the working arrays
-  constexpr int STU = r4i(NL), STG = r4i(NG), STGEO = r4i(GEO);
+  constexpr int STU = r4i(NL), STG = r4i(NG), STGEO = r4i(GEO * 8 / (int)sizeof(T));  // FP64 record
   constexpr int STAGE = STU + (WSEP ? STU : 0) + STG + STGEO;
   constexpr int PER_WARP = 2 * STAGE + D * NBP + D * D * NB1P + (WSEP ? D * NBP + NB1P : 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -775,7 +964,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     warp_copy_async<NL * (int)sizeof(T)>(st_u(b), uL + e * NL, lane);
     if (WSEP) warp_copy_async<NL * (int)sizeof(T)>(st_w(b), wL + e * NL, lane);
     warp_copy_async<NG * (int)sizeof(T)>(st_g(b), gam + e * NG, lane);
-    warp_copy_async<GEO * (int)sizeof(T)>(st_geo(b), static_cast<const T*>(m.geoT) + e * GEO, lane);
+    warp_copy_async<GEO * 8>(st_geo(b), m.geoT + e * GEO, lane);
   };
   // facet lift of this lane's outputs: acc[j] += sum_fm TrM[fm][i] gl[fm][a]; with two
   // outputs per lane of one component and consecutive basis indices (NB even) every
@@ -818,14 +1007,14 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
     cp_commit();
     cp_wait<1>();                                    // this element's copies are done
     __syncwarp();
-    const T* g = st_geo(b);                          // Pf, Pi, M = |det J| Jinv, 1/|det J|
+    const double* g = reinterpret_cast<const double*>(st_geo(b));  // Pf, Pi, M = |det J| Jinv, 1/|det J|
     const T* gl = st_g(b);                           // signed facet moments of the element
     T M[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int c = 0; c < D; ++c) M[a][c] = g[2 * D * D + a * D + c];
-    const T invabs = g[3 * D * D];
+      for (int c = 0; c < D; ++c) M[a][c] = T(g[2 * D * D + a * D + c]);
+    const T invabs = T(g[3 * D * D]);
     // u coefficients [D][NBP]: the staged record itself when its rows need no padding
     T* sC = (NBP == NB) ? st_u(b) : sCpad;
     for (int s2 = lane; s2 < NL; s2 += 32) {
@@ -1000,7 +1189,7 @@ __global__ void __launch_bounds__(32 * kWarps, sizeof(T) == 4 ? 3 : 2) k_volume(
         const int bb = idx / NB, i = idx - bb * NB;
         T c2 = T(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) c2 = fma(g[D * D + bb * D + a], sY[a * NBP + i], c2);
+        for (int a = 0; a < D; ++a) c2 = fma(T(g[D * D + bb * D + a]), sY[a * NBP + i], c2);
         sCh[idx] = c2;
       }
       if (lane < r4i(NL) - NL) sCh[NL + lane] = T(0);

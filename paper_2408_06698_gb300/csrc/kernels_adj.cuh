@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet_adj(DevMesh m, DevTabs tb
   const T* TrM = sbase;
   const T* Psi = sbase + TRM;
   const T* WPsi = sbase + TRM + PSI;
-  const T* geoT = static_cast<const T*>(m.geoT);
+  const double* geoT = m.geoT;
   pdl_wait();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet_adj(DevMesh m, DevTabs tb
     const T aF = T(fg[D]);
     const int l = facet_l ? int(facet_l[F]) : lconst;
     const int nl = (l < 0) ? 0 : cnbasis(D - 1, l);
-    const T iA = geoT[eA * GT + 3 * D * D], iB = geoT[eB * GT + 3 * D * D];  // 1/|det J|
+    const T iA = T(geoT[eA * GT + 3 * D * D]), iB = T(geoT[eB * GT + 3 * D * D]);  // 1/|det J|
     for (int s2 = lane; s2 < NL; s2 += 32) {
       const int a = s2 / NB, i = s2 - a * NB;
       cuA[a * NBP + i] = uL[eA * NL + s2];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_volume_adj(DevMesh m, DevTabs t
   const T* Wq = static_cast<const T*>(tb.Wq);
   const T* Dm = static_cast<const T*>(tb.Dm);
   const T* TrM = static_cast<const T*>(tb.TrM);
-  const T* geoT = static_cast<const T*>(m.geoT);
+  const double* geoT = m.geoT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_trigger();
   pdl_wait();
@@ -220,13 +220,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_volume_adj(DevMesh m, DevTabs t
   T* sGU = sW + (WSEP ? D * NBP : 0);                       // [NG] facet moments for ubar
   T* sGW = sGU + r4i(NG);                                   // [NG] facet moments for wbar
   for (int64_t e = (int64_t)blockIdx.x * kWarps + warp; e < m.E; e += (int64_t)gridDim.x * kWarps) {
-    const T* g = geoT + e * GT;
+    const double* g = geoT + e * GT;
     T M[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int c = 0; c < D; ++c) M[a][c] = g[2 * D * D + a * D + c];
-    const T invabs = g[3 * D * D];
+      for (int c = 0; c < D; ++c) M[a][c] = T(g[2 * D * D + a * D + c]);
+    const T invabs = T(g[3 * D * D]);
     for (int s2 = lane; s2 < NL; s2 += 32) {
       const int a = s2 / NB, i = s2 - a * NB;
       sC[a * NBP + i] = uL[e * NL + s2];

@@ -31,7 +31,8 @@ struct V2lTc {
 };
 
 // Error word bit set by tensor-core kernels when a completion wait gave up.
-constexpr int kErrTcTimeout = 1;
+constexpr int kErrTcTimeoutV2l = 1;  // bits of the device error word (DevMesh::err)
+constexpr int kErrTcTimeoutVol = 2;
 
 template <int D, int K, bool THREE>
 __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restrict__ dinv, int nlp,
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sCode + TM * (D + 1));
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float* geoT = static_cast<const float*>(m.geoT);
+  const double* geoT = m.geoT;
   pdl_trigger();
 
   // B operand (once per CTA) and the zero padding columns of A
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
       }
       tc::commit(mbar);
     }
-    ok = __syncthreads_and(tc::mbar_wait(mbar, phase)) != 0;
+    ok = __syncthreads_and(tc::mbar_wait(mbar, phase, m.tc_wait_limit)) != 0;
     phase ^= 1u;
     tc::fence_after_sync();
     if (!ok) break;
@@ -162,12 +163,12 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
       float* stage = reinterpret_cast<float*>(sAh);  // [TM][SST]; the MMAs reading A are done
       const int64_t e = e0 + row;
       if (e < m.E) {
-        const float* gp = geoT + e * GT;  // Pf = J / det J
+        const double* gp = geoT + e * GT;  // Pf = J / det J
         float P[D][D];
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-          for (int b = 0; b < D; ++b) P[a][b] = __ldg(gp + a * D + b);
+          for (int b = 0; b < D; ++b) P[a][b] = float(__ldg(gp + a * D + b));
         constexpr int HALF = (NL + 1) / 2;
         const int lo = (warp >> 2) * HALF, hi = lo + HALF < NL ? lo + HALF : NL;
 #pragma unroll
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(256) k_v2l_tc(DevMesh m, const float* __restri
     __syncthreads();
   }
   if (!ok) {
-    if (tid == 0) atomicOr(m.err, kErrTcTimeout);
-    tc::mbar_wait(mbar, phase ^ 1u);  // bounded: let the MMAs in flight drain before freeing TMEM
+    if (tid == 0) atomicOr(m.err, kErrTcTimeoutV2l);
+    tc::mbar_wait(mbar, phase ^ 1u);  // bounded (full limit): the MMAs in flight drain before TMEM is freed
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
   float* sY = reinterpret_cast<float*>(sXh);                   // [EB][NL] (epilogue, X is free)
   float* sCh = reinterpret_cast<float*>(sFl);                  // [EB][NL] (epilogue, F is free)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float* geoT = static_cast<const float*>(m.geoT);
+  const double* geoT = m.geoT;
   pdl_trigger();
 
   if (warp == 0) tc::tmem_alloc(tslot, C::TCOLS);
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
     const int64_t e0 = sc * EB;
     for (int t = tid; t < EB * GT; t += NT) {
       const int64_t e = e0 + t / GT;
-      sGeo[t] = e < m.E ? geoT[e0 * GT + t] : 0.0f;
+      sGeo[t] = e < m.E ? float(geoT[e0 * GT + t]) : 0.0f;
     }
 #pragma unroll 1
     for (int c = 0; c < C::NCH && ok; ++c) {
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
         }
         tc::commit(mb_mma);
       }
-      ok = __syncthreads_and(tc::mbar_wait(mb_mma, phase)) != 0;
+      ok = __syncthreads_and(tc::mbar_wait(mb_mma, phase, m.tc_wait_limit)) != 0;
       phase ^= 1u;
       tc::fence_after_sync();
       if (!ok) break;
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
       }
       tc::commit(mb_mma);
     }
-    ok = __syncthreads_and(tc::mbar_wait(mb_mma, phase)) != 0;
+    ok = __syncthreads_and(tc::mbar_wait(mb_mma, phase, m.tc_wait_limit)) != 0;
     phase ^= 1u;
     tc::fence_after_sync();
     if (!ok) break;
@@ -491,8 +492,8 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
     __syncthreads();
   }
   if (!ok) {
-    if (tid == 0) atomicOr(m.err, kErrTcTimeout);
-    tc::mbar_wait(mb_tab, 0);          // bounded: the table copy and the MMAs in flight drain
+    if (tid == 0) atomicOr(m.err, kErrTcTimeoutVol);
+    tc::mbar_wait(mb_tab, 0);          // bounded (full limit): the table copy and the MMAs in flight drain
     tc::mbar_wait(mb_mma, phase ^ 1u);
   }
   tc::fence_before_sync();

@@ -33,8 +33,9 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of g_noalloc_scratch per device.  In host code the symbol is only a
-// host-side stand-in, so the address is looked up with cudaGetSymbolAddress, once per
-// device, with that device current.
+// host-side stand-in, so the address is looked up with cudaGetSymbolAddress with that
+// device current: on every call made outside a stream capture, and the last address found
+// is reused by calls made while the stream is being captured.
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mutex;
 
@@ -74,17 +75,25 @@ extern "C" hopu_status hopu_apply_convection_noalloc(hopu_ctx* c, const void* w_
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(c, HOPU_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(c, HOPU_ENOTSUP, "apply_convection_noalloc: device index too large");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(c->stream, &cs);
+  if (e != cudaSuccess)
+    return noalloc_fail(c, HOPU_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-      // first call on this device: resolve the device address of the static buffer
-      // (this call must come before any stream capture that uses the entry point)
+    if (cs == cudaStreamCaptureStatusNone) {
+      // outside a capture the device address of the static buffer is looked up on every
+      // call (cheap), so a device reset or a new primary context never leaves a stale one
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess)
         return noalloc_fail(c, HOPU_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+      // inside a capture the address of an earlier call on this device is reused
+      return noalloc_fail(c, HOPU_EINVAL,
+                          "apply_convection_noalloc: the first call on a device must come before any stream capture");
     }
     base = g_scratch_ptr[dev];
   }
@@ -92,9 +101,10 @@ extern "C" hopu_status hopu_apply_convection_noalloc(hopu_ctx* c, const void* w_
   void* gam = static_cast<unsigned char*>(base) + wl_bytes;
 
   hopu::Combine plain;
-  c->ops->v2l(c->dm, c->dt, w_hdiv, wl, c->stream);
-  c->ops->facet(c->dm, c->dt, u_l2, wl, c->l, facet_l ? facet_l : c->facet_l, gam, nullptr, c->stream);
-  c->ops->volume(c->dm, c->dt, u_l2, wl, gam, plain, y_l2, c->stream);
+  const int8_t* fl = facet_l ? facet_l : c->facet_l;
+  hopu::timed(c, HOPU_K_V2L, [&] { c->ops->v2l(c->dm, c->dt, w_hdiv, wl, c->stream); });
+  hopu::timed(c, HOPU_K_FACET, [&] { c->ops->facet(c->dm, c->dt, u_l2, wl, c->l, fl, gam, nullptr, c->stream); });
+  hopu::timed(c, HOPU_K_VOLUME, [&] { c->ops->volume(c->dm, c->dt, u_l2, wl, gam, plain, y_l2, c->stream); });
   e = cudaGetLastError();
   if (e != cudaSuccess)
     return noalloc_fail(c, HOPU_ECUDA, std::string("apply_convection_noalloc kernels: ") + cudaGetErrorString(e));

@@ -19,6 +19,10 @@ class OpsImpl final : public Ops {
   static constexpr size_t r4(size_t n) { return ((n + 3) / 4) * 4; }
 
   using PW = ProjWCfg<D, K, T>;  // warp tiles of the projections
+  // V_h -> L2 in FP32: the refined projection (its launch shape is set by configure())
+  static constexpr bool kRef = std::is_same<T, float>::value;
+  int ref_warps_ = 8, ref_staged_ = 0, csr_n_ = 0;
+  size_t ref_smem_ = 0;
 
   // facet kernel: padded modal trace matrices, Psi, WPsi, Wf; per warp: coefficient
   // blocks, two [nqf][4] point buffers, modal jump / wind, moments (layout of k_facet)
@@ -36,7 +40,7 @@ class OpsImpl final : public Ops {
   static constexpr size_t kVolTab =  // Dm rows padded, Dm and TrM 16-byte aligned (layout of k_volume)
       r4(r4(r4(size_t(S::nq) * kNBQ + S::nq) + size_t(D) * kNB1 * r4(S::nb)) + size_t(D + 1) * S::nf * S::nb) * sz;
   static constexpr size_t volume_stage(bool wsep) {
-    return r4(S::nloc) * (wsep ? 2 : 1) + r4(size_t(D + 1) * S::nf * D) + r4(S::gt);
+    return r4(S::nloc) * (wsep ? 2 : 1) + r4(size_t(D + 1) * S::nf * D) + r4(S::gt * 8 / sz);  // FP64 geometry
   }
   static constexpr size_t volume_warp(bool wsep) {
     return (2 * volume_stage(wsep) + size_t(D) * r4(S::nb) + size_t(D) * D * r4(kNB1) +
@@ -71,7 +75,7 @@ class OpsImpl final : public Ops {
   static constexpr bool kTcVol = std::is_same<T, float>::value && VolTc<D, K>::OK;
   int g_vol_tc_ = 1;
   bool use_tc_v2l_ = true, use_tc_vol_ = true;  // autotuner choices (tensor-core modes)
-  int g_v2l_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
+  int g_v2l_ = 1, g_v2lpt_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
 
   template <typename Kern>
   cudaError_t setup(Kern kern, size_t smem, int threads, int* grid, bool max_carveout = false) {
@@ -128,7 +132,10 @@ class OpsImpl final : public Ops {
 
  public:
   explicit OpsImpl(int tc = 0) : tc_(std::is_same<T, float>::value ? tc : 0) {}
-  bool tensor_cores() const override { return tc_ != 0 && kTcV2l; }
+  // The V_h -> L2 change of basis runs on the tensor cores only in TF32 mode: its FP32
+  // accumulation (also in 3xTF32) loses the small high-degree coefficients of smooth
+  // fields, which the compensated FMA product keeps (FP32 and 3xTF32 modes).
+  bool tensor_cores() const override { return tc_ == 1 && kTcV2l; }
   bool tensor_core_volume() const override { return tc_ != 0 && kTcVol; }
   void select(int v2l_tc, int volume_tc) override {
     use_tc_v2l_ = v2l_tc != 0 && tensor_cores();
@@ -144,17 +151,18 @@ class OpsImpl final : public Ops {
     err = cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
     const int th = 32 * kWarps;
-    if ((err = setup(k_v2l<D, K, T, false>, PW::SMEM, 32 * PW::WARPS, &g_v2l_)) != cudaSuccess) return err;
-    if ((err = setup(k_v2l<D, K, T, true>, PW::SMEM, 32 * PW::WARPS, &g_v2l_)) != cudaSuccess) return err;
+    if constexpr (!kRef) {
+      if ((err = setup(k_v2l<D, K, T, false>, PW::SMEM, 32 * PW::WARPS, &g_v2l_)) != cudaSuccess) return err;
+    }
+    if ((err = setup(k_v2l<D, K, T, true>, PW::SMEM, 32 * PW::WARPS, &g_v2lpt_)) != cudaSuccess) return err;
     if constexpr (kTcVol) {
       if (tc_ && (err = setup(k_volume_tc<D, K>, VolTc<D, K>::SMEM, VolTc<D, K>::THREADS, &g_vol_tc_, true)) !=
                      cudaSuccess)
         return err;
     }
     if constexpr (kTcV2l) {
-      if (tc_) {
-        if (tc_ == 3) err = setup(k_v2l_tc<D, K, true>, V2lTc<D, K>::SMEM, V2lTc<D, K>::THREADS, &g_v2l_tc_, true);
-        else err = setup(k_v2l_tc<D, K, false>, V2lTc<D, K>::SMEM, V2lTc<D, K>::THREADS, &g_v2l_tc_, true);
+      if (tc_ == 1) {
+        err = setup(k_v2l_tc<D, K, false>, V2lTc<D, K>::SMEM, V2lTc<D, K>::THREADS, &g_v2l_tc_, true);
         if (err != cudaSuccess) return err;
       }
     }
@@ -176,23 +184,42 @@ class OpsImpl final : public Ops {
     return cudaSuccess;
   }
 
+  // The refined FP32 projection stages the sparse rows of D and, when they fit, Dinv^T per
+  // CTA; as many warps per CTA as fit in ~220 KB (16, 12, 8 or 4).
+  cudaError_t configure(const DevTabs& t) override {
+    if constexpr (kRef) {
+      using R = ProjRCfg<D, K>;
+      csr_n_ = t.csr_n;
+      const size_t csr = size_t(csr_n_) * 16, tab = (R::TAB + 15) / 16 * 16;
+      ref_staged_ = csr + tab + 8 * R::TILE <= 220 * 1024;
+      const size_t fixed = csr + (ref_staged_ ? tab : 0);
+      ref_warps_ = R::fit_warps(fixed);
+      ref_smem_ = fixed + size_t(ref_warps_) * R::TILE;
+      return setup(k_v2l<D, K, T, false>, ref_smem_, 32 * ref_warps_, &g_v2l_);
+    }
+    return cudaSuccess;
+  }
+
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
     if constexpr (kTcV2l) {
-      if (tc_ && use_tc_v2l_) {
+      if (tensor_cores() && use_tc_v2l_) {
         const int g = clamp_grid(g_v2l_tc_, m.E, V2lTc<D, K>::TM);
         const int nlp = (S::nloc + 3) / 4 * 4;
-        if (tc_ == 3)
-          launch(k_v2l_tc<D, K, true>, g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st, m, static_cast<const float*>(t.Dinv), nlp,
-                                                                  static_cast<const float*>(uV), static_cast<float*>(uL));
-        else
-          launch(k_v2l_tc<D, K, false>, g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st, m, static_cast<const float*>(t.Dinv), nlp,
-                                                                   static_cast<const float*>(uV), static_cast<float*>(uL));
+        launch(k_v2l_tc<D, K, false>, g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st, m,
+               static_cast<const float*>(t.Dinv), nlp, static_cast<const float*>(uV), static_cast<float*>(uL));
         return 1;
       }
     }
-    const int g = clamp_grid(g_v2l_, (m.E + PW::EW - 1) / PW::EW, PW::WARPS);
-    launch(k_v2l<D, K, T, false>, g, 32 * PW::WARPS, PW::SMEM, st, 
-        m, static_cast<const T*>(t.DinvT), static_cast<const T*>(uV), static_cast<T*>(uL));
+    if constexpr (kRef) {
+      const int g = clamp_grid(g_v2l_, (m.E + PW::EW - 1) / PW::EW, 1);
+      launch(k_v2l<D, K, T, false>, g, 32 * ref_warps_, ref_smem_, st, m, static_cast<const T*>(t.DinvT),
+             static_cast<const float4*>(t.Dcsr), csr_n_, ref_staged_, static_cast<const T*>(uV),
+             static_cast<T*>(uL));
+    } else {
+      const int g = clamp_grid(g_v2l_, (m.E + PW::EW - 1) / PW::EW, 1);
+      launch(k_v2l<D, K, T, false>, g, 32 * PW::WARPS, PW::SMEM, st, m, static_cast<const T*>(t.DinvT),
+             static_cast<const float4*>(nullptr), 0, 0, static_cast<const T*>(uV), static_cast<T*>(uL));
+    }
     return 1;
   }
 
@@ -234,9 +261,9 @@ class OpsImpl final : public Ops {
   }
 
   int v2l_pt(const DevMesh& m, const DevTabs& t, const void* vV, void* yL, cudaStream_t st) override {
-    const int g = clamp_grid(g_v2l_, (m.E + PW::EW - 1) / PW::EW, PW::WARPS);
-    launch(k_v2l<D, K, T, true>, g, 32 * PW::WARPS, PW::SMEM, st, 
-        m, static_cast<const T*>(t.Dn), static_cast<const T*>(vV), static_cast<T*>(yL));
+    const int g = clamp_grid(g_v2lpt_, (m.E + PW::EW - 1) / PW::EW, 1);
+    launch(k_v2l<D, K, T, true>, g, 32 * PW::WARPS, PW::SMEM, st, m, static_cast<const T*>(t.Dn),
+           static_cast<const float4*>(nullptr), 0, 0, static_cast<const T*>(vV), static_cast<T*>(yL));
     return 1;
   }
 
@@ -296,7 +323,7 @@ class OpsImpl final : public Ops {
 
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,
                void* outV, cudaStream_t st) override {
-    const int g = clamp_grid(g_elem_[dual ? 1 : 0], (m.E + PW::EW - 1) / PW::EW, PW::WARPS);
+    const int g = clamp_grid(g_elem_[dual ? 1 : 0], (m.E + PW::EW - 1) / PW::EW, 1);
     if (dual)
       launch(k_l2v_elem<D, K, T, true>, g, 32 * PW::WARPS, PW::SMEM, st, 
           m, static_cast<const T*>(t.Dinv), static_cast<const T*>(yL), static_cast<T*>(lf), static_cast<T*>(outV), c);

@@ -204,6 +204,14 @@ class Hopu:
         """Synchronise the context stream; raises on a device-side failure (ETIMEOUT)."""
         self._check(self.lib.hopu_sync(self.ctx), "hopu_sync")
 
+    def set_wait_limit(self, polls: int | None):
+        """Polls of the tensor-core MMA completion waits (None: the default, 2^22)."""
+        self._check(self.lib.hopu_set_wait_limit(self.ctx, -1 if polls is None else int(polls)),
+                    "hopu_set_wait_limit")
+
+    def clear_error(self):
+        self.lib.hopu_clear_error(self.ctx)
+
     def set_frozen_wind(self, w_hdiv: torch.Tensor):
         self._sync_stream()
         self._check(self.lib.hopu_set_frozen_wind(self.ctx, self._vec(w_hdiv, self.n_hdiv, "w_hdiv")),
