@@ -1,15 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the HOPU convection hot path on one GB300 (or N independent replicas).
 
-Workload: 3D periodic box [0, 2pi]^3, 16^3 cubes x 6 tetrahedra (24,576 elements),
-order k = 3, HOPU projection order l = k-1, Taylor-Green velocity interpolated into the
-normal-continuous velocity space plus U[-1e-3, 1e-3] noise (seed 0), dt = 5e-4.
+Headline workload (the precision configuration, the largest single-GPU mesh the metric
+is quoted on): 3D periodic box [0, 2pi]^3, 32^3 cubes x 6 tetrahedra (196,608 elements),
+order k = 4, HOPU projection order l = k-1 = 3, Taylor-Green velocity interpolated into
+the normal-continuous velocity space plus U[-1e-3, 1e-3] noise (seed 0), dt = 5e-4, FP32.
 
 One step = one explicit SSP-RK3 substep in STAGE wind mode (per stage: V_h -> L2
 projection, facet flux, volume term + lift + inverse mass, L2 -> V_h back-projection
 with the stage combination) including the FP64 kinetic-energy reduction of the state
 (logged on the device).  The metric counts DOF-updates of the convection apply: L2 DOFs x
-3 applies per substep.
+3 applies per substep.  The stated error is that of the FP32 apply against the FP64
+oracle (sampled elements) and against the FP64 GPU path (every output).
+
+Also reported: FP64 and the tensor-core precision modes on the same workload, the
+16^3 x 6, k = 3 box, the 2D k = 2 square, the 512-mesh batch and the rollout adjoint.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 (torchrun for N > 1: every rank runs the same workload on its own GPU, weak scaling,
@@ -33,9 +38,10 @@ if ROOT not in sys.path:
 
 METRIC = "DOF-updates/s of HOPU convection apply, FP32 vs FP64 at stated error; % HBM peak"
 UNIT = "DOF-updates/s"
-WORKLOAD = dict(dim=3, n=16, k=3, l=2, dt=5e-4, noise=1e-3, seed=0)
-WORKLOAD_NAME = ("3D periodic box [0,2pi]^3, 16^3 cubes x 6 tets (24,576 elements), k=3, HOPU l=2, "
+WORKLOAD = dict(dim=3, n=32, k=4, l=3, dt=5e-4, noise=1e-3, seed=0)
+WORKLOAD_NAME = ("3D periodic box [0,2pi]^3, 32^3 cubes x 6 tets (196,608 elements), k=4, HOPU l=3, "
                  "Taylor-Green + 1e-3 seeded noise, SSP-RK3 STAGE substeps dt=5e-4")
+BOX16 = dict(dim=3, n=16, k=3, l=2, dt=5e-4, noise=1e-3, seed=0)
 APPLIES_PER_STEP = 3
 L2_FLUSH_BYTES = 256 << 20
 FAMILIES = ["v2l", "facet", "volume", "l2v_elem", "l2v_facet"]        # the forward substep
@@ -145,42 +151,25 @@ class Clocks:
                 "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ oracle worker (CPU)
+# ------------------------------------------------------------------ oracle (CPU)
 def oracle_worker(args):
     """Runs in a child process with one BLAS thread: the FP64 CPU oracle, as it stands."""
     import numpy as np
 
     import workloads as W
-    from oracle import fe, hdiv, mesh, rk
+    from oracle import fe, hdiv, mesh
     cfg = json.loads(args.oracle_worker)
-    dim, k, l, dt = WORKLOAD["dim"], WORKLOAD["k"], WORKLOAD["l"], WORKLOAD["dt"]
-    n = cfg["n"]
+    dim, n, k, l, dt = cfg["dim"], cfg["n"], cfg["k"], cfg["l"], cfg["dt"]
     m = W.periodic_box_mesh(dim, n)
     sp = hdiv.HDiv(mesh.MeshTopo(m.coords, m.elems, m.rep), fe.ref_element(dim, k))
-    u = sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, WORKLOAD["noise"], WORKLOAD["seed"])
+    u = sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, cfg["noise"], cfg["seed"])
     res = {"n": n, "n_l2": sp.n_l2, "elements": sp.topo.n_elems}
-    if cfg["mode"] == "vjp_sample":
-        from oracle import adjoint as A
-        t0 = time.perf_counter()
-        loss, _ = A.rollout_vjp(sp, u, dt, cfg["steps"], l)
-        res["seconds"] = time.perf_counter() - t0
-        res["steps"] = cfg["steps"]
-        res["loss"] = float(loss)
-    elif cfg["mode"] == "sample":
-        t0 = time.perf_counter()
-        u1 = rk.substeps_stage(sp, u, dt, 1, l)
-        res["seconds"] = time.perf_counter() - t0
-        res["steps"] = 1
-        np.save(cfg["out"], u1)
-    else:
-        for _ in range(cfg["warmup"]):
-            u = rk.substeps_stage(sp, u, dt, 1, l)
-        t0 = time.perf_counter()
-        for _ in range(cfg["steps"]):
-            u = rk.substeps_stage(sp, u, dt, 1, l)
-            sp.to_l2(u)
-        res["seconds"] = time.perf_counter() - t0
-        res["steps"] = cfg["steps"]
+    from oracle import adjoint as A
+    t0 = time.perf_counter()
+    loss, _ = A.rollout_vjp(sp, u, dt, cfg["steps"], l)
+    res["seconds"] = time.perf_counter() - t0
+    res["steps"] = cfg["steps"]
+    res["loss"] = float(loss)
     with open(cfg["out"] + ".json", "w") as f:
         json.dump(res, f)
 
@@ -196,6 +185,30 @@ def run_oracle(cfg: dict, timeout: float = 1800):
         raise RuntimeError("oracle worker failed:\n" + r.stdout[-2000:] + r.stderr[-4000:])
     with open(cfg["out"] + ".json") as f:
         return json.load(f)
+
+
+def oracle_pool(block, workers=None):
+    """The oracle on every host core (oracle.pool: spawned processes, one block of the
+    headline box each)."""
+    from oracle.pool import OraclePool
+    w = WORKLOAD
+    return OraclePool(w["n"], w["k"], w["l"], block=block, workers=workers, seed=w["seed"])
+
+
+def sampled_oracle_apply(uV, l, dim, n, k, n_sample=300, seed=5):
+    """The oracle's apply (w = u = E uV) on n_sample seeded elements of the n^dim box,
+    element by element (oracle.sampled); returns (sample ids, y[sample])."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import fe, hdiv, mesh
+    from oracle.sampled import sampled_apply
+    m = W.periodic_box_mesh(dim, n)
+    topo = mesh.MeshTopo(m.coords, m.elems, m.rep)
+    sp = hdiv.HDiv(topo, fe.ref_element(dim, k))
+    uL = sp.to_l2(uV)
+    sample = np.random.default_rng(seed).choice(topo.n_elems, n_sample, replace=False)
+    return sample, uL, sampled_apply(m.coords, m.elems, m.rep, topo, sp.ref, uL, uL, l, sample)
 
 
 # ------------------------------------------------------------------ ranks (control plane only)
@@ -223,30 +236,27 @@ def whole_job_value(units_per_rank: float, world: int, max_seconds: float) -> fl
 
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args, rank):
+    """The FP64 CPU oracle as it stands, on every host core, on the headline workload: each
+    step is one oracle apply of a bounded sample (blocks of --ref-block cubes of the
+    32^3 x 6 box, default 8 x 8 x 4, one block per core), counted in the headline's unit."""
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
     K, Wm = args.steps, args.warmup
-    # size the per-step sample so that the whole run stays within a few minutes:
-    # time one substep on the 3^3 x 6 box, scale by n^3
-    tmp = tempfile.mkdtemp()
-    probe = run_oracle({"mode": "loop", "n": 3, "steps": 1, "warmup": 0, "out": os.path.join(tmp, "p")})
-    t3 = probe["seconds"]
-    budget = args.ref_budget_s / max(1, K + Wm)
-    n = int(max(3, min(16, math.floor(3 * (budget / t3) ** (1.0 / 3.0)))))
-    res = run_oracle({"mode": "loop", "n": n, "steps": K, "warmup": Wm, "out": os.path.join(tmp, "r")},
-                     timeout=3600)
-    secs = res["seconds"]
-    value = res["n_l2"] * APPLIES_PER_STEP * K / secs
-    sample = (f"{n}^3 x 6 tets ({res['elements']} elements, {res['n_l2']} L2 DOFs), k=3, l=2: one "
-              f"SSP-RK3 STAGE substep + L2 image per step"
-              + ("" if n == WORKLOAD["n"] else " (same workload structure on a smaller box)"))
+    pool = oracle_pool(tuple(int(x) for x in args.ref_block.split(",")))
+    try:
+        for _ in range(Wm):
+            pool.step()
+        secs = sum(pool.step() for _ in range(K))
+    finally:
+        pool.close()
+    value = pool.dofs_per_step * K / secs
+    sample = pool.describe()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": K, "warmup": Wm, "ms_per_step": 1e3 * secs / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "sample": sample, "oracle": "numpy FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -294,9 +304,8 @@ def _events_ms(stream, fn, K):
 
 
 def other_configs(dev, stream, world):
-    """2D k=2 FP64 (8x8x2 triangles), the 32^3 x 6 k=4 precision comparison and the
-    512-mesh batch: throughput in the headline's unit plus the stated errors."""
-    import numpy as np
+    """2D k=2 FP64 (8x8x2 triangles) and the 512-mesh batch: throughput in the headline's
+    unit."""
     import torch
 
     import workloads as W
@@ -313,53 +322,6 @@ def other_configs(dev, stream, world):
     out["square_8x8x2_k2_f64"] = {"elements": g.n_elems, "substeps": 100, "ms_per_substep": ms / 100,
                                   "value": g.n_l2 * APPLIES_PER_STEP * 100 / (ms / 1e3), "unit": UNIT}
     del g
-    # 32^3 x 6, k = 4: one apply in every precision against the FP64 GPU result (itself at
-    # oracle parity on small meshes), 10 substeps each with the per-substep energy drift
-    m = W.periodic_box_mesh(3, 32)
-    prec_rows = {}
-    ref_y = None
-    u64 = None
-    g64 = None
-    for prec in ("f64", "f32", "f32_tc", "tf32"):
-        g = Hopu(m.coords, m.elems, m.rep, k=4, l=3, prec=prec, device=dev)
-        if u64 is None:                          # one interpolant, rounded per precision
-            u64 = g.interpolate_function(W.taylor_green)
-            u64 += torch.as_tensor(W.uniform_noise(g.n_hdiv, 1e-3, 0), device=dev)
-        u = u64.to(g.dtype).clone()
-        with torch.cuda.stream(stream):
-            uL = g.project("hdiv_to_l2", u)
-            yv = g.apply_convection(u, uL)
-        stream.synchronize()
-        yd = yv.double()
-        if prec == "f64":
-            ref_y = yd
-            g64 = g
-            err_same = 0.0
-        else:                                    # the FP64 path on the same (rounded) input
-            with torch.cuda.stream(stream):
-                ur = u.double()
-                y64r = g64.apply_convection(ur, g64.project("hdiv_to_l2", ur))
-            stream.synchronize()
-            err_same = float((yd - y64r).abs().max() / y64r.abs().max())
-            l2_same = float(torch.linalg.vector_norm(yd - y64r) / torch.linalg.vector_norm(y64r))
-        err = float((yd - ref_y).abs().max() / ref_y.abs().max())
-        if prec == "f64":
-            l2_same = 0.0
-        log = torch.zeros(12, dtype=torch.float64, device=dev)
-        g.set_energy_log(log)
-        ms = _events_ms(stream, lambda: g.rk_substep(u, 5e-4, 1), 10)
-        g.set_energy_log(None)
-        e = log[:10].cpu().numpy()
-        prec_rows[prec] = {"ms_per_substep": ms / 10, "value": g.n_l2 * APPLIES_PER_STEP * 10 / (ms / 1e3),
-                           "unit": UNIT, "apply_max_rel_err_vs_gpu_f64": err,
-                           "apply_max_rel_err_vs_gpu_f64_same_rounded_input": err_same,
-                           "apply_l2_rel_err_vs_gpu_f64_same_rounded_input": l2_same,
-                           "energy_drift_per_substep": float(np.mean(np.diff(e)) / e[0])}
-        if prec != "f64":
-            del g
-        del u, uL, yv
-    del g64
-    out["box_32cubed_k4_precisions"] = {"elements": 6 * 32 ** 3, "substeps": 10, "by_precision": prec_rows}
     # 512 meshes, n ~ U{4..12}, k ~ U{2..5} (seed 1), FP32, one graph replay per substep
     draws = W.batch_draws(512, seed=1)
     meshes = [W.periodic_box_mesh(3, n) for n, _ in draws]
@@ -396,27 +358,36 @@ def our_arm(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    dim, n, k, l, dt = (WORKLOAD[x] for x in ("dim", "n", "k", "l", "dt"))
-    m = W.periodic_box_mesh(dim, n)
+    meshes, states = {}, {}
 
-    def make(prec):
-        g = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec=prec, device=dev)
-        u0 = g.interpolate_function(W.taylor_green)
-        noise = torch.as_tensor(W.uniform_noise(g.n_hdiv, WORKLOAD["noise"], WORKLOAD["seed"]), device=dev)
-        u0 += noise.to(g.dtype)
-        return g, u0
+    def make(cfg, prec, tile_hint=0):
+        """A context on the configuration's mesh and its initial state: the Taylor-Green
+        interpolant plus the seeded noise, computed by the first context made on that mesh
+        and shared (rounded once to FP32) by every precision."""
+        key = (cfg["dim"], cfg["n"], cfg["k"])
+        if key not in meshes:
+            meshes[key] = W.periodic_box_mesh(cfg["dim"], cfg["n"])
+        m = meshes[key]
+        g = Hopu(m.coords, m.elems, m.rep, k=cfg["k"], l=cfg["l"], prec=prec, device=dev, tile_hint=tile_hint)
+        if key not in states:
+            u0 = g.interpolate_function(W.taylor_green)
+            noise = torch.as_tensor(W.uniform_noise(g.n_hdiv, cfg["noise"], cfg["seed"]), device=dev)
+            u0 += noise.to(g.dtype)
+            states[key] = u0.float().double()
+        return g, states[key].to(g.dtype).clone()
 
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def timed_steps(g, state, K, Wm, profile=False, clocks=None, e2e=False):
+    def timed_steps(g, state, K, Wm, dt, profile=False, clocks=None, e2e=False):
         """K substeps, each bracketed by CUDA events on the launching stream.
 
         One step = one SSP-RK3 substep (all rows of the hot path: projections, facet and
         volume kernels, inverse mass, stage combinations, back-projection) including the
         FP64 kinetic-energy reduction of the state, which the substep writes into a
         device-side log (no host round trip inside the step).  The L2 flush and the
-        profile read-out run between the events.
+        profile read-out run between the events.  e2e: the state is copied in from pinned
+        host memory and back out inside the events of every step.
         """
         host = torch.empty(g.n_hdiv, dtype=g.dtype, pin_memory=True) if e2e else None
         if e2e:
@@ -457,57 +428,136 @@ def our_arm(args, rank, world):
         energies = log[Wm:Wm + K].cpu().numpy().tolist()
         return dev_ms, wall, acc, ck, energies
 
+    def kernel_table(acc, alg=None):
+        out = {}
+        for f in FAMILIES:
+            n = max(1, acc[f][1])
+            avg = acc[f][0] / n
+            row = {"launches": acc[f][1], "avg_us": 1e3 * avg}
+            if alg is not None and acc[f][1]:
+                row["tflops"] = alg[f][0] / (avg / 1e3) / 1e12
+                row["gbs"] = alg[f][1] / (avg / 1e3) / 1e9
+            out[f] = row
+        return out
+
     K, Wm = args.steps, args.warmup
-    # ---------------- FP32 headline
-    g32, s32 = make("f32")
+    H = WORKLOAD
+    dt = H["dt"]
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
     clocks = Clocks(uuid)
-    # the headline runs without per-kernel events (they would split the substep graph's
-    # programmatic launch overlap and add their own cost); a second, profiled pass of the
-    # same workload gives the per-kernel times
-    dev_ms, wall, _, ck, energies = timed_steps(g32, s32, K, Wm, profile=False, clocks=clocks)
+
+    # ---------------- headline: FP32 on the 32^3 x 6, k = 4 box.  It runs without
+    # per-kernel events (they would split the substep graph's programmatic launch
+    # overlap); a second, profiled pass of the same workload gives the kernel times.
+    g32, s32 = make(H, "f32")
+    u_start = s32.clone()
+    dev_ms, wall, _, ck, energies = timed_steps(g32, s32, K, Wm, dt, clocks=clocks)
     tmax_ms = max_over_ranks(dev_ms, world)
     dofs = g32.n_l2 * APPLIES_PER_STEP
     value = whole_job_value(dofs * K, world, tmax_ms / 1e3)
-    g32p, s32p = make("f32")
-    Kp = min(K, 300)
-    prof_ms, _, acc, _, _ = timed_steps(g32p, s32p, Kp, Wm, profile=True)
-    del g32p, s32p
+    s32p = u_start.clone()
+    Kp = min(K, 30)
+    prof_ms, _, acc, _, _ = timed_steps(g32, s32p, Kp, 2, dt, profile=True)
+    del s32p
 
     # ---------------- e2e through host buffers (pinned), same metric
-    g32e, s32e = make("f32")
-    Ke = min(K, 200)
-    e_ms, _, _, _, _ = timed_steps(g32e, s32e, Ke, Wm, e2e=True)
+    s32e = u_start.clone()
+    Ke = min(K, 30)
+    e_ms, _, _, _, _ = timed_steps(g32, s32e, Ke, 2, dt, e2e=True)
     e_max = max_over_ranks(e_ms, world)
     e2e = {"value": whole_job_value(dofs * Ke, world, e_max / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": g32e.n_hdiv * 4, "d2h_bytes_per_step": g32e.n_hdiv * 4,
-           "steps": Ke, "note": "pinned host state copied in and out around every substep"}
-    del g32e, s32e
+           "h2d_bytes_per_step": g32.n_hdiv * 4, "d2h_bytes_per_step": g32.n_hdiv * 4,
+           "steps": Ke, "note": "pinned host state copied in and out around every substep, inside the events"}
+    del s32e
 
     # ---------------- FP64 path (same workload, fewer steps)
-    g64, s64 = make("f64")
-    K64 = min(K, 100)
-    d64, _, _, _, _ = timed_steps(g64, s64, K64, min(Wm, 3))
+    g64, s64 = make(H, "f64")
+    K64 = min(K, 10)
+    d64, _, _, _, _ = timed_steps(g64, s64.clone(), K64, 2, dt)
     d64 = max_over_ranks(d64, world)
-    _, _, acc64, _, _ = timed_steps(g64, s64, min(K64, 30), 1, profile=True)
+    _, _, acc64, _, _ = timed_steps(g64, s64.clone(), min(K64, 5), 1, dt, profile=True)
     fp64 = {"value": whole_job_value(dofs * K64, world, d64 / 1e3), "unit": UNIT, "steps": K64,
-            "ms_per_step": d64 / K64}
+            "ms_per_step": d64 / K64, "kernels": kernel_table(acc64)}
 
-    # ---------------- FP32 with the tensor-core (3xTF32) projection GEMM
-    gtc, stc = make("f32_tc")
-    Ktc = min(K, 500)
-    dtc, _, _, _, _ = timed_steps(gtc, stc, Ktc, Wm)
-    dtc = max_over_ranks(dtc, world)
-    _, _, acctc, _, _ = timed_steps(gtc, stc, min(Ktc, 100), 1, profile=True)
-    fp32_tc = {"value": whole_job_value(dofs * Ktc, world, dtc / 1e3), "unit": UNIT, "steps": Ktc,
-               "ms_per_step": dtc / Ktc, "autotuned_variants": gtc.tuning(),
-               "kernels": {f: {"avg_us": 1e3 * acctc[f][0] / max(1, acctc[f][1]), "launches": acctc[f][1]}
-                           for f in FAMILIES}}
-    del gtc, stc
+    # ---------------- the stated error of the headline: FP32 apply against the FP64 GPU
+    # path (every output, same rounded input) and against the oracle (sampled elements,
+    # rank 0), one FP32 substep against the FP64 one
+    uV32 = u_start.clone()
+    with torch.cuda.stream(stream):
+        uL32 = g32.project("hdiv_to_l2", uV32)
+        y32 = g32.apply_convection(uV32, uL32)
+        uV64 = uV32.double()
+        y64 = g64.apply_convection(uV64, g64.project("hdiv_to_l2", uV64))
+        x32, x64 = uV32.clone(), uV64.clone()
+        g32.rk_substep(x32, dt, 1)
+        g64.rk_substep(x64, dt, 1)
+    stream.synchronize()
+    d = y32.double() - y64
+    stated = {"apply_max_rel_vs_gpu_f64": float(d.abs().max() / y64.abs().max()),
+              "apply_l2_rel_vs_gpu_f64": float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(y64)),
+              "substep_state_max_rel_vs_gpu_f64": float((x32.double() - x64).abs().max() / x64.abs().max()),
+              "inputs": "the FP32 state, rounded once, given to both paths"}
+    if rank == 0 and not args.no_cpu_baseline:
+        sample, _, yref = sampled_oracle_apply(uV32.double().cpu().numpy(), H["l"], H["dim"], H["n"], H["k"])
+        nb = yref.shape[-1]
+        for prec, y in (("f32", y32), ("f64", y64)):
+            got = y.double().cpu().numpy().reshape(-1, H["dim"], nb)[sample]
+            stated[f"apply_max_rel_vs_oracle_{prec}"] = float(np.abs(got - yref).max() / np.abs(yref).max())
+        stated["oracle_sample"] = f"{len(sample)} seeded elements (oracle.sampled: their facet neighbourhood)"
+    worst = max(stated["apply_max_rel_vs_gpu_f64"], stated["apply_l2_rel_vs_gpu_f64"],
+                stated.get("apply_max_rel_vs_oracle_f32", 0.0))
+    stated["fp32_bound"] = 1e-6
+    stated["fp32_meets_bound"] = bool(worst <= 1e-6)
+    stated["summary"] = (f"FP32 apply within 1e-6 of FP64 (worst {worst:.2e})" if worst <= 1e-6 else
+                         f"FP32 apply misses 1e-6: {worst:.2e}")
+    del y32, y64, uL32, x32, x64, uV64
+
+    # ---------------- tensor-core precision modes on the same workload
+    prec_rows = {}
+    for name, prec, hint in (("f32_tc_autotuned", "f32_tc", 0), ("f32_tc_tensor_cores", "f32_tc", 2),
+                             ("tf32_tensor_cores", "tf32", 2)):
+        g, s = make(H, prec, tile_hint=hint)
+        Kt = min(K, 20)
+        dtm, _, _, _, en = timed_steps(g, s, Kt, 2, dt)
+        _, _, acct, _, _ = timed_steps(g, s, min(Kt, 5), 1, dt, profile=True)
+        with torch.cuda.stream(stream):
+            ua = u_start.clone().to(g.dtype)
+            ya = g.apply_convection(ua, g.project("hdiv_to_l2", ua))
+            ub = ua.double()
+            yb = g64.apply_convection(ub, g64.project("hdiv_to_l2", ub))
+        stream.synchronize()
+        dd = ya.double() - yb
+        prec_rows[name] = {"ms_per_step": dtm / Kt, "value": dofs * Kt / (dtm / 1e3), "unit": UNIT,
+                           "kernel_variants": g.tuning(), "kernels": kernel_table(acct),
+                           "apply_max_rel_vs_gpu_f64": float(dd.abs().max() / yb.abs().max()),
+                           "apply_l2_rel_vs_gpu_f64": float(torch.linalg.vector_norm(dd) / torch.linalg.vector_norm(yb)),
+                           "energy_drift_per_substep": float(np.mean(np.diff(en)) / en[0])}
+        del g, s, ya, yb, ua, ub
+    del g64, s64
+
+    # ---------------- the 16^3 x 6, k = 3 box (FP32, FP64, 3xTF32 autotuned)
+    box16 = {}
+    for prec in ("f32", "f64", "f32_tc"):
+        g, s = make(BOX16, prec)
+        K16 = min(K, 200) if prec != "f64" else min(K, 20)
+        d16, _, _, _, _ = timed_steps(g, s, K16, 3, BOX16["dt"])
+        _, _, acc16, _, _ = timed_steps(g, s, min(K16, 30), 1, BOX16["dt"], profile=True)
+        box16[prec] = {"ms_per_step": d16 / K16, "value": g.n_l2 * APPLIES_PER_STEP * K16 / (d16 / 1e3),
+                       "unit": UNIT, "steps": K16, "kernel_variants": g.tuning(), "kernels": kernel_table(acc16)}
+        if prec == "f32" and rank == 0 and not args.no_cpu_baseline:
+            uV = s.clone()
+            with torch.cuda.stream(stream):
+                y = g.apply_convection(uV, g.project("hdiv_to_l2", uV))
+            stream.synchronize()
+            sample, _, yref = sampled_oracle_apply(uV.double().cpu().numpy(), BOX16["l"], 3, BOX16["n"], BOX16["k"])
+            got = y.double().cpu().numpy().reshape(-1, 3, yref.shape[-1])[sample]
+            box16[prec]["apply_max_rel_vs_oracle"] = float(np.abs(got - yref).max() / np.abs(yref).max())
+        del g, s
+    box16["workload"] = "3D periodic box, 16^3 cubes x 6 tets (24,576 elements), k=3, l=2, same recipe"
 
     # ---------------- differentiation: 24^3 x 6, k = 3, 200-substep rollout, VJP with
     # checkpoints every 20 substeps (FP32)
@@ -533,11 +583,10 @@ def our_arm(args, rank, world):
                "dof_updates_per_s_forward_equivalent": gv.n_l2 * APPLIES_PER_STEP * 200 / (vms / 1e3)}
         del gv, uv
 
-    # ---------------- the other configurations (extra keys; the headline is 16^3 x 6)
     others = None if args.quick else other_configs(dev, stream, world)
 
-    # ---------------- roofline of the dominant kernel (FP32 run, live CUDA events)
-    alg = algorithmic(dim, k, g32.n_elems, g32.n_facets, 4)
+    # ---------------- roofline of the dominant kernel (FP32 headline, live CUDA events)
+    alg = algorithmic(H["dim"], H["k"], g32.n_elems, g32.n_facets, 4)
     dom = max(FAMILIES, key=lambda f: acc[f][0])
     avg_ms = acc[dom][0] / max(1, acc[dom][1])
     flops, byts = alg[dom]
@@ -566,12 +615,8 @@ def our_arm(args, rank, world):
                 "hbm_frac_of_measured": byts / (avg_ms / 1e3) / 1e9 / hbm_peak,
                 "flops_per_launch": flops, "algorithmic_bytes_per_launch": byts,
                 "avg_launch_ms": avg_ms, "launches": acc[dom][1]}
-    kernels = {f: {"ms_total": acc[f][0], "launches": acc[f][1],
-                   "avg_us": 1e3 * acc[f][0] / max(1, acc[f][1]),
-                   "gflops": alg[f][0] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9,
-                   "gbs": alg[f][1] / max(1e-12, acc[f][0] / max(1, acc[f][1]) / 1e3) / 1e9} for f in FAMILIES}
     step_bytes = sum(alg[f][1] * (acc[f][1] / max(1, Kp)) for f in FAMILIES)
-    hbm_step_frac = step_bytes / (dev_ms / K / 1e3) / 1e9 / hbm_peak
+    hbm_step_frac = step_bytes / (tmax_ms / K / 1e3) / 1e9 / hbm_peak
     launches = round(sum(acc[f][1] for f in FAMILIES) * K / Kp) + K   # + the energy-log kernel of every substep
 
     line = {
@@ -580,43 +625,33 @@ def our_arm(args, rank, world):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "elements": g32.n_elems, "l2_dofs": g32.n_l2,
                    "hdiv_dofs": g32.n_hdiv, "applies_per_step": APPLIES_PER_STEP,
-                   "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events)",
+                   "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events); "
+                               "the step's working set is also larger than L2",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "stated_error": stated,
         "roofline": roofline, "alu_peaks_measured": alu_meas, "e2e": e2e, "gpu_launches": launches,
-        "clocks": ck, "fp64": fp64,
-        "fp32_tc": fp32_tc, "vjp": vjp, "other_configs": others,
-        "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernels,
+        "clocks": ck, "fp64": fp64, "fp32_over_fp64_speedup": fp64["ms_per_step"] / (tmax_ms / K),
+        "precision_modes": prec_rows, "box_16cubed_k3": box16, "vjp": vjp, "other_configs": others,
+        "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernel_table(acc, alg),
         "profiled_pass": {"steps": Kp, "ms_per_step": prof_ms / Kp,
                           "note": "per-kernel CUDA events around every launch (roofline, kernels_f32)"},
-        "kernels_f64": {f: {"avg_us": 1e3 * acc64[f][0] / max(1, acc64[f][1]), "launches": acc64[f][1]}
-                        for f in FAMILIES},
         "energy_drift_per_step": (energies[-1] - energies[0]) / max(1, len(energies) - 1) / energies[0],
         "wall_s_timed": wall,
     }
 
-    # ---------------- CPU baseline (oracle, 1 thread) and the stated error
+    # ---------------- CPU baseline: the oracle on every host core (rank 0)
     if rank == 0 and not args.no_cpu_baseline:
-        tmp = tempfile.mkdtemp()
-        out = os.path.join(tmp, "u1")
-        res = run_oracle({"mode": "sample", "n": n, "out": out})
-        u1 = np.load(out + ".npy")
-        cpu_value = res["n_l2"] * APPLIES_PER_STEP / res["seconds"]
-        line["cpu_baseline"] = {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "one SSP-RK3 STAGE substep (3 applies + projections) of the full "
-                                          "16^3 x 6 k=3 workload, numpy FP64, 1 BLAS thread",
-                                "seconds": res["seconds"]}
-        errs = {}
-        for prec in ("f32", "f32_tc", "f64"):
-            g, s = make(prec)
-            with torch.cuda.stream(stream):
-                g.rk_substep(s, dt, 1)
-            stream.synchronize()
-            got = s.double().cpu().numpy()
-            errs[prec] = {"max_rel": float(np.abs(got - u1).max() / np.abs(u1).max()),
-                          "l2_rel": float(np.linalg.norm(got - u1) / np.linalg.norm(u1))}
-        line["error_vs_oracle_one_substep"] = errs
+        pool = oracle_pool((8, 8, 8))
+        try:
+            secs = pool.step()
+        finally:
+            pool.close()
+        line["cpu_baseline"] = {"value": pool.dofs_per_step / secs, "unit": UNIT, "cores": pool.workers,
+                                "kind": "oracle", "sample": pool.describe(), "seconds": secs,
+                                "host_cores": os.cpu_count()}
         if line.get("vjp"):
-            rv = run_oracle({"mode": "vjp_sample", "n": 6, "steps": 2, "out": os.path.join(tmp, "v")})
+            rv = run_oracle({"dim": 3, "n": 6, "k": 3, "l": 2, "dt": dt, "noise": 1e-3, "seed": 0, "steps": 2,
+                             "out": os.path.join(tempfile.mkdtemp(), "v")})
             line["vjp"]["cpu_baseline"] = {
                 "value": rv["n_l2"] * APPLIES_PER_STEP * rv["steps"] / rv["seconds"], "unit": UNIT,
                 "cores": 1, "kind": "oracle",
@@ -630,14 +665,14 @@ def our_arm(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-vjp", action="store_true", help="skip the rollout-adjoint measurement")
-    ap.add_argument("--quick", action="store_true", help="skip the 2D, 32^3 and batch configurations")
-    ap.add_argument("--ref-budget-s", type=float, default=150.0,
-                    help="seconds of oracle work the reference arm aims for (sizes its per-step sample)")
+    ap.add_argument("--quick", action="store_true", help="skip the 2D and batch configurations")
+    ap.add_argument("--ref-block", default="8,8,4",
+                    help="cubes per core of the reference arm's per-step oracle sample (bx,by,bz)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker:

@@ -165,14 +165,14 @@ def test_bench_control_plane_world_size_2(tmp_path):
 
 
 def test_reference_arm_prints_on_rank0_only(tmp_path):
-    """torchrun-style launch of --impl reference at world size 2 (tiny oracle budget)."""
+    """torchrun-style launch of --impl reference at world size 2 (tiny oracle sample)."""
     port = _free_port()
     procs = []
     for r in range(2):
         env = dict(os.environ, RANK=str(r), WORLD_SIZE="2", LOCAL_RANK=str(r), MASTER_ADDR="127.0.0.1",
                    MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
         procs.append(subprocess.Popen([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                                       "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-budget-s", "1"],
+                                       "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-block", "2,2,2"],
                                       env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
     outs = [p.communicate(timeout=600) for p in procs]
     assert all(p.returncode == 0 for p in procs), outs
