@@ -662,6 +662,30 @@ def our_arm(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def profile_case(spec: str):
+    """A small case for ncu captures: n^3 x 6 box, order k, precision prec ("n,k,prec"):
+    build the context, interpolate Taylor-Green, three V_h -> L2 projections, one apply and
+    two STAGE substeps on a side stream (graph-captured)."""
+    import torch
+
+    import workloads as W
+    from paper_2408_06698_gb300 import Hopu
+    n, k, prec = spec.split(",")
+    n, k = int(n), int(k)
+    m = W.periodic_box_mesh(3, n)
+    g = Hopu(m.coords, m.elems, m.rep, k=k, l=k - 1, prec=prec)
+    u = g.interpolate_function(W.taylor_green)
+    for _ in range(3):
+        uL = g.project("hdiv_to_l2", u)
+    y = g.apply_convection(u, uL)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g.rk_substep(u, 5e-4, 2)
+    s.synchronize()
+    torch.cuda.synchronize()
+    print("profile case ok", spec, float(y.abs().max()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -673,10 +697,14 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the 2D and batch configurations")
     ap.add_argument("--ref-block", default="8,8,4",
                     help="cubes per core of the reference arm's per-step oracle sample (bx,by,bz)")
+    ap.add_argument("--profile-case", default=None, help="n,k,prec: a small case for ncu captures, then exit")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker:
         oracle_worker(args)
+        return
+    if args.profile_case:
+        profile_case(args.profile_case)
         return
     if args.warmup < 3:
         args.warmup = 3
