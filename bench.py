@@ -532,7 +532,8 @@ def our_arm(args, rank, world):
         stream.synchronize()
         dd = ya.double() - yb
         prec_rows[name] = {"ms_per_step": dtm / Kt, "value": dofs * Kt / (dtm / 1e3), "unit": UNIT,
-                           "kernel_variants": g.tuning(), "kernels": kernel_table(acct),
+                           "kernel_variants": g.tuning(), "volume_variant": g.tuning_volume(),
+                           "kernels": kernel_table(acct),
                            "apply_max_rel_vs_gpu_f64": float(dd.abs().max() / yb.abs().max()),
                            "apply_l2_rel_vs_gpu_f64": float(torch.linalg.vector_norm(dd) / torch.linalg.vector_norm(yb)),
                            "energy_drift_per_substep": float(np.mean(np.diff(en)) / en[0])}
@@ -547,7 +548,8 @@ def our_arm(args, rank, world):
         d16, _, _, _, _ = timed_steps(g, s, K16, 3, BOX16["dt"])
         _, _, acc16, _, _ = timed_steps(g, s, min(K16, 30), 1, BOX16["dt"], profile=True)
         box16[prec] = {"ms_per_step": d16 / K16, "value": g.n_l2 * APPLIES_PER_STEP * K16 / (d16 / 1e3),
-                       "unit": UNIT, "steps": K16, "kernel_variants": g.tuning(), "kernels": kernel_table(acc16)}
+                       "unit": UNIT, "steps": K16, "kernel_variants": g.tuning(),
+                       "volume_variant": g.tuning_volume(), "kernels": kernel_table(acc16)}
         if prec == "f32" and rank == 0 and not args.no_cpu_baseline:
             uV = s.clone()
             with torch.cuda.stream(stream):
@@ -625,6 +627,7 @@ def our_arm(args, rank, world):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "elements": g32.n_elems, "l2_dofs": g32.n_l2,
                    "hdiv_dofs": g32.n_hdiv, "applies_per_step": APPLIES_PER_STEP,
+                   "volume_kernel_variant": g32.tuning_volume(),
                    "l2_flush": f"{L2_FLUSH_BYTES >> 20} MB memset between timed steps (outside the events); "
                                "the step's working set is also larger than L2",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},

@@ -607,16 +607,30 @@ hopu_status weighted_dot(hopu_ctx* c, const void* a, const void* b, int slot) {
 namespace {
 thread_local std::string g_create_error;
 
-// Autotuner of the kernel variants.  In the tensor-core precision modes each kernel
-// family that has both an FP32 FMA and a tensor-core kernel is timed on this context's
-// mesh (zero-filled scratch; one warm-up launch, then three launches between CUDA
-// events on the context stream) and the faster variant is kept.  tile_hint 1 keeps the
-// FMA kernels, 2 the tensor-core kernels.  The choice is reported by hopu_tuning.
+// Autotuner of the kernel variants, run at create on this context's own mesh
+// (zero-filled scratch; one warm-up launch, then three launches between CUDA events on
+// the context stream, the faster variant kept):
+//  * the element part of a STAGE stage (volume term, lift, inverse mass and the element
+//    back-projection): the register-resident kernel with the back-projection fused or as a
+//    separate launch, the warp-per-element fused kernel, the tensor-core kernel - whichever
+//    this (dim, k, precision) has;
+//  * the V_h -> L2 projection in HOPU_TF32: FMA or tensor cores.
+// tile_hint 1 keeps to the FMA kernels, 2 to the tensor-core kernels where they exist.
+// hopu_tuning / hopu_tuning_volume report the choice and the times.
 hopu_status autotune(hopu_ctx* c, int hint) {
   Ops* o = c->ops;
-  if (!o->tensor_cores() && !o->tensor_core_volume()) return HOPU_OK;
-  if (hint == 1 || hint == 2) {
-    o->select(hint == 2, hint == 2);
+  std::vector<int> cand;
+  for (int v = 0; v < kVolVariants; ++v) {
+    if (!o->volume_variant_ok(v)) continue;
+    if (hint == 1 && v == kVolTensor) continue;
+    if (hint == 2 && o->volume_variant_ok(kVolTensor) && v != kVolTensor) continue;
+    cand.push_back(v);
+  }
+  const bool tc_v2l = o->tensor_cores();
+  int v2l = (tc_v2l && hint == 2) ? 1 : 0;
+  o->select(v2l, 0);
+  if (cand.size() <= 1 && !(tc_v2l && hint == 0)) {
+    if (cand.size() == 1) o->select_volume_variant(cand[0]);
     return HOPU_OK;
   }
   const int64_t nstate = std::max(c->n_hdiv, c->n_l2);
@@ -636,31 +650,35 @@ hopu_status autotune(hopu_ctx* c, int hint) {
     if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) ms = 1e30f;
     return ms;
   };
+  if (tc_v2l && hint == 0) {
+    o->select(0, 0);
+    const float t0 = timed_ms([&] { o->v2l(c->dm, c->dt, c->d_s1, c->d_uL, c->stream); });
+    o->select(1, 0);
+    const float t1 = timed_ms([&] { o->v2l(c->dm, c->dt, c->d_s1, c->d_uL, c->stream); });
+    v2l = t1 < t0;
+    o->select(v2l, 0);
+  }
   Combine plain;
-  // the element part of a STAGE stage after the facet kernel: fused volume + back-projection
-  // when the family has it, else the volume kernel and the element back-projection
   auto stage_volume = [&]() {
     if (!o->volume_l2v(c->dm, c->dt, c->d_uL, c->d_gam, c->d_lf, plain, c->d_s2, c->stream)) {
       o->volume(c->dm, c->dt, c->d_uL, c->d_uL, c->d_gam, plain, c->d_yL, c->stream);
       o->l2v_elem(c->dm, c->dt, c->d_yL, false, c->d_lf, plain, c->d_s2, c->stream);
     }
   };
-  int v2l = 0, vol = 0;
-  if (o->tensor_cores()) {
-    o->select(0, 0);
-    const float t0 = timed_ms([&] { o->v2l(c->dm, c->dt, c->d_s1, c->d_uL, c->stream); });
-    o->select(1, 0);
-    const float t1 = timed_ms([&] { o->v2l(c->dm, c->dt, c->d_s1, c->d_uL, c->stream); });
-    v2l = t1 < t0;
+  int best = cand.empty() ? -1 : cand[0];
+  if (cand.size() > 1) {
+    float tbest = 1e30f;
+    for (int v : cand) {
+      o->select_volume_variant(v);
+      const float t = timed_ms(stage_volume);
+      c->vol_ms[v] = t / 3.0;
+      if (t < tbest) {
+        tbest = t;
+        best = v;
+      }
+    }
   }
-  if (o->tensor_core_volume()) {
-    o->select(v2l, 0);
-    const float t0 = timed_ms(stage_volume);
-    o->select(v2l, 1);
-    const float t1 = timed_ms(stage_volume);
-    vol = t1 < t0;
-  }
-  o->select(v2l, vol);
+  if (best >= 0) o->select_volume_variant(best);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   HOPU_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -843,6 +861,14 @@ hopu_status hopu_tuning(const hopu_ctx* c, int* out2) {
   if (!c || !out2) return HOPU_EINVAL;
   out2[0] = c->ops ? c->ops->selected_v2l() : 0;
   out2[1] = c->ops ? c->ops->selected_volume() : 0;
+  return HOPU_OK;
+}
+
+hopu_status hopu_tuning_volume(const hopu_ctx* c, int* variant, double* ms4) {
+  if (!c || !variant) return HOPU_EINVAL;
+  *variant = c->ops ? c->ops->volume_variant() : -1;
+  if (ms4)
+    for (int v = 0; v < kVolVariants; ++v) ms4[v] = c->vol_ms[v];
   return HOPU_OK;
 }
 

@@ -81,6 +81,8 @@ inline constexpr int compact_volume_points(int d, int k) {
   return d != 3 ? 0 : k == 3 ? 46 : k == 4 ? 100 : k == 5 ? 190 : 0;
 }
 
+enum VolumeVariant { kVolRegFused = 0, kVolRegSplit = 1, kVolWarpFused = 2, kVolTensor = 3, kVolVariants = 4 };
+
 // One family of kernels for a fixed (dim, k, precision).  Every call enqueues on the
 // given stream and returns the number of kernels it launched.
 class Ops {
@@ -112,6 +114,12 @@ class Ops {
   virtual void select(int v2l_tc, int volume_tc) = 0;
   virtual int selected_v2l() const = 0;
   virtual int selected_volume() const = 0;
+  // kernel variants of the element part of a STAGE stage (volume term, lift, inverse mass,
+  // element back-projection): kVolRegFused, kVolRegSplit (+ l2v_elem), kVolWarpFused,
+  // kVolTensor; the autotuner times the available ones and selects one
+  virtual bool volume_variant_ok(int v) const = 0;
+  virtual void select_volume_variant(int v) = 0;
+  virtual int volume_variant() const = 0;
   // adjoint kernels: (R E_T^{-1})^T, the facet and the volume parts of the VJP of the
   // apply (ybar = cotangent of y; wL == uL means w = u and the cotangents are summed
   // into ubar, wbar unused); gamU / gamW are element-major facet-moment scratch.

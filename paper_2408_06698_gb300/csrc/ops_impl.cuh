@@ -8,6 +8,7 @@
 #include "kernels_adj.cuh"
 #include "kernels_tc.cuh"
 #include "kernels_adapt.cuh"
+#include "kernels_vr.cuh"
 
 namespace hopu {
 
@@ -74,7 +75,12 @@ class OpsImpl final : public Ops {
   static constexpr bool kTcV2l = std::is_same<T, float>::value && V2lTc<D, K>::OK;
   static constexpr bool kTcVol = std::is_same<T, float>::value && VolTc<D, K>::OK;
   int g_vol_tc_ = 1;
-  bool use_tc_v2l_ = true, use_tc_vol_ = true;  // autotuner choices (tensor-core modes)
+  bool use_tc_v2l_ = true;  // autotuner choice of the projection (TF32 mode)
+  int vvar_ = -1;           // STAGE volume variant (VolumeVariant), -1: unfused warp-per-element
+  // register-resident FP32 volume kernel (STAGE wind) where the lane's registers suffice
+  static constexpr bool kVolR = std::is_same<T, float>::value && VolR<D, K>::OK;
+  static constexpr bool kVolRF = std::is_same<T, float>::value && VolR<D, K>::FUSE_OK;
+  int g_volr_ = 1, g_volrf_ = 1;
   int g_v2l_ = 1, g_v2lpt_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
 
   template <typename Kern>
@@ -131,7 +137,7 @@ class OpsImpl final : public Ops {
   }
 
  public:
-  explicit OpsImpl(int tc = 0) : tc_(std::is_same<T, float>::value ? tc : 0) {}
+  explicit OpsImpl(int tc = 0) : tc_(std::is_same<T, float>::value ? tc : 0) { vvar_ = default_volume_variant(); }
   // The V_h -> L2 change of basis runs on the tensor cores only in TF32 mode: its FP32
   // accumulation (also in 3xTF32) loses the small high-degree coefficients of smooth
   // fields, which the compensated FMA product keeps (FP32 and 3xTF32 modes).
@@ -139,10 +145,27 @@ class OpsImpl final : public Ops {
   bool tensor_core_volume() const override { return tc_ != 0 && kTcVol; }
   void select(int v2l_tc, int volume_tc) override {
     use_tc_v2l_ = v2l_tc != 0 && tensor_cores();
-    use_tc_vol_ = volume_tc != 0 && tensor_core_volume();
+    if (volume_tc != 0 && tensor_core_volume()) vvar_ = kVolTensor;
+    else if (vvar_ == kVolTensor || vvar_ < 0) vvar_ = default_volume_variant();
   }
   int selected_v2l() const override { return (use_tc_v2l_ && tensor_cores()) ? 1 : 0; }
-  int selected_volume() const override { return (use_tc_vol_ && tensor_core_volume()) ? 1 : 0; }
+  int selected_volume() const override { return vvar_ == kVolTensor ? 1 : 0; }
+  bool volume_variant_ok(int v) const override {
+    switch (v) {
+      case kVolRegFused: return kVolRF;
+      case kVolRegSplit: return kVolR;
+      case kVolWarpFused: return kFuse;
+      case kVolTensor: return tensor_core_volume();
+      default: return false;
+    }
+  }
+  void select_volume_variant(int v) override {
+    if (volume_variant_ok(v)) vvar_ = v;
+  }
+  int volume_variant() const override { return vvar_; }
+  int default_volume_variant() const {
+    return kVolR ? kVolRegSplit : (kFuse ? kVolWarpFused : -1);
+  }
 
   cudaError_t prepare() override {
     int dev = 0;
@@ -175,6 +198,15 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_facet<D, K, T, true, kFacetTab>, facet_smem(true), th, &g_fac_[1])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, false, kVolumeTab, false>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, true, kVolumeTab, false>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
+    if constexpr (kVolR) {
+      if ((err = setup(k_volume_r<D, K, false>, VolR<D, K>::SMEM, 32 * VolR<D, K>::WARPS, &g_volr_)) != cudaSuccess)
+        return err;
+    }
+    if constexpr (kVolRF) {
+      if ((err = setup(k_volume_r<D, K, true>, VolR<D, K>::SMEM_FUSE, 32 * VolR<D, K>::WARPS, &g_volrf_)) !=
+          cudaSuccess)
+        return err;
+    }
     if constexpr (kFuse) {
       if ((err = setup(k_volume<D, K, T, false, true, true>, kFuseSmem, th, &g_fuse_)) != cudaSuccess) return err;
     }
@@ -239,6 +271,15 @@ class OpsImpl final : public Ops {
   int volume(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* gam,
              Combine c, void* out, cudaStream_t st) override {
     const bool wsep = (wL != nullptr && wL != uL);
+    if constexpr (kVolR) {
+      if (!wsep) {
+        using R = VolR<D, K>;
+        const int g = clamp_grid(g_volr_, (m.E + R::ELW - 1) / R::ELW, 1);
+        launch(k_volume_r<D, K, false>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(gam), static_cast<float*>(out), c, static_cast<float*>(nullptr));
+        return 1;
+      }
+    }
     const int g = clamp_grid(g_vol_[wsep ? 1 : 0], m.E, kWarps);
     if (wsep)
       launch(k_volume<D, K, T, true, kVolumeTab, false>, g, 32 * kWarps, volume_smem(true), st, 
@@ -251,7 +292,9 @@ class OpsImpl final : public Ops {
     return 1;
   }
 
-  bool has_fused() const override { return kFuse || (tc_ != 0 && kTcVol && use_tc_vol_); }
+  bool has_fused() const override {
+    return vvar_ == kVolRegFused || vvar_ == kVolWarpFused || vvar_ == kVolTensor;
+  }
 
   int eta(const DevMesh& m, const DevTabs& t, const void* uL, int l, int8_t* facet_l, const EtaThresholds& th,
           double* eta_out, cudaStream_t st) override {
@@ -300,25 +343,35 @@ class OpsImpl final : public Ops {
   int volume_l2v(const DevMesh& m, const DevTabs& t, const void* uL, const void* gam, void* lf, Combine c,
                  void* outV, cudaStream_t st) override {
     if constexpr (kTcVol) {
-      if (tc_ && use_tc_vol_ && t.tcvol) {
+      if (vvar_ == kVolTensor && tensor_core_volume() && t.tcvol) {
         const int g = clamp_grid(g_vol_tc_, m.E, VolTc<D, K>::EB);
         const int nlr = row_stride<float>(S::nloc);
-        launch(k_volume_tc<D, K>, g, VolTc<D, K>::THREADS, VolTc<D, K>::SMEM, st, 
+        launch(k_volume_tc<D, K>, g, VolTc<D, K>::THREADS, VolTc<D, K>::SMEM, st,
             m, static_cast<const float*>(t.tcvol), static_cast<const float*>(t.Dm), static_cast<const float*>(t.Wq),
             static_cast<const float*>(t.TrM), static_cast<const float*>(t.Drow), nlr, static_cast<const float*>(uL),
             static_cast<const float*>(gam), static_cast<float*>(outV), c, static_cast<float*>(lf));
         return 1;
       }
     }
-    if constexpr (kFuse) {
-      const int g = clamp_grid(g_fuse_, m.E, kWarps);
-      launch(k_volume<D, K, T, false, true, true>, g, 32 * kWarps, kFuseSmem, st, 
-          m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
-          static_cast<T*>(outV), c, static_cast<T*>(lf));
-      return 1;
-    } else {
-      return 0;
+    if constexpr (kVolRF) {
+      if (vvar_ == kVolRegFused) {
+        using R = VolR<D, K>;
+        const int g = clamp_grid(g_volrf_, (m.E + R::ELW - 1) / R::ELW, 1);
+        launch(k_volume_r<D, K, true>, g, 32 * R::WARPS, R::SMEM_FUSE, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(gam), static_cast<float*>(outV), c, static_cast<float*>(lf));
+        return 1;
+      }
     }
+    if constexpr (kFuse) {
+      if (vvar_ == kVolWarpFused) {
+        const int g = clamp_grid(g_fuse_, m.E, kWarps);
+        launch(k_volume<D, K, T, false, true, true>, g, 32 * kWarps, kFuseSmem, st,
+            m, t, static_cast<const T*>(uL), static_cast<const T*>(uL), static_cast<const T*>(gam),
+            static_cast<T*>(outV), c, static_cast<T*>(lf));
+        return 1;
+      }
+    }
+    return 0;
   }
 
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,

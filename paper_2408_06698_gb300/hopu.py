@@ -200,6 +200,19 @@ class Hopu:
         self._check(self.lib.hopu_tuning(self.ctx, out), "hopu_tuning")
         return {"v2l": "tc" if out[0] else "fma", "volume": "tc" if out[1] else "fma"}
 
+    VOLUME_VARIANTS = {0: "register, fused back-projection", 1: "register + separate back-projection",
+                       2: "warp per element, fused back-projection", 3: "tensor cores",
+                       -1: "warp per element + separate back-projection"}
+
+    def tuning_volume(self) -> dict:
+        """The STAGE volume kernel variant the autotuner kept and its timings (ms per launch)."""
+        v = ctypes.c_int()
+        ms = (c_double * 4)()
+        self._check(self.lib.hopu_tuning_volume(self.ctx, byref(v), ms), "hopu_tuning_volume")
+        names = ["reg_fused", "reg_split", "warp_fused", "tensor"]
+        return {"variant": v.value, "name": self.VOLUME_VARIANTS.get(v.value, "?"),
+                "ms": {names[i]: ms[i] for i in range(4) if ms[i] >= 0}}
+
     def sync(self):
         """Synchronise the context stream; raises on a device-side failure (ETIMEOUT)."""
         self._check(self.lib.hopu_sync(self.ctx), "hopu_sync")

@@ -120,7 +120,7 @@ def test_energy_functionals(dim, n, k, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 3, 3)])
+@pytest.mark.parametrize("dim,n,k", [(2, 8, 2), (3, 3, 3), (3, 3, 4), (2, 4, 4)])
 def test_rk_substep_stage(dim, n, k, prec):
     g, sp = _mk(dim, n, k, prec, l=k - 1)
     uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
