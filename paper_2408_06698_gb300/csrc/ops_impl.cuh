@@ -9,6 +9,7 @@
 #include "kernels_tc.cuh"
 #include "kernels_adapt.cuh"
 #include "kernels_vr.cuh"
+#include "kernels_fr.cuh"
 
 namespace hopu {
 
@@ -81,6 +82,10 @@ class OpsImpl final : public Ops {
   static constexpr bool kVolR = std::is_same<T, float>::value && VolR<D, K>::OK;
   static constexpr bool kVolRF = std::is_same<T, float>::value && VolR<D, K>::FUSE_OK;
   int g_volr_ = 1, g_volrf_ = 1;
+  // register-resident FP32 facet kernel
+  static constexpr bool kFacR = std::is_same<T, float>::value && FacR<D, K>::OK;
+  static constexpr bool kFacRW = std::is_same<T, float>::value && FacR<D, K>::OK_WSEP;
+  int g_facr_[2] = {1, 1};
   int g_v2l_ = 1, g_v2lpt_ = 1, g_fac_[2] = {1, 1}, g_vol_[2] = {1, 1}, g_elem_[2] = {1, 1}, g_fsum_ = 1;
 
   template <typename Kern>
@@ -194,6 +199,14 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_facet_adj<D, K, T, true>, facet_adj_smem(true), th, &g_fadj_)) != cudaSuccess) return err;
     if ((err = setup(k_volume_adj<D, K, T, false>, volume_adj_smem(false), th, &g_vadj_)) != cudaSuccess) return err;
     if ((err = setup(k_volume_adj<D, K, T, true>, volume_adj_smem(true), th, &g_vadj_)) != cudaSuccess) return err;
+    if constexpr (kFacR) {
+      using R = FacR<D, K>;
+      if ((err = setup(k_facet_r<D, K, false>, R::SMEM, 32 * R::WARPS, &g_facr_[0])) != cudaSuccess) return err;
+    }
+    if constexpr (kFacRW) {
+      using R = FacR<D, K>;
+      if ((err = setup(k_facet_r<D, K, true>, R::SMEM, 32 * R::WARPS, &g_facr_[1])) != cudaSuccess) return err;
+    }
     if ((err = setup(k_facet<D, K, T, false, kFacetTab>, facet_smem(false), th, &g_fac_[0])) != cudaSuccess) return err;
     if ((err = setup(k_facet<D, K, T, true, kFacetTab>, facet_smem(true), th, &g_fac_[1])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, false, kVolumeTab, false>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
@@ -258,6 +271,24 @@ class OpsImpl final : public Ops {
   int facet(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, int l,
             const int8_t* facet_l, void* gam, double* diss, cudaStream_t st) override {
     const bool wsep = (wL != nullptr && wL != uL);
+    if constexpr (kFacRW) {
+      if (wsep) {
+        using R = FacR<D, K>;
+        const int g = clamp_grid(g_facr_[1], (m.NF + R::FPW - 1) / R::FPW, 1);
+        launch(k_facet_r<D, K, true>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(wL), l, facet_l, static_cast<float*>(gam), diss);
+        return 1;
+      }
+    }
+    if constexpr (kFacR) {
+      if (!wsep) {
+        using R = FacR<D, K>;
+        const int g = clamp_grid(g_facr_[0], (m.NF + R::FPW - 1) / R::FPW, 1);
+        launch(k_facet_r<D, K, false>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(uL), l, facet_l, static_cast<float*>(gam), diss);
+        return 1;
+      }
+    }
     const int g = clamp_grid(g_fac_[wsep ? 1 : 0], m.NF, kWarps);
     if (wsep)
       launch(k_facet<D, K, T, true, kFacetTab>, g, 32 * kWarps, facet_smem(true), st, 
