@@ -158,15 +158,23 @@ hopu_status hopu_tuning(const hopu_ctx* ctx, int* out2);
 
 /* The kernel variant of the element part of a STAGE stage (volume term, facet lift,
  * inverse mass, element part of the back-projection) that hopu_create's autotuner kept:
- *   0 = register-resident FP32 kernel (a lane per element component) with the
- *       back-projection fused, 1 = the same kernel followed by the separate element
- *       back-projection, 2 = warp-per-element kernel with the back-projection fused,
- *   3 = tensor-core kernel (HOPU_FP32_TC / HOPU_TF32), -1 = warp-per-element kernel and
- *       the separate back-projection (no other variant for this order and precision).
- * ms4 (host, 4 doubles, may be NULL): the autotuner's time per launch of each variant on
+ *   0 = register-resident FP32 kernel (a lane per element component, modal gradients in
+ *       registers) with the back-projection fused, 1 = the same kernel followed by the
+ *       separate element back-projection, 2 = warp-per-element kernel with the
+ *       back-projection fused, 3 = tensor-core kernel (HOPU_FP32_TC / HOPU_TF32),
+ *   4 = register-resident kernel reading the reference gradients from tables (fewer
+ *       registers, more resident warps) + the separate back-projection,
+ *  -1 = warp-per-element kernel and the separate back-projection (no other variant for
+ *       this order and precision).
+ * ms5 (host, 5 doubles, may be NULL): the autotuner's time per launch of each variant on
  * this mesh in ms, -1 for variants not timed (one variant only, or not available).  No
  * paper counterpart (launch tuning).                                                  */
-hopu_status hopu_tuning_volume(const hopu_ctx* ctx, int* variant, double* ms4);
+hopu_status hopu_tuning_volume(const hopu_ctx* ctx, int* variant, double* ms5);
+
+/* Override the autotuner's STAGE volume variant (the numbering of hopu_tuning_volume;
+ * EINVAL for a variant this order and precision does not have).  Drops the cached substep
+ * graph.  No paper counterpart (launch tuning).                                       */
+hopu_status hopu_set_volume_variant(hopu_ctx* ctx, int variant);
 
 /* Synchronise the context stream and report device-side failures: ETIMEOUT when a
  * tensor-core kernel (HOPU_FP32_TC / HOPU_TF32) gave up waiting for its MMAs (its

@@ -291,7 +291,7 @@ void convert(const std::vector<double>& src, std::vector<unsigned char>& dst, si
 }
 
 // Reorder the host FP64 tables into the kernel layouts (see hopu_internal.h).
-constexpr int kNumTables = 13;
+constexpr int kNumTables = 14;
 
 // Row stride of the point-major tables: an odd multiple of 16 bytes (matches
 // row_stride<T> in kernels.cuh).
@@ -331,6 +331,16 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
         double acc = 0.0;
         for (int q = 0; q < nq; ++q) acc += R.wq[q] * R.dphi[((size_t)q * nb + i) * d + c] * R.phi[(size_t)q * nb + j];
         Dm[((size_t)c * nb1 + j) * nb + i] = acc;
+      }
+  // reference gradients at the kernels' volume points: d phi_i / d xhat_c = sum_j Dm[c][j][i] phi_j
+  auto& dBt = out[13];
+  dBt.assign((size_t)d * nqk * nbq, 0.0);
+  for (int c = 0; c < d; ++c)
+    for (int q = 0; q < nqk; ++q)
+      for (int i = 0; i < nb; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < nb1; ++j) acc += Dm[((size_t)c * nb1 + j) * nb + i] * R.phik[(size_t)q * nb + j];
+        dBt[((size_t)c * nqk + q) * nbq + i] = acc;
       }
   TrM = R.trm;
   TrP.assign((size_t)(d + 1) * nqf * nbq, 0.0);  // point-major [f][q][nbq]
@@ -783,7 +793,8 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
   unsigned char* tb = static_cast<unsigned char*>(c->d_tabs);
   const void** slots[kNumTables] = {&c->dt.Bt,   &c->dt.Wq,  &c->dt.Dm,    &c->dt.TrM,
                                     &c->dt.TrP,  &c->dt.Psi, &c->dt.WPsi,  &c->dt.Wf,
-                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow, &c->dt.Dn};
+                                    &c->dt.DinvT, &c->dt.DT, &c->dt.Dinv, &c->dt.Drow, &c->dt.Dn,
+                                    &c->dt.dBt};
   for (int i = 0; i < kNumTables; ++i) *slots[i] = tb + offs[i];
   if (!c->fp64) {
     std::vector<float> csr;
@@ -864,11 +875,23 @@ hopu_status hopu_tuning(const hopu_ctx* c, int* out2) {
   return HOPU_OK;
 }
 
-hopu_status hopu_tuning_volume(const hopu_ctx* c, int* variant, double* ms4) {
+hopu_status hopu_set_volume_variant(hopu_ctx* c, int variant) {
+  HOPU_PRECHECK(c);
+  if (variant < 0 || variant >= kVolVariants || !c->ops->volume_variant_ok(variant))
+    return fail(c, HOPU_EINVAL, "set_volume_variant: not available for this order and precision");
+  c->ops->select_volume_variant(variant);
+  if (c->gexec) {  // the captured substep uses the previous variant
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return HOPU_OK;
+}
+
+hopu_status hopu_tuning_volume(const hopu_ctx* c, int* variant, double* ms5) {
   if (!c || !variant) return HOPU_EINVAL;
   *variant = c->ops ? c->ops->volume_variant() : -1;
-  if (ms4)
-    for (int v = 0; v < kVolVariants; ++v) ms4[v] = c->vol_ms[v];
+  if (ms5)
+    for (int v = 0; v < kVolVariants; ++v) ms5[v] = c->vol_ms[v];
   return HOPU_OK;
 }
 

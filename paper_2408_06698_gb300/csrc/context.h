@@ -28,7 +28,7 @@ struct hopu_ctx {
   DevTabs dt;
   Ops* ops = nullptr;
   int nsm = 1, red_blocks = 1;
-  double vol_ms[4] = {-1.0, -1.0, -1.0, -1.0};  // autotuner: ms per launch of each STAGE volume variant
+  double vol_ms[5] = {-1.0, -1.0, -1.0, -1.0, -1.0};  // autotuner: ms per launch of each STAGE volume variant
   // device memory
   void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
   void* d_geoT = nullptr;   // working-precision geometry factors

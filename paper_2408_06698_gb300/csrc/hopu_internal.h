@@ -30,6 +30,7 @@ struct DevMesh {
 // Device reference tables in working precision (all element-type T, 16-byte aligned).
 struct DevTabs {
   const void* Bt = nullptr;     // [nq][nbq]       phi_i(x_q), point-major, rows padded to nbq
+  const void* dBt = nullptr;    // [d][nq][nbq]    d phi_i / d xhat_c (x_q), same layout as Bt
                                 //                 (an odd multiple of 16 bytes)
   const void* Wq = nullptr;     // [nq]            volume weights
   const void* Dm = nullptr;     // [d][nb(k-1)][nb] d phi_i / d xhat_c = sum_j Dm[c][j][i] phi_j
@@ -81,7 +82,14 @@ inline constexpr int compact_volume_points(int d, int k) {
   return d != 3 ? 0 : k == 3 ? 46 : k == 4 ? 100 : k == 5 ? 190 : 0;
 }
 
-enum VolumeVariant { kVolRegFused = 0, kVolRegSplit = 1, kVolWarpFused = 2, kVolTensor = 3, kVolVariants = 4 };
+enum VolumeVariant {
+  kVolRegFused = 0,   // register kernel, back-projection fused
+  kVolRegSplit = 1,   // register kernel + separate back-projection
+  kVolWarpFused = 2,  // warp-per-element kernel, back-projection fused
+  kVolTensor = 3,     // tensor-core kernel
+  kVolRegTab = 4,     // register kernel with reference-gradient tables + separate back-projection
+  kVolVariants = 5
+};
 
 // One family of kernels for a fixed (dim, k, precision).  Every call enqueues on the
 // given stream and returns the number of kernels it launched.
@@ -115,8 +123,8 @@ class Ops {
   virtual int selected_v2l() const = 0;
   virtual int selected_volume() const = 0;
   // kernel variants of the element part of a STAGE stage (volume term, lift, inverse mass,
-  // element back-projection): kVolRegFused, kVolRegSplit (+ l2v_elem), kVolWarpFused,
-  // kVolTensor; the autotuner times the available ones and selects one
+  // element back-projection), VolumeVariant; the autotuner times the available ones and
+  // selects one
   virtual bool volume_variant_ok(int v) const = 0;
   virtual void select_volume_variant(int v) = 0;
   virtual int volume_variant() const = 0;

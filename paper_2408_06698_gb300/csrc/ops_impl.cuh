@@ -81,6 +81,8 @@ class OpsImpl final : public Ops {
   // register-resident FP32 volume kernel (STAGE wind) where the lane's registers suffice
   static constexpr bool kVolR = std::is_same<T, float>::value && VolR<D, K>::OK;
   static constexpr bool kVolRF = std::is_same<T, float>::value && VolR<D, K>::FUSE_OK;
+  static constexpr bool kVolRT = std::is_same<T, float>::value && VolR<D, K, true>::OK;
+  int g_volrt_ = 1;
   int g_volr_ = 1, g_volrf_ = 1;
   // register-resident FP32 facet kernel
   static constexpr bool kFacR = std::is_same<T, float>::value && FacR<D, K>::OK;
@@ -161,6 +163,7 @@ class OpsImpl final : public Ops {
       case kVolRegSplit: return kVolR;
       case kVolWarpFused: return kFuse;
       case kVolTensor: return tensor_core_volume();
+      case kVolRegTab: return kVolRT;
       default: return false;
     }
   }
@@ -212,11 +215,16 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_volume<D, K, T, false, kVolumeTab, false>, volume_smem(false), th, &g_vol_[0])) != cudaSuccess) return err;
     if ((err = setup(k_volume<D, K, T, true, kVolumeTab, false>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
     if constexpr (kVolR) {
-      if ((err = setup(k_volume_r<D, K, false>, VolR<D, K>::SMEM, 32 * VolR<D, K>::WARPS, &g_volr_)) != cudaSuccess)
+      if ((err = setup(k_volume_r<D, K, false, false>, VolR<D, K>::SMEM, 32 * VolR<D, K>::WARPS, &g_volr_)) != cudaSuccess)
+        return err;
+    }
+    if constexpr (kVolRT) {
+      if ((err = setup(k_volume_r<D, K, false, true>, VolR<D, K, true>::SMEM, 32 * VolR<D, K, true>::WARPS,
+                       &g_volrt_)) != cudaSuccess)
         return err;
     }
     if constexpr (kVolRF) {
-      if ((err = setup(k_volume_r<D, K, true>, VolR<D, K>::SMEM_FUSE, 32 * VolR<D, K>::WARPS, &g_volrf_)) !=
+      if ((err = setup(k_volume_r<D, K, true, false>, VolR<D, K>::SMEM_FUSE, 32 * VolR<D, K>::WARPS, &g_volrf_)) !=
           cudaSuccess)
         return err;
     }
@@ -302,11 +310,20 @@ class OpsImpl final : public Ops {
   int volume(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* gam,
              Combine c, void* out, cudaStream_t st) override {
     const bool wsep = (wL != nullptr && wL != uL);
+    if constexpr (kVolRT) {
+      if (!wsep && vvar_ == kVolRegTab) {
+        using R = VolR<D, K, true>;
+        const int g = clamp_grid(g_volrt_, (m.E + R::ELW - 1) / R::ELW, 1);
+        launch(k_volume_r<D, K, false, true>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(gam), static_cast<float*>(out), c, static_cast<float*>(nullptr));
+        return 1;
+      }
+    }
     if constexpr (kVolR) {
       if (!wsep) {
         using R = VolR<D, K>;
         const int g = clamp_grid(g_volr_, (m.E + R::ELW - 1) / R::ELW, 1);
-        launch(k_volume_r<D, K, false>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+        launch(k_volume_r<D, K, false, false>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
                static_cast<const float*>(gam), static_cast<float*>(out), c, static_cast<float*>(nullptr));
         return 1;
       }
@@ -388,7 +405,7 @@ class OpsImpl final : public Ops {
       if (vvar_ == kVolRegFused) {
         using R = VolR<D, K>;
         const int g = clamp_grid(g_volrf_, (m.E + R::ELW - 1) / R::ELW, 1);
-        launch(k_volume_r<D, K, true>, g, 32 * R::WARPS, R::SMEM_FUSE, st, m, t, static_cast<const float*>(uL),
+        launch(k_volume_r<D, K, true, false>, g, 32 * R::WARPS, R::SMEM_FUSE, st, m, t, static_cast<const float*>(uL),
                static_cast<const float*>(gam), static_cast<float*>(outV), c, static_cast<float*>(lf));
         return 1;
       }

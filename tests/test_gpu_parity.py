@@ -139,6 +139,37 @@ def test_rk_substep_stage(dim, n, k, prec):
     assert _rel(_host(s3), ref5) < TOL[prec] * 10
 
 
+@pytest.mark.parametrize("dim,n,k", [(2, 6, 2), (2, 4, 4), (3, 3, 2), (3, 3, 3), (3, 3, 4)])
+def test_every_volume_variant_substep(dim, n, k):
+    """Every STAGE volume kernel variant the autotuner can choose (FP32) gives the oracle's
+    substep: register kernels (modal gradients or gradient tables; back-projection fused or
+    separate), the warp-per-element kernel, the tensor-core kernel (FP32_TC)."""
+    from paper_2408_06698_gb300._lib import HopuError
+    uV = None
+    seen = 0
+    for prec in ("f32", "f32_tc"):
+        g, sp = _mk(dim, n, k, prec, l=k - 1)
+        if uV is None:
+            uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
+            ref = rk.substeps_stage(sp, uV, 1e-2, 1, k - 1)
+        for v in range(5):
+            try:
+                g.set_volume_variant(v)
+            except HopuError:
+                g.clear_error()
+                continue
+            if prec == "f32_tc" and v != 3:
+                continue
+            s = _dev(g, uV)
+            g.rk_substep(s, 1e-2, 1)
+            g.sync()
+            err = _rel(_host(s), ref)
+            print(f"d={dim} k={k} {prec} volume variant {v}: substep error {err:.2e}")
+            assert err < 2e-6, (v, err)
+            seen += 1
+    assert seen >= 2
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("dim,n,k", [(3, 3, 3), (2, 4, 1)])
 def test_energy_log_records_every_substep(dim, n, k, prec):
