@@ -213,6 +213,24 @@ hopu_status hopu_apply_convection(hopu_ctx* ctx, const void* w_hdiv, const void*
                                   void* y_l2, const int8_t* facet_l);
 /* (facet_l NULL: the orders of hopu_set_facet_l when set, else the context's l.) */
 
+/* The same operator with the wind given as an L2 vector w_l2 (element-major, the layout of
+ * u_l2) instead of a V_h vector: y_l2 = M_L^{-1} c(w; u, .) with w.n on a facet taken from
+ * the average of both sides' traces (equal to w.n for normal-continuous w).  Used by the
+ * element-partitioned apply, whose partitions hold the wind of their halo elements in L2
+ * (Section 3.2, eq. "hopudefinition", as hopu_apply_convection).  The vectors must not
+ * alias y_l2.                                                                          */
+hopu_status hopu_apply_convection_l2(hopu_ctx* ctx, const void* w_l2, const void* u_l2, void* y_l2,
+                                     const int8_t* facet_l);
+
+/* Halo exchange of an element partition (no paper counterpart: the data movement of a
+ * partitioned apply).  ids: device int32 array of n element ids of this context's mesh.
+ *   hopu_pack_elements:   buf[j] = l2 block of element ids[j]   (buf: n * dim * nb values)
+ *   hopu_unpack_elements: l2 block of element ids[j] = buf[j]
+ * Working precision, asynchronous on the stream.  An id outside the mesh is skipped and
+ * reported as EINVAL by the next hopu_sync / hopu_energy.                              */
+hopu_status hopu_pack_elements(hopu_ctx* ctx, const int32_t* ids, int64_t n, const void* l2, void* buf);
+hopu_status hopu_unpack_elements(hopu_ctx* ctx, const int32_t* ids, int64_t n, const void* buf, void* l2);
+
 /* n_substeps explicit SSP-RK3 substeps (Shu-Osher) of du/dt = -y(u) with step dt.
  * STAGE wind: state is a V_h vector, updated in place, w = u at every stage.
  * FROZEN wind: state is an L2 vector updated in place; the wind is the V_h vector last

@@ -43,6 +43,9 @@ SIGNATURES = {
     "hopu_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "hopu_project": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "hopu_apply_convection": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hopu_apply_convection_l2": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hopu_pack_elements": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "hopu_unpack_elements": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "hopu_rk_substep": (c_int, [c_void_p, c_void_p, c_double, c_int]),
     "hopu_set_frozen_wind": (c_int, [c_void_p, c_void_p]),
     "hopu_set_energy_log": (c_int, [c_void_p, c_void_p, c_int64]),

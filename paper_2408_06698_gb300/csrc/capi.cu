@@ -199,6 +199,25 @@ __global__ void __launch_bounds__(256) k_axpby(int64_t n, Combine w, T* x, const
     else x[t] = fmaf(w.h2, y[t], fmaf(w.h0, x[t], fmaf(w.l2, y[t], w.l0 * x[t])));
 }
 
+// Copy element blocks of nl values: pack (dst[j] = src[ids[j]]) or unpack (dst[ids[j]] =
+// src[j]), j < n.  An id outside [0, E) is skipped and flagged in the error word (bit 2).
+template <typename T, bool PACK>
+__global__ void __launch_bounds__(256) k_copy_blocks(int64_t E, int nl, const int32_t* __restrict__ ids, int64_t n,
+                                                     const T* __restrict__ src, T* __restrict__ dst, int* err) {
+  const int64_t total = n * nl;
+  for (int64_t t = (int64_t)blockIdx.x * 256 + threadIdx.x; t < total; t += (int64_t)gridDim.x * 256) {
+    const int64_t j = t / nl;
+    const int off = (int)(t - j * nl);
+    const int32_t id = ids[j];
+    if (id < 0 || id >= E) {
+      atomicOr(err, 4);
+      continue;
+    }
+    if (PACK) dst[t] = src[(int64_t)id * nl + off];
+    else dst[(int64_t)id * nl + off] = src[t];
+  }
+}
+
 // y = M x for an L2 field (M = |det J| I per element): the gradient of 1/2 int |x|^2
 template <typename T>
 __global__ void __launch_bounds__(256) k_mass(int64_t E, int NL, int G, const double* geo, const T* x, T* y) {
@@ -261,6 +280,10 @@ hopu_status check_launch(hopu_ctx* c, const char* where) {
 hopu_status device_status(hopu_ctx* c) {
   int e = 0;
   HOPU_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e & 4) {
+    HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    return fail(c, HOPU_EINVAL, "pack / unpack: an element id was outside the mesh (those blocks were skipped)");
+  }
   if (e & 3) {
     HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
     std::string who = (e & 1) ? "k_v2l_tc (V_h -> L2 projection)" : "";
@@ -944,6 +967,45 @@ hopu_status hopu_apply_convection(hopu_ctx* c, const void* w_hdiv, const void* u
   enqueue_v2l(c, w_hdiv, c->d_wL);
   Combine plain;
   return enqueue_stage_apply(c, u_l2, c->d_wL, c->l, facet_l ? facet_l : c->facet_l, nullptr, plain, y_l2);
+}
+
+hopu_status hopu_apply_convection_l2(hopu_ctx* c, const void* w_l2, const void* u_l2, void* y_l2,
+                                     const int8_t* facet_l) {
+  HOPU_PRECHECK(c);
+  if (!w_l2 || !u_l2 || !y_l2 || y_l2 == u_l2 || y_l2 == w_l2)
+    return fail(c, HOPU_EINVAL, "apply_convection_l2: NULL or aliased vectors");
+  if (!aligned16(w_l2) || !aligned16(u_l2) || !aligned16(y_l2))
+    return fail(c, HOPU_EINVAL, "apply_convection_l2: vectors must be 16-byte aligned");
+  Combine plain;
+  return enqueue_stage_apply(c, u_l2, w_l2, c->l, facet_l ? facet_l : c->facet_l, nullptr, plain, y_l2);
+}
+
+hopu_status hopu_pack_elements(hopu_ctx* c, const int32_t* ids, int64_t n, const void* l2, void* buf) {
+  HOPU_PRECHECK(c);
+  if (n < 0 || (n > 0 && (!ids || !l2 || !buf))) return fail(c, HOPU_EINVAL, "pack_elements: bad arguments");
+  if (n == 0) return HOPU_OK;
+  const int g = (int)std::min<int64_t>((n * c->ref.nloc + 255) / 256, (int64_t)c->nsm * 8);
+  if (c->fp64)
+    k_copy_blocks<double, true><<<g, 256, 0, c->stream>>>(c->topo.n_elems, c->ref.nloc, ids, n, (const double*)l2,
+                                                          (double*)buf, c->d_err);
+  else
+    k_copy_blocks<float, true><<<g, 256, 0, c->stream>>>(c->topo.n_elems, c->ref.nloc, ids, n, (const float*)l2,
+                                                         (float*)buf, c->d_err);
+  return check_launch(c, "pack_elements");
+}
+
+hopu_status hopu_unpack_elements(hopu_ctx* c, const int32_t* ids, int64_t n, const void* buf, void* l2) {
+  HOPU_PRECHECK(c);
+  if (n < 0 || (n > 0 && (!ids || !l2 || !buf))) return fail(c, HOPU_EINVAL, "unpack_elements: bad arguments");
+  if (n == 0) return HOPU_OK;
+  const int g = (int)std::min<int64_t>((n * c->ref.nloc + 255) / 256, (int64_t)c->nsm * 8);
+  if (c->fp64)
+    k_copy_blocks<double, false><<<g, 256, 0, c->stream>>>(c->topo.n_elems, c->ref.nloc, ids, n, (const double*)buf,
+                                                           (double*)l2, c->d_err);
+  else
+    k_copy_blocks<float, false><<<g, 256, 0, c->stream>>>(c->topo.n_elems, c->ref.nloc, ids, n, (const float*)buf,
+                                                          (float*)l2, c->d_err);
+  return check_launch(c, "unpack_elements");
 }
 
 hopu_status hopu_set_frozen_wind(hopu_ctx* c, const void* w_hdiv) {

@@ -102,6 +102,41 @@ class Hopu:
                                                    self._vec(out, self.n_l2, "y_l2"), fl), "hopu_apply_convection")
         return out
 
+    def apply_convection_l2(self, w_l2, u_l2, out=None) -> torch.Tensor:
+        """y = M^{-1} c(w; u, .) with the wind given as an L2 vector."""
+        if out is None:
+            out = self.new("l2")
+        self._sync_stream()
+        self._check(self.lib.hopu_apply_convection_l2(self.ctx, self._vec(w_l2, self.n_l2, "w_l2"),
+                                                      self._vec(u_l2, self.n_l2, "u_l2"),
+                                                      self._vec(out, self.n_l2, "y_l2"), None),
+                    "hopu_apply_convection_l2")
+        return out
+
+    def _ids(self, ids: torch.Tensor) -> int:
+        if ids.dtype != torch.int32 or ids.device != self.device or not ids.is_contiguous():
+            raise ValueError("ids must be a contiguous int32 tensor on the context's device")
+        return ids.data_ptr()
+
+    def pack_elements(self, ids: torch.Tensor, l2: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """out[j] = the L2 block of element ids[j] (flat, len(ids) * dim * nb values)."""
+        nl = self.n_l2 // self.n_elems
+        if out is None:
+            out = torch.empty(ids.numel() * nl, dtype=self.dtype, device=self.device)
+        self._sync_stream()
+        self._check(self.lib.hopu_pack_elements(self.ctx, self._ids(ids), ids.numel(), self._vec(l2, self.n_l2, "l2"),
+                                                self._vec(out, ids.numel() * nl, "buf")), "hopu_pack_elements")
+        return out
+
+    def unpack_elements(self, ids: torch.Tensor, buf: torch.Tensor, l2: torch.Tensor) -> torch.Tensor:
+        """The L2 blocks of elements ids[j] of l2 are set from buf[j]."""
+        nl = self.n_l2 // self.n_elems
+        self._sync_stream()
+        self._check(self.lib.hopu_unpack_elements(self.ctx, self._ids(ids), ids.numel(),
+                                                  self._vec(buf, ids.numel() * nl, "buf"),
+                                                  self._vec(l2, self.n_l2, "l2")), "hopu_unpack_elements")
+        return l2
+
     def vjp_apply(self, w_hdiv, u_l2, ybar_l2, need_w: bool = True, need_u: bool = True):
         """(wbar_hdiv, ubar_l2) = cotangents of apply_convection(w, u) for ybar (None if not needed)."""
         wbar = self.new("hdiv") if need_w else None
