@@ -561,6 +561,32 @@ def our_arm(args, rank, world):
         del g, s
     box16["workload"] = "3D periodic box, 16^3 cubes x 6 tets (24,576 elements), k=3, l=2, same recipe"
 
+    # ---------------- element-partitioned apply on this GPU: 4 z-slab partitions of the
+    # headline box (logical partitions; halo exchange by the pack / unpack kernels)
+    from paper_2408_06698_gb300.partition import PartitionedHopu, slab_partitions
+    mH = meshes[(H["dim"], H["n"], H["k"])]
+    parts = slab_partitions(mH, 4)
+    pg = PartitionedHopu(mH.coords, mH.elems, mH.rep, parts, k=H["k"], l=H["l"], prec="f32", device=dev)
+    with torch.cuda.stream(stream):
+        uLw = g32.project("hdiv_to_l2", u_start.clone())
+        ul = pg.scatter(uLw)
+        yw = g32.apply_convection_l2(uLw, uLw)
+        yp = pg.gather(pg.apply_convection_l2(ul, ul), torch.empty_like(uLw))
+    stream.synchronize()
+    Kpa = 5
+    t_whole = _events_ms(stream, lambda: g32.apply_convection_l2(uLw, uLw, out=yw), Kpa) / Kpa
+    t_part = _events_ms(stream, lambda: pg.apply_convection_l2(ul, ul), Kpa) / Kpa
+    t_exch = _events_ms(stream, lambda: pg.exchange(ul), Kpa) / Kpa
+    halo = sum(len(p.halo) for p in parts)
+    part_row = {"partitions": len(parts), "kind": "z slabs, logical partitions on one GPU",
+                "ms_per_apply_partitioned": t_part, "ms_per_apply_whole_mesh": t_whole,
+                "ms_halo_exchange": t_exch, "halo_elements": halo,
+                "halo_fraction": halo / g32.n_elems,
+                "exchange_bytes_per_apply": halo * (g32.n_l2 // g32.n_elems) * 4,
+                "owned_outputs_bit_identical": bool(torch.equal(yp, yw)),
+                "note": "apply with the wind in L2 (w = u); P applies run one after another on one stream"}
+    del pg, ul, yp, yw, uLw
+
     # ---------------- differentiation: 24^3 x 6, k = 3, 200-substep rollout, VJP with
     # checkpoints every 20 substeps (FP32)
     vjp = None
@@ -634,7 +660,8 @@ def our_arm(args, rank, world):
         "stated_error": stated,
         "roofline": roofline, "alu_peaks_measured": alu_meas, "e2e": e2e, "gpu_launches": launches,
         "clocks": ck, "fp64": fp64, "fp32_over_fp64_speedup": fp64["ms_per_step"] / (tmax_ms / K),
-        "precision_modes": prec_rows, "box_16cubed_k3": box16, "vjp": vjp, "other_configs": others,
+        "precision_modes": prec_rows, "box_16cubed_k3": box16, "partitioned_apply": part_row, "vjp": vjp,
+        "other_configs": others,
         "hbm_frac_whole_step_of_measured": hbm_step_frac, "kernels_f32": kernel_table(acc, alg),
         "profiled_pass": {"steps": Kp, "ms_per_step": prof_ms / Kp,
                           "note": "per-kernel CUDA events around every launch (roofline, kernels_f32)"},
