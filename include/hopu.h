@@ -151,9 +151,11 @@ hopu_status hopu_destroy(hopu_ctx* ctx);
 /* Replace the stream later calls enqueue on. */
 hopu_status hopu_set_stream(hopu_ctx* ctx, void* cuda_stream);
 
-/* Kernel variants in use: out2[0] for the V_h -> L2 projection (a tensor-core variant
- * exists in HOPU_TF32 only), out2[1] for the fused STAGE volume kernel; 0 = FP32 FMA
- * kernel, 1 = tensor-core kernel.  No paper counterpart (launch tuning).               */
+/* Kernel variants in use: out2[0] for the V_h -> L2 projection (HOPU_TF32: one TF32
+ * product, k_v2l_tc; HOPU_FP32_TC: the refined projection with its two dense products on
+ * the tensor cores and the compensated residual on the CUDA cores, k_v2l_tcr, 3D k <= 4
+ * and 2D), out2[1] for the fused STAGE volume kernel; 0 = FP32 FMA kernel, 1 =
+ * tensor-core kernel.  No paper counterpart (launch tuning).                           */
 hopu_status hopu_tuning(const hopu_ctx* ctx, int* out2);
 
 /* The kernel variant of the element part of a STAGE stage (volume term, facet lift,
@@ -176,6 +178,21 @@ hopu_status hopu_tuning_volume(const hopu_ctx* ctx, int* variant, double* ms5);
  * graph.  No paper counterpart (launch tuning).                                       */
 hopu_status hopu_set_volume_variant(hopu_ctx* ctx, int variant);
 
+/* The element part of the back-projection R E^{-1} (Section 2.3, the local functionals
+ * D (det J Jinv y) of an L2 field y, not dual) that the autotuner kept: *tc = 1 for the
+ * tensor-core kernel (k_l2v_tc: 128 elements per tile as the MMA rows, D as the B
+ * operand; HOPU_FP32_TC runs it in 3xTF32, HOPU_TF32 in 1xTF32; 3D k <= 4 and 2D),
+ * 0 for the FMA kernel.  ms2 (host, 2 doubles, may be NULL): the autotuner's time per
+ * launch of the FMA and of the tensor-core kernel on this mesh in ms, -1 where not timed
+ * (FP32 / FP64 modes, tile_hint 1 or 2, or no tensor-core kernel for this order).  No
+ * paper counterpart (launch tuning).                                                  */
+hopu_status hopu_tuning_l2v(const hopu_ctx* ctx, int* tc, double* ms2);
+
+/* Override the autotuner's back-projection kernel: tc = 0 FMA, 1 tensor cores (EINVAL
+ * where this order and precision have none).  Drops the cached substep graph.  No paper
+ * counterpart (launch tuning).                                                        */
+hopu_status hopu_set_l2v_variant(hopu_ctx* ctx, int tc);
+
 /* Synchronise the context stream and report device-side failures: ETIMEOUT when a
  * tensor-core kernel (HOPU_FP32_TC / HOPU_TF32) gave up waiting for its MMAs (its
  * output is then incomplete).  hopu_energy performs the same check.  No paper
@@ -183,7 +200,7 @@ hopu_status hopu_set_volume_variant(hopu_ctx* ctx, int variant);
 hopu_status hopu_sync(hopu_ctx* ctx);
 
 /* Poll limit of the tensor-core kernels' MMA completion waits (k_v2l_tc in HOPU_TF32,
- * k_volume_tc in HOPU_FP32_TC / HOPU_TF32): polls >= 0 sets it (0 makes the first such
+ * k_volume_tc and k_l2v_tc in HOPU_FP32_TC / HOPU_TF32): polls >= 0 sets it (0 makes the first such
  * wait give up at once), polls < 0 restores the default of 2^22 polls (~0.3 s).  A wait
  * that gives up records ETIMEOUT in the device error word (hopu_sync / hopu_energy
  * report it and name the kernel); the kernel then stops issuing work, waits with the

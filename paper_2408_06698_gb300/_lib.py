@@ -73,6 +73,8 @@ SIGNATURES = {
     "hopu_tuning": (c_int, [c_void_p, POINTER(c_int)]),
     "hopu_tuning_volume": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
     "hopu_set_volume_variant": (c_int, [c_void_p, c_int]),
+    "hopu_tuning_l2v": (c_int, [c_void_p, POINTER(c_int), POINTER(c_double)]),
+    "hopu_set_l2v_variant": (c_int, [c_void_p, c_int]),
     "hopu_set_facet_l": (c_int, [c_void_p, c_void_p]),
     "hopu_adapt_l": (c_int, [c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p]),
     "hopu_vjp_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

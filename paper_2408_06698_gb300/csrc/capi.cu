@@ -275,8 +275,8 @@ hopu_status check_launch(hopu_ctx* c, const char* where) {
 }
 
 // Read the device error word (the stream must have been synchronised): ETIMEOUT when a
-// tensor-core kernel gave up waiting for its MMAs (bit 0: k_v2l_tc, bit 1: k_volume_tc);
-// the word is cleared once read.
+// tensor-core kernel gave up waiting for its MMAs (bit 0: k_v2l_tc, bit 1: k_volume_tc,
+// bit 3: k_l2v_tc); EINVAL for bit 2 (pack / unpack ids); the word is cleared once read.
 hopu_status device_status(hopu_ctx* c) {
   int e = 0;
   HOPU_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -284,10 +284,11 @@ hopu_status device_status(hopu_ctx* c) {
     HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
     return fail(c, HOPU_EINVAL, "pack / unpack: an element id was outside the mesh (those blocks were skipped)");
   }
-  if (e & 3) {
+  if (e & 11) {
     HOPU_CUDA(c, cudaMemset(c->d_err, 0, sizeof(int)));
-    std::string who = (e & 1) ? "k_v2l_tc (V_h -> L2 projection)" : "";
+    std::string who = (e & 1) ? "k_v2l_tc / k_v2l_tcr (V_h -> L2 projection)" : "";
     if (e & 2) who += std::string(who.empty() ? "" : " and ") + "k_volume_tc (volume term)";
+    if (e & 8) who += std::string(who.empty() ? "" : " and ") + "k_l2v_tc (back-projection)";
     return fail(c, HOPU_ETIMEOUT, "a tensor-core MMA completion wait gave up in " + who +
                                       "; the outputs of that launch are incomplete");
   }
@@ -299,7 +300,7 @@ void free_all(hopu_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
                   c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err, c->d_tcvol,
-                  c->d_inlet, c->d_inlet_modes, c->d_csr};
+                  c->d_inlet, c->d_inlet_modes, c->d_csr, c->d_tcl2v, c->d_tcv2l};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c->ops;
@@ -404,7 +405,7 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
 // (int32 bits) sorted by count, largest first, then one entry {r (int32 bits), hi, lo, 0}
 // per nonzero with hi = float(D[s][r]), lo = float(D[s][r] - hi).  Entries below 1e-13 of
 // max |D| are the exact zeros of the orthogonality relations, rounded by the quadrature.
-void dof_matrix_csr(const RefTables& R, std::vector<float>& out) {
+std::vector<std::vector<std::pair<int, double>>> dof_matrix_rows(const RefTables& R) {
   const int nl = R.nloc;
   double mx = 0.0;
   for (double v : R.D) mx = std::max(mx, std::fabs(v));
@@ -414,9 +415,22 @@ void dof_matrix_csr(const RefTables& R, std::vector<float>& out) {
       const double v = R.D[(size_t)s * nl + r];
       if (std::fabs(v) > 1e-13 * mx) rows[s].push_back({r, v});
     }
-  std::vector<int> order(nl);
-  for (int s = 0; s < nl; ++s) order[s] = s;
+  return rows;
+}
+
+// The order of the CSR rows: by number of nonzeros, largest first (stable).
+std::vector<int> csr_row_order(const RefTables& R) {
+  const auto rows = dof_matrix_rows(R);
+  std::vector<int> order(R.nloc);
+  for (int s = 0; s < R.nloc; ++s) order[s] = s;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a].size() > rows[b].size(); });
+  return order;
+}
+
+void dof_matrix_csr(const RefTables& R, std::vector<float>& out) {
+  const int nl = R.nloc;
+  const auto rows = dof_matrix_rows(R);
+  const std::vector<int> order = csr_row_order(R);
   size_t nnz = 0;
   for (const auto& r : rows) nnz += r.size();
   out.assign(4 * (nl + nnz), 0.0f);
@@ -467,6 +481,51 @@ void tensor_core_volume_table(const RefTables& R, std::vector<float>& out) {
       out[PA + off(q, i, KP1)] = l;
       out[2 * PA + off(i, q, K2)] = h;
       out[2 * PA + PB + off(i, q, K2)] = l;
+    }
+}
+
+// B operand of the tensor-core back-projection: B[r][kappa(b, i)] = D[r][b nb + i] (r the
+// local functional, b the component, i the basis index, kappa the K column of l2v_tc_gw),
+// N = nloc padded to 16 rows; hi = tf32(D), lo = tf32(D - hi), the hi parts then the lo
+// parts, in the blocked K-major layout of tensor_core_volume_table.
+void tensor_core_l2v_table(const RefTables& R, std::vector<float>& out) {
+  const int d = R.dim, nb = R.nb, nl = R.nloc;
+  const int IPG = l2v_tc_ipg(nb), GW = l2v_tc_gw(d, nb), KP = l2v_tc_kp(d, nb), NP = l2v_tc_np(nl);
+  const size_t P = (size_t)NP * KP;
+  out.assign(2 * P, 0.0f);
+  auto off = [&](int row, int col) {
+    return (size_t)(((row >> 3) * (KP >> 2) + (col >> 2)) * 32 + (row & 7) * 4 + (col & 3));
+  };
+  for (int r = 0; r < nl; ++r)
+    for (int s2 = 0; s2 < nl; ++s2) {
+      const double v = R.D[(size_t)r * nl + s2];
+      const float h = tf32_round((float)v), l = tf32_round((float)(v - (double)h));
+      const int b = s2 / nb, i = s2 % nb, g = i / IPG;
+      const int col = g * GW + b * IPG + (i - g * IPG);
+      out[off(r, col)] = h;
+      out[P + off(r, col)] = l;
+    }
+}
+
+// B operand of the refined tensor-core projection: B[r][kappa(h)] = Dinv[r][s_h] (r the basis
+// index, s_h the local functional of CSR row h, kappa(h) = (h % 4) GW + h / 4 the K column
+// of v2l_tc_gw), N = nloc padded to 16 rows; hi / lo TF32 parts, the hi parts then the lo
+// parts, blocked K-major as above.
+void tensor_core_v2l_table(const RefTables& R, std::vector<float>& out) {
+  const int nl = R.nloc, GW = v2l_tc_gw(nl), KP = v2l_tc_kp(nl), NP = (nl + 15) / 16 * 16;
+  const std::vector<int> order = csr_row_order(R);
+  const size_t P = (size_t)NP * KP;
+  out.assign(2 * P, 0.0f);
+  auto off = [&](int row, int col) {
+    return (size_t)(((row >> 3) * (KP >> 2) + (col >> 2)) * 32 + (row & 7) * 4 + (col & 3));
+  };
+  for (int r = 0; r < nl; ++r)
+    for (int h = 0; h < nl; ++h) {
+      const double v = R.Dinv[(size_t)r * nl + order[h]];
+      const float hi = tf32_round((float)v), lo = tf32_round((float)(v - (double)hi));
+      const int col = (h % 4) * GW + h / 4;
+      out[off(r, col)] = hi;
+      out[P + off(r, col)] = lo;
     }
 }
 
@@ -647,9 +706,11 @@ thread_local std::string g_create_error;
 //    back-projection): the register-resident kernel with the back-projection fused or as a
 //    separate launch, the warp-per-element fused kernel, the tensor-core kernel - whichever
 //    this (dim, k, precision) has;
-//  * the V_h -> L2 projection in HOPU_TF32: FMA or tensor cores.
+//  * the V_h -> L2 projection in HOPU_TF32: FMA or tensor cores;
+//  * the element back-projection in the tensor-core modes: FMA or tensor cores (timed
+//    first, so that the volume variants with a separate back-projection use the choice).
 // tile_hint 1 keeps to the FMA kernels, 2 to the tensor-core kernels where they exist.
-// hopu_tuning / hopu_tuning_volume report the choice and the times.
+// hopu_tuning / hopu_tuning_volume / hopu_tuning_l2v report the choice and the times.
 hopu_status autotune(hopu_ctx* c, int hint) {
   Ops* o = c->ops;
   std::vector<int> cand;
@@ -662,7 +723,9 @@ hopu_status autotune(hopu_ctx* c, int hint) {
   const bool tc_v2l = o->tensor_cores();
   int v2l = (tc_v2l && hint == 2) ? 1 : 0;
   o->select(v2l, 0);
-  if (cand.size() <= 1 && !(tc_v2l && hint == 0)) {
+  const bool tc_l2v = o->tensor_core_l2v();
+  o->select_l2v(tc_l2v && hint == 2);
+  if (cand.size() <= 1 && !(tc_v2l && hint == 0) && !(tc_l2v && hint == 0)) {
     if (cand.size() == 1) o->select_volume_variant(cand[0]);
     return HOPU_OK;
   }
@@ -692,6 +755,16 @@ hopu_status autotune(hopu_ctx* c, int hint) {
     o->select(v2l, 0);
   }
   Combine plain;
+  if (tc_l2v && hint == 0) {
+    auto l2v = [&] { o->l2v_elem(c->dm, c->dt, c->d_uL, false, c->d_lf, plain, c->d_s2, c->stream); };
+    o->select_l2v(0);
+    const float t0 = timed_ms(l2v);
+    o->select_l2v(1);
+    const float t1 = timed_ms(l2v);
+    c->l2v_ms[0] = t0 / 3.0;
+    c->l2v_ms[1] = t1 / 3.0;
+    o->select_l2v(t1 < t0);
+  }
   auto stage_volume = [&]() {
     if (!o->volume_l2v(c->dm, c->dt, c->d_uL, c->d_gam, c->d_lf, plain, c->d_s2, c->stream)) {
       o->volume(c->dm, c->dt, c->d_uL, c->d_uL, c->d_gam, plain, c->d_yL, c->stream);
@@ -834,6 +907,20 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
     HOPU_CUDA(c, cudaMemcpy(c->d_tcvol, tv.data(), tv.size() * sizeof(float), cudaMemcpyHostToDevice));
     c->dt.tcvol = c->d_tcvol;
   }
+  if (c->ops->tensor_cores() && c->prec == HOPU_FP32_TC) {
+    std::vector<float> tv;
+    tensor_core_v2l_table(R, tv);
+    HOPU_CUDA(c, cudaMalloc(&c->d_tcv2l, tv.size() * sizeof(float)));
+    HOPU_CUDA(c, cudaMemcpy(c->d_tcv2l, tv.data(), tv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->dt.tcv2l = c->d_tcv2l;
+  }
+  if (c->ops->tensor_core_l2v()) {
+    std::vector<float> tv;
+    tensor_core_l2v_table(R, tv);
+    HOPU_CUDA(c, cudaMalloc(&c->d_tcl2v, tv.size() * sizeof(float)));
+    HOPU_CUDA(c, cudaMemcpy(c->d_tcl2v, tv.data(), tv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->dt.tcl2v = c->d_tcl2v;
+  }
 
   // scratch
   const size_t ts = c->tsize;
@@ -903,6 +990,29 @@ hopu_status hopu_set_volume_variant(hopu_ctx* c, int variant) {
   if (variant < 0 || variant >= kVolVariants || !c->ops->volume_variant_ok(variant))
     return fail(c, HOPU_EINVAL, "set_volume_variant: not available for this order and precision");
   c->ops->select_volume_variant(variant);
+  if (c->gexec) {  // the captured substep uses the previous variant
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return HOPU_OK;
+}
+
+hopu_status hopu_tuning_l2v(const hopu_ctx* c, int* tc, double* ms2) {
+  if (!c || !tc) return HOPU_EINVAL;
+  *tc = c->ops ? c->ops->selected_l2v() : 0;
+  if (ms2) {
+    ms2[0] = c->l2v_ms[0];
+    ms2[1] = c->l2v_ms[1];
+  }
+  return HOPU_OK;
+}
+
+hopu_status hopu_set_l2v_variant(hopu_ctx* c, int tc) {
+  HOPU_PRECHECK(c);
+  if (tc != 0 && tc != 1) return fail(c, HOPU_EINVAL, "set_l2v_variant: 0 (FMA) or 1 (tensor cores)");
+  if (tc == 1 && !c->ops->tensor_core_l2v())
+    return fail(c, HOPU_EINVAL, "set_l2v_variant: no tensor-core back-projection for this order and precision");
+  c->ops->select_l2v(tc);
   if (c->gexec) {  // the captured substep uses the previous variant
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;

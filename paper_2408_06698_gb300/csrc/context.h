@@ -28,12 +28,15 @@ struct hopu_ctx {
   DevTabs dt;
   Ops* ops = nullptr;
   int nsm = 1, red_blocks = 1;
+  double l2v_ms[2] = {-1.0, -1.0};  // autotuner: ms per launch of the FMA / tensor-core back-projection
   double vol_ms[5] = {-1.0, -1.0, -1.0, -1.0, -1.0};  // autotuner: ms per launch of each STAGE volume variant
   // device memory
   void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
   void* d_geoT = nullptr;   // working-precision geometry factors
   void* d_tabs = nullptr;   // every reference table
   void* d_tcvol = nullptr;  // tensor-core volume tables (FP32 tensor-core modes)
+  void* d_tcv2l = nullptr;  // tensor-core refined projection table (HOPU_FP32_TC)
+  void* d_tcl2v = nullptr;  // tensor-core back-projection table (FP32 tensor-core modes)
   void* d_csr = nullptr;    // FP32: nonzeros of the dof matrix D (refined projection)
   void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major
   void* d_lf = nullptr;     // [E][d+1][nf] local facet functionals

@@ -18,8 +18,9 @@ struct DevMesh {
   const int32_t* fa = nullptr;   // [NF]: element*4 + local facet of side A
   const int32_t* fb = nullptr;   // [NF]: same for side B
   const double* fgeo = nullptr;  // [NF][d+1]: canonical unit normal n_F, a_F = |F|/|param|
-  int* err = nullptr;            // device error word (bit 0 / bit 1: a completion wait of the
-                                 // tensor-core projection / volume kernel gave up)
+  int* err = nullptr;            // device error word (bits 0 / 1 / 3: a completion wait of the
+                                 // tensor-core projection / volume / back-projection kernel gave
+                                 // up; bit 2: element ids out of range in pack / unpack)
   uint32_t tc_wait_limit = 1u << 22;  // polls of the tensor-core MMA completion waits (hopu_set_wait_limit)
   // boundary facets have fb[F] == fa[F] (wall / outlet rule: the exterior trace is the
   // interior one); inlet facets also have inlet[F] >= 0, the row of their exterior data
@@ -50,6 +51,10 @@ struct DevTabs {
                                 //   TF32 hi and lo parts), or NULL
   const void* Drow = nullptr;   // [nloc][nlr]     D[r][s] row-major, rows padded to nlr (an odd
                                 //                 multiple of 16 bytes), zero padding
+  const void* tcv2l = nullptr;  // FP32 3xTF32 refined projection table (Dinv as the B operand,
+                                //   TF32 hi and lo parts, layout of V2lTcr), or NULL
+  const void* tcl2v = nullptr;  // FP32 tensor-core back-projection table (D as the B operand,
+                                //   TF32 hi and lo parts, layout of L2vTc), or NULL
 };
 
 // out = a0*x0 + a1*x1 + a2*v  (x0 / x1 may be null; out may alias x0 or x1).
@@ -72,6 +77,23 @@ struct Combine {
 struct EtaThresholds {
   double t[6];
 };
+
+// K layout of the tensor-core back-projection (k_l2v_tc and its host table): the basis
+// indices are split into 4 groups of IPG (one warp group each); group g owns the GW
+// consecutive K columns g GW + b IPG + t for component b and basis index i = g IPG + t,
+// zero-padded to a multiple of 4; K = 4 GW; N = nloc padded to 16.
+inline constexpr int l2v_tc_ipg(int nb) { return (nb + 3) / 4; }
+inline constexpr int l2v_tc_gw(int d, int nb) { return (d * l2v_tc_ipg(nb) + 3) / 4 * 4; }
+inline constexpr int l2v_tc_kp(int d, int nb) { return 4 * l2v_tc_gw(d, nb); }
+inline constexpr int l2v_tc_np(int nloc) { return (nloc + 15) / 16 * 16; }
+
+// K layout of the refined tensor-core projection (k_v2l_tcr and its host table): the rows h
+// of the sorted dof-matrix CSR (csr_row_order) are dealt to 4 warp groups, h = g + 4 j;
+// group g owns the RPG rows j and the K columns g GW + j (zero-padded to GW, a multiple
+// of 4); K = 4 GW; N = nloc padded to 16.
+inline constexpr int v2l_tc_rpg(int nloc) { return (nloc + 3) / 4; }
+inline constexpr int v2l_tc_gw(int nloc) { return (v2l_tc_rpg(nloc) + 3) / 4 * 4; }
+inline constexpr int v2l_tc_kp(int nloc) { return 4 * v2l_tc_gw(nloc); }
 
 // layout of the working-precision geometry record (offsets in elements)
 inline constexpr int geoT_stride(int d) { return ((3 * d * d + 1 + 3) / 4) * 4; }
@@ -146,6 +168,11 @@ class Ops {
                        Combine c, void* outV, cudaStream_t) = 0;
   virtual int l2v_facet(const DevMesh&, const void* lf, bool dual, Combine c, void* outV,
                         cudaStream_t) = 0;
+  // the element part of R E^{-1} (not dual) on the tensor cores: available in the tensor-core
+  // modes where the tiles fit; selected by the autotuner (1) or not (0)
+  virtual bool tensor_core_l2v() const = 0;
+  virtual void select_l2v(int tc) = 0;
+  virtual int selected_l2v() const = 0;
 };
 
 Ops* make_ops(int dim, int k, bool fp64);

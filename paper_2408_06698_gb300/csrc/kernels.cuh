@@ -83,6 +83,15 @@ __device__ __forceinline__ void allreduce(T (&v)[N]) {
   }
 }
 
+// FP32 combination a0 x0 + a1 x1 + a2 v with x0, x1 already loaded (0 where absent); the
+// arithmetic of combine_at.
+__device__ __forceinline__ float combine_f32(const Combine& c, float v, float x0, float x1) {
+  float o = fmaf(c.l2, v, fmaf(c.l0, x0, c.l1 * x1));  // the small parts first
+  o = fmaf(c.h1, x1, o);
+  o = fmaf(c.h0, x0, o);
+  return fmaf(c.h2, v, o);
+}
+
 template <typename T>
 __device__ __forceinline__ T combine_at(const Combine& c, T v, int64_t idx) {
   if constexpr (sizeof(T) == 8) {
@@ -93,10 +102,7 @@ __device__ __forceinline__ T combine_at(const Combine& c, T v, int64_t idx) {
   } else {
     const float x0 = c.x0 ? static_cast<const float*>(c.x0)[idx] : 0.0f;
     const float x1 = c.x1 ? static_cast<const float*>(c.x1)[idx] : 0.0f;
-    float o = fmaf(c.l2, v, fmaf(c.l0, x0, c.l1 * x1));  // the small parts first
-    o = fmaf(c.h1, x1, o);
-    o = fmaf(c.h0, x0, o);
-    return fmaf(c.h2, v, o);
+    return combine_f32(c, v, x0, x1);
   }
 }
 

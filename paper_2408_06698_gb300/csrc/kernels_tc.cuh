@@ -505,3 +505,245 @@ __global__ void __launch_bounds__(512, 1) k_volume_tc(DevMesh m, const float* __
 }
 
 }  // namespace hopu
+
+namespace hopu {
+
+// ------------------------------------------------------------------------------------
+// a7 (element part, not dual) on the tensor cores: ell = D (det J Jinv y) per element.
+//
+// 128 elements per tile are the M = 128 rows and the 128 TMEM lanes.  The tile's L2 blocks
+// (contiguous in memory) arrive in shared memory by one bulk copy, issued as soon as the
+// previous tile's blocks have been read, so that it lands while that tile's MMAs and
+// stores run.  Thread (lane quarter q, warp group g) owns element 32 q + lane and the
+// basis indices i = g IPG .. g IPG + IPG - 1: it forms X[(b, i)] = sum_a (det J Jinv)[b][a]
+// y[a][i] for every component b from its element's row (odd row stride: conflict-free)
+// and its element's geometry (loaded into registers one tile ahead), splits them into
+// TF32 parts and writes them into its own TMEM lane, columns g GW + b IPG + t: the A
+// operand of the MMA is read from TMEM.  B = D[r][kappa] (N = n_loc padded to 16), hi /
+// lo TF32 parts from the host, resident in shared memory.  ell lands in TMEM (lane =
+// element, column = functional r) and leaves through a shared staging buffer to coalesced
+// stores: facet rows to lf with the sign sigma, interior rows combined into the V_h output
+// (the combination inputs of a batch of rows are loaded before any is used).  3xTF32 or
+// 1xTF32.
+template <int D, int K>
+struct L2vTc {
+  using S = Shape<D, K>;
+  static constexpr int NB = S::nb, NL = S::nloc;
+  static constexpr int IPG = l2v_tc_ipg(NB);       // basis indices per warp group
+  static constexpr int GW = l2v_tc_gw(D, NB);      // A columns per warp group
+  static constexpr int KP = l2v_tc_kp(D, NB);      // K
+  static constexpr int NP = l2v_tc_np(NL);         // N
+  static constexpr int TM = 128, THREADS = 512;    // 4 warp groups x 4 lane quarters
+  static constexpr int SST = NL | 1;               // staging row stride (odd: conflict-free)
+  // TMEM columns: accumulator [0, NP), A hi [AH, AH + KP), A lo [AL, AL + KP)
+  static constexpr uint32_t AH = (NP + 31) / 32 * 32, AL = AH + (KP + 31) / 32 * 32;
+  static constexpr uint32_t TCOLS = AL + KP <= 32 ? 32 : AL + KP <= 64 ? 64 : AL + KP <= 128 ? 128
+                                  : AL + KP <= 256 ? 256 : 512;
+  static constexpr size_t B_BYTES = size_t(NP) * KP * 4;
+  static constexpr size_t Y_BYTES = size_t(TM) * NL * 4;  // one tile of L2 blocks
+  static constexpr size_t O_Y = 2 * B_BYTES;
+  static constexpr size_t O_ST = O_Y + (Y_BYTES + 15) / 16 * 16;
+  static constexpr size_t O_CODE = O_ST + (size_t(TM) * SST * 4 + 15) / 16 * 16;
+  static constexpr size_t O_BAR = O_CODE + size_t(TM) * (D + 1) * 4;
+  static constexpr size_t SMEM = O_BAR + 32;
+  static constexpr bool OK = SMEM <= 227 * 1024 && NP <= 256 && AL + KP <= 512 && (2 * B_BYTES) % 16 == 0 &&
+                             Y_BYTES % 16 == 0 && TM * (D + 1) <= THREADS && GW % 4 == 0;
+  static constexpr size_t TABLE_FLOATS = 2 * size_t(NP) * KP;  // hi parts, then lo parts
+};
+
+constexpr int kErrTcTimeoutL2v = 8;  // device error word bit of k_l2v_tc
+
+template <int D, int K, bool THREE>
+__global__ void __launch_bounds__(512, 1) k_l2v_tc(DevMesh m, const float* __restrict__ tab,
+                                                   const float* __restrict__ yL, float* __restrict__ lf,
+                                                   float* outV, Combine cmb) {
+  using C = L2vTc<D, K>;
+  using S = Shape<D, K>;
+  constexpr int NB = C::NB, NL = C::NL, NF = S::nf, NINT = S::nint, GT = S::gt, DD = D * D;
+  constexpr int KP = C::KP, NP = C::NP, IPG = C::IPG, GW = C::GW, TM = C::TM, NT = C::THREADS;
+  constexpr int NFL = (D + 1) * NF, SST = C::SST;
+  constexpr uint32_t LBO = 128, SBO = (KP / 4) * 128;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* sB = smem_raw;                                         // hi parts, then lo parts
+  float* sY = reinterpret_cast<float*>(smem_raw + C::O_Y);              // [TM][NL]  this tile's y
+  float* stage = reinterpret_cast<float*>(smem_raw + C::O_ST);          // [TM][SST] ell
+  int* sCode = reinterpret_cast<int*>(smem_raw + C::O_CODE);            // [TM][D+1]
+  uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::O_BAR);      // table, MMAs, y copy
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mb + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, grp = warp >> 2;  // lane quarter, warp group
+  const int el = q * 32 + lane;             // this thread's element (TMEM lane)
+  pdl_trigger();
+
+  if (warp == 0) tc::tmem_alloc(tslot, C::TCOLS);
+  if (tid == 0) {
+    tc::mbar_init(mb, 1);
+    tc::mbar_init(mb + 1, 1);
+    tc::mbar_init(mb + 2, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid == 0) {  // the constant B operand (written at context creation)
+    tc::mbar_expect_tx(mb, (uint32_t)(2 * C::B_BYTES));
+    tc::bulk_g2s(sB, tab, (uint32_t)(2 * C::B_BYTES), mb);
+  }
+  const uint32_t tbase = *tslot;
+  const uint32_t tquad = tbase + ((uint32_t)(q * 32) << 16);
+  const uint32_t idesc = tc::idesc_tf32(128, NP);
+  const int64_t ntiles = (m.E + TM - 1) / TM;
+  const double* geoT = m.geoT;
+  double pg[DD];  // (det J Jinv)[b][a] of this thread's element, one tile ahead
+  int code = 0;   // facet code tid of the tile, one tile ahead
+  auto load_regs = [&](int64_t tile) {
+    const int64_t e = tile * TM + el;
+#pragma unroll
+    for (int t = 0; t < DD; ++t) pg[t] = e < m.E ? __ldg(geoT + e * GT + DD + t) : 0.0;
+    if (tid < TM * (D + 1))
+      code = (tile * TM + tid / (D + 1) < m.E) ? __ldg(m.efc + tile * TM * (D + 1) + tid) : 0;
+  };
+  bool ypend = false;  // a bulk copy of y is in flight
+  uint32_t yph = 0, phase = 0;
+  // bring tile's y into sY: one bulk copy for a full tile, plain loads for the ragged tail
+  // (the caller synchronises before sY is read)
+  auto fetch_y = [&](int64_t tile) {
+    const int64_t e0 = tile * TM;
+    if (e0 + TM <= m.E) {
+      if (tid == 0) {
+        tc::mbar_expect_tx(mb + 2, (uint32_t)C::Y_BYTES);
+        tc::bulk_g2s(sY, yL + e0 * NL, (uint32_t)C::Y_BYTES, mb + 2);
+      }
+      ypend = true;
+    } else {
+      for (int64_t t = tid; t < (m.E - e0) * NL; t += NT) sY[t] = yL[e0 * NL + t];
+    }
+  };
+  bool ok = __syncthreads_and(tc::mbar_wait(mb, 0)) != 0;
+  pdl_wait();
+  int64_t tile = blockIdx.x;
+  if (tile < ntiles) {
+    load_regs(tile);
+    fetch_y(tile);
+    __syncthreads();
+  }
+  for (; ok && tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TM;
+    const int nrow = (m.E - e0 < TM) ? (int)(m.E - e0) : TM;
+    if (ypend) {  // this tile's bulk copy
+      ok = __syncthreads_and(tc::mbar_wait(mb + 2, yph)) != 0;
+      yph ^= 1u;
+      ypend = false;
+      if (!ok) break;
+    }
+    // A: X for this thread's element and basis indices, TF32 parts into its TMEM lane
+    {
+      float xh[GW], xl[GW];
+      const float* y = sY + el * NL;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        float P[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) P[a] = float(pg[b * D + a]);
+#pragma unroll
+        for (int t = 0; t < IPG; ++t) {
+          const int i = grp * IPG + t;
+          float x = 0.0f;
+          if (el < nrow && i < NB) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) x = fmaf(P[a], y[a * NB + i], x);
+          }
+          tc::split_tf32(x, xh[b * IPG + t], xl[b * IPG + t], THREE);
+        }
+      }
+#pragma unroll
+      for (int t = D * IPG; t < GW; ++t) xh[t] = xl[t] = 0.0f;
+      tc::tmem_st_cols<GW>(tquad + C::AH + (uint32_t)(grp * GW), xh);
+      if (THREE) tc::tmem_st_cols<GW>(tquad + C::AL + (uint32_t)(grp * GW), xl);
+      tc::tmem_st_wait();
+    }
+    if (tid < TM * (D + 1)) sCode[tid] = code;
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t bH = tc::smem_u32(sB), bL = bH + (uint32_t)C::B_BYTES;
+#pragma unroll 1
+      for (int ks = 0; ks < KP / 8; ++ks) {
+        const uint32_t off = ks * 256;
+        const uint32_t aH = tbase + C::AH + 8 * ks, aL = tbase + C::AL + 8 * ks;
+        tc::mma_tf32_ts(tbase, aH, tc::sdesc(bH + off, LBO, SBO), idesc, ks > 0);
+        if (THREE) {
+          tc::mma_tf32_ts(tbase, aH, tc::sdesc(bL + off, LBO, SBO), idesc, 1);
+          tc::mma_tf32_ts(tbase, aL, tc::sdesc(bH + off, LBO, SBO), idesc, 1);
+        }
+      }
+      tc::commit(mb + 1);
+    }
+    // the next tile's y (sY has been read) and registers, in flight while the MMAs run
+    const int64_t nxt = tile + gridDim.x;
+    if (nxt < ntiles) {
+      load_regs(nxt);
+      fetch_y(nxt);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(mb + 1, phase, m.tc_wait_limit)) != 0;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok) break;
+    // TMEM -> staging: warp (q, g) reads lane quarter q, column groups g, g + 4, ...
+#pragma unroll 1
+    for (int c0 = grp * 16; c0 < NP; c0 += 64) {
+      float v[16];
+      tc::ld16(tquad + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < NL) stage[el * SST + c0 + j] = v[j];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    for (int t = tid; t < nrow * NFL; t += NT) {
+      const int r = t / NFL, f = t - r * NFL;
+      const float v = stage[r * SST + f];
+      lf[e0 * NFL + t] = (sCode[r * (D + 1) + f / NF] & 2) ? -v : v;
+    }
+    if constexpr (NINT > 0) {
+      constexpr int NB8 = 6;  // rows per thread and batch
+      const float* x0 = static_cast<const float*>(cmb.x0);
+      const float* x1 = static_cast<const float*>(cmb.x1);
+      const int64_t base = (int64_t)m.NF * NF + e0 * NINT;
+      for (int t0 = tid; t0 < nrow * NINT; t0 += NB8 * NT) {
+        float xa[NB8], xb[NB8];
+#pragma unroll
+        for (int u = 0; u < NB8; ++u) {
+          const int t = t0 + u * NT;
+          const bool in = t < nrow * NINT;
+          xa[u] = (in && x0) ? x0[base + t] : 0.0f;
+          xb[u] = (in && x1) ? x1[base + t] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < NB8; ++u) {
+          const int t = t0 + u * NT;
+          if (t < nrow * NINT) {
+            const int r = t / NINT, ii = t - r * NINT;
+            outV[base + t] = combine_f32(cmb, stage[r * SST + NFL + ii], xa[u], xb[u]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(m.err, kErrTcTimeoutL2v);
+    tc::mbar_wait(mb, 0);                 // bounded (full limit): the table copy lands before exit,
+    if (ypend) tc::mbar_wait(mb + 2, yph);  // so does a y copy in flight,
+    tc::mbar_wait(mb + 1, phase ^ 1u);    // and the MMAs in flight drain before TMEM is freed
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, C::TCOLS);
+  }
+}
+
+}  // namespace hopu

@@ -7,6 +7,7 @@
 #include "kernels.cuh"
 #include "kernels_adj.cuh"
 #include "kernels_tc.cuh"
+#include "kernels_tcr.cuh"
 #include "kernels_adapt.cuh"
 #include "kernels_vr.cuh"
 #include "kernels_fr.cuh"
@@ -74,8 +75,14 @@ class OpsImpl final : public Ops {
   int tc_ = 0;  // FP32 only: 0 = FMA, 3 = 3xTF32 tensor cores, 1 = 1xTF32 tensor cores
   int g_v2l_tc_ = 1;
   static constexpr bool kTcV2l = std::is_same<T, float>::value && V2lTc<D, K>::OK;
+  static constexpr bool kTcV2lR = std::is_same<T, float>::value && V2lTcr<D, K>::OK;
+  int g_v2l_tcr_ = 1;
+  bool tcr_fits_ = true;  // the CSR of D fits beside the refined tensor-core projection's tiles
   static constexpr bool kTcVol = std::is_same<T, float>::value && VolTc<D, K>::OK;
   int g_vol_tc_ = 1;
+  static constexpr bool kTcL2v = std::is_same<T, float>::value && L2vTc<D, K>::OK;
+  int g_l2v_tc_ = 1;
+  bool use_tc_l2v_ = false;  // autotuner choice of the element back-projection
   bool use_tc_v2l_ = true;  // autotuner choice of the projection (TF32 mode)
   int vvar_ = -1;           // STAGE volume variant (VolumeVariant), -1: unfused warp-per-element
   // register-resident FP32 volume kernel (STAGE wind) where the lane's registers suffice
@@ -145,10 +152,11 @@ class OpsImpl final : public Ops {
 
  public:
   explicit OpsImpl(int tc = 0) : tc_(std::is_same<T, float>::value ? tc : 0) { vvar_ = default_volume_variant(); }
-  // The V_h -> L2 change of basis runs on the tensor cores only in TF32 mode: its FP32
-  // accumulation (also in 3xTF32) loses the small high-degree coefficients of smooth
-  // fields, which the compensated FMA product keeps (FP32 and 3xTF32 modes).
-  bool tensor_cores() const override { return tc_ == 1 && kTcV2l; }
+  // The V_h -> L2 change of basis on the tensor cores: one TF32 product in TF32 mode
+  // (k_v2l_tc); in 3xTF32 mode the refined projection (k_v2l_tcr), whose two dense products
+  // run on the tensor cores and whose compensated residual keeps the small high-degree
+  // coefficients of smooth fields that a plain FP32 or 3xTF32 product loses.
+  bool tensor_cores() const override { return (tc_ == 1 && kTcV2l) || (tc_ == 3 && kTcV2lR && tcr_fits_); }
   bool tensor_core_volume() const override { return tc_ != 0 && kTcVol; }
   void select(int v2l_tc, int volume_tc) override {
     use_tc_v2l_ = v2l_tc != 0 && tensor_cores();
@@ -197,6 +205,14 @@ class OpsImpl final : public Ops {
         if (err != cudaSuccess) return err;
       }
     }
+
+    if constexpr (kTcL2v) {
+      if (tc_) {
+        err = tc_ == 3 ? setup(k_l2v_tc<D, K, true>, L2vTc<D, K>::SMEM, L2vTc<D, K>::THREADS, &g_l2v_tc_, true)
+                       : setup(k_l2v_tc<D, K, false>, L2vTc<D, K>::SMEM, L2vTc<D, K>::THREADS, &g_l2v_tc_, true);
+        if (err != cudaSuccess) return err;
+      }
+    }
     if ((err = setup(k_eta<D, K, T>, eta_smem(), th, &g_eta_)) != cudaSuccess) return err;
     if ((err = setup(k_facet_adj<D, K, T, false>, facet_adj_smem(false), th, &g_fadj_)) != cudaSuccess) return err;
     if ((err = setup(k_facet_adj<D, K, T, true>, facet_adj_smem(true), th, &g_fadj_)) != cudaSuccess) return err;
@@ -240,6 +256,16 @@ class OpsImpl final : public Ops {
   // The refined FP32 projection stages the sparse rows of D and, when they fit, Dinv^T per
   // CTA; as many warps per CTA as fit in ~220 KB (16, 12, 8 or 4).
   cudaError_t configure(const DevTabs& t) override {
+    if constexpr (kTcV2lR) {
+      if (tc_ == 3) {
+        const size_t sm = V2lTcr<D, K>::smem(t.csr_n);
+        tcr_fits_ = sm <= 227 * 1024;
+        if (tcr_fits_) {
+          cudaError_t err = setup(k_v2l_tcr<D, K>, sm, V2lTcr<D, K>::THREADS, &g_v2l_tcr_, true);
+          if (err != cudaSuccess) return err;
+        }
+      }
+    }
     if constexpr (kRef) {
       using R = ProjRCfg<D, K>;
       csr_n_ = t.csr_n;
@@ -254,8 +280,17 @@ class OpsImpl final : public Ops {
   }
 
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
+    if constexpr (kTcV2lR) {
+      if (tc_ == 3 && tcr_fits_ && use_tc_v2l_ && t.tcv2l) {
+        const int g = clamp_grid(g_v2l_tcr_, m.E, V2lTcr<D, K>::TM);
+        launch(k_v2l_tcr<D, K>, g, V2lTcr<D, K>::THREADS, V2lTcr<D, K>::smem(t.csr_n), st, m,
+               static_cast<const float*>(t.tcv2l), static_cast<const float4*>(t.Dcsr), t.csr_n,
+               static_cast<const float*>(uV), static_cast<float*>(uL));
+        return 1;
+      }
+    }
     if constexpr (kTcV2l) {
-      if (tensor_cores() && use_tc_v2l_) {
+      if (tc_ == 1 && use_tc_v2l_) {
         const int g = clamp_grid(g_v2l_tc_, m.E, V2lTc<D, K>::TM);
         const int nlp = (S::nloc + 3) / 4 * 4;
         launch(k_v2l_tc<D, K, false>, g, V2lTc<D, K>::THREADS, V2lTc<D, K>::SMEM, st, m,
@@ -422,8 +457,25 @@ class OpsImpl final : public Ops {
     return 0;
   }
 
+  bool tensor_core_l2v() const override { return kTcL2v && tc_ != 0; }
+  void select_l2v(int tc) override { use_tc_l2v_ = tc != 0 && tensor_core_l2v(); }
+  int selected_l2v() const override { return use_tc_l2v_ && tensor_core_l2v() ? 1 : 0; }
+
   int l2v_elem(const DevMesh& m, const DevTabs& t, const void* yL, bool dual, void* lf, Combine c,
                void* outV, cudaStream_t st) override {
+    if constexpr (kTcL2v) {
+      if (!dual && use_tc_l2v_ && tc_ && t.tcl2v) {
+        using LC = L2vTc<D, K>;
+        const int g = clamp_grid(g_l2v_tc_, m.E, LC::TM);
+        if (tc_ == 3)
+          launch(k_l2v_tc<D, K, true>, g, LC::THREADS, LC::SMEM, st, m, static_cast<const float*>(t.tcl2v),
+                 static_cast<const float*>(yL), static_cast<float*>(lf), static_cast<float*>(outV), c);
+        else
+          launch(k_l2v_tc<D, K, false>, g, LC::THREADS, LC::SMEM, st, m, static_cast<const float*>(t.tcl2v),
+                 static_cast<const float*>(yL), static_cast<float*>(lf), static_cast<float*>(outV), c);
+        return 1;
+      }
+    }
     const int g = clamp_grid(g_elem_[dual ? 1 : 0], (m.E + PW::EW - 1) / PW::EW, 1);
     if (dual)
       launch(k_l2v_elem<D, K, T, true>, g, 32 * PW::WARPS, PW::SMEM, st, 

@@ -65,6 +65,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
       : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B[smem]^T, issued by a single thread: A is M = 128 TMEM lanes (one
+// row each) x K consecutive 32-bit columns from the address atmem (lane field 0).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive once on the mbarrier when every MMA this thread issued before has completed.
 __device__ __forceinline__ void commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -140,6 +151,55 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// ---------------------------------------------------------------- registers -> TMEM
+// N consecutive FP32 columns (N = 4, 8 or 16) of this thread's TMEM lane (same lane rule
+// as ld16); tmem_st_wait() makes them complete before a thread synchronisation hands the
+// columns to the tensor core.
+template <int N>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float* v) {
+  static_assert(N == 4 || N == 8 || N == 16, "x4, x8 or x16");
+  if constexpr (N == 4) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3]))
+                 : "memory");
+  } else if constexpr (N == 8) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+  }
+}
+
+// W consecutive columns (W a multiple of 4) in x16 / x8 / x4 pieces
+template <int W>
+__device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const float* v) {
+  static_assert(W % 4 == 0, "multiple of 4 columns");
+  if constexpr (W >= 16) {
+    tmem_st<16>(taddr, v);
+    if constexpr (W > 16) tmem_st_cols<W - 16>(taddr + 16, v + 16);
+  } else if constexpr (W >= 8) {
+    tmem_st<8>(taddr, v);
+    if constexpr (W > 8) tmem_st_cols<W - 8>(taddr + 8, v + 8);
+  } else {
+    tmem_st<4>(taddr, v);
+  }
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- TF32 splitting
 __device__ __forceinline__ float tf32_rna(float x) {

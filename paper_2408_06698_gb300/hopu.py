@@ -230,10 +230,27 @@ class Hopu:
         return state
 
     def tuning(self) -> dict:
-        """Kernel variants the autotuner kept: {'v2l': 'fma'|'tc', 'volume': 'fma'|'tc'}."""
+        """Kernel variants the autotuner kept, 'fma' or 'tc' per family: the V_h -> L2
+        projection ('v2l'), the STAGE volume kernel ('volume') and the element part of the
+        back-projection ('l2v')."""
         out = (ctypes.c_int * 2)()
         self._check(self.lib.hopu_tuning(self.ctx, out), "hopu_tuning")
-        return {"v2l": "tc" if out[0] else "fma", "volume": "tc" if out[1] else "fma"}
+        tc = ctypes.c_int()
+        self._check(self.lib.hopu_tuning_l2v(self.ctx, byref(tc), None), "hopu_tuning_l2v")
+        return {"v2l": "tc" if out[0] else "fma", "volume": "tc" if out[1] else "fma",
+                "l2v": "tc" if tc.value else "fma"}
+
+    def tuning_l2v(self) -> dict:
+        """The back-projection kernel the autotuner kept and its timings (ms per launch)."""
+        tc = ctypes.c_int()
+        ms = (c_double * 2)()
+        self._check(self.lib.hopu_tuning_l2v(self.ctx, byref(tc), ms), "hopu_tuning_l2v")
+        return {"kernel": "tc" if tc.value else "fma",
+                "ms": {n: ms[i] for i, n in enumerate(("fma", "tc")) if ms[i] >= 0}}
+
+    def set_l2v_variant(self, tc: int):
+        """Override the autotuner's back-projection kernel: 0 FMA, 1 tensor cores."""
+        self._check(self.lib.hopu_set_l2v_variant(self.ctx, int(tc)), "hopu_set_l2v_variant")
 
     VOLUME_VARIANTS = {0: "register, fused back-projection", 1: "register + separate back-projection",
                        2: "warp per element, fused back-projection", 3: "tensor cores",
