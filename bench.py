@@ -341,8 +341,8 @@ def other_configs(dev, stream, world):
     # 512 meshes, n ~ U{4..12}, k ~ U{2..5} (seed 1), FP32, one graph replay per substep
     draws = W.batch_draws(512, seed=1)
     meshes = [W.periodic_box_mesh(3, n) for n, _ in draws]
-    b = HopuBatch([(mm.coords, mm.elems, mm.rep) for mm in meshes], [k for _, k in draws], l=-2, prec="f32",
-                  device=dev)
+    b = HopuBatch([(mm.coords, mm.elems, mm.rep) for mm in meshes], [k for _, k in draws], l=-2,
+                  prec=HEADLINE_PREC, device=dev)
     states = []
     for c, v in enumerate(b.classes):
         states.append(torch.as_tensor(W.uniform_noise(v.n_hdiv, 1.0, 1000 + c), device=dev).float())
@@ -358,6 +358,7 @@ def other_configs(dev, stream, world):
     ms = a0.elapsed_time(a1)
     l2 = sum(v.n_l2 for v in b.classes)
     out["batch_512_meshes_f32"] = {"meshes": 512, "elements": sum(mm.n_elems for mm in meshes),
+                                   "precision_mode": HEADLINE_PREC,
                                    "order_classes": len(b.classes), "substeps": K, "ms_per_substep": ms / K,
                                    "value": l2 * APPLIES_PER_STEP * K / (ms / 1e3), "unit": UNIT}
     b.close()

@@ -166,12 +166,14 @@ hopu_status hopu_tuning(const hopu_ctx* ctx, int* out2);
  *       back-projection fused, 3 = tensor-core kernel (HOPU_FP32_TC / HOPU_TF32),
  *   4 = register-resident kernel reading the reference gradients from tables (fewer
  *       registers, more resident warps) + the separate back-projection,
+ *   5 = register-resident kernel with each (element, component)'s basis split over two
+ *       lanes (half the registers per lane; FP32 k <= 5) + the separate back-projection,
  *  -1 = warp-per-element kernel and the separate back-projection (no other variant for
  *       this order and precision).
- * ms5 (host, 5 doubles, may be NULL): the autotuner's time per launch of each variant on
+ * ms6 (host, 6 doubles, may be NULL): the autotuner's time per launch of each variant on
  * this mesh in ms, -1 for variants not timed (one variant only, or not available).  No
  * paper counterpart (launch tuning).                                                  */
-hopu_status hopu_tuning_volume(const hopu_ctx* ctx, int* variant, double* ms5);
+hopu_status hopu_tuning_volume(const hopu_ctx* ctx, int* variant, double* ms6);
 
 /* Override the autotuner's STAGE volume variant (the numbering of hopu_tuning_volume;
  * EINVAL for a variant this order and precision does not have).  Drops the cached substep

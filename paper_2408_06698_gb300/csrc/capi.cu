@@ -1020,11 +1020,11 @@ hopu_status hopu_set_l2v_variant(hopu_ctx* c, int tc) {
   return HOPU_OK;
 }
 
-hopu_status hopu_tuning_volume(const hopu_ctx* c, int* variant, double* ms5) {
+hopu_status hopu_tuning_volume(const hopu_ctx* c, int* variant, double* ms6) {
   if (!c || !variant) return HOPU_EINVAL;
   *variant = c->ops ? c->ops->volume_variant() : -1;
-  if (ms5)
-    for (int v = 0; v < kVolVariants; ++v) ms5[v] = c->vol_ms[v];
+  if (ms6)
+    for (int v = 0; v < kVolVariants; ++v) ms6[v] = c->vol_ms[v];
   return HOPU_OK;
 }
 

@@ -29,7 +29,7 @@ struct hopu_ctx {
   Ops* ops = nullptr;
   int nsm = 1, red_blocks = 1;
   double l2v_ms[2] = {-1.0, -1.0};  // autotuner: ms per launch of the FMA / tensor-core back-projection
-  double vol_ms[5] = {-1.0, -1.0, -1.0, -1.0, -1.0};  // autotuner: ms per launch of each STAGE volume variant
+  double vol_ms[6] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0};  // autotuner: ms per launch of each STAGE volume variant
   // device memory
   void* d_mesh = nullptr;   // geo, efc, fa, fb, fgeo
   void* d_geoT = nullptr;   // working-precision geometry factors

@@ -110,7 +110,8 @@ enum VolumeVariant {
   kVolWarpFused = 2,  // warp-per-element kernel, back-projection fused
   kVolTensor = 3,     // tensor-core kernel
   kVolRegTab = 4,     // register kernel with reference-gradient tables + separate back-projection
-  kVolVariants = 5
+  kVolRegHalf = 5,    // register kernel, basis split over two lanes + separate back-projection
+  kVolVariants = 6
 };
 
 // One family of kernels for a fixed (dim, k, precision).  Every call enqueues on the

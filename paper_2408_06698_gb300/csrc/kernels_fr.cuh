@@ -32,7 +32,7 @@ struct FacR {
   static constexpr int O_WF = O_WPSI + NQF * NF4;                // [NQF]
   static constexpr size_t SMEM = size_t(O_WF + r4i(NQF)) * 4;
   static constexpr int REGS = 2 * NB + 5 * NF;                   // coefficients, then the modal vectors
-  static constexpr bool OK = REGS <= 190;
+  static constexpr bool OK = REGS <= 230;
   static constexpr bool OK_WSEP = REGS <= 110;  // with a separate wind the w coefficients add 2 nb registers
   static constexpr int MINB = REGS <= 110 ? 3 : 2;
 };

@@ -102,10 +102,12 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
   bool ok = __syncthreads_and(tc::mbar_wait(mb, 0)) != 0;
   uint32_t phase = 0;
 
-  // this thread's functionals l[s_h] of a tile (codes of that tile in sCode)
-  auto gather = [&](int64_t tile, float* x) {
+  // this thread's functionals l[s_h] of a tile (codes of that tile in sCode), as the raw
+  // V_h values and the orientation signs (bit j of *neg): nothing waits for the loads here
+  auto gather = [&](int64_t tile, float* x, uint32_t* neg) {
     const int64_t e = tile * TM + el;
     const bool in = e < m.E;
+    uint32_t sg = 0;
 #pragma unroll
     for (int j = 0; j < RPG; ++j) {
       const int h = grp + 4 * j;
@@ -115,15 +117,17 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
         if (s < NFL) {
           const int f = s / NF, mm = s - f * NF;
           const int code = sCode[el * (D + 1) + f];
-          const float xv = __ldg(uV + (int64_t)(code >> 2) * NF + mm);
-          v = (code & 2) ? -xv : xv;
+          v = __ldg(uV + (int64_t)(code >> 2) * NF + mm);
+          sg |= (uint32_t)((code >> 1) & 1) << j;
         } else {
           v = __ldg(uV + m.NF * NF + e * NINT + (s - NFL));
         }
       }
       x[j] = v;
     }
+    *neg = sg;
   };
+  static_assert(RPG <= 32, "one sign bit per row");
   auto load_code = [&](int64_t tile) -> int {
     return (tid < TM * (D + 1) && tile * TM + tid / (D + 1) < m.E) ? __ldg(m.efc + tile * TM * (D + 1) + tid) : 0;
   };
@@ -159,7 +163,8 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
     tc::commit(mb + 1);
   };
 
-  float xr[RPG];    // this tile's functionals (exact)
+  float xr[RPG];    // this tile's functionals (exact; raw V_h values until the tile starts)
+  uint32_t xneg = 0;  // their orientation signs
   double gr[GPT];   // this tile's geometry, staged into sGeo at the tile start
   pdl_wait();
   int64_t tile = blockIdx.x;
@@ -168,11 +173,14 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
     if (tid < TM * (D + 1)) sCode[tid] = cd;
     load_geo(tile, gr);
     __syncthreads();
-    gather(tile, xr);
+    gather(tile, xr, &xneg);
   }
   for (; ok && tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * TM;
     const int nrow = (m.E - e0 < TM) ? (int)(m.E - e0) : TM;
+#pragma unroll
+    for (int j = 0; j < RPG; ++j)
+      if ((xneg >> j) & 1u) xr[j] = -xr[j];
 #pragma unroll
     for (int u = 0; u < GPT; ++u)
       if (tid + u * NT < TM * DD) sGeo[tid + u * NT] = float(gr[u]);
@@ -208,8 +216,9 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
     __syncthreads();
     // the next tile's functionals, in flight during the residual
     float xn[RPG];
+    uint32_t xnneg = 0;
     if (nxt < ntiles) {
-      gather(nxt, xn);
+      gather(nxt, xn, &xnneg);
     } else {
 #pragma unroll
       for (int j = 0; j < RPG; ++j) xn[j] = 0.0f;
@@ -295,6 +304,7 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < RPG; ++j) xr[j] = xn[j];
+    xneg = xnneg;
   }
   if (!ok) {
     if (tid == 0) atomicOr(m.err, kErrTcTimeoutV2l);

@@ -10,6 +10,7 @@
 #include "kernels_tcr.cuh"
 #include "kernels_adapt.cuh"
 #include "kernels_vr.cuh"
+#include "kernels_vrh.cuh"
 #include "kernels_fr.cuh"
 
 namespace hopu {
@@ -90,6 +91,9 @@ class OpsImpl final : public Ops {
   static constexpr bool kVolRF = std::is_same<T, float>::value && VolR<D, K>::FUSE_OK;
   static constexpr bool kVolRT = std::is_same<T, float>::value && VolR<D, K, true>::OK;
   int g_volrt_ = 1;
+  // register kernel with the basis split over two lanes
+  static constexpr bool kVolRH = std::is_same<T, float>::value && VolRH<D, K>::OK;
+  int g_volrh_ = 1;
   int g_volr_ = 1, g_volrf_ = 1;
   // register-resident FP32 facet kernel
   static constexpr bool kFacR = std::is_same<T, float>::value && FacR<D, K>::OK;
@@ -172,6 +176,7 @@ class OpsImpl final : public Ops {
       case kVolWarpFused: return kFuse;
       case kVolTensor: return tensor_core_volume();
       case kVolRegTab: return kVolRT;
+      case kVolRegHalf: return kVolRH;
       default: return false;
     }
   }
@@ -180,7 +185,7 @@ class OpsImpl final : public Ops {
   }
   int volume_variant() const override { return vvar_; }
   int default_volume_variant() const {
-    return kVolR ? kVolRegSplit : (kFuse ? kVolWarpFused : -1);
+    return kVolR ? kVolRegSplit : (kVolRH ? kVolRegHalf : (kFuse ? kVolWarpFused : -1));
   }
 
   cudaError_t prepare() override {
@@ -232,6 +237,10 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_volume<D, K, T, true, kVolumeTab, false>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
     if constexpr (kVolR) {
       if ((err = setup(k_volume_r<D, K, false, false>, VolR<D, K>::SMEM, 32 * VolR<D, K>::WARPS, &g_volr_)) != cudaSuccess)
+        return err;
+    }
+    if constexpr (kVolRH) {
+      if ((err = setup(k_volume_rh<D, K>, VolRH<D, K>::SMEM, 32 * VolRH<D, K>::WARPS, &g_volrh_)) != cudaSuccess)
         return err;
     }
     if constexpr (kVolRT) {
@@ -345,6 +354,15 @@ class OpsImpl final : public Ops {
   int volume(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* gam,
              Combine c, void* out, cudaStream_t st) override {
     const bool wsep = (wL != nullptr && wL != uL);
+    if constexpr (kVolRH) {
+      if (!wsep && (vvar_ == kVolRegHalf || !kVolR)) {
+        using R = VolRH<D, K>;
+        const int g = clamp_grid(g_volrh_, (m.E + R::ELW - 1) / R::ELW, 1);
+        launch(k_volume_rh<D, K>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(gam), static_cast<float*>(out), c);
+        return 1;
+      }
+    }
     if constexpr (kVolRT) {
       if (!wsep && vvar_ == kVolRegTab) {
         using R = VolR<D, K, true>;

@@ -255,16 +255,17 @@ class Hopu:
     VOLUME_VARIANTS = {0: "register, fused back-projection", 1: "register + separate back-projection",
                        2: "warp per element, fused back-projection", 3: "tensor cores",
                        4: "register with gradient tables + separate back-projection",
+                       5: "register, basis split over two lanes + separate back-projection",
                        -1: "warp per element + separate back-projection"}
 
     def tuning_volume(self) -> dict:
         """The STAGE volume kernel variant the autotuner kept and its timings (ms per launch)."""
         v = ctypes.c_int()
-        ms = (c_double * 5)()
+        ms = (c_double * 6)()
         self._check(self.lib.hopu_tuning_volume(self.ctx, byref(v), ms), "hopu_tuning_volume")
-        names = ["reg_fused", "reg_split", "warp_fused", "tensor", "reg_tables_split"]
+        names = ["reg_fused", "reg_split", "warp_fused", "tensor", "reg_tables_split", "reg_half_split"]
         return {"variant": v.value, "name": self.VOLUME_VARIANTS.get(v.value, "?"),
-                "ms": {names[i]: ms[i] for i in range(5) if ms[i] >= 0}}
+                "ms": {names[i]: ms[i] for i in range(6) if ms[i] >= 0}}
 
     def set_volume_variant(self, variant: int):
         """Override the autotuner's STAGE volume variant (numbering of tuning_volume)."""

@@ -139,11 +139,12 @@ def test_rk_substep_stage(dim, n, k, prec):
     assert _rel(_host(s3), ref5) < TOL[prec] * 10
 
 
-@pytest.mark.parametrize("dim,n,k", [(2, 6, 2), (2, 4, 4), (3, 3, 2), (3, 3, 3), (3, 3, 4)])
+@pytest.mark.parametrize("dim,n,k", [(2, 6, 2), (2, 4, 4), (3, 3, 2), (3, 3, 3), (3, 3, 4), (3, 3, 5)])
 def test_every_volume_variant_substep(dim, n, k):
     """Every STAGE volume kernel variant the autotuner can choose (FP32) gives the oracle's
     substep: register kernels (modal gradients or gradient tables; back-projection fused or
-    separate), the warp-per-element kernel, the tensor-core kernel (FP32_TC)."""
+    separate; the basis on one lane or split over two), the warp-per-element kernel, the
+    tensor-core kernel (FP32_TC)."""
     from paper_2408_06698_gb300._lib import HopuError
     uV = None
     seen = 0
@@ -152,7 +153,7 @@ def test_every_volume_variant_substep(dim, n, k):
         if uV is None:
             uV = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-3, 0))
             ref = rk.substeps_stage(sp, uV, 1e-2, 1, k - 1)
-        for v in range(5):
+        for v in range(6):
             try:
                 g.set_volume_variant(v)
             except HopuError:
@@ -167,7 +168,7 @@ def test_every_volume_variant_substep(dim, n, k):
             print(f"d={dim} k={k} {prec} volume variant {v}: substep error {err:.2e}")
             assert err < 2e-6, (v, err)
             seen += 1
-    assert seen >= 2
+    assert seen >= (1 if k == 5 else 2)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -311,3 +312,28 @@ def test_measured_alu_peaks_are_plausible():
     print(f"measured FMA peaks: FP32 {f32:.1f} TFLOP/s, FP64 {f64:.2f} TFLOP/s")
     assert 40.0 < f32 < 89.0
     assert 0.0 < f64 < 0.5 * f32
+
+
+@pytest.mark.parametrize("n,k", [(32, 4), (20, 5)])
+def test_split_lane_volume_kernel_full_size(n, k):
+    """The register volume kernel with the basis split over two lanes (variant 5) on a
+    full-size box (32^3 k = 4: 196,608 elements; 20^3 k = 5: 48,000): one STAGE substep
+    against the FP64 path on the same FP32-rounded state, beside the autotuned FP32 one."""
+    from paper_2408_06698_gb300 import Hopu
+    m = W.periodic_box_mesh(3, n)
+    a = Hopu(m.coords, m.elems, m.rep, k=k, l=k - 1, prec="f32")
+    a.set_volume_variant(5)
+    b = Hopu(m.coords, m.elems, m.rep, k=k, l=k - 1, prec="f32")
+    c = Hopu(m.coords, m.elems, m.rep, k=k, l=k - 1, prec="f64")
+    u = c.interpolate_function(W.taylor_green)
+    u += torch.as_tensor(W.uniform_noise(c.n_hdiv, 1e-3, 0), device=c.device)
+    xa, xb, xc = u.float().clone(), u.float().clone(), u.float().double().clone()
+    a.rk_substep(xa, 5e-4, 1)
+    b.rk_substep(xb, 5e-4, 1)
+    c.rk_substep(xc, 5e-4, 1)
+    a.sync()
+    ea = float((xa.double() - xc).abs().max() / xc.abs().max())
+    eb = float((xb.double() - xc).abs().max() / xc.abs().max())
+    print(f"{n}^3 k={k} substep vs FP64: split-lane volume kernel {ea:.2e}, autotuned "
+          f"({b.tuning_volume()['name']}) {eb:.2e}")
+    assert ea < 4e-7 and eb < 4e-7
