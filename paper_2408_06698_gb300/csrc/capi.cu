@@ -300,7 +300,7 @@ void free_all(hopu_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   void* ptrs[] = {c->d_elog_pos, c->d_mesh, c->d_geoT, c->d_tabs, c->d_gam, c->d_lf, c->d_uL, c->d_yL, c->d_wL,
                   c->d_wfz, c->d_s1, c->d_s2, c->d_diss, c->d_red, c->d_gamW, c->d_adj, c->d_err, c->d_tcvol,
-                  c->d_inlet, c->d_inlet_modes, c->d_csr, c->d_tcl2v, c->d_tcv2l};
+                  c->d_inlet, c->d_inlet_modes, c->d_csr, c->d_tcl2v, c->d_tcv2l, c->d_csr_tc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c->ops;
@@ -401,8 +401,8 @@ void kernel_tables(const RefTables& R, bool fp64, std::vector<std::vector<double
 }
 
 // The nonzeros of the dof matrix D (row s = functional, column r = basis function b*nb + i)
-// for the residual of the refined FP32 projection: nloc row headers {s, first entry, count, 0}
-// (int32 bits) sorted by count, largest first, then one entry {r (int32 bits), hi, lo, 0}
+// for the residual of the refined FP32 projection: nloc row headers {s, first entry, count,
+// grouped} (int32 bits) sorted by count, largest first, then one entry {r (int32 bits), hi, lo, 0}
 // per nonzero with hi = float(D[s][r]), lo = float(D[s][r] - hi).  Entries below 1e-13 of
 // max |D| are the exact zeros of the orthogonality relations, rounded by the quadrature.
 std::vector<std::vector<std::pair<int, double>>> dof_matrix_rows(const RefTables& R) {
@@ -418,19 +418,53 @@ std::vector<std::vector<std::pair<int, double>>> dof_matrix_rows(const RefTables
   return rows;
 }
 
-// The order of the CSR rows: by number of nonzeros, largest first (stable).
-std::vector<int> csr_row_order(const RefTables& R) {
-  const auto rows = dof_matrix_rows(R);
+// Rows whose dim component blocks are equal entry by entry (the facet whose reference
+// normal has equal components: D[s][b nb + i] = T[s][i] for every b) are grouped: only
+// block 0's nonzeros are kept (column i < nb) and D Y for the row is sum_i T[s][i] S_i with
+// S_i = sum_b Y[b nb + i].  Used by the refined tensor-core projection only.
+std::vector<bool> grouped_rows(const RefTables& R) {
+  const int nl = R.nloc, nb = R.nb, d = R.dim;
+  std::vector<bool> g(nl, false);
+  for (int s = 0; s < nl; ++s) {
+    bool eq = true;
+    for (int i = 0; i < nb && eq; ++i)
+      for (int b = 1; b < d; ++b)
+        if (R.D[(size_t)s * nl + b * nb + i] != R.D[(size_t)s * nl + i]) eq = false;
+    g[s] = eq;
+  }
+  return g;
+}
+
+// The order of the CSR rows: by number of stored nonzeros, largest first (stable).
+std::vector<int> csr_row_order(const RefTables& R, bool grouped) {
+  auto rows = dof_matrix_rows(R);
+  const std::vector<bool> g = grouped ? grouped_rows(R) : std::vector<bool>(R.nloc, false);
+  std::vector<size_t> cnt(R.nloc);
+  for (int s = 0; s < R.nloc; ++s) {
+    size_t c = 0;
+    for (const auto& e : rows[s]) c += (!g[s] || e.first < R.nb);
+    cnt[s] = c;
+  }
   std::vector<int> order(R.nloc);
   for (int s = 0; s < R.nloc; ++s) order[s] = s;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a].size() > rows[b].size(); });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
   return order;
 }
 
-void dof_matrix_csr(const RefTables& R, std::vector<float>& out) {
+// grouped: rows with equal component blocks keep block 0 only and carry the flag 1 in the
+// fourth header word.
+void dof_matrix_csr(const RefTables& R, std::vector<float>& out, bool grouped = false) {
   const int nl = R.nloc;
-  const auto rows = dof_matrix_rows(R);
-  const std::vector<int> order = csr_row_order(R);
+  auto rows = dof_matrix_rows(R);
+  const std::vector<int> order = csr_row_order(R, grouped);
+  const std::vector<bool> g = grouped ? grouped_rows(R) : std::vector<bool>(nl, false);
+  for (int s = 0; s < nl; ++s)
+    if (g[s]) {
+      std::vector<std::pair<int, double>> keep;
+      for (const auto& e : rows[s])
+        if (e.first < R.nb) keep.push_back(e);
+      rows[s] = keep;
+    }
   size_t nnz = 0;
   for (const auto& r : rows) nnz += r.size();
   out.assign(4 * (nl + nnz), 0.0f);
@@ -441,6 +475,7 @@ void dof_matrix_csr(const RefTables& R, std::vector<float>& out) {
     put_int(4 * h, s);
     put_int(4 * h + 1, next);
     put_int(4 * h + 2, (int)rows[s].size());
+    put_int(4 * h + 3, g[s] ? 1 : 0);
     for (const auto& e : rows[s]) {
       const float hi = (float)e.second;
       put_int(4 * (size_t)next, e.first);
@@ -513,7 +548,7 @@ void tensor_core_l2v_table(const RefTables& R, std::vector<float>& out) {
 // parts, blocked K-major as above.
 void tensor_core_v2l_table(const RefTables& R, std::vector<float>& out) {
   const int nl = R.nloc, GW = v2l_tc_gw(nl), KP = v2l_tc_kp(nl), NP = (nl + 15) / 16 * 16;
-  const std::vector<int> order = csr_row_order(R);
+  const std::vector<int> order = csr_row_order(R, true);
   const size_t P = (size_t)NP * KP;
   out.assign(2 * P, 0.0f);
   auto off = [&](int row, int col) {
@@ -908,6 +943,12 @@ hopu_status create_impl(const hopu_mesh_desc* mesh, const hopu_options* opts, vo
     c->dt.tcvol = c->d_tcvol;
   }
   if (c->ops->tensor_cores() && c->prec == HOPU_FP32_TC) {
+    std::vector<float> csr;
+    dof_matrix_csr(R, csr, true);
+    HOPU_CUDA(c, cudaMalloc(&c->d_csr_tc, csr.size() * sizeof(float)));
+    HOPU_CUDA(c, cudaMemcpy(c->d_csr_tc, csr.data(), csr.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->dt.Dcsr_tc = c->d_csr_tc;
+    c->dt.csr_tc_n = (int)(csr.size() / 4);
     std::vector<float> tv;
     tensor_core_v2l_table(R, tv);
     HOPU_CUDA(c, cudaMalloc(&c->d_tcv2l, tv.size() * sizeof(float)));

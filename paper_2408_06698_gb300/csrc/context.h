@@ -36,6 +36,7 @@ struct hopu_ctx {
   void* d_tabs = nullptr;   // every reference table
   void* d_tcvol = nullptr;  // tensor-core volume tables (FP32 tensor-core modes)
   void* d_tcv2l = nullptr;  // tensor-core refined projection table (HOPU_FP32_TC)
+  void* d_csr_tc = nullptr; // its CSR of D with grouped rows
   void* d_tcl2v = nullptr;  // tensor-core back-projection table (FP32 tensor-core modes)
   void* d_csr = nullptr;    // FP32: nonzeros of the dof matrix D (refined projection)
   void* d_gam = nullptr;    // [E][d+1][nf][d] signed facet flux moments, element-major

@@ -44,6 +44,8 @@ struct DevTabs {
   const void* Dcsr = nullptr;   // FP32: the nonzeros of D by rows, 16-byte entries (layout in
                                 //   k_v2l / warp_tile_residual); csr_n entries in all
   int csr_n = 0;
+  const void* Dcsr_tc = nullptr;  // FP32_TC: the same with grouped rows (rows whose component blocks are
+  int csr_tc_n = 0;               //   equal keep block 0 only, flag 1 in the header's fourth word)
   const void* DT = nullptr;     // [nloc][nlp]     DT[s][r]    = D[r][s]
   const void* Dinv = nullptr;   // [nloc][nlp]     Dinv[s][r]
   const void* Dn = nullptr;     // [nloc][nlp]     Dn[s][r] = D[s][r]

@@ -15,7 +15,9 @@
 //        basis is ill-conditioned on the high-degree modes, which a plain FP32 or 3xTF32
 //        product loses): Y0 staged in shared memory (odd row stride), the CSR rows of D in
 //        shared memory (every lane of a warp reads the same entry), the sum D Y0 formed
-//        from zero and X entering last by TwoSum;
+//        from zero and X entering last by TwoSum; rows whose component blocks are equal
+//        (the facet with the normal of equal components) are stored once and contracted
+//        with S_i = sum_b Y0[b nb + i], formed per element as an exact pair by TwoSum;
 //   Y  = Y0 + R Dinv^T: a second 3xTF32 MMA with R in TMEM in X's columns into a second
 //        accumulator, added to the staged Y0 in FP32 (one rounding: accumulating the small
 //        correction onto Y0 inside the tensor core would round Y at every MMA);
@@ -48,7 +50,11 @@ struct V2lTcr {
   static constexpr size_t O_ST = 2 * B_BYTES;
   static constexpr size_t O_CODE = O_ST + (size_t(TM) * SST * 4 + 15) / 16 * 16;
   static constexpr size_t O_GEO = O_CODE + size_t(TM) * (D + 1) * 4;
-  static constexpr size_t O_BAR = O_GEO + (size_t(TM) * D * D * 4 + 15) / 16 * 16;
+  static constexpr int NB = S::nb;
+  static constexpr int SS = 2 * NB + 1;               // S pairs row stride (odd: conflict-free)
+  static constexpr int IPG = (NB + 3) / 4;            // S entries formed per thread
+  static constexpr size_t O_S = O_GEO + (size_t(TM) * D * D * 4 + 15) / 16 * 16;
+  static constexpr size_t O_BAR = O_S + (size_t(TM) * SS * 4 + 15) / 16 * 16;
   static constexpr size_t O_CSR = O_BAR + 32;         // the CSR of D (csr_n 16-byte entries) last
   static constexpr size_t smem(int csr_n) { return O_CSR + size_t(csr_n) * 16; }
   static constexpr bool OK = smem(NL) <= 227 * 1024 && NP <= 256 && TEND <= 512 && (2 * B_BYTES) % 16 == 0 &&
@@ -71,6 +77,7 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
   float* stage = reinterpret_cast<float*>(smem_raw + C::O_ST);        // [TM][SST]  Y0, then Y
   int* sCode = reinterpret_cast<int*>(smem_raw + C::O_CODE);          // [TM][D+1]  next tile's codes
   float* sGeo = reinterpret_cast<float*>(smem_raw + C::O_GEO);        // [TM][D*D]  Pf = J / det J
+  float* sS = reinterpret_cast<float*>(smem_raw + C::O_S);            // [TM][SS]   S_i (hi, lo)
   uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::O_BAR);    // [0] tables, [1] MMAs
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mb + 2);
   float4* sCsr = reinterpret_cast<float4*>(smem_raw + C::O_CSR);
@@ -214,6 +221,29 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
     if (tid < TM * (D + 1)) sCode[tid] = cdn;
     tc::fence_before_sync();
     __syncthreads();
+    // S_i = sum_b Y0[b nb + i] as an exact pair (hi, lo) for the grouped rows: thread (q, g)
+    // forms the entries i = g IPG .. of its element
+    {
+      const float* y = stage + el * SST;
+#pragma unroll
+      for (int t2 = 0; t2 < C::IPG; ++t2) {
+        const int i = grp * C::IPG + t2;
+        if (i < NB) {
+          float hi = y[i], lo = 0.0f;
+#pragma unroll
+          for (int b = 1; b < D; ++b) {
+            const float v = y[b * NB + i];
+            const float t = __fadd_rn(hi, v);
+            const float z = __fsub_rn(t, hi);
+            lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(v, z)));
+            hi = t;
+          }
+          sS[el * C::SS + 2 * i] = hi;
+          sS[el * C::SS + 2 * i + 1] = lo;
+        }
+      }
+    }
+    __syncthreads();
     // the next tile's functionals, in flight during the residual
     float xn[RPG];
     uint32_t xnneg = 0;
@@ -223,13 +253,20 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
 #pragma unroll
       for (int j = 0; j < RPG; ++j) xn[j] = 0.0f;
     }
-    // R = X - D Y0 (Dot2), TF32 parts into X's TMEM columns, four rows at a time
+    // R = X - D Y0 (Dot2), TF32 parts into X's TMEM columns, four rows at a time.  Only the
+    // four rows of a group are unrolled (the row bodies hold data-dependent loops: unrolling
+    // all of them overflows the instruction cache); the group's X values are the first four
+    // of the register array, which moves down by four after every group.
     {
       const float* y0 = stage + el * SST;
       const bool in = el < nrow;
-#pragma unroll
+#pragma unroll 1
       for (int c0 = 0; c0 < GW; c0 += 4) {
-        float h4[4], l4[4];
+        float h4[4], l4[4], x4[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) x4[jj] = (jj < RPG) ? xr[jj < RPG ? jj : 0] : 0.0f;
+#pragma unroll
+        for (int j2 = 0; j2 + 4 < RPG; ++j2) xr[j2] = xr[j2 + 4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
           const int j = c0 + jj, h = grp + 4 * j;
@@ -241,20 +278,41 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
             float a = 0.0f, c = 0.0f, a1 = 0.0f, c1 = 0.0f;
             const int kend = hd.y + hd.z;
             int k = hd.y;
+            if (hd.w) {  // grouped row: entries (i, T) against the pairs S_i
+              const float* sp = sS + el * C::SS;
 #pragma unroll 2
-            for (; k + 1 < kend; k += 2) {
-              const float4 e0 = sCsr[k], e1 = sCsr[k + 1];
-              const float v0 = y0[__float_as_int(e0.x)], v1 = y0[__float_as_int(e1.x)];
-              dot2_step(a, c, e0.y, v0);
-              dot2_step(a1, c1, e1.y, v1);
-              c = __fmaf_rn(e0.z, v0, c);
-              c1 = __fmaf_rn(e1.z, v1, c1);
-            }
-            if (k < kend) {
-              const float4 e0 = sCsr[k];
-              const float v0 = y0[__float_as_int(e0.x)];
-              dot2_step(a, c, e0.y, v0);
-              c = __fmaf_rn(e0.z, v0, c);
+              for (; k + 1 < kend; k += 2) {
+                const float4 e0 = sCsr[k], e1 = sCsr[k + 1];
+                const int i0 = 2 * __float_as_int(e0.x), i1 = 2 * __float_as_int(e1.x);
+                const float v0 = sp[i0], w0 = sp[i0 + 1], v1 = sp[i1], w1 = sp[i1 + 1];
+                dot2_step(a, c, e0.y, v0);
+                dot2_step(a1, c1, e1.y, v1);
+                c = __fmaf_rn(e0.y, w0, __fmaf_rn(e0.z, v0, c));
+                c1 = __fmaf_rn(e1.y, w1, __fmaf_rn(e1.z, v1, c1));
+              }
+              if (k < kend) {
+                const float4 e0 = sCsr[k];
+                const int i0 = 2 * __float_as_int(e0.x);
+                const float v0 = sp[i0], w0 = sp[i0 + 1];
+                dot2_step(a, c, e0.y, v0);
+                c = __fmaf_rn(e0.y, w0, __fmaf_rn(e0.z, v0, c));
+              }
+            } else {
+#pragma unroll 2
+              for (; k + 1 < kend; k += 2) {
+                const float4 e0 = sCsr[k], e1 = sCsr[k + 1];
+                const float v0 = y0[__float_as_int(e0.x)], v1 = y0[__float_as_int(e1.x)];
+                dot2_step(a, c, e0.y, v0);
+                dot2_step(a1, c1, e1.y, v1);
+                c = __fmaf_rn(e0.z, v0, c);
+                c1 = __fmaf_rn(e1.z, v1, c1);
+              }
+              if (k < kend) {
+                const float4 e0 = sCsr[k];
+                const float v0 = y0[__float_as_int(e0.x)];
+                dot2_step(a, c, e0.y, v0);
+                c = __fmaf_rn(e0.z, v0, c);
+              }
             }
             {
               const float t = __fadd_rn(a, a1);
@@ -264,7 +322,7 @@ __global__ void __launch_bounds__(512, 1) k_v2l_tcr(DevMesh m, const float* __re
               c = __fadd_rn(c, __fadd_rn(c1, te));
             }
             // r = x - (a + c): t + te = x - a exactly (TwoSum), then the small parts
-            const float x = xr[j];
+            const float x = x4[jj];
             const float t = __fsub_rn(x, a);
             const float z = __fsub_rn(t, x);
             const float te = __fadd_rn(__fsub_rn(x, __fsub_rn(t, z)), __fsub_rn(-a, z));

@@ -267,7 +267,7 @@ class OpsImpl final : public Ops {
   cudaError_t configure(const DevTabs& t) override {
     if constexpr (kTcV2lR) {
       if (tc_ == 3) {
-        const size_t sm = V2lTcr<D, K>::smem(t.csr_n);
+        const size_t sm = V2lTcr<D, K>::smem(t.csr_tc_n);
         tcr_fits_ = sm <= 227 * 1024;
         if (tcr_fits_) {
           cudaError_t err = setup(k_v2l_tcr<D, K>, sm, V2lTcr<D, K>::THREADS, &g_v2l_tcr_, true);
@@ -290,10 +290,10 @@ class OpsImpl final : public Ops {
 
   int v2l(const DevMesh& m, const DevTabs& t, const void* uV, void* uL, cudaStream_t st) override {
     if constexpr (kTcV2lR) {
-      if (tc_ == 3 && tcr_fits_ && use_tc_v2l_ && t.tcv2l) {
+      if (tc_ == 3 && tcr_fits_ && use_tc_v2l_ && t.tcv2l && t.Dcsr_tc) {
         const int g = clamp_grid(g_v2l_tcr_, m.E, V2lTcr<D, K>::TM);
-        launch(k_v2l_tcr<D, K>, g, V2lTcr<D, K>::THREADS, V2lTcr<D, K>::smem(t.csr_n), st, m,
-               static_cast<const float*>(t.tcv2l), static_cast<const float4*>(t.Dcsr), t.csr_n,
+        launch(k_v2l_tcr<D, K>, g, V2lTcr<D, K>::THREADS, V2lTcr<D, K>::smem(t.csr_tc_n), st, m,
+               static_cast<const float*>(t.tcv2l), static_cast<const float4*>(t.Dcsr_tc), t.csr_tc_n,
                static_cast<const float*>(uV), static_cast<float*>(uL));
         return 1;
       }
