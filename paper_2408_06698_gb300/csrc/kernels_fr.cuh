@@ -97,7 +97,13 @@ __global__ void __launch_bounds__(32 * FacR<D, K>::WARPS, FacR<D, K>::MINB)
     const int inl = m.inlet ? m.inlet[F] : -1;
     const float* ext = inl >= 0 ? static_cast<const float*>(m.inlet_modes) + (int64_t)inl * NF * D : nullptr;
     // modal traces of component a: jump J and averaged wind Wv
-    float J[NF], Wv[NF];
+    // modes in groups of MG (a rolled loop: the unrolled trace phase of every mode did not
+    // fit the instruction cache beside the point loop); J and Wv stay in registers, moving
+    // down by MG after every group and taking the new group at their end
+    constexpr int MG = 5, NGRP = (NF + MG - 1) / MG, NFP = NGRP * MG;
+    float J[NFP], Wv[NFP];
+#pragma unroll
+    for (int t = 0; t < NFP; ++t) J[t] = Wv[t] = 0.0f;
     {
       float cA[NB], cB[NB];
       const float* ua = uL + eA * NL + a * NB;
@@ -109,35 +115,51 @@ __global__ void __launch_bounds__(32 * FacR<D, K>::WARPS, FacR<D, K>::MINB)
       }
       const float* trA = sTrM + fA * NF * NB4;
       const float* trB = sTrM + fB * NF * NB4;
+#pragma unroll 1
+      for (int g5 = 0; g5 < NGRP; ++g5) {
+        float J5[MG], W5[MG];
 #pragma unroll
-      for (int mm = 0; mm < NF; ++mm) {
-        float sa = 0.0f, ca = 0.0f, pa_ = 0.0f, sb = 0.0f, cb = 0.0f, pb_ = 0.0f;
+        for (int t = 0; t < MG; ++t) {
+          const int mm = g5 * MG + t;
+          const int mr = mm < NF ? mm : NF - 1;
+          float sa = 0.0f, ca = 0.0f, pa_ = 0.0f, sb = 0.0f, cb = 0.0f, pb_ = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NB; i += 4) {
-          float ta[4], tbv[4];
-          lds_v(trA + mm * NB4 + i, ta);
-          lds_v(trB + mm * NB4 + i, tbv);
+          for (int i = 0; i < NB; i += 4) {
+            float ta[4], tbv[4];
+            lds_v(trA + mr * NB4 + i, ta);
+            lds_v(trB + mr * NB4 + i, tbv);
 #pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const int idx = i + w;
-            if (idx < D + 1) {
-              dot2_step(sa, ca, ta[w], cA[idx]);
-              dot2_step(sb, cb, tbv[w], cB[idx]);
-            } else if (idx < NB) {
-              pa_ = fmaf(ta[w], cA[idx], pa_);
-              pb_ = fmaf(tbv[w], cB[idx], pb_);
+            for (int w = 0; w < 4; ++w) {
+              const int idx = i + w;
+              if (idx < D + 1) {
+                dot2_step(sa, ca, ta[w], cA[idx]);
+                dot2_step(sb, cb, tbv[w], cB[idx]);
+              } else if (idx < NB) {
+                pa_ = fmaf(ta[w], cA[idx], pa_);
+                pb_ = fmaf(tbv[w], cB[idx], pb_);
+              }
             }
           }
+          ca = __fadd_rn(ca, pa_);
+          cb = __fadd_rn(cb, pb_);
+          if (ext) {
+            sb = ext[mr * D + a];
+            cb = 0.0f;
+          }
+          const float ta_ = __fadd_rn(sa, ca), tb_ = __fadd_rn(sb, cb);
+          J5[t] = mm < NF ? __fadd_rn(__fsub_rn(sa, sb), __fsub_rn(ca, cb)) : 0.0f;
+          W5[t] = mm < NF ? (ext ? ta_ : 0.5f * (ta_ + tb_)) : 0.0f;  // an inlet keeps the wind's own trace
         }
-        ca = __fadd_rn(ca, pa_);
-        cb = __fadd_rn(cb, pb_);
-        if (ext) {
-          sb = ext[mm * D + a];
-          cb = 0.0f;
+#pragma unroll
+        for (int t = 0; t + MG < NFP; ++t) {
+          J[t] = J[t + MG];
+          Wv[t] = Wv[t + MG];
         }
-        const float ta_ = __fadd_rn(sa, ca), tb_ = __fadd_rn(sb, cb);
-        J[mm] = __fadd_rn(__fsub_rn(sa, sb), __fsub_rn(ca, cb));
-        Wv[mm] = ext ? ta_ : 0.5f * (ta_ + tb_);  // an inlet keeps the wind's own trace
+#pragma unroll
+        for (int t = 0; t < MG; ++t) {
+          J[NFP - MG + t] = J5[t];
+          Wv[NFP - MG + t] = W5[t];
+        }
       }
     }
     if (WSEP) {  // the wind's traces from its own coefficients
