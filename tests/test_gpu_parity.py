@@ -268,10 +268,11 @@ def test_c3_size_taylor_green_apply():
     """32^3 x 6 tetrahedra, k = 4, l = 3 (the precision workload, 196,608 elements).
 
     Element by element against the oracle on 600 seeded sampled elements (the oracle
-    evaluates them exactly on the sub-mesh of their facet neighbourhood), in FP64 and in
-    FP32; then every output of the FP32 apply against the FP64 GPU apply on the same
-    rounded inputs.  Bounds: 1e-12 (FP64), 1e-6 (FP32), relative to the largest
-    reference entry, and 1e-6 normwise for the full comparison.
+    evaluates them exactly on the sub-mesh of their facet neighbourhood), in FP64, FP32 and
+    HOPU_FP32_TC (the wind's projection on the tensor cores); then every output of the two
+    FP32 modes' applies against the FP64 GPU apply on the same rounded inputs.  Bounds:
+    1e-12 (FP64), 1e-6 (FP32 modes), relative to the largest reference entry, and 1e-6
+    normwise for the full comparison.
     """
     from paper_2408_06698_gb300 import Hopu
     from oracle.sampled import sampled_apply
@@ -279,6 +280,8 @@ def test_c3_size_taylor_green_apply():
     m = W.periodic_box_mesh(3, 32)
     g64 = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec="f64")
     g32 = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec="f32")
+    gtc = Hopu(m.coords, m.elems, m.rep, k=k, l=l, prec="f32_tc")
+    assert gtc.tuning()["v2l"] == "tc"
     topo = mesh.MeshTopo(m.coords, m.elems, m.rep)
     sp = hdiv.HDiv(topo, fe.ref_element(3, k))
     u = g64.interpolate_function(W.taylor_green)
@@ -289,17 +292,18 @@ def test_c3_size_taylor_green_apply():
     sample = np.random.default_rng(5).choice(topo.n_elems, 600, replace=False)
     ref = sampled_apply(m.coords, m.elems, m.rep, topo, sp.ref, wL, uL, l, sample)
     ys = {}
-    for prec, g in (("f64", g64), ("f32", g32)):
+    for prec, g in (("f64", g64), ("f32", g32), ("f32_tc", gtc)):
         y = _host(g.apply_convection(_dev(g, uV), _dev(g, uL))).reshape(topo.n_elems, 3, -1)
         ys[prec] = y
         err = _rel(y[sample], ref)
         print(f"32^3 k=4 {prec} apply vs oracle on {len(sample)} sampled elements: {err:.2e}")
-        assert err < TOL[prec], (prec, err)
-    d = ys["f32"] - ys["f64"]
-    mx = float(np.abs(d).max() / np.abs(ys["f64"]).max())
-    l2 = float(np.linalg.norm(d) / np.linalg.norm(ys["f64"]))
-    print(f"32^3 k=4 FP32 vs FP64 GPU apply, every output: max {mx:.2e}, L2 {l2:.2e}")
-    assert mx < TOL["f32"] and l2 < TOL["f32"], (mx, l2)
+        assert err < TOL["f64" if prec == "f64" else "f32"], (prec, err)
+    for prec in ("f32", "f32_tc"):
+        d = ys[prec] - ys["f64"]
+        mx = float(np.abs(d).max() / np.abs(ys["f64"]).max())
+        l2 = float(np.linalg.norm(d) / np.linalg.norm(ys["f64"]))
+        print(f"32^3 k=4 {prec} vs FP64 GPU apply, every output: max {mx:.2e}, L2 {l2:.2e}")
+        assert mx < TOL["f32"] and l2 < TOL["f32"], (prec, mx, l2)
 
 
 def test_measured_alu_peaks_are_plausible():
