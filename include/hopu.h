@@ -92,14 +92,16 @@ typedef enum {
   HOPU_FP32 = 1,     /* FP32 coefficients, FP32 FMA arithmetic; the V_h -> L2 projection and
                         the facet traces of the jump as compensated FP32 dot products (as if
                         in twice the working precision), the geometry kept in FP64            */
-  HOPU_FP32_TC = 2,  /* as HOPU_FP32, with the volume contractions of the STAGE substep on the
-                        tensor cores in 3xTF32 (hi*hi + hi*lo + lo*hi, FP32 accumulation);
-                        the V_h -> L2 projection stays the compensated FP32 product (on the
-                        tensor cores its FP32 accumulation would lose the small high-degree
-                        coefficients of smooth fields)                                      */
-  HOPU_TF32 = 3      /* FP32 coefficients; the V_h -> L2 projection GEMM and the STAGE volume
-                        contractions on the tensor cores with one TF32 product (about 1e-3
-                        relative); FP32 FMA elsewhere                                       */
+  HOPU_FP32_TC = 2,  /* as HOPU_FP32, with dense contractions on the tensor cores in 3xTF32
+                        (hi*hi + hi*lo + lo*hi, FP32 accumulation) where the autotuner finds
+                        them faster: the two dense products of the refined V_h -> L2
+                        projection (its residual stays compensated FP32 on the CUDA cores,
+                        so the projection keeps the accuracy of HOPU_FP32), the element part
+                        of the back-projection, and the STAGE volume contractions (3D k <= 3)
+                                                                                            */
+  HOPU_TF32 = 3      /* FP32 coefficients; the V_h -> L2 projection GEMM, the back-projection
+                        and the STAGE volume contractions on the tensor cores with one TF32
+                        product (about 1e-3 relative); FP32 FMA elsewhere                    */
 } hopu_prec;
 
 typedef enum {
