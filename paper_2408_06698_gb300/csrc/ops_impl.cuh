@@ -11,6 +11,7 @@
 #include "kernels_adapt.cuh"
 #include "kernels_vr.cuh"
 #include "kernels_vrh.cuh"
+#include "kernels_var.cuh"
 #include "kernels_fr.cuh"
 
 namespace hopu {
@@ -94,6 +95,9 @@ class OpsImpl final : public Ops {
   // register kernel with the basis split over two lanes
   static constexpr bool kVolRH = std::is_same<T, float>::value && VolRH<D, K>::OK;
   int g_volrh_ = 1;
+  // register-resident adjoint volume kernel (w = u)
+  static constexpr bool kVolAR = std::is_same<T, float>::value && VolAR<D, K>::OK;
+  int g_volar_ = 1;
   int g_volr_ = 1, g_volrf_ = 1;
   // register-resident FP32 facet kernel
   static constexpr bool kFacR = std::is_same<T, float>::value && FacR<D, K>::OK;
@@ -237,6 +241,10 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_volume<D, K, T, true, kVolumeTab, false>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
     if constexpr (kVolR) {
       if ((err = setup(k_volume_r<D, K, false, false>, VolR<D, K>::SMEM, 32 * VolR<D, K>::WARPS, &g_volr_)) != cudaSuccess)
+        return err;
+    }
+    if constexpr (kVolAR) {
+      if ((err = setup(k_volume_adj_r<D, K>, VolAR<D, K>::SMEM, 32 * VolAR<D, K>::WARPS, &g_volar_)) != cudaSuccess)
         return err;
     }
     if constexpr (kVolRH) {
@@ -429,6 +437,16 @@ class OpsImpl final : public Ops {
   int volume_adj(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* ybar,
                  const void* gamU, const void* gamW, void* ubar, void* wbar, cudaStream_t st) override {
     const bool wsep = (wL != nullptr && wL != uL);
+    if constexpr (kVolAR) {
+      if (!wsep) {
+        using R = VolAR<D, K>;
+        const int g = clamp_grid(g_volar_, (m.E + R::ELW - 1) / R::ELW, 1);
+        launch(k_volume_adj_r<D, K>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(ybar), static_cast<const float*>(gamU), static_cast<const float*>(gamW),
+               static_cast<float*>(ubar));
+        return 1;
+      }
+    }
     const int g = clamp_grid(g_vadj_, m.E, kWarps);
     if (wsep)
       launch(k_volume_adj<D, K, T, true>, g, 32 * kWarps, volume_adj_smem(true), st, 
