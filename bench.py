@@ -623,7 +623,7 @@ def our_arm(args, rank, world):
     vjp = None
     if not args.no_vjp:
         mv = W.periodic_box_mesh(3, 24)
-        gv = Hopu(mv.coords, mv.elems, mv.rep, k=3, l=2, prec="f32", device=dev)
+        gv = Hopu(mv.coords, mv.elems, mv.rep, k=3, l=2, prec=HEADLINE_PREC, device=dev)
         uv = gv.interpolate_function(W.taylor_green)
         uv += torch.as_tensor(W.uniform_noise(gv.n_hdiv, 1e-3, 0), device=dev).float()
         with torch.cuda.stream(stream):
@@ -636,7 +636,7 @@ def our_arm(args, rank, world):
             t1.record(stream)
         stream.synchronize()
         vms = max_over_ranks(t0.elapsed_time(t1), world)
-        vjp = {"workload": "24^3 x 6 tets (82,944 elements), k=3, l=2, FP32, 200 STAGE substeps dt=5e-4, "
+        vjp = {"workload": "24^3 x 6 tets (82,944 elements), k=3, l=2, HOPU_FP32_TC, 200 STAGE substeps dt=5e-4, "
                            "loss = final kinetic energy, checkpoints every 20 substeps",
                "ms_rollout_and_adjoint": vms, "loss": loss_v,
                "dof_updates_per_s_forward_equivalent": gv.n_l2 * APPLIES_PER_STEP * 200 / (vms / 1e3)}

@@ -12,6 +12,7 @@
 #include "kernels_vr.cuh"
 #include "kernels_vrh.cuh"
 #include "kernels_var.cuh"
+#include "kernels_far.cuh"
 #include "kernels_fr.cuh"
 
 namespace hopu {
@@ -98,6 +99,9 @@ class OpsImpl final : public Ops {
   // register-resident adjoint volume kernel (w = u)
   static constexpr bool kVolAR = std::is_same<T, float>::value && VolAR<D, K>::OK;
   int g_volar_ = 1;
+  // register-resident adjoint facet kernel (w = u)
+  static constexpr bool kFacAR = std::is_same<T, float>::value && FacAR<D, K>::OK;
+  int g_facar_ = 1;
   int g_volr_ = 1, g_volrf_ = 1;
   // register-resident FP32 facet kernel
   static constexpr bool kFacR = std::is_same<T, float>::value && FacR<D, K>::OK;
@@ -241,6 +245,10 @@ class OpsImpl final : public Ops {
     if ((err = setup(k_volume<D, K, T, true, kVolumeTab, false>, volume_smem(true), th, &g_vol_[1])) != cudaSuccess) return err;
     if constexpr (kVolR) {
       if ((err = setup(k_volume_r<D, K, false, false>, VolR<D, K>::SMEM, 32 * VolR<D, K>::WARPS, &g_volr_)) != cudaSuccess)
+        return err;
+    }
+    if constexpr (kFacAR) {
+      if ((err = setup(k_facet_adj_r<D, K>, FacAR<D, K>::SMEM, 32 * FacAR<D, K>::WARPS, &g_facar_)) != cudaSuccess)
         return err;
     }
     if constexpr (kVolAR) {
@@ -422,6 +430,15 @@ class OpsImpl final : public Ops {
   int facet_adj(const DevMesh& m, const DevTabs& t, const void* uL, const void* wL, const void* ybar, int l,
                 const int8_t* facet_l, void* gamU, void* gamW, cudaStream_t st) override {
     const bool wsep = (wL != nullptr && wL != uL);
+    if constexpr (kFacAR) {
+      if (!wsep) {
+        using R = FacAR<D, K>;
+        const int g = clamp_grid(g_facar_, (m.NF + R::FPW - 1) / R::FPW, 1);
+        launch(k_facet_adj_r<D, K>, g, 32 * R::WARPS, R::SMEM, st, m, t, static_cast<const float*>(uL),
+               static_cast<const float*>(ybar), l, facet_l, static_cast<float*>(gamU), static_cast<float*>(gamW));
+        return 1;
+      }
+    }
     const int g = clamp_grid(g_fadj_, m.NF, kWarps);
     if (wsep)
       launch(k_facet_adj<D, K, T, true>, g, 32 * kWarps, facet_adj_smem(true), st, 
