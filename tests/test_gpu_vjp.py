@@ -99,6 +99,22 @@ def test_vjp_rollout_fp32_small():
     assert _rel(_host(grad), grad_ref) < 2e-5
 
 
+@pytest.mark.parametrize("dim,n,k", [(2, 4, 4), (3, 3, 2), (3, 3, 4)])
+def test_vjp_rollout_fp32_orders(dim, n, k):
+    """The FP32 STAGE rollout gradient (register adjoint kernels: w = u) against the oracle's
+    adjoint at the orders the other rollout tests do not cover, same bounds as above."""
+    l = k - 1
+    g, sp = _mk(dim, n, k, "f32", l=l)
+    u0 = _rounded(g, sp.interpolate(W.taylor_green) + W.uniform_noise(sp.n_hdiv, 1e-2, 29))
+    dt, steps = 1e-2, 3
+    loss, grad = g.vjp_rollout(_dev(g, u0), dt, steps, 2)
+    loss_ref, grad_ref = A.rollout_vjp(sp, u0, dt, steps, l)
+    err = _rel(_host(grad), grad_ref)
+    print(f"d={dim} k={k}: FP32 rollout gradient vs oracle adjoint {err:.2e}")
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    assert err < 2e-5
+
+
 def test_vjp_zero_substeps_and_errors():
     g, sp = _mk(3, 3, 2, "f64", l=1)
     u0 = sp.interpolate(W.taylor_green)
