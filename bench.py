@@ -280,11 +280,23 @@ def reference_arm(args, rank):
 
 # ------------------------------------------------------------------ our arm
 def kernel_sources_sha() -> str:
-    """sha256[:16] of every kernel and table header of the library (csrc/*.cuh and
-    csrc/*.h, sorted by name, concatenated)."""
+    """sha256[:16] of the headers the 3D k = 4 translation unit (csrc/ops_d3k4.cu, every
+    kernel of the 32^3 k = 4 substep) includes, followed transitively within csrc/, sorted
+    by name and concatenated."""
     d = os.path.join(ROOT, "paper_2408_06698_gb300", "csrc")
+    seen, todo = set(), ["ops_d3k4.cu"]
+    while todo:
+        name = todo.pop()
+        with open(os.path.join(d, name)) as f:
+            for line in f:
+                t = line.strip()
+                if t.startswith('#include "'):
+                    inc = t.split('"')[1]
+                    if inc not in seen and os.path.exists(os.path.join(d, inc)):
+                        seen.add(inc)
+                        todo.append(inc)
     h = hashlib.sha256()
-    for name in sorted(f for f in os.listdir(d) if f.endswith(".cuh") or f.endswith(".h")):
+    for name in sorted(seen):
         with open(os.path.join(d, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -1,0 +1,228 @@
+"""Pins of the hexahedral oracle (oracle/hexa.py) against what the mathematics fixes:
+closed forms of the Legendre polynomials and Gauss moments, orthonormality, finite
+differences, the divergence theorem on the reference cell, the box's volume and closed cells,
+facet points that coincide from both sides, the constant-state and energy identities of
+Section 3.2, the l = k limit, the Q^l orthogonality of (I - Pi^l), and the value of the form
+on the same box split into tetrahedra (the simplicial oracle, pinned on its own) for
+polynomial fields."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import convection as C
+from oracle import hexa as H
+from oracle.fe import ref_element
+from oracle.mesh import MeshTopo
+
+
+def test_legendre_closed_forms():
+    x = np.array([0.0, 0.13, 0.5, 0.77, 1.0])
+    V, D = H.legendre01(3, x)
+    assert np.allclose(V[:, 0], 1.0, atol=1e-15)
+    assert np.allclose(V[:, 1], math.sqrt(3) * (2 * x - 1), atol=1e-14)
+    assert np.allclose(V[:, 2], math.sqrt(5) * (6 * x * x - 6 * x + 1), atol=1e-14)
+    assert np.allclose(V[:, 3], math.sqrt(7) * (20 * x**3 - 30 * x**2 + 12 * x - 1), atol=1e-13)
+    assert np.allclose(D[:, 0], 0.0)
+    assert np.allclose(D[:, 1], 2 * math.sqrt(3), atol=1e-14)
+    assert np.allclose(D[:, 2], math.sqrt(5) * (12 * x - 6), atol=1e-13)
+    assert np.allclose(D[:, 3], math.sqrt(7) * (60 * x**2 - 60 * x + 12), atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [2, 4, 7])
+def test_gauss_moments(m):
+    x, w = H.gauss01(m)
+    for p in range(2 * m):
+        assert np.dot(w, x**p) == pytest.approx(1.0 / (p + 1), rel=1e-13)
+    assert abs(np.dot(w, x ** (2 * m)) - 1.0 / (2 * m + 1)) > 1e-10    # and not beyond 2m-1
+
+
+def test_points_per_direction():
+    assert [H.points_per_direction(k) for k in (1, 2, 3, 4, 5)] == [2, 4, 5, 7, 8]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_orthonormal_and_exact(k):
+    ref = H.RefHex(k)
+    G = np.einsum("q,qi,qj->ij", ref.wq, ref.phi, ref.phi)
+    assert np.abs(G - np.eye(ref.nb)).max() < 1e-13
+    # basis index i = i1 + (k+1)(i2 + (k+1) i3): phi_i at x = L_i1(x1) L_i2(x2) L_i3(x3)
+    x = np.array([[0.2, 0.7, 0.4]])
+    L = [H.legendre01(k, x[:, a])[0][0] for a in range(3)]
+    i1, i2, i3 = k, 1 % (k + 1), 0
+    assert H.basis(k, x)[0][0, i1 + (k + 1) * (i2 + (k + 1) * i3)] == pytest.approx(L[0][i1] * L[1][i2] * L[2][i3])
+    # the facet rule integrates degree 3k in each direction
+    g = ref.sq[:, 0] ** (3 * k) * ref.sq[:, 1] ** (3 * k)
+    assert np.dot(ref.wf, g) == pytest.approx(1.0 / (3 * k + 1) ** 2, rel=1e-12)
+
+
+def test_gradient_finite_differences():
+    k = 3
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0.1, 0.9, size=(5, 3))
+    _, dphi = H.basis(k, x)
+    h = 1e-6
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        fd = (H.basis(k, x + e)[0] - H.basis(k, x - e)[0]) / (2 * h)
+        assert np.abs(fd - dphi[:, :, c]).max() < 1e-6
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_reference_divergence_theorem(k):
+    """int_T^ d_c phi_i = sum_f N^_f,c int_F^ phi_i (facet traces, normals, volume gradients)."""
+    ref = H.RefHex(k)
+    lhs = np.einsum("q,qic->ic", ref.wq, ref.dphi)
+    rhs = np.einsum("fc,p,fpi->ic", ref.Nhat, ref.wf, ref.phi_f)
+    assert np.abs(lhs - rhs).max() < 1e-12
+
+
+def _box(seed=1, n=3):
+    return W.hex_box(n, jitter=0.25, shear=0.4, seed=seed)
+
+
+def test_mesh_geometry():
+    hb = _box(2, (3, 4, 5))
+    m = H.HexMesh(hb)
+    vol = np.linalg.det(hb.A) * np.prod([x[-1] for x in hb.lines])
+    assert m.absdet.sum() == pytest.approx(vol, rel=1e-13)
+    assert m.n_facets == 3 * m.n_elems
+    # every cell is closed: its outward area vectors sum to zero
+    acc = np.zeros((m.n_elems, 3))
+    np.add.at(acc, m.fa[:, 0], m.aF[:, None] * m.nF)
+    np.add.at(acc, m.fb[:, 0], -m.aF[:, None] * m.nF)
+    assert np.abs(acc).max() < 1e-12
+    # each facet once as side A and once as side B of each cell direction
+    assert np.all(np.bincount(m.fa[:, 0], minlength=m.n_elems) == 3)
+    assert np.all(np.bincount(m.fb[:, 0], minlength=m.n_elems) == 3)
+    # the facet points of both sides coincide up to a period of the box
+    ref = H.RefHex(2)
+    d = m.facet_points(ref, "A") - m.facet_points(ref, "B")
+    coef = np.einsum("Fpc,ac->Fpa", d, np.linalg.inv(m.lattice.T))  # d = sum_a coef_a period_a
+    assert np.abs(coef - np.rint(coef)).max() < 1e-12
+    assert np.abs(d[:, 1:] - d[:, :1]).max() < 1e-12                   # one shift per facet
+
+
+def _const(v):
+    return lambda x: np.broadcast_to(np.asarray(v, dtype=float), x.shape).copy()
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_constant_state_gives_zero(k):
+    m, ref = H.HexMesh(_box(3)), H.RefHex(k)
+    u = H.project(m, ref, _const([1.0, -2.0, 0.5]))
+    w = H.project(m, ref, _const([0.3, 0.7, -0.4]))
+    for l in (-1, 0, k - 1, k):
+        assert np.abs(H.apply(m, ref, w, u, l)).max() < 1e-12
+
+
+def _div_free(k):
+    """A divergence-free polynomial wind of total degree <= k whose component a does not
+    depend on x_a, so that on an axis-aligned periodic box its normal component is
+    continuous across every facet, the periodic seams included."""
+    if k >= 3:
+        return lambda x: np.stack([1e-2 * x[..., 1] ** 2 * x[..., 2] + 0.4,
+                                   1e-2 * x[..., 0] * x[..., 2] ** 2 - 0.3,
+                                   1e-2 * x[..., 0] ** 2 * x[..., 1] + 0.2], axis=-1)
+    return lambda x: np.stack([0.1 * x[..., 1] * x[..., 2] + 0.4, 0.1 * x[..., 0] * x[..., 2] - 0.3,
+                               0.1 * x[..., 0] * x[..., 1] + 0.2], axis=-1)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_energy_identity(k):
+    """c(w; u, u) = sum_F int 1/2 |w.n| |(I - Pi^l)[[u]]|^2 for a divergence-free w with a
+    continuous normal component (axis-aligned cells of uneven size: no shear)."""
+    m, ref = H.HexMesh(W.hex_box(3, jitter=0.25, shear=0.0, seed=4)), H.RefHex(k)
+    w = H.project(m, ref, _div_free(k))
+    u = W.uniform_noise(m.n_elems * 3 * ref.nb, 1.0, 5).reshape(m.n_elems, 3, ref.nb)
+    for l in (-1, 0, 1, k):
+        cv = H.form_value(m, ref, w, u, l)
+        dis = H.facet_dissipation(m, ref, w, u, l)
+        assert dis > 0
+        assert cv == pytest.approx(dis, rel=1e-11)
+
+
+def test_l_equals_k_keeps_the_normal_jump_only():
+    k = 3
+    m, ref = H.HexMesh(_box(5)), H.RefHex(k)
+    u = W.uniform_noise(m.n_elems * 3 * ref.nb, 1.0, 6).reshape(m.n_elems, 3, ref.nb)
+    w = W.uniform_noise(m.n_elems * 3 * ref.nb, 1.0, 7).reshape(m.n_elems, 3, ref.nb)
+    _, jump, _, PJ, _ = H.facet_quantities(m, ref, w, u, k)
+    normal = np.einsum("Fpa,Fa->Fp", jump, m.nF)[..., None] * m.nF[:, None, :]
+    assert np.abs(PJ - normal).max() < 1e-12
+    _, jump, _, PJ, _ = H.facet_quantities(m, ref, w, u, -1)
+    assert np.abs(PJ - jump).max() == 0.0
+
+
+@pytest.mark.parametrize("l", [0, 1, 2])
+def test_complement_is_orthogonal_to_tangential_q_l(l):
+    """(I - Pi^l) V is L2(F)-orthogonal to every tangential field with Q^l components, and
+    not to the Q^(l+1) modes outside Q^l (a P^l projection would fail the first check)."""
+    k = 3
+    ref = H.RefHex(k)
+    rng = np.random.default_rng(8)
+    V = rng.standard_normal((4, ref.wf.size, 3))
+    nF = rng.standard_normal((4, 3))
+    nF /= np.linalg.norm(nF, axis=1, keepdims=True)
+    R = H.complement_projection(ref, l, nF, V)
+    Rt = R - np.einsum("Fpa,Fa->Fp", R, nF)[..., None] * nF[:, None, :]
+    for mm in ref.q_modes(l):
+        assert np.abs(np.einsum("p,p,Fpa->Fa", ref.wf, ref.psi[:, mm], Rt)).max() < 1e-12
+    outside = [mm for mm in range(ref.psi.shape[1]) if ref.psi_deg[mm] == l + 1]
+    big = max(np.abs(np.einsum("p,p,Fpa->Fa", ref.wf, ref.psi[:, mm], Rt)).max() for mm in outside)
+    assert big > 1e-3
+    # the normal part is untouched
+    assert np.abs(np.einsum("Fpa,Fa->Fp", R - V, nF)).max() < 1e-12
+
+
+def _poly(k, seed, scale=1.0, base=None):
+    """A random vector polynomial of total degree <= k in x / (2 pi)."""
+    rng = np.random.default_rng(seed)
+    exps = [(a, b, c) for a in range(k + 1) for b in range(k + 1) for c in range(k + 1) if a + b + c <= k]
+    coef = rng.uniform(-1.0, 1.0, size=(len(exps), 3)) * scale / len(exps)
+
+    def f(x):
+        y = x / (2 * math.pi)
+        out = np.zeros(x.shape[:-1] + (3,))
+        for (a, b, c), cf in zip(exps, coef):
+            out += (y[..., 0] ** a * y[..., 1] ** b * y[..., 2] ** c)[..., None] * cf
+        if base is not None:
+            out += base
+        return out
+
+    return f
+
+
+def _tet_project(topo, ref, f):
+    X = topo.volume_points(ref.xq)
+    return np.einsum("q,eqa,qi->eai", ref.wq, f(X), ref.phi)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_form_equals_the_simplicial_oracle(k):
+    """For global polynomial u, v, w of total degree <= k (in both spaces), pure upwind
+    (l = -1), the form c(w; u, v) on the hexahedral box equals the one on the same box
+    split into tetrahedra: the volume integrals are the same polynomial integrals, interior
+    jumps vanish, and on the periodic seam both integrate the same facet terms (w.n keeps
+    one sign there, so |w.n| is a polynomial).  The two oracles share no code."""
+    hb = _box(6)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    tets = W.hex_box_tets(hb)
+    topo, tref = MeshTopo(tets.coords, tets.elems, tets.rep), ref_element(3, k)
+    base = hb.A @ np.ones(3)                          # A^-1 w = (1, 1, 1): w.n > 0 on every seam
+    fw = _poly(k, 11, 0.2, base)
+    fu, fv = _poly(k, 12), _poly(k, 13)
+    wn, *_ = H.facet_quantities(m, ref, H.project(m, ref, fw), H.project(m, ref, fu), -1)
+    assert wn.min() > 0.1
+    vals = []
+    for proj, res, mesh_, ref_ in ((H.project, None, m, ref), (_tet_project, None, topo, tref)):
+        uL, wL, vL = proj(mesh_, ref_, fu), proj(mesh_, ref_, fw), proj(mesh_, ref_, fv)
+        if mesh_ is m:
+            r = H.residual(m, ref, wL, uL, -1)
+        else:
+            r = C.residual_conservative(topo, tref, wL, uL, -1)
+        vals.append(float(np.sum(vL * r)))
+    assert abs(vals[0]) > 1e-3
+    assert vals[0] == pytest.approx(vals[1], rel=1e-11)

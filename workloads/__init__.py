@@ -109,6 +109,65 @@ def periodic_box_mesh(dim: int, n: int, length: float = TWO_PI) -> Mesh:
     return Mesh(coords, elems.reshape(-1, dim + 1), rep, dim, n, float(length))
 
 
+# ---------------------------------------------------------------- hexahedral boxes
+@dataclass(frozen=True)
+class HexBox:
+    """Structured periodic box of hexahedra (parallelepipeds), for the hexahedral path.
+
+    lines:  three increasing arrays of grid-line positions (n_a + 1 values, from 0);
+            cube (i, j, l) spans [lines[0][i], lines[0][i+1]] x ... before the map.
+    A:      3x3 matrix with det A > 0; every point xi of the grid is placed at A xi,
+            so each cube becomes a parallelepiped.  The box is periodic with the
+            lattice vectors A (L_a e_a), L_a = lines[a][-1].
+    Cells are numbered with axis 0 fastest: e = i + n0 (j + n1 l).
+    """
+
+    lines: tuple
+    A: np.ndarray
+
+    @property
+    def n(self) -> tuple:
+        return tuple(len(x) - 1 for x in self.lines)
+
+    @property
+    def n_elems(self) -> int:
+        n = self.n
+        return int(n[0] * n[1] * n[2])
+
+
+def hex_box(n, length: float = TWO_PI, jitter: float = 0.0, shear: float = 0.0, seed: int = 0) -> HexBox:
+    """A periodic hexahedral box: n = (n0, n1, n2) cubes per direction (or one int),
+    grid spacings length/n_a perturbed by a relative U[-jitter, jitter] (seeded) and
+    the map A = I + shear * (seeded strictly upper-triangular matrix, entries U[-1, 1])."""
+    if np.isscalar(n):
+        n = (int(n),) * 3
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lines = []
+    for na in n:
+        if na < 3:
+            raise ValueError("n must be >= 3 in every direction")
+        h = np.full(na, length / na) * (1.0 + rng.uniform(-jitter, jitter, size=na))
+        lines.append(np.concatenate([[0.0], np.cumsum(h)]))
+    U = np.triu(rng.uniform(-1.0, 1.0, size=(3, 3)), 1)
+    A = np.eye(3) + shear * U
+    return HexBox(tuple(lines), A)
+
+
+def hex_box_tets(hb: HexBox) -> Mesh:
+    """The same periodic box split into 6 tetrahedra per cell (the Kuhn split of
+    periodic_box_mesh on the grid lines of hb, placed by hb.A)."""
+    base = periodic_box_mesh(3, hb.n[0]) if len(set(hb.n)) == 1 else None
+    if base is None:
+        raise ValueError("the tetrahedral split needs the same count in every direction")
+    n = hb.n[0]
+    h = base.length / n
+    idx = np.rint(base.coords / h).astype(np.int64)                  # grid indices
+    xi = np.stack([hb.lines[a][idx[:, a]] for a in range(3)], axis=-1)
+    coords = xi @ hb.A.T
+    L = np.array([hb.lines[a][-1] for a in range(3)])
+    return Mesh(coords, base.elems, base.rep, 3, n, float(L[0]))
+
+
 # ---------------------------------------------------------------- analytic fields
 def taylor_green(x: np.ndarray) -> np.ndarray:
     """Taylor-Green velocity at points x [..., dim].
