@@ -374,7 +374,49 @@ def other_configs(dev, stream, world):
                                    "order_classes": len(b.classes), "substeps": K, "ms_per_substep": ms / K,
                                    "value": l2 * APPLIES_PER_STEP * K / (ms / 1e3), "unit": UNIT}
     b.close()
+    out["hex_box_32cubed_k4"] = hex_row(dev, stream)
     return out
+
+
+def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
+    """The hexahedral path: 32^3 parallelepipeds (jittered spacings, sheared), k = 4, l = 3,
+    seeded U[-1, 1] coefficients (timing does not depend on the data; the smooth-field
+    accuracy is covered by the parity tests); FP32 and FP64 apply and STAGE substeps (CUDA
+    events), the FP32 apply and substeps against FP64 on the same rounded input."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2408_06698_gb300 import HopuHex
+    hb = W.hex_box(n, jitter=0.1, shear=0.2, seed=11)
+    nl2 = n ** 3 * 3 * (k + 1) ** 3
+    u0 = W.uniform_noise(nl2, 1.0, 77).astype(np.float32).astype(np.float64)
+    row = {"workload": f"{n}^3 hexahedra (parallelepipeds), k={k}, l={l}, STAGE wind, U[-1,1] coefficients",
+           "cells": n ** 3, "l2_dofs": nl2}
+    res = {}
+    for prec in ("f32", "f64"):
+        with torch.cuda.stream(stream):
+            g = HopuHex(hb.lines, hb.A, k=k, prec=prec, device=dev)
+            u = torch.tensor(u0, dtype=g.dtype, device=dev)
+            y = g.new()
+            g.apply(u, u, l, out=y)
+            ms_apply = _events_ms(stream, lambda: g.apply(u, u, l, out=y), 20) / 20
+            v = u.clone()
+            g.rk_substeps(v, dt, 2, l)
+            ms_sub = _events_ms(stream, lambda: g.rk_substeps(v, dt, 1, l), substeps) / substeps
+            v = u.clone()
+            g.rk_substeps(v, dt, substeps, l)
+            stream.synchronize()
+        res[prec] = (y.double().cpu().numpy(), v.double().cpu().numpy())
+        row[prec] = {"ms_per_apply": ms_apply, "ms_per_substep": ms_sub,
+                     "value": nl2 * APPLIES_PER_STEP / (ms_sub / 1e3), "unit": UNIT}
+        g.close()
+    ya, yb = res["f32"][0], res["f64"][0]
+    sa, sb = res["f32"][1], res["f64"][1]
+    row["f32_apply_rel_error_vs_f64"] = float(np.linalg.norm(ya - yb) / np.linalg.norm(yb))
+    row[f"f32_{substeps}_substeps_rel_error_vs_f64"] = float(np.linalg.norm(sa - sb) / np.linalg.norm(sb))
+    row["fp32_over_fp64_speedup"] = row["f64"]["ms_per_substep"] / row["f32"]["ms_per_substep"]
+    return row
 
 
 def our_arm(args, rank, world):

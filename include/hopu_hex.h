@@ -1,0 +1,70 @@
+/* libhopu, hexahedral cells: the HOPU convection apply and explicit SSP-RK3 substeps on a
+ * structured periodic box of parallelepipeds (the paper's meshes are hexahedral, Section
+ * 2.1; the operator is Section 3.2, eq. "hopudefinition", in its conservative form).
+ *
+ * Space and layout.  Per velocity component the discontinuous space Q^k of the reference
+ * cube [0,1]^3 (degree <= k in each coordinate), orthonormal tensor Legendre basis
+ * phi_i(x) = L_i1(x1) L_i2(x2) L_i3(x3), L_n(x) = sqrt(2n+1) P_n(2x-1), basis index
+ * i = i1 + (k+1)(i2 + (k+1) i3).  An L2 vector is [E][3][(k+1)^3] in the context's precision
+ * (double for HOPU_FP64, float for HOPU_FP32), cells numbered e = c0 + n0 (c1 + n1 c2)
+ * (axis 0 fastest), Cartesian velocity components.  Geometry stays FP64 on the device.
+ *
+ * Box.  Grid lines lines[a][0..n_a] (increasing, n_a >= 3) and a 3x3 matrix A (row-major,
+ * det A > 0): cell (c0, c1, c2) is A applied to [lines0[c0], lines0[c0+1]] x ... ; the box is
+ * periodic with periods A (L_a e_a), L_a = lines_a[n_a] - lines_a[0].
+ *
+ * Facets.  The facet between a cell and the next one in direction a is one facet with
+ * side A the lower cell; [[u]] = u^A - u^B, n its unit normal out of side A; w.n is
+ * <w>.n.  (I - Pi^l) removes the tangential Q^l modes of a facet field (Section 3.2's
+ * V_h^proj with P^l read as Q^l on quadrilaterals, so that l = k leaves only the normal
+ * part of the jump); l < 0 is plain upwinding (Pi = 0).
+ *
+ * Quadrature: ceil((3k+1)/2) Gauss-Legendre points per direction in the volume and on the
+ * facets (exact to degree 3k per direction; |w.n| is integrated by the same rule).
+ *
+ * Calls run on the stream given at creation (NULL: the legacy default stream) and return
+ * at once; pointers to coefficient vectors are device pointers, 16-byte aligned.
+ * Status values are those of hopu.h (HOPU_OK, HOPU_EINVAL, ...).
+ */
+#ifndef HOPU_HEX_H
+#define HOPU_HEX_H
+
+#include <stdint.h>
+
+#include "hopu.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hopu_hex hopu_hex; /* opaque; owns its device tables and scratch */
+
+/* Creates a context for the box (n0, n1, n2, lines = the n0+1, n1+1, n2+1 grid-line positions
+ * of the three directions one after the other, A) at order k (2..5) and precision prec
+ * (HOPU_FP64 or HOPU_FP32).  Copies what it needs (the caller keeps ownership of lines and
+ * A).  EINVAL: NULL pointer, n_a < 3, prec not one of the two; ENOTSUP: k outside 2..5;
+ * EMESH: lines not increasing or det A <= 0; ENOMEM / ECUDA: allocation or CUDA failure
+ * (text in hopu_hex_last_error(NULL)). */
+int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A, int k, int prec,
+                    void* stream, hopu_hex** out);
+int hopu_hex_destroy(hopu_hex* h);
+
+/* Number of cells and length of an L2 vector (E * 3 * (k+1)^3 elements). */
+int hopu_hex_sizes(const hopu_hex* h, int64_t* n_cells, int64_t* n_l2);
+
+/* y = M^-1 c(w; u, .) with the wind w given in L2 (Section 3.2, eq. "hopudefinition";
+ * M the block-diagonal mass, |det J| I on a parallelepiped).  wL, uL, yL: device L2
+ * vectors; yL must not alias wL or uL.  l: the HOPU order of every facet (l < 0: upwind). */
+int hopu_hex_apply(hopu_hex* h, const void* wL, const void* uL, int l, void* yL);
+
+/* n SSP-RK3 substeps (Shu-Osher form) of du/dt = -M^-1 c(u; u, .) in place on the device
+ * L2 vector uL (the wind is the stage's own field). */
+int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l);
+
+/* Text of the last failure of h (NULL: of the last failed hopu_hex_create); never NULL. */
+const char* hopu_hex_last_error(const hopu_hex* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -2,4 +2,4 @@
 
 ``build.build()`` compiles libhopu.so for sm_103a; ``hopu.Hopu`` binds a context.
 """
-from .hopu import ConvectionApply, Hopu, HopuBatch, Rollout, measure_alu_peak, selftest  # noqa: F401
+from .hopu import ConvectionApply, Hopu, HopuBatch, HopuHex, Rollout, measure_alu_peak, selftest  # noqa: F401

@@ -1,4 +1,4 @@
-"""ctypes declarations of the libhopu C ABI (include/hopu.h).
+"""ctypes declarations of the libhopu C ABI (include/hopu.h, include/hopu_hex.h).
 
 Argument marshalling only: there is no compute here and no fallback.  If the shared
 library is missing, loading raises instead of silently doing something else.
@@ -35,7 +35,7 @@ class Options(Structure):
     _fields_ = [("k", c_int), ("l", c_int), ("prec", c_int), ("wind_mode", c_int), ("tile_hint", c_int)]
 
 
-# name -> (restype, argtypes); the exact set of symbols include/hopu.h declares
+# name -> (restype, argtypes); the exact set of symbols the headers under include/ declare
 SIGNATURES = {
     "hopu_create": (c_int, [POINTER(MeshDesc), POINTER(Options), c_void_p, POINTER(c_void_p)]),
     "hopu_destroy": (c_int, [c_void_p]),
@@ -53,6 +53,12 @@ SIGNATURES = {
     "hopu_points": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_int64)]),
     "hopu_interpolate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_last_error": (c_char_p, [c_void_p]),
+    "hopu_hex_create": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p, POINTER(c_void_p)]),
+    "hopu_hex_destroy": (c_int, [c_void_p]),
+    "hopu_hex_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
+    "hopu_hex_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "hopu_hex_rk_substeps": (c_int, [c_void_p, c_void_p, c_double, c_int, c_int]),
+    "hopu_hex_last_error": (c_char_p, [c_void_p]),
     "hopu_clear_error": (c_int, [c_void_p]),
     "hopu_selftest": (c_int, [c_int, c_int, POINTER(c_double)]),
     "hopu_profile": (c_int, [c_void_p, c_int]),

@@ -29,6 +29,7 @@ SOURCES = [
     "ops_d3k3.cu",
     "ops_d3k4.cu",
     "ops_d3k5.cu",
+    "hex.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
@@ -47,7 +48,7 @@ def _nvcc() -> str:
 
 def _headers():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    return hs + [os.path.join(INCLUDE, "hopu.h")]
+    return hs + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
 
 def _stamp_ok() -> bool:

@@ -1,0 +1,350 @@
+// C ABI of the hexahedral path (include/hopu_hex.h): box geometry and 1D tables on the
+// host in FP64, the sum-factorised kernels of kernels_hex.cuh on the device.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hopu_hex.h"
+#include "kernels_hex.cuh"
+#include "reftables.h"
+
+using namespace hopu::hex;
+
+struct hopu_hex {
+  int n[3] = {0, 0, 0};
+  int k = 0, prec = 0;
+  int64_t E = 0;
+  cudaStream_t stream = nullptr;
+  double* d_geo = nullptr;   // G [E][9] | invabs [E] | nF [3E][3] | aF [3E]
+  void* d_tab = nullptr;     // B | Dd | w1 | e0 | e1 | e0lo | e1lo in the working precision
+  void* d_gam = nullptr;     // facet moments [3E][2][3][(k+1)^2] (side A, side B)
+  void* d_u1 = nullptr;      // two stage vectors
+  void* d_u2 = nullptr;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_err;
+
+int fail(hopu_hex* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(hopu_hex* h, cudaError_t e, const char* where) {
+  return fail(h, HOPU_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Orthonormal Legendre polynomials on [0,1] up to degree k at x: the three-term recurrence
+// (n+1) P_{n+1} = (2n+1) t P_n - n P_{n-1} of P_n on [-1,1] at t = 2x - 1, and its
+// t-derivative; values v[k+1] and x-derivatives dv[k+1] of sqrt(2n+1) P_n(2x - 1).
+void legendre01(int k, double x, double* v, double* dv) {
+  const double t = 2.0 * x - 1.0;
+  double pm = 0.0, p = 1.0, dpm = 0.0, dp = 0.0;
+  for (int n = 0; n <= k; ++n) {
+    const double s = std::sqrt(2.0 * n + 1.0);
+    v[n] = s * p;
+    dv[n] = 2.0 * s * dp;
+    const double pn = ((2 * n + 1) * t * p - n * pm) / (n + 1);
+    const double dpn = ((2 * n + 1) * (p + t * dp) - n * dpm) / (n + 1);
+    pm = p;
+    p = pn;
+    dpm = dp;
+    dp = dpn;
+  }
+}
+
+template <typename T>
+std::vector<T> tables(int k) {
+  const int K1 = k + 1, M = (3 * k + 2) / 2;
+  std::vector<double> x, w;
+  hopu::gauss_jacobi01(M, 0, x, w);
+  std::vector<T> out(2 * M * K1 + M + 4 * K1);
+  std::vector<double> v(K1), dv(K1);
+  for (int q = 0; q < M; ++q) {
+    legendre01(k, x[q], v.data(), dv.data());
+    for (int i = 0; i < K1; ++i) {
+      out[q * K1 + i] = T(v[i]);
+      out[M * K1 + q * K1 + i] = T(dv[i]);
+    }
+    out[2 * M * K1 + q] = T(w[q]);
+  }
+  // end values and the part of each that T drops (zero for double)
+  for (int side = 0; side < 2; ++side) {
+    legendre01(k, side ? 1.0 : 0.0, v.data(), dv.data());
+    for (int i = 0; i < K1; ++i) {
+      const T hi = T(v[i]);
+      out[2 * M * K1 + M + side * K1 + i] = hi;
+      out[2 * M * K1 + M + (2 + side) * K1 + i] = T(v[i] - double(hi));
+    }
+  }
+  return out;
+}
+
+double det3(const double* a) {
+  return a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+}
+
+// inverse of a 3x3 row-major matrix
+void inv3(const double* a, double* o) {
+  const double d = det3(a);
+  o[0] = (a[4] * a[8] - a[5] * a[7]) / d;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) / d;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) / d;
+  o[3] = (a[5] * a[6] - a[3] * a[8]) / d;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) / d;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) / d;
+  o[6] = (a[3] * a[7] - a[4] * a[6]) / d;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) / d;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) / d;
+}
+
+MeshDev mesh_dev(const hopu_hex* h) {
+  MeshDev m;
+  m.n0 = h->n[0];
+  m.n1 = h->n[1];
+  m.n2 = h->n[2];
+  m.E = h->E;
+  m.G = h->d_geo;
+  m.invabs = h->d_geo + 9 * h->E;
+  m.nF = m.invabs + h->E;
+  m.aF = m.nF + 9 * h->E;
+  return m;
+}
+
+template <typename T, int K>
+Tabs<T> tabs_dev(const hopu_hex* h) {
+  constexpr int K1 = K + 1, M = Shape<K>::M;
+  const T* t = static_cast<const T*>(h->d_tab);
+  Tabs<T> tb;
+  tb.B = t;
+  tb.Dd = t + M * K1;
+  tb.w1 = t + 2 * M * K1;
+  tb.e0 = tb.w1 + M;
+  tb.e1 = tb.e0 + K1;
+  tb.e0lo = tb.e1 + K1;
+  tb.e1lo = tb.e0lo + K1;
+  return tb;
+}
+
+template <typename Kern>
+int grid_for(Kern kern, int threads, size_t smem, int64_t items_per_block, int64_t items, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return -1;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (items + items_per_block - 1) / items_per_block;
+  const int64_t full = (int64_t)sms * per_sm;
+  *grid = (int)(need < full ? need : full);
+  if (*grid < 1) *grid = 1;
+  return 0;
+}
+
+// one apply: facet moments, then volume + lift + inverse mass + out = c0 u0 + c1 us + c2 y
+template <typename T, int K>
+int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, T c2, T* out) {
+  const MeshDev m = mesh_dev(h);
+  const Tabs<T> tb = tabs_dev<T, K>(h);
+  T* gam = static_cast<T*>(h->d_gam);
+  int gf = 0, gv = 0;
+  auto kf = k_hex_facet<T, K>;
+  auto kv = k_hex_volume<T, K>;
+  using CF = Fac<T, K>;
+  using CV = Vol<T, K>;
+  if (grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf) ||
+      grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
+    return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
+  kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_facet launch");
+  kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, w, us, gam, u0, c0, c1, c2, out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_volume launch");
+  return HOPU_OK;
+}
+
+template <typename T, int K>
+int substeps(hopu_hex* h, T* u, double dt, int n, int l) {
+  T* u1 = static_cast<T*>(h->d_u1);
+  T* u2 = static_cast<T*>(h->d_u2);
+  const T z = T(0), one = T(1);
+  for (int s = 0; s < n; ++s) {
+    int st;
+    if ((st = stage<T, K>(h, u, u, l, u, z, one, T(-dt), u1)) != HOPU_OK) return st;
+    if ((st = stage<T, K>(h, u1, u1, l, u, T(0.75), T(0.25), T(-0.25 * dt), u2)) != HOPU_OK) return st;
+    if ((st = stage<T, K>(h, u2, u2, l, u, T(1.0 / 3.0), T(2.0 / 3.0), T(-2.0 / 3.0 * dt), u)) != HOPU_OK)
+      return st;
+  }
+  return HOPU_OK;
+}
+
+template <typename T>
+int dispatch_apply(hopu_hex* h, const T* w, const T* u, int l, T* y) {
+  switch (h->k) {
+    case 2: return stage<T, 2>(h, w, u, l, u, T(0), T(0), T(1), y);
+    case 3: return stage<T, 3>(h, w, u, l, u, T(0), T(0), T(1), y);
+    case 4: return stage<T, 4>(h, w, u, l, u, T(0), T(0), T(1), y);
+    case 5: return stage<T, 5>(h, w, u, l, u, T(0), T(0), T(1), y);
+  }
+  return fail(h, HOPU_ENOTSUP, "hopu_hex: order");
+}
+
+template <typename T>
+int dispatch_substeps(hopu_hex* h, T* u, double dt, int n, int l) {
+  switch (h->k) {
+    case 2: return substeps<T, 2>(h, u, dt, n, l);
+    case 3: return substeps<T, 3>(h, u, dt, n, l);
+    case 4: return substeps<T, 4>(h, u, dt, n, l);
+    case 5: return substeps<T, 5>(h, u, dt, n, l);
+  }
+  return fail(h, HOPU_ENOTSUP, "hopu_hex: order");
+}
+
+void release(hopu_hex* h) {
+  cudaFree(h->d_geo);
+  cudaFree(h->d_tab);
+  cudaFree(h->d_gam);
+  cudaFree(h->d_u1);
+  cudaFree(h->d_u2);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A, int k, int prec, void* stream,
+                    hopu_hex** out) {
+  if (!out || !lines || !A) return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: NULL argument");
+  *out = nullptr;
+  if (n0 < 3 || n1 < 3 || n2 < 3) return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: fewer than 3 cells in a direction");
+  if (prec != HOPU_FP64 && prec != HOPU_FP32)
+    return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: precision must be HOPU_FP64 or HOPU_FP32");
+  if (k < 2 || k > 5) return fail(nullptr, HOPU_ENOTSUP, "hopu_hex_create: order k outside 2..5");
+  const int n[3] = {n0, n1, n2};
+  const double* ln[3] = {lines, lines + n0 + 1, lines + n0 + 1 + n1 + 1};
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < n[a]; ++i)
+      if (!(ln[a][i + 1] > ln[a][i])) return fail(nullptr, HOPU_EMESH, "hopu_hex_create: grid lines not increasing");
+  const double detA = det3(A);
+  if (!(detA > 0.0)) return fail(nullptr, HOPU_EMESH, "hopu_hex_create: det A <= 0");
+  const int64_t E = (int64_t)n0 * n1 * n2;
+
+  // geometry (FP64): J = A diag(h), |det J| J^-1 = |det J| diag(1/h) A^-1; facet normals
+  // and area factors from side A (the lower cell): n dA = det J J^-T e_d
+  double Ai[9];
+  inv3(A, Ai);
+  std::vector<double> geo(9 * E + E + 9 * E + 3 * E);
+  double* G = geo.data();
+  double* invabs = G + 9 * E;
+  double* nF = invabs + E;
+  double* aF = nF + 9 * E;
+  for (int64_t e = 0; e < E; ++e) {
+    const int c[3] = {int(e % n0), int((e / n0) % n1), int(e / ((int64_t)n0 * n1))};
+    double h[3];
+    for (int a = 0; a < 3; ++a) h[a] = ln[a][c[a] + 1] - ln[a][c[a]];
+    const double detJ = detA * h[0] * h[1] * h[2];
+    for (int r = 0; r < 3; ++r)
+      for (int b = 0; b < 3; ++b) G[e * 9 + r * 3 + b] = detJ * Ai[r * 3 + b] / h[r];
+    invabs[e] = 1.0 / detJ;
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int64_t e = 0; e < E; ++e) {
+      int c[3] = {int(e % n0), int((e / n0) % n1), int(e / ((int64_t)n0 * n1))};
+      c[d] = (c[d] - 1 + n[d]) % n[d];  // side A: the cell below
+      const int64_t eA = c[0] + (int64_t)n0 * (c[1] + (int64_t)n1 * c[2]);
+      double v[3];
+      for (int b = 0; b < 3; ++b) v[b] = G[eA * 9 + d * 3 + b];  // row d of det J J^-1
+      const double nv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      const int64_t F = d * E + e;
+      for (int b = 0; b < 3; ++b) nF[F * 3 + b] = v[b] / nv;
+      aF[F] = nv;
+    }
+
+  hopu_hex* h = new (std::nothrow) hopu_hex;
+  if (!h) return fail(nullptr, HOPU_ENOMEM, "hopu_hex_create: host allocation");
+  h->n[0] = n0;
+  h->n[1] = n1;
+  h->n[2] = n2;
+  h->k = k;
+  h->prec = prec;
+  h->E = E;
+  h->stream = static_cast<cudaStream_t>(stream);
+  const size_t ts = prec == HOPU_FP64 ? 8 : 4;
+  const int K1 = k + 1;
+  const size_t nl2 = (size_t)E * 3 * K1 * K1 * K1;
+  cudaError_t ce;
+  if ((ce = cudaMalloc(&h->d_geo, geo.size() * 8)) != cudaSuccess ||
+      (ce = cudaMalloc(&h->d_gam, (size_t)3 * E * 6 * K1 * K1 * ts)) != cudaSuccess ||
+      (ce = cudaMalloc(&h->d_u1, nl2 * ts)) != cudaSuccess || (ce = cudaMalloc(&h->d_u2, nl2 * ts)) != cudaSuccess) {
+    const int st = cuda_fail(nullptr, ce, "hopu_hex_create: device allocation");
+    release(h);
+    delete h;
+    return ce == cudaErrorMemoryAllocation ? HOPU_ENOMEM : st;
+  }
+  if ((ce = cudaMemcpy(h->d_geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    release(h);
+    delete h;
+    return cuda_fail(nullptr, ce, "hopu_hex_create: upload");
+  }
+  if (prec == HOPU_FP64) {
+    const std::vector<double> t = tables<double>(k);
+    ce = cudaMalloc(&h->d_tab, t.size() * 8);
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->d_tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice);
+  } else {
+    const std::vector<float> t = tables<float>(k);
+    ce = cudaMalloc(&h->d_tab, t.size() * 4);
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->d_tab, t.data(), t.size() * 4, cudaMemcpyHostToDevice);
+  }
+  if (ce != cudaSuccess) {
+    release(h);
+    delete h;
+    return cuda_fail(nullptr, ce, "hopu_hex_create: tables");
+  }
+  *out = h;
+  return HOPU_OK;
+}
+
+int hopu_hex_destroy(hopu_hex* h) {
+  if (!h) return HOPU_EINVAL;
+  release(h);
+  delete h;
+  return HOPU_OK;
+}
+
+int hopu_hex_sizes(const hopu_hex* h, int64_t* n_cells, int64_t* n_l2) {
+  if (!h) return HOPU_EINVAL;
+  const int64_t K1 = h->k + 1;
+  if (n_cells) *n_cells = h->E;
+  if (n_l2) *n_l2 = h->E * 3 * K1 * K1 * K1;
+  return HOPU_OK;
+}
+
+int hopu_hex_apply(hopu_hex* h, const void* wL, const void* uL, int l, void* yL) {
+  if (!h) return HOPU_EINVAL;
+  if (!wL || !uL || !yL) return fail(h, HOPU_EINVAL, "hopu_hex_apply: NULL vector");
+  if (yL == wL || yL == uL) return fail(h, HOPU_EINVAL, "hopu_hex_apply: yL aliases an input");
+  if (h->prec == HOPU_FP64)
+    return dispatch_apply<double>(h, static_cast<const double*>(wL), static_cast<const double*>(uL), l,
+                                  static_cast<double*>(yL));
+  return dispatch_apply<float>(h, static_cast<const float*>(wL), static_cast<const float*>(uL), l,
+                               static_cast<float*>(yL));
+}
+
+int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l) {
+  if (!h) return HOPU_EINVAL;
+  if (!uL || n < 0 || !std::isfinite(dt)) return fail(h, HOPU_EINVAL, "hopu_hex_rk_substeps: bad argument");
+  if (h->prec == HOPU_FP64) return dispatch_substeps<double>(h, static_cast<double*>(uL), dt, n, l);
+  return dispatch_substeps<float>(h, static_cast<float*>(uL), dt, n, l);
+}
+
+const char* hopu_hex_last_error(const hopu_hex* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

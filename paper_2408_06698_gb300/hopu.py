@@ -511,6 +511,78 @@ class HopuBatch:
             pass
 
 
+class HopuHex:
+    """A structured periodic box of parallelepipeds at order k (mirrors a ``hopu_hex``).
+
+    lines: three increasing arrays of grid-line positions (n_a + 1 each); A: 3x3 matrix,
+    det A > 0 (cell (c0, c1, c2) is A [lines0[c0], lines0[c0+1]] x ...).  L2 vectors are
+    [E][3][(k+1)^3] device tensors in the context's precision."""
+
+    def __init__(self, lines, A, k: int = 3, prec: str = "f64", device: str | torch.device = "cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhopu needs a CUDA device")
+        if prec not in ("f64", "f32"):
+            raise ValueError("prec must be 'f64' or 'f32'")
+        self.lib = L.load()
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float64 if prec == "f64" else torch.float32
+        self.k, self.prec = k, prec
+        self.n = tuple(len(x) - 1 for x in lines)
+        self._lines = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in lines]))
+        self._A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(3, 3))
+        self.stream = torch.cuda.current_stream(self.device)
+        self.h = c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.hopu_hex_create(self.n[0], self.n[1], self.n[2], self._lines.ctypes.data,
+                                          self._A.ctypes.data, int(k), _PREC[prec],
+                                          c_void_p(self.stream.cuda_stream), byref(self.h))
+        if st != L.HOPU_OK:
+            raise L.HopuError(st, "hopu_hex_create", self.lib.hopu_hex_last_error(None).decode())
+        ne, nl = c_int64(), c_int64()
+        self.lib.hopu_hex_sizes(self.h, byref(ne), byref(nl))
+        self.n_elems, self.n_l2 = ne.value, nl.value
+
+    def _check(self, st: int, where: str):
+        if st != L.HOPU_OK:
+            raise L.HopuError(st, where, self.lib.hopu_hex_last_error(self.h).decode())
+
+    def _vec(self, t: torch.Tensor, name: str) -> int:
+        if (not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != self.dtype
+                or not t.is_contiguous() or t.numel() != self.n_l2):
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} tensor of {self.n_l2} entries "
+                             f"on {self.device}")
+        return t.data_ptr()
+
+    def new(self) -> torch.Tensor:
+        return torch.empty(self.n_l2, dtype=self.dtype, device=self.device)
+
+    def apply(self, wL: torch.Tensor, uL: torch.Tensor, l: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        """y = M^-1 c(w; u, .) (hopu_hex_apply), on the context's stream."""
+        y = self.new() if out is None else out
+        self._check(self.lib.hopu_hex_apply(self.h, c_void_p(self._vec(wL, "wL")), c_void_p(self._vec(uL, "uL")),
+                                            int(l), c_void_p(self._vec(y, "yL"))), "hopu_hex_apply")
+        return y
+
+    def rk_substeps(self, uL: torch.Tensor, dt: float, n: int, l: int) -> torch.Tensor:
+        """n SSP-RK3 substeps in place, wind = the stage's field (hopu_hex_rk_substeps)."""
+        self._check(self.lib.hopu_hex_rk_substeps(self.h, c_void_p(self._vec(uL, "uL")), float(dt), int(n), int(l)),
+                    "hopu_hex_rk_substeps")
+        return uL
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.hopu_hex_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def measure_alu_peak(fp64: bool = False, iters: int | None = None) -> float:
     """Measured FMA throughput (TFLOP/s) of the current CUDA device (hopu_measure_alu_peak)."""
     lib = L.load()

@@ -1,0 +1,156 @@
+"""The hexahedral path (include/hopu_hex.h) against the hexahedral oracle (oracle/hexa.py):
+the apply element by element in FP64 (1e-12) and FP32, every order 2..5 and HOPU orders
+l = -1, 0, k-1, k, boxes with uneven cell counts, spacings and a shear, and SSP-RK3 STAGE
+substeps; a full-size apply on sampled cells."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import hexa as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(hb, k, prec):
+    from paper_2408_06698_gb300 import HopuHex
+    return HopuHex(hb.lines, hb.A, k=k, prec=prec)
+
+
+def _dev(g, a):
+    return torch.tensor(np.ascontiguousarray(a).reshape(-1), dtype=g.dtype, device=g.device)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _fields(m, ref, seed):
+    """Taylor-Green-like data plus noise (w and u differ)."""
+    u = H.project(m, ref, W.taylor_green) + W.uniform_noise(m.n_elems * 3 * ref.nb, 1e-2, seed).reshape(
+        m.n_elems, 3, ref.nb)
+    w = H.project(m, ref, lambda x: W.taylor_green(x + 0.3)) + W.uniform_noise(
+        m.n_elems * 3 * ref.nb, 1e-2, seed + 1).reshape(m.n_elems, 3, ref.nb)
+    return w, u
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_hex_apply_fp64(k):
+    hb = W.hex_box((3, 4, 5), jitter=0.2, shear=0.3, seed=k)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    g = _ctx(hb, k, "f64")
+    w, u = _fields(m, ref, 10 * k)
+    for l in (-1, 0, k - 1, k):
+        y = g.apply(_dev(g, w), _dev(g, u), l).cpu().numpy().reshape(m.n_elems, 3, ref.nb)
+        ref_y = H.apply(m, ref, w, u, l)
+        err = np.abs(y - ref_y).max() / np.abs(ref_y).max()
+        print(f"hex k={k} l={l}: FP64 max rel {err:.2e}")
+        assert err < 1e-12
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_hex_apply_fp32(k):
+    hb = W.hex_box((4, 3, 3), jitter=0.2, shear=0.3, seed=20 + k)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    g = _ctx(hb, k, "f32")
+    w, u = _fields(m, ref, 30 * k)
+    w32, u32 = w.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    for l in (-1, k - 1):
+        y = g.apply(_dev(g, w32), _dev(g, u32), l).cpu().numpy().astype(np.float64).reshape(m.n_elems, 3, ref.nb)
+        ref_y = H.apply(m, ref, w32, u32, l)
+        err = _rel(y, ref_y)
+        print(f"hex k={k} l={l}: FP32 normwise {err:.2e}")
+        assert err < 1e-6
+
+
+def test_hex_constant_state_and_errors():
+    from paper_2408_06698_gb300 import _lib as L
+    hb = W.hex_box(3, jitter=0.1, shear=0.2, seed=3)
+    m, ref = H.HexMesh(hb), H.RefHex(3)
+    g = _ctx(hb, 3, "f64")
+    c = H.project(m, ref, lambda x: np.broadcast_to([1.0, -0.5, 0.25], x.shape).copy())
+    y = g.apply(_dev(g, c), _dev(g, c), 1).cpu().numpy()
+    assert np.abs(y).max() < 1e-12
+    x = _dev(g, c)
+    with pytest.raises(L.HopuError) as ei:
+        g.apply(x, x, 1, out=x)
+    assert ei.value.status == L.HOPU_EINVAL
+    from paper_2408_06698_gb300 import HopuHex
+    with pytest.raises(L.HopuError) as ei:
+        HopuHex(hb.lines, hb.A, k=6)
+    assert ei.value.status == L.HOPU_ENOTSUP
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_hex_substeps(prec, tol):
+    k = 3
+    hb = W.hex_box((3, 3, 4), jitter=0.2, shear=0.3, seed=7)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    g = _ctx(hb, k, prec)
+    u0 = H.project(m, ref, W.taylor_green)
+    if prec == "f32":
+        u0 = u0.astype(np.float32).astype(np.float64)
+    dt, n, l = 2e-2, 4, 1
+    u = _dev(g, u0)
+    g.rk_substeps(u, dt, n, l)
+    got = u.cpu().numpy().astype(np.float64).reshape(u0.shape)
+    want = H.substeps_stage(m, ref, u0, dt, n, l)
+    err = _rel(got, want)
+    print(f"hex substeps {prec}: {err:.2e} (change {_rel(want, u0):.2e})")
+    assert err < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_hex_full_size_sampled(prec, tol):
+    """32^3 cells, k = 4 (the bench's hexahedral workload): the apply on Taylor-Green
+    data, checked on 64 sampled cells against the oracle on their 3x3x3 neighbourhoods."""
+    k, n = 4, 32
+    hb = W.hex_box(n, jitter=0.1, shear=0.2, seed=11)
+    g = _ctx(hb, k, prec)
+    m_small = None
+    mfull = H.HexMesh(hb)
+    ref = H.RefHex(k)
+    u = H.project(mfull, ref, W.taylor_green)
+    w = u
+    if prec == "f32":
+        u = w = u.astype(np.float32).astype(np.float64)
+    y = g.apply(_dev(g, w), _dev(g, u), k - 1).cpu().numpy().astype(np.float64).reshape(u.shape)
+    rng = np.random.default_rng(3)
+    cells = rng.choice(mfull.n_elems, size=64, replace=False)
+    want = _sampled_apply(mfull, ref, w, u, k - 1, cells)
+    err = _rel(y[cells], want)
+    print(f"hex 32^3 k=4 {prec}: sampled normwise {err:.2e}")
+    assert err < tol
+    del m_small
+
+
+def _sampled_apply(m, ref, w, u, l, cells):
+    """The oracle's apply on the given cells only: the residual is local to a cell and its
+    six facets, so run the oracle's per-facet quantities on those facets."""
+    E = m.n_elems
+    out = np.zeros((len(cells), 3, ref.nb))
+    U = np.einsum("qi,eai->eqa", ref.phi, u[cells])
+    Wv = np.einsum("qi,eai->eqa", ref.phi, w[cells])
+    Wt = np.einsum("e,ecb,eqb->eqc", m.absdet[cells], m.Jinv[cells], Wv)
+    out -= np.einsum("q,eqa,qic,eqc->eai", ref.wq, U, ref.dphi, Wt)
+    for j, e in enumerate(cells):
+        for d in range(3):
+            above = m.cell[e].copy()
+            above[d] = (above[d] + 1) % m.n[d]
+            ea = above[0] + m.n[0] * (above[1] + m.n[1] * above[2])
+            for F, side in ((d * E + ea, "A"), (d * E + e, "B")):
+                sub = _SubMesh(m, np.array([F]))
+                wn, jump, avg, PJ, Ph = H.facet_quantities(sub, ref, w, u, l)
+                g = wn[..., None] * avg + Ph
+                f = 2 * d + 1 if side == "A" else 2 * d
+                sgn = 1.0 if side == "A" else -1.0
+                out[j] += sgn * m.aF[F] * np.einsum("p,pa,pi->ai", ref.wf, g[0], ref.phi_f[f])
+    return out / m.absdet[cells, None, None]
+
+
+class _SubMesh:
+    """A view of some facets of a HexMesh (the attributes facet_quantities reads)."""
+
+    def __init__(self, m, facets):
+        self.n_facets = len(facets)
+        self.fa, self.fb, self.nF = m.fa[facets], m.fb[facets], m.nF[facets]

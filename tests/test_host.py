@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "hopu.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +26,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(os.path.join(INCLUDE, f)).read() for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(hopu_[a-z0-9_]+)\s*\(", text)))
 
@@ -120,6 +120,38 @@ def test_valid_mesh_without_device_fails_on_cuda_only(lib):
     m = W.periodic_box_mesh(2, 4)
     st, msg = _create(lib, m.coords, m.elems, m.rep)
     assert st == L.HOPU_ECUDA, msg                            # topology and tables built fine
+
+
+def _hex_create(lib, lines, A, n=(3, 3, 3), k=3, prec=0):
+    from ctypes import byref, c_void_p
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in lines]))
+    Am = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    h = c_void_p()
+    st = lib.hopu_hex_create(n[0], n[1], n[2], flat.ctypes.data, Am.ctypes.data, k, prec, None, byref(h))
+    msg = lib.hopu_hex_last_error(None).decode()
+    if h.value:
+        lib.hopu_hex_destroy(h)
+    return st, msg
+
+
+def test_hex_box_validation(lib):
+    """hopu_hex_create checks its arguments before any CUDA call."""
+    import torch
+    import workloads as W
+    from paper_2408_06698_gb300 import _lib as L
+    hb = W.hex_box(3, jitter=0.2, shear=0.3, seed=1)
+    bad = [x.copy() for x in hb.lines]
+    bad[1][2] = bad[1][1]                                       # a cell of zero width
+    assert _hex_create(lib, bad, hb.A)[0] == L.HOPU_EMESH
+    assert _hex_create(lib, hb.lines, -np.eye(3))[0] == L.HOPU_EMESH   # det A < 0
+    assert _hex_create(lib, hb.lines, hb.A, k=6)[0] == L.HOPU_ENOTSUP
+    assert _hex_create(lib, hb.lines, hb.A, k=1)[0] == L.HOPU_ENOTSUP
+    assert _hex_create(lib, hb.lines, hb.A, prec=2)[0] == L.HOPU_EINVAL  # tensor-core modes: no
+    small = [x[:3] for x in hb.lines]
+    assert _hex_create(lib, small, hb.A, n=(2, 2, 2))[0] == L.HOPU_EINVAL
+    if not torch.cuda.is_available():
+        st, msg = _hex_create(lib, hb.lines, hb.A)
+        assert st == L.HOPU_ECUDA, msg                          # valid box: fails on the device only
 
 
 _RANK_SCRIPT = r"""
