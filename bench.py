@@ -416,7 +416,28 @@ def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
     row["f32_apply_rel_error_vs_f64"] = float(np.linalg.norm(ya - yb) / np.linalg.norm(yb))
     row[f"f32_{substeps}_substeps_rel_error_vs_f64"] = float(np.linalg.norm(sa - sb) / np.linalg.norm(sb))
     row["fp32_over_fp64_speedup"] = row["f64"]["ms_per_substep"] / row["f32"]["ms_per_substep"]
+    vol, fac = hex_flops(k)
+    flops = vol * n ** 3 + fac * 3 * n ** 3
+    ach = flops / (row["f32"]["ms_per_apply"] / 1e3) / 1e12
+    peak = fp32_alu_peak_tflops(2070.0)
+    row["roofline_f32_apply"] = {"bound": "alu", "flops_per_apply": flops, "achieved": ach, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": ach / peak,
+                                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (maximum SM clock)",
+                                 "flops_per_cell_volume": vol, "flops_per_facet": fac}
     return row
+
+
+def hex_flops(k):
+    """Algorithmic flops (2 per multiply-add) of the hexahedral kernels, per cell (volume:
+    six fields' value + gradient passes, the point integrands, the three test passes, the
+    lift) and per facet (12 traces, 11 point fields to the points, 9 moment fields back)."""
+    K1, M = k + 1, (3 * k + 2) // 2
+    NB, NQ, NFM, NQF = K1 ** 3, M ** 3, K1 ** 2, M ** 2
+    interp = K1 * (2 * K1 * K1 * M + 3 * K1 * M * M + 4 * M ** 3)
+    test = M ** 3 * K1 + K1 ** 2 * M ** 2 + K1 ** 3 * M
+    vol = 2 * (6 * interp + 3 * test + 33 * NQ + 18 * NB)
+    fac = 2 * (12 * NFM * K1 + 11 * (K1 * M * K1 + M * M * K1) + 27 * NQF + 9 * (M * M * K1 + K1 * K1 * M))
+    return vol, fac
 
 
 def our_arm(args, rank, world):
@@ -778,7 +799,8 @@ def our_arm(args, rank, world):
 
 
 def profile_case(spec: str):
-    """A small case for ncu captures: n^3 x 6 box, order k, precision prec
+    """A small case for ncu captures ("hex,n,k,prec": the hexahedral path, three applies on
+    an n^3 box); else an n^3 x 6 box, order k, precision prec
     ("n,k,prec[,volume_variant[,tile_hint]]"): build the context (tile_hint as in
     hopu_options; optionally overriding the autotuner's STAGE volume variant, whose choice
     under a profiler can differ from the plain run's), interpolate Taylor-Green, three
@@ -789,6 +811,19 @@ def profile_case(spec: str):
     import workloads as W
     from paper_2408_06698_gb300 import Hopu
     f = spec.split(",")
+    if f[0] == "hex":
+        # "hex,n,k,prec": n^3 hexahedral box (the bench's hexahedral geometry), 3 applies
+        from paper_2408_06698_gb300 import HopuHex
+        n, k, prec = int(f[1]), int(f[2]), f[3]
+        hb = W.hex_box(n, jitter=0.1, shear=0.2, seed=11)
+        gh = HopuHex(hb.lines, hb.A, k=k, prec=prec)
+        u = torch.tensor(W.uniform_noise(gh.n_l2, 1.0, 3), dtype=gh.dtype, device=gh.device)
+        y = gh.new()
+        for _ in range(3):
+            gh.apply(u, u, k - 1, out=y)
+        torch.cuda.synchronize()
+        print("profile case ok", spec, float(y.abs().max()))
+        return
     n, k, prec = int(f[0]), int(f[1]), f[2]
     m = W.periodic_box_mesh(3, n)
     g = Hopu(m.coords, m.elems, m.rep, k=k, l=k - 1, prec=prec, tile_hint=int(f[4]) if len(f) > 4 else 0)

@@ -9,8 +9,8 @@
 // M_T = |det J| I, so the inverse mass is 1/|det J| per cell.
 //
 // One warp per cell (k_hex_volume) or per facet (k_hex_facet); the contractions run as
-// one-dimensional passes through the warp's shared-memory buffers (lanes over the outputs
-// of a pass).  Cell e = i0 + n0 (i1 + n1 i2); facet F = d E + e is the low facet of cell e
+// one-dimensional passes through the warp's shared-memory buffers (the volume kernel's lanes
+// own lines of the tensor, the facet kernel's the outputs of a pass).  Cell e = i0 + n0 (i1 + n1 i2); facet F = d E + e is the low facet of cell e
 // in direction d: side A the cell below (periodic), local facet x_d = 1; side B = e,
 // x_d = 0.  The facet coordinates (s, t) are the two other axes in increasing order.
 //
@@ -84,38 +84,52 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 
-template <typename T, int K>
-struct Vol {
-  using S = Shape<K>;
-  static constexpr int K1 = S::K1, M = S::M, NB = S::NB, NQ = S::NQ, NFM = S::NFM;
-  static constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
-  // one field's coefficients | x-pass (B, D) | y-pass (BB, BD, DB) | wind at the points
-  // (G w, |det J| div w) | the three integrands
-  static constexpr int O_C = 0;
-  static constexpr int O_X = O_C + NB;
-  static constexpr int O_Y = O_X + 2 * K1 * K1 * M;
-  static constexpr int O_W = O_Y + 3 * K1 * M * M;
-  static constexpr int O_F = O_W + 4 * NQ;
-  static constexpr int PER_WARP = O_F + 3 * NQ;
-  static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
-  static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
+// The 1D tables B[q][i], D[q][i] of one order, in registers (FP32) or read from shared
+// memory (FP64, where the FP64 FMA rate, not the loads, bounds the passes).
+template <typename T, int K, bool REG>
+struct Tab1 {
+  static constexpr int K1 = K + 1, M = Shape<K>::M;
+  T b_[REG ? M * K1 : 1], d_[REG ? M * K1 : 1];
+  const T* sb;
+  const T* sd;
+  __device__ __forceinline__ void load(const T* sB, const T* sD) {
+    sb = sB;
+    sd = sD;
+    if constexpr (REG) {
+#pragma unroll
+      for (int j = 0; j < M * K1; ++j) {
+        b_[j] = sB[j];
+        d_[j] = sD[j];
+      }
+    }
+  }
+  __device__ __forceinline__ T b(int q, int i) const {
+    if constexpr (REG) return b_[q * K1 + i];
+    else return sb[q * K1 + i];
+  }
+  __device__ __forceinline__ T d(int q, int i) const {
+    if constexpr (REG) return d_[q * K1 + i];
+    else return sd[q * K1 + i];
+  }
 };
 
 template <typename T, int K>
 struct Fac {
   using S = Shape<K>;
   static constexpr int K1 = S::K1, M = S::M, NB = S::NB, NFM = S::NFM, NQF = S::NQF;
+  static constexpr int K1o = K1 | 1, Mo = M | 1;  // odd line strides
   static constexpr int WARPS = 4;
+  static constexpr bool REG = sizeof(T) == 4;
   static constexpr int NV = 11;  // point fields: w.n, [[w.n]], [[u]] (3), <u> (3), (I-Pi)[[u]] (3)
   static constexpr int NM = 9;   // moment fields: S (3), T (3), h (3)
-  static constexpr int O_TR = 0;                 // traces: u^A, w^A, u^B, w^B (3 each)
-  static constexpr int O_TL = O_TR + 12 * NFM;   // their low parts (compensated sums)
-  static constexpr int O_V = O_TL + 12 * NFM;    // modal point fields
-  static constexpr int O_T = O_V + NV * NFM;     // x-pass
-  static constexpr int O_P = O_T + NV * K1 * M;  // point values
-  static constexpr int O_Q = O_P + NV * NQF;     // weighted integrands
-  static constexpr int O_U = O_Q + NM * NQF;     // transposed x-pass
-  static constexpr int O_MO = O_U + NM * M * K1; // moments
+  static constexpr int O_TR = 0;                     // traces: u^A, w^A, u^B, w^B (3 each)
+  static constexpr int O_TL = O_TR + 12 * NFM;       // their low parts (compensated sums)
+  static constexpr int O_V = O_TL + 12 * NFM;        // modal point fields [f][t][s]
+  static constexpr int O_T = O_V + NV * K1 * K1o;    // x-pass [f][p1][t]
+  static constexpr int O_P = O_T + NV * M * K1o;     // point values [f][p2][p1]
+  static constexpr int O_Q = O_P + NV * NQF;         // weighted integrands [f][p2][p1]
+  static constexpr int O_U = O_Q + NM * M * Mo;      // transposed x-pass [f][s][p2]
+  static constexpr int O_MO = O_U + NM * K1 * Mo;    // moments [f][t][s]
   static constexpr int PER_WARP = O_MO + NM * NFM;
   static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
   static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
@@ -160,11 +174,13 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
                 T* __restrict__ gam) {
   using C = Fac<T, K>;
   constexpr int K1 = C::K1, M = C::M, NB = C::NB, NFM = C::NFM, NQF = C::NQF, NV = C::NV, NM = C::NM;
+  constexpr int K1o = C::K1o, Mo = C::Mo;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   stage_tabs<T, K>(tb, sm);
   __syncthreads();
-  const T* sB = sm;
+  Tab1<T, K, C::REG> t1;
+  t1.load(sm, sm + M * K1);
   const T* sW = sm + 2 * M * K1;
   const T* sE0 = sW + M;
   const T* sE1 = sE0 + K1;
@@ -205,11 +221,14 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
       buf[C::O_TL + t] = lo;
     }
     __syncwarp();
-    // 2. modal point fields; the jumps from the pairs (hi_A - hi_B is exact for close traces)
+    // 2. modal point fields [f][t][s]; the jumps from the pairs (hi_A - hi_B is exact for
+    //    close traces)
     for (int mm = lane; mm < NFM; mm += 32) {
       const T* tr = buf + C::O_TR;
       const T* tl = buf + C::O_TL;
-      T* v = buf + C::O_V + mm;
+      const int s = mm % K1, tt = mm / K1;
+      T* v = buf + C::O_V + tt * K1o + s;
+      constexpr int FS = K1 * K1o;  // one field
       T ja[3], wa = T(0), wj = T(0);
       const T nv[3] = {n0, n1, n2};
 #pragma unroll
@@ -220,36 +239,45 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
         wa += T(0.5) * (wA + wB) * nv[a];
         wj += djw * nv[a];
         ja[a] = (uA - uB) + (tl[a * NFM + mm] - tl[(6 + a) * NFM + mm]);
-        v[(2 + a) * NFM] = ja[a];
-        v[(5 + a) * NFM] = T(0.5) * (uA + uB);
+        v[(2 + a) * FS] = ja[a];
+        v[(5 + a) * FS] = T(0.5) * (uA + uB);
       }
       v[0] = wa;
-      v[NFM] = wj;
-      const int s = mm % K1, tt = mm / K1;
+      v[FS] = wj;
       const bool low = (s > tt ? s : tt) <= l;
       const T jn = ja[0] * n0 + ja[1] * n1 + ja[2] * n2;
-      v[8 * NFM] = low ? jn * n0 : ja[0];
-      v[9 * NFM] = low ? jn * n1 : ja[1];
-      v[10 * NFM] = low ? jn * n2 : ja[2];
+      v[8 * FS] = low ? jn * n0 : ja[0];
+      v[9 * FS] = low ? jn * n1 : ja[1];
+      v[10 * FS] = low ? jn * n2 : ja[2];
     }
     __syncwarp();
-    // 3. to the points: x-pass over s, then y-pass over t
-    for (int t = lane; t < NV * K1 * M; t += 32) {
-      const int f = t / (K1 * M), r = t - f * K1 * M, tt = r / M, p1 = r - tt * M;
-      const T* v = buf + C::O_V + f * NFM + tt * K1;
-      T acc = T(0);
+    // 3. to the points, lanes owning lines: over s (lines (f, t)), then over t (lines (f, p1))
+    for (int L = lane; L < NV * K1; L += 32) {
+      const int f = L / K1, tt = L - f * K1;
+      T c[K1];
 #pragma unroll
-      for (int s = 0; s < K1; ++s) acc += sB[p1 * K1 + s] * v[s];
-      buf[C::O_T + t] = acc;
+      for (int s = 0; s < K1; ++s) c[s] = buf[C::O_V + L * K1o + s];
+#pragma unroll
+      for (int p1 = 0; p1 < M; ++p1) {
+        T acc = T(0);
+#pragma unroll
+        for (int s = 0; s < K1; ++s) acc = fma(t1.b(p1, s), c[s], acc);
+        buf[C::O_T + (f * M + p1) * K1o + tt] = acc;
+      }
     }
     __syncwarp();
-    for (int t = lane; t < NV * NQF; t += 32) {
-      const int f = t / NQF, p = t - f * NQF, p2 = p / M, p1 = p - p2 * M;
-      const T* v = buf + C::O_T + f * K1 * M + p1;
-      T acc = T(0);
+    for (int L = lane; L < NV * M; L += 32) {
+      const int f = L / M, p1 = L - f * M;
+      T c[K1];
 #pragma unroll
-      for (int tt = 0; tt < K1; ++tt) acc += sB[p2 * K1 + tt] * v[tt * M];
-      buf[C::O_P + t] = acc;
+      for (int tt = 0; tt < K1; ++tt) c[tt] = buf[C::O_T + L * K1o + tt];
+#pragma unroll
+      for (int p2 = 0; p2 < M; ++p2) {
+        T acc = T(0);
+#pragma unroll
+        for (int tt = 0; tt < K1; ++tt) acc = fma(t1.b(p2, tt), c[tt], acc);
+        buf[C::O_P + f * NQF + p2 * M + p1] = acc;
+      }
     }
     __syncwarp();
     // 4. weighted integrands at the points: 0-2 S, 3-5 T, 6-8 h = 1/2|w.n| (I-Pi)[[u]]
@@ -262,29 +290,40 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T ju = P[(2 + a) * NQF], au = P[(5 + a) * NQF], pj = P[(8 + a) * NQF];
-        buf[C::O_Q + a * NQF + p] = T(-0.5) * wgt * (wn * ju + wj * au);
-        buf[C::O_Q + (3 + a) * NQF + p] = T(-0.25) * wgt * wj * ju;
-        buf[C::O_Q + (6 + a) * NQF + p] = hw * pj;
+        const int qo = p2 * Mo + p1;
+        buf[C::O_Q + a * M * Mo + qo] = T(-0.5) * wgt * (wn * ju + wj * au);
+        buf[C::O_Q + (3 + a) * M * Mo + qo] = T(-0.25) * wgt * wj * ju;
+        buf[C::O_Q + (6 + a) * M * Mo + qo] = hw * pj;
       }
     }
     __syncwarp();
-    // 5. moments: transposed x-pass over p1, then y-pass over p2
-    for (int t = lane; t < NM * M * K1; t += 32) {
-      const int f = t / (M * K1), r = t - f * M * K1, p2 = r / K1, s = r - p2 * K1;
-      const T* q = buf + C::O_Q + f * NQF + p2 * M;
-      T acc = T(0);
+    // 5. moments: over p1 (lines (f, p2)), then over p2 (lines (f, s))
+    for (int L = lane; L < NM * M; L += 32) {
+      const int f = L / M, p2 = L - f * M;
+      T q[M];
 #pragma unroll
-      for (int p1 = 0; p1 < M; ++p1) acc += sB[p1 * K1 + s] * q[p1];
-      buf[C::O_U + t] = acc;
+      for (int p1 = 0; p1 < M; ++p1) q[p1] = buf[C::O_Q + L * Mo + p1];
+#pragma unroll
+      for (int s = 0; s < K1; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int p1 = 0; p1 < M; ++p1) acc = fma(t1.b(p1, s), q[p1], acc);
+        buf[C::O_U + (f * K1 + s) * Mo + p2] = acc;
+      }
     }
     __syncwarp();
-    for (int t = lane; t < NM * NFM; t += 32) {
-      const int f = t / NFM, mm = t - f * NFM, tt = mm / K1, s = mm - tt * K1;
-      const T* u = buf + C::O_U + f * M * K1 + s;
-      T acc = T(0);
+    for (int L = lane; L < NM * K1; L += 32) {
+      const int f = L / K1, s = L - f * K1;
+      T u[M];
 #pragma unroll
-      for (int p2 = 0; p2 < M; ++p2) acc += sB[p2 * K1 + tt] * u[p2 * K1];
-      buf[C::O_MO + t] = acc;
+      for (int p2 = 0; p2 < M; ++p2) u[p2] = buf[C::O_U + L * Mo + p2];
+#pragma unroll
+      for (int tt = 0; tt < K1; ++tt) {
+        T acc = T(0);
+#pragma unroll
+        for (int p2 = 0; p2 < M; ++p2) acc = fma(t1.b(p2, tt), u[p2], acc);
+        buf[C::O_MO + f * NFM + s + K1 * tt] = acc;
+      }
     }
     __syncwarp();
     // 6. Ph = (I - Pi^l) h on the moments; gA = S + T + Ph, gB = S - T - Ph; times a_F
@@ -307,107 +346,245 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
   }
 }
 
+template <typename T, int K>
+struct Vol {
+  using S = Shape<K>;
+  static constexpr int K1 = S::K1, M = S::M, NB = S::NB, NQ = S::NQ, NFM = S::NFM;
+  static constexpr int K1o = K1 | 1, Mo = M | 1;  // odd line strides: no bank conflicts
+  static constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
+  static constexpr bool REG = sizeof(T) == 4;
+  // three fields' coefficients [f][line (i2,i3)][i1] | x-pass B, D [f][line (q1,i3)][i2] |
+  // y-pass BB, BD, DB [f][line (q1,q2)][i3] | wind at the points [4][NQ] | integrands [3][NQ]
+  static constexpr int O_C = 0;
+  static constexpr int XS = 3 * K1 * M * K1o;   // one x-pass output set (three fields)
+  static constexpr int YS = 3 * M * M * K1o;    // one y-pass output set (three fields)
+  static constexpr int O_X = O_C + 3 * K1 * K1 * K1o;
+  static constexpr int O_Y = O_X + 2 * XS;
+  static constexpr int O_W = O_Y + 3 * YS;
+  static constexpr int O_F = O_W + 4 * NQ;
+  static constexpr int PER_WARP = O_F + 3 * NQ;
+  static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
+  static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
+  // the test passes reuse the y region (z-pass out, [a][line (q1,i3)][q2]) and the x region
+  // (y-pass out, [a][line (i2,i3)][q1])
+  static_assert(3 * K1 * M * Mo <= 3 * YS, "test z-pass buffer");
+  static_assert(3 * K1 * K1 * Mo <= 2 * XS, "test y-pass buffer");
+};
+
+// x- and y-pass of three fields (the coefficients in C): B and D over i1, then BB, BD
+// (from B) and DB (from D) over i2.  Lanes own lines of the tensor.
+template <typename T, int K, bool REG>
+__device__ __forceinline__ void interp_xy(const Tab1<T, K, REG>& tb, T* base, int lane) {
+  using C = Vol<T, K>;
+  constexpr int K1 = C::K1, M = C::M, K1o = C::K1o;
+  const T* Cf = base + C::O_C;
+  T* XB = base + C::O_X;
+  T* XD = XB + C::XS;
+  for (int L = lane; L < 3 * K1 * K1; L += 32) {
+    const int f = L / (K1 * K1), line = L - f * K1 * K1, i2 = line % K1, i3 = line / K1;
+    T c[K1];
+#pragma unroll
+    for (int i1 = 0; i1 < K1; ++i1) c[i1] = Cf[(f * K1 * K1 + line) * K1o + i1];
+    T* xb = XB + (f * K1 * M + i3 * M) * K1o + i2;
+    T* xd = XD + (f * K1 * M + i3 * M) * K1o + i2;
+#pragma unroll
+    for (int q1 = 0; q1 < M; ++q1) {
+      T sb = T(0), sd = T(0);
+#pragma unroll
+      for (int i1 = 0; i1 < K1; ++i1) {
+        sb = fma(tb.b(q1, i1), c[i1], sb);
+        sd = fma(tb.d(q1, i1), c[i1], sd);
+      }
+      xb[q1 * K1o] = sb;
+      xd[q1 * K1o] = sd;
+    }
+  }
+  __syncwarp();
+  T* YBB = base + C::O_Y;
+  T* YBD = YBB + C::YS;
+  T* YDB = YBD + C::YS;
+  for (int L = lane; L < 3 * K1 * M; L += 32) {
+    const int f = L / (K1 * M), line = L - f * K1 * M, q1 = line % M, i3 = line / M;
+    T xb[K1], xd[K1];
+#pragma unroll
+    for (int i2 = 0; i2 < K1; ++i2) {
+      xb[i2] = XB[(f * K1 * M + line) * K1o + i2];
+      xd[i2] = XD[(f * K1 * M + line) * K1o + i2];
+    }
+    const int o = (f * M * M + q1) * K1o + i3;
+#pragma unroll
+    for (int q2 = 0; q2 < M; ++q2) {
+      T bb = T(0), bd = T(0), db = T(0);
+#pragma unroll
+      for (int i2 = 0; i2 < K1; ++i2) {
+        bb = fma(tb.b(q2, i2), xb[i2], bb);
+        bd = fma(tb.d(q2, i2), xb[i2], bd);
+        db = fma(tb.b(q2, i2), xd[i2], db);
+      }
+      YBB[o + q2 * M * K1o] = bb;
+      YBD[o + q2 * M * K1o] = bd;
+      YDB[o + q2 * M * K1o] = db;
+    }
+  }
+  __syncwarp();
+}
+
+// z-pass of field f at one line (q1, q2): value v and reference derivatives d1, d2, d3 at
+// every q3
+template <typename T, int K, bool REG>
+__device__ __forceinline__ void interp_z(const Tab1<T, K, REG>& tb, const T* base, int f, int line, T (&v)[Shape<K>::M],
+                                         T (&d1)[Shape<K>::M], T (&d2)[Shape<K>::M], T (&d3)[Shape<K>::M]) {
+  using C = Vol<T, K>;
+  constexpr int K1 = C::K1, M = C::M, K1o = C::K1o;
+  const T* YBB = base + C::O_Y + (f * M * M + line) * K1o;
+  const T* YBD = YBB + C::YS;
+  const T* YDB = YBD + C::YS;
+  T bb[K1], bd[K1], db[K1];
+#pragma unroll
+  for (int i3 = 0; i3 < K1; ++i3) {
+    bb[i3] = YBB[i3];
+    bd[i3] = YBD[i3];
+    db[i3] = YDB[i3];
+  }
+#pragma unroll
+  for (int q3 = 0; q3 < M; ++q3) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+    for (int i3 = 0; i3 < K1; ++i3) {
+      const T b = tb.b(q3, i3);
+      a0 = fma(b, bb[i3], a0);
+      a3 = fma(tb.d(q3, i3), bb[i3], a3);
+      a2 = fma(b, bd[i3], a2);
+      a1 = fma(b, db[i3], a1);
+    }
+    v[q3] = a0;
+    d1[q3] = a1;
+    d2[q3] = a2;
+    d3[q3] = a3;
+  }
+}
+
 // Volume kernel + lift of the six facets' moments + inverse mass + the stage combination:
 //   y = (1/|det J|) (r_vol + r_fac),
 //   r_vol[a][i] = sum_q w_q ( sum_c (G w)_c d^_c u_a + |det J| div w  u_a ) phi_i,  G = |det J| J^-1,
 //   |det J| div w = sum_{c,b} G[c][b] d^_c w_b,
 //   out = c0 u0 + c1 us + c2 y   (out may alias u0: each warp reads and writes its own cell).
-// Each of the six fields (w_0..2, then u_0..2) goes through one x-pass (B and D tables), one
-// y-pass (BB, BD, DB) and a z-pass fused with its use at the points: the value and the three
-// reference derivatives are BBB, DBB, BDB, BBD.
+// One warp per cell; each pass is a set of one-dimensional contractions, a lane owning one
+// line of the tensor (its inputs in registers, the 1D tables in registers in FP32): the wind's
+// three components (x-, y-pass, then a z-pass that accumulates G w and |det J| div w at the
+// points), the velocity's (z-pass forming the integrands), and the test with phi_i (passes
+// over q3, q2, q1).  The values and reference derivatives are BBB, DBB, BDB, BBD.
 template <typename T, int K>
 __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
     k_hex_volume(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* us, const T* __restrict__ gam,
                  const T* u0, T c0, T c1, T c2, T* out) {
   using C = Vol<T, K>;
-  constexpr int K1 = C::K1, M = C::M, NB = C::NB, NQ = C::NQ, NFM = C::NFM;
-  constexpr int XS = K1 * K1 * M, YS = K1 * M * M, MM = M * M;
+  constexpr int K1 = C::K1, M = C::M, NB = C::NB, NQ = C::NQ, NFM = C::NFM, K1o = C::K1o, Mo = C::Mo;
+  constexpr int MM = M * M;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   stage_tabs<T, K>(tb, sm);
   __syncthreads();
-  const T* sB = sm;
-  const T* sD = sm + M * K1;
+  Tab1<T, K, C::REG> t1;
+  t1.load(sm, sm + M * K1);
   const T* sW = sm + 2 * M * K1;
   const T* sE0 = sW + M;
   const T* sE1 = sE0 + K1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* base = sm + C::TAB + warp * C::PER_WARP;
   T* Cf = base + C::O_C;
-  T* X = base + C::O_X;
-  T* Y = base + C::O_Y;
   T* Wp = base + C::O_W;  // [4][NQ]: (G w)_0..2, |det J| div w
   T* Fp = base + C::O_F;  // [3][NQ]
   for (int64_t e = (int64_t)blockIdx.x * C::WARPS + warp; e < m.E; e += (int64_t)gridDim.x * C::WARPS) {
     T G[9];
 #pragma unroll
     for (int j = 0; j < 9; ++j) G[j] = T(m.G[e * 9 + j]);
-    for (int f = 0; f < 6; ++f) {
-      const bool wind = f < 3;
-      const int comp = wind ? f : f - 3;
-      const T* src = (wind ? wL : us) + (e * 3 + comp) * NB;
-      for (int t = lane; t < NB; t += 32) Cf[t] = src[t];
-      __syncwarp();
-      // x-pass: X[0] = B over i1, X[1] = D over i1
-      for (int t = lane; t < 2 * XS; t += 32) {
-        const int v = t / XS, r = t - v * XS, i32 = r / M, q1 = r - i32 * M;
-        const T* tab = v ? sD : sB;
-        const T* c = Cf + i32 * K1;
-        T acc = T(0);
-#pragma unroll
-        for (int i1 = 0; i1 < K1; ++i1) acc += tab[q1 * K1 + i1] * c[i1];
-        X[t] = acc;
-      }
-      __syncwarp();
-      // y-pass: Y[0] = BB, Y[1] = BD (D over i2), Y[2] = DB (from the x-derivative)
-      for (int t = lane; t < 3 * YS; t += 32) {
-        const int o = t / YS, r = t - o * YS, i3 = r / MM, r2 = r - i3 * MM, q2 = r2 / M, q1 = r2 - q2 * M;
-        const T* tab = (o == 1) ? sD : sB;
-        const T* c = X + (o == 2 ? XS : 0) + i3 * K1 * M + q1;
-        T acc = T(0);
-#pragma unroll
-        for (int i2 = 0; i2 < K1; ++i2) acc += tab[q2 * K1 + i2] * c[i2 * M];
-        Y[t] = acc;
-      }
-      __syncwarp();
-      // z-pass fused with the use at the points; column comp of G (selects, not an indexed load)
-      const T gc0 = comp == 0 ? G[0] : (comp == 1 ? G[1] : G[2]);
-      const T gc1 = comp == 0 ? G[3] : (comp == 1 ? G[4] : G[5]);
-      const T gc2 = comp == 0 ? G[6] : (comp == 1 ? G[7] : G[8]);
-      for (int q = lane; q < NQ; q += 32) {
-        const int q3 = q / MM, r2 = q - q3 * MM;
-        T v = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
-#pragma unroll
-        for (int i3 = 0; i3 < K1; ++i3) {
-          const T b = sB[q3 * K1 + i3], dz = sD[q3 * K1 + i3];
-          const T bb = Y[i3 * MM + r2];
-          v += b * bb;
-          d3 += dz * bb;
-          d2 += b * Y[YS + i3 * MM + r2];
-          d1 += b * Y[2 * YS + i3 * MM + r2];
-        }
-        if (wind) {
-          const T W0 = gc0 * v, W1 = gc1 * v, W2 = gc2 * v;
-          const T dv = gc0 * d1 + gc1 * d2 + gc2 * d3;
-          if (comp == 0) {
-            Wp[q] = W0;
-            Wp[NQ + q] = W1;
-            Wp[2 * NQ + q] = W2;
-            Wp[3 * NQ + q] = dv;
-          } else {
-            Wp[q] += W0;
-            Wp[NQ + q] += W1;
-            Wp[2 * NQ + q] += W2;
-            Wp[3 * NQ + q] += dv;
-          }
-        } else {
-          const int q2 = r2 / M, q1 = r2 - q2 * M;
-          const T wq = sW[q1] * sW[q2] * sW[q3];
-          Fp[comp * NQ + q] = wq * (Wp[q] * d1 + Wp[NQ + q] * d2 + Wp[2 * NQ + q] * d3 + Wp[3 * NQ + q] * v);
-        }
-      }
-      __syncwarp();
+    // wind: coefficients, x- and y-pass, z-pass accumulating (G w) and |det J| div w
+    for (int t = lane; t < 3 * NB; t += 32) {
+      const int f = t / NB, i = t - f * NB;
+      Cf[(f * K1 * K1 + i / K1) * K1o + i % K1] = wL[e * 3 * NB + t];
     }
+    __syncwarp();
+    interp_xy<T, K, C::REG>(t1, base, lane);
+    for (int line = lane; line < MM; line += 32) {
+      T W0[M], W1[M], W2[M], DV[M];
+#pragma unroll
+      for (int q3 = 0; q3 < M; ++q3) W0[q3] = W1[q3] = W2[q3] = DV[q3] = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        T v[M], d1[M], d2[M], d3[M];
+        interp_z<T, K, C::REG>(t1, base, b, line, v, d1, d2, d3);
+#pragma unroll
+        for (int q3 = 0; q3 < M; ++q3) {
+          W0[q3] = fma(G[0 * 3 + b], v[q3], W0[q3]);
+          W1[q3] = fma(G[1 * 3 + b], v[q3], W1[q3]);
+          W2[q3] = fma(G[2 * 3 + b], v[q3], W2[q3]);
+          DV[q3] = fma(G[0 * 3 + b], d1[q3], fma(G[1 * 3 + b], d2[q3], fma(G[2 * 3 + b], d3[q3], DV[q3])));
+        }
+      }
+#pragma unroll
+      for (int q3 = 0; q3 < M; ++q3) {
+        Wp[line + q3 * MM] = W0[q3];
+        Wp[NQ + line + q3 * MM] = W1[q3];
+        Wp[2 * NQ + line + q3 * MM] = W2[q3];
+        Wp[3 * NQ + line + q3 * MM] = DV[q3];
+      }
+    }
+    __syncwarp();
+    // velocity: the integrands w_q ((G w) . grad^ u_a + |det J| div w u_a)
+    for (int t = lane; t < 3 * NB; t += 32) {
+      const int f = t / NB, i = t - f * NB;
+      Cf[(f * K1 * K1 + i / K1) * K1o + i % K1] = us[e * 3 * NB + t];
+    }
+    __syncwarp();
+    interp_xy<T, K, C::REG>(t1, base, lane);
+    for (int line = lane; line < MM; line += 32) {
+      const int q1 = line % M, q2 = line / M;
+      const T w12 = sW[q1] * sW[q2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T v[M], d1[M], d2[M], d3[M];
+        interp_z<T, K, C::REG>(t1, base, a, line, v, d1, d2, d3);
+#pragma unroll
+        for (int q3 = 0; q3 < M; ++q3) {
+          const int q = line + q3 * MM;
+          const T s = Wp[q] * d1[q3] + Wp[NQ + q] * d2[q3] + Wp[2 * NQ + q] * d3[q3] + Wp[3 * NQ + q] * v[q3];
+          Fp[a * NQ + q] = (w12 * sW[q3]) * s;
+        }
+      }
+    }
+    __syncwarp();
+    // test with phi_i: over q3 (lines (q1, q2)), q2 (lines (q1, i3)), q1 (lines (i2, i3))
+    T* Gz = base + C::O_Y;  // [a][line (q1, i3)][q2], stride Mo
+    T* Hx = base + C::O_X;  // [a][line (i2, i3)][q1], stride Mo
+    for (int L = lane; L < 3 * MM; L += 32) {
+      const int a = L / MM, line = L - a * MM, q1 = line % M, q2 = line / M;
+      T f[M];
+#pragma unroll
+      for (int q3 = 0; q3 < M; ++q3) f[q3] = Fp[a * NQ + line + q3 * MM];
+#pragma unroll
+      for (int i3 = 0; i3 < K1; ++i3) {
+        T s = T(0);
+#pragma unroll
+        for (int q3 = 0; q3 < M; ++q3) s = fma(t1.b(q3, i3), f[q3], s);
+        Gz[(a * K1 * M + q1 + M * i3) * Mo + q2] = s;
+      }
+    }
+    __syncwarp();
+    for (int L = lane; L < 3 * K1 * M; L += 32) {
+      const int a = L / (K1 * M), line = L - a * K1 * M, q1 = line % M, i3 = line / M;
+      T g[M];
+#pragma unroll
+      for (int q2 = 0; q2 < M; ++q2) g[q2] = Gz[(a * K1 * M + line) * Mo + q2];
+#pragma unroll
+      for (int i2 = 0; i2 < K1; ++i2) {
+        T s = T(0);
+#pragma unroll
+        for (int q2 = 0; q2 < M; ++q2) s = fma(t1.b(q2, i2), g[q2], s);
+        Hx[(a * K1 * K1 + i2 + K1 * i3) * Mo + q1] = s;
+      }
+    }
+    __syncwarp();
     const T ia = T(m.invabs[e]);
     int64_t fA[3], fB[3];
 #pragma unroll
@@ -415,45 +592,37 @@ __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
       fB[d] = d * m.E + e;
       fA[d] = d * m.E + cell_shift(m, e, d, 1);
     }
-    for (int a = 0; a < 3; ++a) {
-      // test with phi_i: passes over q3, q2, q1 (B tables)
-      for (int t = lane; t < YS; t += 32) {
-        const int i3 = t / MM, r2 = t - i3 * MM;
-        const T* f = Fp + a * NQ + r2;
-        T acc = T(0);
+    for (int L = lane; L < 3 * K1 * K1; L += 32) {
+      const int a = L / (K1 * K1), line = L - a * K1 * K1, i2 = line % K1, i3 = line / K1;
+      T h[M];
 #pragma unroll
-        for (int q3 = 0; q3 < M; ++q3) acc += sB[q3 * K1 + i3] * f[q3 * MM];
-        Y[t] = acc;
-      }
-      __syncwarp();
-      for (int t = lane; t < XS; t += 32) {
-        const int i3 = t / (K1 * M), r = t - i3 * K1 * M, i2 = r / M, q1 = r - i2 * M;
-        const T* g = Y + i3 * MM + q1;
-        T acc = T(0);
+      for (int q1 = 0; q1 < M; ++q1) h[q1] = Hx[(a * K1 * K1 + line) * Mo + q1];
+      // facet moments: direction 0 -> mode (i2, i3), 1 -> (i1, i3), 2 -> (i1, i2)
+      const T* gA0 = gam + (fA[0] * 6 + a) * NFM + i2 + K1 * i3;
+      const T* gB0 = gam + (fB[0] * 6 + 3 + a) * NFM + i2 + K1 * i3;
+      const T* gA1 = gam + (fA[1] * 6 + a) * NFM + K1 * i3;
+      const T* gB1 = gam + (fB[1] * 6 + 3 + a) * NFM + K1 * i3;
+      const T* gA2 = gam + (fA[2] * 6 + a) * NFM + K1 * i2;
+      const T* gB2 = gam + (fB[2] * 6 + 3 + a) * NFM + K1 * i2;
+      const T f0A = *gA0, f0B = *gB0;
+      const T l1 = sE1[i2], l0 = sE0[i2];
+      const T m1 = sE1[i3], m0 = sE0[i3];
 #pragma unroll
-        for (int q2 = 0; q2 < M; ++q2) acc += sB[q2 * K1 + i2] * g[q2 * M];
-        X[t] = acc;
-      }
-      __syncwarp();
-      for (int i = lane; i < NB; i += 32) {
-        const int i3 = i / (K1 * K1), i2 = (i / K1) % K1, i1 = i % K1;
-        const T* h = X + (i3 * K1 + i2) * M;
+      for (int i1 = 0; i1 < K1; ++i1) {
         T r = T(0);
 #pragma unroll
-        for (int q1 = 0; q1 < M; ++q1) r += sB[q1 * K1 + i1] * h[q1];
-        // facets: direction 0 -> (s, t) = (i2, i3), 1 -> (i1, i3), 2 -> (i1, i2)
-        const int md0 = i2 + K1 * i3, md1 = i1 + K1 * i3, md2 = i1 + K1 * i2;
-        r += sE1[i1] * gam[(fA[0] * 6 + a) * NFM + md0] + sE0[i1] * gam[(fB[0] * 6 + 3 + a) * NFM + md0];
-        r += sE1[i2] * gam[(fA[1] * 6 + a) * NFM + md1] + sE0[i2] * gam[(fB[1] * 6 + 3 + a) * NFM + md1];
-        r += sE1[i3] * gam[(fA[2] * 6 + a) * NFM + md2] + sE0[i3] * gam[(fB[2] * 6 + 3 + a) * NFM + md2];
-        const int64_t o = (e * 3 + a) * NB + i;
+        for (int q1 = 0; q1 < M; ++q1) r = fma(t1.b(q1, i1), h[q1], r);
+        r += sE1[i1] * f0A + sE0[i1] * f0B;
+        r += l1 * gA1[i1] + l0 * gB1[i1];
+        r += m1 * gA2[i1] + m0 * gB2[i1];
+        const int64_t o = (e * 3 + a) * NB + i1 + K1 * line;
         T v = c2 * (r * ia);
         if (c1 != T(0)) v += c1 * us[o];
         if (c0 != T(0)) v += c0 * u0[o];
         out[o] = v;
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
 }
 
