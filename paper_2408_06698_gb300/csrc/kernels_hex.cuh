@@ -198,7 +198,13 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
     // 1. traces: fields 0-2 u^A, 3-5 w^A, 6-8 u^B, 9-11 w^B, each a compensated sum
     //    (hi + lo: error-free products by FMA, Knuth's TwoSum, L(0 or 1) as hi + lo), so that
     //    the jumps of nearly equal traces keep their relative accuracy in FP32
-    for (int t = lane; t < 12 * NFM; t += 32) {
+    //    (a compile-time trip count, so that the loads of every output of the lane are
+    //    issued before the sums wait on them)
+    constexpr int NTR = (12 * NFM + 31) / 32;
+#pragma unroll
+    for (int it = 0; it < NTR; ++it) {
+      const int t = lane + 32 * it;
+      if (t >= 12 * NFM) break;
       const int f = t / NFM, mm = t - f * NFM;
       const int s = mm % K1, tt = mm / K1;
       const bool sideA = f < 6;
@@ -206,10 +212,13 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
       const T* src = ((f % 6) < 3 ? uL : wL) + ((sideA ? eA : eB) * 3 + comp) * NB;
       const T* en = sideA ? sE1 : sE0;
       const T* el = sideA ? sE1l : sE0l;
+      T cv[K1];
+#pragma unroll
+      for (int ad = 0; ad < K1; ++ad) cv[ad] = __ldg(src + mode_index<K1>(d, ad, s, tt));
       T hi = T(0), lo = T(0);
 #pragma unroll
       for (int ad = 0; ad < K1; ++ad) {
-        const T c = src[mode_index<K1>(d, ad, s, tt)];
+        const T c = cv[ad];
         const T p = mul_rn(en[ad], c);
         const T pe = fma(en[ad], c, -p);
         const T sum = add_rn(hi, p);
@@ -351,28 +360,26 @@ struct Vol {
   using S = Shape<K>;
   static constexpr int K1 = S::K1, M = S::M, NB = S::NB, NQ = S::NQ, NFM = S::NFM;
   static constexpr int K1o = K1 | 1, Mo = M | 1;  // odd line strides: no bank conflicts
-  static constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
+  static constexpr int WARPS = 4;
   static constexpr bool REG = sizeof(T) == 4;
-  // three fields' coefficients [f][line (i2,i3)][i1] | x-pass B, D [f][line (q1,i3)][i2] |
-  // y-pass BB, BD, DB [f][line (q1,q2)][i3] | wind at the points [4][NQ] | integrands [3][NQ]
+  // one field's coefficients [line (i2,i3)][i1] | x-pass B, D [line (q1,i3)][i2] | y-pass BB,
+  // BD, DB [line (q1,q2)][i3] | wind at the points [4][NQ] | test pass over q3 of one
+  // component [line (q1,i3)][q2]; the test pass over q2 reuses the x region
+  static constexpr int XS = K1 * M * K1o;
+  static constexpr int YS = M * M * K1o;
   static constexpr int O_C = 0;
-  static constexpr int XS = 3 * K1 * M * K1o;   // one x-pass output set (three fields)
-  static constexpr int YS = 3 * M * M * K1o;    // one y-pass output set (three fields)
-  static constexpr int O_X = O_C + 3 * K1 * K1 * K1o;
+  static constexpr int O_X = O_C + K1 * K1 * K1o;
   static constexpr int O_Y = O_X + 2 * XS;
   static constexpr int O_W = O_Y + 3 * YS;
-  static constexpr int O_F = O_W + 4 * NQ;
-  static constexpr int PER_WARP = O_F + 3 * NQ;
+  static constexpr int O_G = O_W + 4 * NQ;
+  static constexpr int PER_WARP = O_G + K1 * M * Mo;
   static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
   static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
-  // the test passes reuse the y region (z-pass out, [a][line (q1,i3)][q2]) and the x region
-  // (y-pass out, [a][line (i2,i3)][q1])
-  static_assert(3 * K1 * M * Mo <= 3 * YS, "test z-pass buffer");
-  static_assert(3 * K1 * K1 * Mo <= 2 * XS, "test y-pass buffer");
+  static_assert(K1 * K1 * Mo <= 2 * XS, "test pass over q2 in the x region");
 };
 
-// x- and y-pass of three fields (the coefficients in C): B and D over i1, then BB, BD
-// (from B) and DB (from D) over i2.  Lanes own lines of the tensor.
+// x- and y-pass of one field (its coefficients in C): B and D over i1, then BB, BD (from B)
+// and DB (from D) over i2.  Lanes own lines of the tensor.
 template <typename T, int K, bool REG>
 __device__ __forceinline__ void interp_xy(const Tab1<T, K, REG>& tb, T* base, int lane) {
   using C = Vol<T, K>;
@@ -380,13 +387,13 @@ __device__ __forceinline__ void interp_xy(const Tab1<T, K, REG>& tb, T* base, in
   const T* Cf = base + C::O_C;
   T* XB = base + C::O_X;
   T* XD = XB + C::XS;
-  for (int L = lane; L < 3 * K1 * K1; L += 32) {
-    const int f = L / (K1 * K1), line = L - f * K1 * K1, i2 = line % K1, i3 = line / K1;
+  for (int line = lane; line < K1 * K1; line += 32) {
+    const int i2 = line % K1, i3 = line / K1;
     T c[K1];
 #pragma unroll
-    for (int i1 = 0; i1 < K1; ++i1) c[i1] = Cf[(f * K1 * K1 + line) * K1o + i1];
-    T* xb = XB + (f * K1 * M + i3 * M) * K1o + i2;
-    T* xd = XD + (f * K1 * M + i3 * M) * K1o + i2;
+    for (int i1 = 0; i1 < K1; ++i1) c[i1] = Cf[line * K1o + i1];
+    T* xb = XB + i3 * M * K1o + i2;
+    T* xd = XD + i3 * M * K1o + i2;
 #pragma unroll
     for (int q1 = 0; q1 < M; ++q1) {
       T sb = T(0), sd = T(0);
@@ -403,15 +410,15 @@ __device__ __forceinline__ void interp_xy(const Tab1<T, K, REG>& tb, T* base, in
   T* YBB = base + C::O_Y;
   T* YBD = YBB + C::YS;
   T* YDB = YBD + C::YS;
-  for (int L = lane; L < 3 * K1 * M; L += 32) {
-    const int f = L / (K1 * M), line = L - f * K1 * M, q1 = line % M, i3 = line / M;
+  for (int line = lane; line < K1 * M; line += 32) {
+    const int q1 = line % M, i3 = line / M;
     T xb[K1], xd[K1];
 #pragma unroll
     for (int i2 = 0; i2 < K1; ++i2) {
-      xb[i2] = XB[(f * K1 * M + line) * K1o + i2];
-      xd[i2] = XD[(f * K1 * M + line) * K1o + i2];
+      xb[i2] = XB[line * K1o + i2];
+      xd[i2] = XD[line * K1o + i2];
     }
-    const int o = (f * M * M + q1) * K1o + i3;
+    const int o = q1 * K1o + i3;
 #pragma unroll
     for (int q2 = 0; q2 < M; ++q2) {
       T bb = T(0), bd = T(0), db = T(0);
@@ -429,14 +436,13 @@ __device__ __forceinline__ void interp_xy(const Tab1<T, K, REG>& tb, T* base, in
   __syncwarp();
 }
 
-// z-pass of field f at one line (q1, q2): value v and reference derivatives d1, d2, d3 at
-// every q3
+// z-pass at one line (q1, q2): value v and reference derivatives d1, d2, d3 at every q3
 template <typename T, int K, bool REG>
-__device__ __forceinline__ void interp_z(const Tab1<T, K, REG>& tb, const T* base, int f, int line, T (&v)[Shape<K>::M],
+__device__ __forceinline__ void interp_z(const Tab1<T, K, REG>& tb, const T* base, int line, T (&v)[Shape<K>::M],
                                          T (&d1)[Shape<K>::M], T (&d2)[Shape<K>::M], T (&d3)[Shape<K>::M]) {
   using C = Vol<T, K>;
   constexpr int K1 = C::K1, M = C::M, K1o = C::K1o;
-  const T* YBB = base + C::O_Y + (f * M * M + line) * K1o;
+  const T* YBB = base + C::O_Y + line * K1o;
   const T* YBD = YBB + C::YS;
   const T* YDB = YBD + C::YS;
   T bb[K1], bd[K1], db[K1];
@@ -469,11 +475,12 @@ __device__ __forceinline__ void interp_z(const Tab1<T, K, REG>& tb, const T* bas
 //   r_vol[a][i] = sum_q w_q ( sum_c (G w)_c d^_c u_a + |det J| div w  u_a ) phi_i,  G = |det J| J^-1,
 //   |det J| div w = sum_{c,b} G[c][b] d^_c w_b,
 //   out = c0 u0 + c1 us + c2 y   (out may alias u0: each warp reads and writes its own cell).
-// One warp per cell; each pass is a set of one-dimensional contractions, a lane owning one
-// line of the tensor (its inputs in registers, the 1D tables in registers in FP32): the wind's
-// three components (x-, y-pass, then a z-pass that accumulates G w and |det J| div w at the
-// points), the velocity's (z-pass forming the integrands), and the test with phi_i (passes
-// over q3, q2, q1).  The values and reference derivatives are BBB, DBB, BDB, BBD.
+// One warp per cell, one field at a time (w_0..2, then u_0..2); each pass is a set of
+// one-dimensional contractions, a lane owning one line of the tensor (its inputs in
+// registers, the 1D tables in registers in FP32).  The wind's z-pass accumulates G w and
+// |det J| div w at the points; a velocity component's z-pass forms its integrand along the
+// line and contracts it with phi over q3 at once, then the passes over q2 and q1 finish its
+// test.  The values and reference derivatives are BBB, DBB, BDB, BBD.
 template <typename T, int K>
 __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
     k_hex_volume(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* us, const T* __restrict__ gam,
@@ -494,97 +501,12 @@ __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
   T* base = sm + C::TAB + warp * C::PER_WARP;
   T* Cf = base + C::O_C;
   T* Wp = base + C::O_W;  // [4][NQ]: (G w)_0..2, |det J| div w
-  T* Fp = base + C::O_F;  // [3][NQ]
+  T* Gz = base + C::O_G;  // [line (q1, i3)][q2]
+  T* Hx = base + C::O_X;  // [line (i2, i3)][q1]
   for (int64_t e = (int64_t)blockIdx.x * C::WARPS + warp; e < m.E; e += (int64_t)gridDim.x * C::WARPS) {
     T G[9];
 #pragma unroll
     for (int j = 0; j < 9; ++j) G[j] = T(m.G[e * 9 + j]);
-    // wind: coefficients, x- and y-pass, z-pass accumulating (G w) and |det J| div w
-    for (int t = lane; t < 3 * NB; t += 32) {
-      const int f = t / NB, i = t - f * NB;
-      Cf[(f * K1 * K1 + i / K1) * K1o + i % K1] = wL[e * 3 * NB + t];
-    }
-    __syncwarp();
-    interp_xy<T, K, C::REG>(t1, base, lane);
-    for (int line = lane; line < MM; line += 32) {
-      T W0[M], W1[M], W2[M], DV[M];
-#pragma unroll
-      for (int q3 = 0; q3 < M; ++q3) W0[q3] = W1[q3] = W2[q3] = DV[q3] = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        T v[M], d1[M], d2[M], d3[M];
-        interp_z<T, K, C::REG>(t1, base, b, line, v, d1, d2, d3);
-#pragma unroll
-        for (int q3 = 0; q3 < M; ++q3) {
-          W0[q3] = fma(G[0 * 3 + b], v[q3], W0[q3]);
-          W1[q3] = fma(G[1 * 3 + b], v[q3], W1[q3]);
-          W2[q3] = fma(G[2 * 3 + b], v[q3], W2[q3]);
-          DV[q3] = fma(G[0 * 3 + b], d1[q3], fma(G[1 * 3 + b], d2[q3], fma(G[2 * 3 + b], d3[q3], DV[q3])));
-        }
-      }
-#pragma unroll
-      for (int q3 = 0; q3 < M; ++q3) {
-        Wp[line + q3 * MM] = W0[q3];
-        Wp[NQ + line + q3 * MM] = W1[q3];
-        Wp[2 * NQ + line + q3 * MM] = W2[q3];
-        Wp[3 * NQ + line + q3 * MM] = DV[q3];
-      }
-    }
-    __syncwarp();
-    // velocity: the integrands w_q ((G w) . grad^ u_a + |det J| div w u_a)
-    for (int t = lane; t < 3 * NB; t += 32) {
-      const int f = t / NB, i = t - f * NB;
-      Cf[(f * K1 * K1 + i / K1) * K1o + i % K1] = us[e * 3 * NB + t];
-    }
-    __syncwarp();
-    interp_xy<T, K, C::REG>(t1, base, lane);
-    for (int line = lane; line < MM; line += 32) {
-      const int q1 = line % M, q2 = line / M;
-      const T w12 = sW[q1] * sW[q2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        T v[M], d1[M], d2[M], d3[M];
-        interp_z<T, K, C::REG>(t1, base, a, line, v, d1, d2, d3);
-#pragma unroll
-        for (int q3 = 0; q3 < M; ++q3) {
-          const int q = line + q3 * MM;
-          const T s = Wp[q] * d1[q3] + Wp[NQ + q] * d2[q3] + Wp[2 * NQ + q] * d3[q3] + Wp[3 * NQ + q] * v[q3];
-          Fp[a * NQ + q] = (w12 * sW[q3]) * s;
-        }
-      }
-    }
-    __syncwarp();
-    // test with phi_i: over q3 (lines (q1, q2)), q2 (lines (q1, i3)), q1 (lines (i2, i3))
-    T* Gz = base + C::O_Y;  // [a][line (q1, i3)][q2], stride Mo
-    T* Hx = base + C::O_X;  // [a][line (i2, i3)][q1], stride Mo
-    for (int L = lane; L < 3 * MM; L += 32) {
-      const int a = L / MM, line = L - a * MM, q1 = line % M, q2 = line / M;
-      T f[M];
-#pragma unroll
-      for (int q3 = 0; q3 < M; ++q3) f[q3] = Fp[a * NQ + line + q3 * MM];
-#pragma unroll
-      for (int i3 = 0; i3 < K1; ++i3) {
-        T s = T(0);
-#pragma unroll
-        for (int q3 = 0; q3 < M; ++q3) s = fma(t1.b(q3, i3), f[q3], s);
-        Gz[(a * K1 * M + q1 + M * i3) * Mo + q2] = s;
-      }
-    }
-    __syncwarp();
-    for (int L = lane; L < 3 * K1 * M; L += 32) {
-      const int a = L / (K1 * M), line = L - a * K1 * M, q1 = line % M, i3 = line / M;
-      T g[M];
-#pragma unroll
-      for (int q2 = 0; q2 < M; ++q2) g[q2] = Gz[(a * K1 * M + line) * Mo + q2];
-#pragma unroll
-      for (int i2 = 0; i2 < K1; ++i2) {
-        T s = T(0);
-#pragma unroll
-        for (int q2 = 0; q2 < M; ++q2) s = fma(t1.b(q2, i2), g[q2], s);
-        Hx[(a * K1 * K1 + i2 + K1 * i3) * Mo + q1] = s;
-      }
-    }
-    __syncwarp();
     const T ia = T(m.invabs[e]);
     int64_t fA[3], fB[3];
 #pragma unroll
@@ -592,37 +514,107 @@ __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
       fB[d] = d * m.E + e;
       fA[d] = d * m.E + cell_shift(m, e, d, 1);
     }
-    for (int L = lane; L < 3 * K1 * K1; L += 32) {
-      const int a = L / (K1 * K1), line = L - a * K1 * K1, i2 = line % K1, i3 = line / K1;
-      T h[M];
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+      const bool wind = f < 3;
+      const int comp = wind ? f : f - 3;
+      const T* src = (wind ? wL : us) + (e * 3 + comp) * NB;
+      for (int i = lane; i < NB; i += 32) Cf[(i / K1) * K1o + i % K1] = src[i];
+      __syncwarp();
+      interp_xy<T, K, C::REG>(t1, base, lane);
+      // column comp of G (selects, not an indexed load)
+      const T gc0 = comp == 0 ? G[0] : (comp == 1 ? G[1] : G[2]);
+      const T gc1 = comp == 0 ? G[3] : (comp == 1 ? G[4] : G[5]);
+      const T gc2 = comp == 0 ? G[6] : (comp == 1 ? G[7] : G[8]);
+      for (int line = lane; line < MM; line += 32) {
+        T v[M], d1[M], d2[M], d3[M];
+        interp_z<T, K, C::REG>(t1, base, line, v, d1, d2, d3);
+        if (wind) {
 #pragma unroll
-      for (int q1 = 0; q1 < M; ++q1) h[q1] = Hx[(a * K1 * K1 + line) * Mo + q1];
-      // facet moments: direction 0 -> mode (i2, i3), 1 -> (i1, i3), 2 -> (i1, i2)
-      const T* gA0 = gam + (fA[0] * 6 + a) * NFM + i2 + K1 * i3;
-      const T* gB0 = gam + (fB[0] * 6 + 3 + a) * NFM + i2 + K1 * i3;
-      const T* gA1 = gam + (fA[1] * 6 + a) * NFM + K1 * i3;
-      const T* gB1 = gam + (fB[1] * 6 + 3 + a) * NFM + K1 * i3;
-      const T* gA2 = gam + (fA[2] * 6 + a) * NFM + K1 * i2;
-      const T* gB2 = gam + (fB[2] * 6 + 3 + a) * NFM + K1 * i2;
-      const T f0A = *gA0, f0B = *gB0;
-      const T l1 = sE1[i2], l0 = sE0[i2];
-      const T m1 = sE1[i3], m0 = sE0[i3];
+          for (int q3 = 0; q3 < M; ++q3) {
+            const int q = line + q3 * MM;
+            const T W0 = gc0 * v[q3], W1 = gc1 * v[q3], W2 = gc2 * v[q3];
+            const T dv = fma(gc0, d1[q3], fma(gc1, d2[q3], gc2 * d3[q3]));
+            if (comp == 0) {
+              Wp[q] = W0;
+              Wp[NQ + q] = W1;
+              Wp[2 * NQ + q] = W2;
+              Wp[3 * NQ + q] = dv;
+            } else {
+              Wp[q] += W0;
+              Wp[NQ + q] += W1;
+              Wp[2 * NQ + q] += W2;
+              Wp[3 * NQ + q] += dv;
+            }
+          }
+        } else {
+          const int q1 = line % M, q2 = line / M;
+          const T w12 = sW[q1] * sW[q2];
+          T fz[M];
 #pragma unroll
-      for (int i1 = 0; i1 < K1; ++i1) {
-        T r = T(0);
+          for (int q3 = 0; q3 < M; ++q3) {
+            const int q = line + q3 * MM;
+            const T s = Wp[q] * d1[q3] + Wp[NQ + q] * d2[q3] + Wp[2 * NQ + q] * d3[q3] + Wp[3 * NQ + q] * v[q3];
+            fz[q3] = (w12 * sW[q3]) * s;
+          }
+          // test over q3
 #pragma unroll
-        for (int q1 = 0; q1 < M; ++q1) r = fma(t1.b(q1, i1), h[q1], r);
-        r += sE1[i1] * f0A + sE0[i1] * f0B;
-        r += l1 * gA1[i1] + l0 * gB1[i1];
-        r += m1 * gA2[i1] + m0 * gB2[i1];
-        const int64_t o = (e * 3 + a) * NB + i1 + K1 * line;
-        T v = c2 * (r * ia);
-        if (c1 != T(0)) v += c1 * us[o];
-        if (c0 != T(0)) v += c0 * u0[o];
-        out[o] = v;
+          for (int i3 = 0; i3 < K1; ++i3) {
+            T acc = T(0);
+#pragma unroll
+            for (int q3 = 0; q3 < M; ++q3) acc = fma(t1.b(q3, i3), fz[q3], acc);
+            Gz[(q1 + M * i3) * Mo + q2] = acc;
+          }
+        }
       }
+      __syncwarp();
+      if (wind) continue;
+      // test over q2 (lines (q1, i3)), then over q1 (lines (i2, i3)) + lift + epilogue
+      for (int line = lane; line < K1 * M; line += 32) {
+        const int q1 = line % M, i3 = line / M;
+        T g[M];
+#pragma unroll
+        for (int q2 = 0; q2 < M; ++q2) g[q2] = Gz[line * Mo + q2];
+#pragma unroll
+        for (int i2 = 0; i2 < K1; ++i2) {
+          T acc = T(0);
+#pragma unroll
+          for (int q2 = 0; q2 < M; ++q2) acc = fma(t1.b(q2, i2), g[q2], acc);
+          Hx[(i2 + K1 * i3) * Mo + q1] = acc;
+        }
+      }
+      __syncwarp();
+      const int a = comp;
+      for (int line = lane; line < K1 * K1; line += 32) {
+        const int i2 = line % K1, i3 = line / K1;
+        T h[M];
+#pragma unroll
+        for (int q1 = 0; q1 < M; ++q1) h[q1] = Hx[line * Mo + q1];
+        // facet moments: direction 0 -> mode (i2, i3), 1 -> (i1, i3), 2 -> (i1, i2)
+        const T f0A = gam[(fA[0] * 6 + a) * NFM + i2 + K1 * i3];
+        const T f0B = gam[(fB[0] * 6 + 3 + a) * NFM + i2 + K1 * i3];
+        const T* gA1 = gam + (fA[1] * 6 + a) * NFM + K1 * i3;
+        const T* gB1 = gam + (fB[1] * 6 + 3 + a) * NFM + K1 * i3;
+        const T* gA2 = gam + (fA[2] * 6 + a) * NFM + K1 * i2;
+        const T* gB2 = gam + (fB[2] * 6 + 3 + a) * NFM + K1 * i2;
+        const T l1 = sE1[i2], l0 = sE0[i2], m1 = sE1[i3], m0 = sE0[i3];
+#pragma unroll
+        for (int i1 = 0; i1 < K1; ++i1) {
+          T r = T(0);
+#pragma unroll
+          for (int q1 = 0; q1 < M; ++q1) r = fma(t1.b(q1, i1), h[q1], r);
+          r += sE1[i1] * f0A + sE0[i1] * f0B;
+          r += l1 * gA1[i1] + l0 * gB1[i1];
+          r += m1 * gA2[i1] + m0 * gB2[i1];
+          const int64_t o = (e * 3 + a) * NB + i1 + K1 * line;
+          T v = c2 * (r * ia);
+          if (c1 != T(0)) v += c1 * us[o];
+          if (c0 != T(0)) v += c0 * u0[o];
+          out[o] = v;
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
