@@ -503,7 +503,22 @@ __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
   T* Wp = base + C::O_W;  // [4][NQ]: (G w)_0..2, |det J| div w
   T* Gz = base + C::O_G;  // [line (q1, i3)][q2]
   T* Hx = base + C::O_X;  // [line (i2, i3)][q1]
-  for (int64_t e = (int64_t)blockIdx.x * C::WARPS + warp; e < m.E; e += (int64_t)gridDim.x * C::WARPS) {
+  // the next field's coefficients are loaded into registers while the current one is
+  // processed (the first field of the warp's next cell after the last one)
+  constexpr int NPRE = (NB + 31) / 32;
+  const int64_t estep = (int64_t)gridDim.x * C::WARPS;
+  T pre[NPRE];
+  auto prefetch = [&](int64_t ee, int ff) {
+    if (ee >= m.E) return;
+    const T* src = (ff < 3 ? wL : us) + (ee * 3 + (ff < 3 ? ff : ff - 3)) * NB;
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int i = lane + 32 * j;
+      if (i < NB) pre[j] = src[i];
+    }
+  };
+  prefetch((int64_t)blockIdx.x * C::WARPS + warp, 0);
+  for (int64_t e = (int64_t)blockIdx.x * C::WARPS + warp; e < m.E; e += estep) {
     T G[9];
 #pragma unroll
     for (int j = 0; j < 9; ++j) G[j] = T(m.G[e * 9 + j]);
@@ -518,9 +533,14 @@ __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
     for (int f = 0; f < 6; ++f) {
       const bool wind = f < 3;
       const int comp = wind ? f : f - 3;
-      const T* src = (wind ? wL : us) + (e * 3 + comp) * NB;
-      for (int i = lane; i < NB; i += 32) Cf[(i / K1) * K1o + i % K1] = src[i];
+#pragma unroll
+      for (int j = 0; j < NPRE; ++j) {
+        const int i = lane + 32 * j;
+        if (i < NB) Cf[(i / K1) * K1o + i % K1] = pre[j];
+      }
       __syncwarp();
+      if (f < 5) prefetch(e, f + 1);
+      else prefetch(e + estep, 0);
       interp_xy<T, K, C::REG>(t1, base, lane);
       // column comp of G (selects, not an indexed load)
       const T gc0 = comp == 0 ? G[0] : (comp == 1 ? G[1] : G[2]);
