@@ -156,16 +156,25 @@ int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, 
   T* gam = static_cast<T*>(h->d_gam);
   int gf = 0, gv = 0;
   auto kf = k_hex_facet<T, K>;
-  auto kv = k_hex_volume<T, K>;
   using CF = Fac<T, K>;
-  using CV = Vol<T, K>;
-  if (grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf) ||
-      grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
+  if (grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf))
     return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
   kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_facet launch");
-  kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, w, us, gam, u0, c0, c1, c2, out);
+  if (w == us) {  // the wind is the convected field: each component interpolated once
+    auto kv = k_hex_volume_same<T, K>;
+    using CV = VolS<T, K>;
+    if (grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
+      return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
+    kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, us, gam, u0, c0, c1, c2, out);
+  } else {
+    auto kv = k_hex_volume<T, K>;
+    using CV = Vol<T, K>;
+    if (grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
+      return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
+    kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, w, us, gam, u0, c0, c1, c2, out);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_volume launch");
   return HOPU_OK;

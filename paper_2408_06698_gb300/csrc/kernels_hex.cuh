@@ -133,6 +133,7 @@ struct Fac {
   static constexpr int PER_WARP = O_MO + NM * NFM;
   static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
   static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
+  static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
 
 template <typename T, int K>
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* buf = sm + C::TAB + warp * C::PER_WARP;
   const int64_t NF = 3 * m.E;
+  const bool same = wL == uL;
   for (int64_t F = (int64_t)blockIdx.x * C::WARPS + warp; F < NF; F += (int64_t)gridDim.x * C::WARPS) {
     const int d = int(F / m.E);
     const int64_t eB = F - d * m.E;
@@ -200,12 +202,17 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
     //    the jumps of nearly equal traces keep their relative accuracy in FP32
     //    (a compile-time trip count, so that the loads of every output of the lane are
     //    issued before the sums wait on them)
+    //    (when the wind is the convected field, w = u as in a STAGE substep, only the six
+    //    velocity traces are formed and read for both)
     constexpr int NTR = (12 * NFM + 31) / 32;
+    const int ntr = same ? 6 * NFM : 12 * NFM;
 #pragma unroll
     for (int it = 0; it < NTR; ++it) {
-      const int t = lane + 32 * it;
-      if (t >= 12 * NFM) break;
-      const int f = t / NFM, mm = t - f * NFM;
+      const int t0 = lane + 32 * it;
+      if (t0 >= ntr) break;
+      const int f0 = t0 / NFM, mm = t0 - f0 * NFM;
+      const int f = same && f0 >= 3 ? f0 + 3 : f0;
+      const int t = f * NFM + mm;
       const int s = mm % K1, tt = mm / K1;
       const bool sideA = f < 6;
       const int comp = (f % 6) % 3;
@@ -243,8 +250,9 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T uA = tr[a * NFM + mm], uB = tr[(6 + a) * NFM + mm];
-        const T wA = tr[(3 + a) * NFM + mm], wB = tr[(9 + a) * NFM + mm];
-        const T djw = (wA - wB) + (tl[(3 + a) * NFM + mm] - tl[(9 + a) * NFM + mm]);
+        const int iwA = same ? a : 3 + a, iwB = same ? 6 + a : 9 + a;
+        const T wA = tr[iwA * NFM + mm], wB = tr[iwB * NFM + mm];
+        const T djw = (wA - wB) + (tl[iwA * NFM + mm] - tl[iwB * NFM + mm]);
         wa += T(0.5) * (wA + wB) * nv[a];
         wj += djw * nv[a];
         ja[a] = (uA - uB) + (tl[a * NFM + mm] - tl[(6 + a) * NFM + mm]);
@@ -376,6 +384,7 @@ struct Vol {
   static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
   static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
   static_assert(K1 * K1 * Mo <= 2 * XS, "test pass over q2 in the x region");
+  static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
 
 // x- and y-pass of one field (its coefficients in C): B and D over i1, then BB, BD (from B)
@@ -635,6 +644,237 @@ __global__ void __launch_bounds__(32 * Vol<T, K>::WARPS)
       }
       __syncwarp();
     }
+  }
+}
+
+// The volume kernel when the wind is the convected field (w = u, a STAGE substep): the three
+// components pass through x and y once (batched), and one z-pass per line of points forms,
+// point by point, the values and reference derivatives of all three, G u, |det J| div u, the
+// three integrands and their test over q3; the passes over q2 and q1, the lift, the inverse
+// mass and the stage combination follow as in k_hex_volume.  Half the interpolation work.
+template <typename T, int K>
+struct VolS {
+  using S = Shape<K>;
+  static constexpr int K1 = S::K1, M = S::M, NB = S::NB, NQ = S::NQ, NFM = S::NFM;
+  static constexpr int K1o = K1 | 1, Mo = M | 1;
+  static constexpr int WARPS = sizeof(T) == 8 ? 2 : 4;
+  static constexpr bool REG = sizeof(T) == 4;
+  static constexpr int CS = K1 * K1 * K1o;  // one field's coefficients [line (i2,i3)][i1]
+  static constexpr int XS = K1 * M * K1o;   // one x-pass output [line (q1,i3)][i2]
+  static constexpr int YS = M * M * K1o;    // one y-pass output [line (q1,q2)][i3]
+  static constexpr int GS = K1 * M * Mo;    // one test pass over q3 [line (q1,i3)][q2]
+  static constexpr int O_C = 0;
+  static constexpr int O_X = O_C + 3 * CS;      // [f][B|D]
+  static constexpr int O_Y = O_X + 6 * XS;      // [f][BB|BD|DB]
+  static constexpr int O_G = O_Y + 9 * YS;      // [a]
+  static constexpr int PER_WARP = O_G + 3 * GS;
+  static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
+  static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
+  static_assert(3 * K1 * K1 * Mo <= 6 * XS, "test pass over q2 in the x region");
+  static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(32 * VolS<T, K>::WARPS)
+    k_hex_volume_same(MeshDev m, Tabs<T> tb, const T* us, const T* __restrict__ gam, const T* u0, T c0, T c1,
+                      T c2, T* out) {
+  using C = VolS<T, K>;
+  constexpr int K1 = C::K1, M = C::M, NB = C::NB, NFM = C::NFM, K1o = C::K1o, Mo = C::Mo;
+  constexpr int MM = M * M, XS = C::XS, YS = C::YS, GS = C::GS, CS = C::CS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  stage_tabs<T, K>(tb, sm);
+  __syncthreads();
+  Tab1<T, K, C::REG> t1;
+  t1.load(sm, sm + M * K1);
+  const T* sW = sm + 2 * M * K1;
+  const T* sE0 = sW + M;
+  const T* sE1 = sE0 + K1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* base = sm + C::TAB + warp * C::PER_WARP;
+  T* Cf = base + C::O_C;
+  T* X = base + C::O_X;
+  T* Y = base + C::O_Y;
+  T* Gz = base + C::O_G;
+  T* Hx = X;  // [a][line (i2, i3)][q1]
+  constexpr int NPRE = (3 * NB + 31) / 32;
+  const int64_t estep = (int64_t)gridDim.x * C::WARPS;
+  T pre[NPRE];
+  auto prefetch = [&](int64_t ee) {
+    if (ee >= m.E) return;
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int t = lane + 32 * j;
+      if (t < 3 * NB) pre[j] = us[ee * 3 * NB + t];
+    }
+  };
+  prefetch((int64_t)blockIdx.x * C::WARPS + warp);
+  for (int64_t e = (int64_t)blockIdx.x * C::WARPS + warp; e < m.E; e += estep) {
+    T G[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) G[j] = T(m.G[e * 9 + j]);
+    const T ia = T(m.invabs[e]);
+    int64_t fA[3], fB[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      fB[d] = d * m.E + e;
+      fA[d] = d * m.E + cell_shift(m, e, d, 1);
+    }
+#pragma unroll
+    for (int j = 0; j < NPRE; ++j) {
+      const int t = lane + 32 * j;
+      if (t < 3 * NB) {
+        const int f = t / NB, i = t - f * NB;
+        Cf[f * CS + (i / K1) * K1o + i % K1] = pre[j];
+      }
+    }
+    __syncwarp();
+    prefetch(e + estep);
+    // x-pass (lines (f, i2, i3)): B and D over i1
+    for (int L = lane; L < 3 * K1 * K1; L += 32) {
+      const int f = L / (K1 * K1), line = L - f * K1 * K1, i2 = line % K1, i3 = line / K1;
+      T c[K1];
+#pragma unroll
+      for (int i1 = 0; i1 < K1; ++i1) c[i1] = Cf[f * CS + line * K1o + i1];
+      T* xb = X + 2 * f * XS + i3 * M * K1o + i2;
+#pragma unroll
+      for (int q1 = 0; q1 < M; ++q1) {
+        T sb = T(0), sd = T(0);
+#pragma unroll
+        for (int i1 = 0; i1 < K1; ++i1) {
+          sb = fma(t1.b(q1, i1), c[i1], sb);
+          sd = fma(t1.d(q1, i1), c[i1], sd);
+        }
+        xb[q1 * K1o] = sb;
+        xb[XS + q1 * K1o] = sd;
+      }
+    }
+    __syncwarp();
+    // y-pass (lines (f, q1, i3)): BB, BD, DB over i2
+    for (int L = lane; L < 3 * K1 * M; L += 32) {
+      const int f = L / (K1 * M), line = L - f * K1 * M, q1 = line % M, i3 = line / M;
+      T xb[K1], xd[K1];
+#pragma unroll
+      for (int i2 = 0; i2 < K1; ++i2) {
+        xb[i2] = X[2 * f * XS + line * K1o + i2];
+        xd[i2] = X[(2 * f + 1) * XS + line * K1o + i2];
+      }
+      T* y = Y + 3 * f * YS + q1 * K1o + i3;
+#pragma unroll
+      for (int q2 = 0; q2 < M; ++q2) {
+        T bb = T(0), bd = T(0), db = T(0);
+#pragma unroll
+        for (int i2 = 0; i2 < K1; ++i2) {
+          bb = fma(t1.b(q2, i2), xb[i2], bb);
+          bd = fma(t1.d(q2, i2), xb[i2], bd);
+          db = fma(t1.b(q2, i2), xd[i2], db);
+        }
+        y[q2 * M * K1o] = bb;
+        y[YS + q2 * M * K1o] = bd;
+        y[2 * YS + q2 * M * K1o] = db;
+      }
+    }
+    __syncwarp();
+    // z-pass (lines (q1, q2)), point by point: values and derivatives of the three
+    // components, G u, |det J| div u, the integrands and their test over q3
+    for (int line = lane; line < MM; line += 32) {
+      const int q1 = line % M, q2 = line / M;
+      const T w12 = sW[q1] * sW[q2];
+      T in[3][3][K1];  // [component][BB, BD, DB][i3]
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int o = 0; o < 3; ++o)
+#pragma unroll
+          for (int i3 = 0; i3 < K1; ++i3) in[f][o][i3] = Y[(3 * f + o) * YS + line * K1o + i3];
+      T acc[3][K1];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i3 = 0; i3 < K1; ++i3) acc[a][i3] = T(0);
+#pragma unroll
+      for (int q3 = 0; q3 < M; ++q3) {
+        T v[3], d1[3], d2[3], d3[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+          for (int i3 = 0; i3 < K1; ++i3) {
+            const T b = t1.b(q3, i3);
+            a0 = fma(b, in[f][0][i3], a0);
+            a3 = fma(t1.d(q3, i3), in[f][0][i3], a3);
+            a2 = fma(b, in[f][1][i3], a2);
+            a1 = fma(b, in[f][2][i3], a1);
+          }
+          v[f] = a0;
+          d1[f] = a1;
+          d2[f] = a2;
+          d3[f] = a3;
+        }
+        const T W0 = G[0] * v[0] + G[1] * v[1] + G[2] * v[2];
+        const T W1 = G[3] * v[0] + G[4] * v[1] + G[5] * v[2];
+        const T W2 = G[6] * v[0] + G[7] * v[1] + G[8] * v[2];
+        T dv = T(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) dv += G[b] * d1[b] + G[3 + b] * d2[b] + G[6 + b] * d3[b];
+        const T wq = w12 * sW[q3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T fz = wq * (W0 * d1[a] + W1 * d2[a] + W2 * d3[a] + dv * v[a]);
+#pragma unroll
+          for (int i3 = 0; i3 < K1; ++i3) acc[a][i3] = fma(t1.b(q3, i3), fz, acc[a][i3]);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i3 = 0; i3 < K1; ++i3) Gz[a * GS + (q1 + M * i3) * Mo + q2] = acc[a][i3];
+    }
+    __syncwarp();
+    // test over q2 (lines (a, q1, i3))
+    for (int L = lane; L < 3 * K1 * M; L += 32) {
+      const int a = L / (K1 * M), line = L - a * K1 * M, q1 = line % M, i3 = line / M;
+      T g[M];
+#pragma unroll
+      for (int q2 = 0; q2 < M; ++q2) g[q2] = Gz[a * GS + line * Mo + q2];
+#pragma unroll
+      for (int i2 = 0; i2 < K1; ++i2) {
+        T s = T(0);
+#pragma unroll
+        for (int q2 = 0; q2 < M; ++q2) s = fma(t1.b(q2, i2), g[q2], s);
+        Hx[(a * K1 * K1 + i2 + K1 * i3) * Mo + q1] = s;
+      }
+    }
+    __syncwarp();
+    // test over q1 (lines (a, i2, i3)) + lift + inverse mass + stage combination
+    for (int L = lane; L < 3 * K1 * K1; L += 32) {
+      const int a = L / (K1 * K1), line = L - a * K1 * K1, i2 = line % K1, i3 = line / K1;
+      T h[M];
+#pragma unroll
+      for (int q1 = 0; q1 < M; ++q1) h[q1] = Hx[(a * K1 * K1 + line) * Mo + q1];
+      const T f0A = gam[(fA[0] * 6 + a) * NFM + i2 + K1 * i3];
+      const T f0B = gam[(fB[0] * 6 + 3 + a) * NFM + i2 + K1 * i3];
+      const T* gA1 = gam + (fA[1] * 6 + a) * NFM + K1 * i3;
+      const T* gB1 = gam + (fB[1] * 6 + 3 + a) * NFM + K1 * i3;
+      const T* gA2 = gam + (fA[2] * 6 + a) * NFM + K1 * i2;
+      const T* gB2 = gam + (fB[2] * 6 + 3 + a) * NFM + K1 * i2;
+      const T l1 = sE1[i2], l0 = sE0[i2], m1 = sE1[i3], m0 = sE0[i3];
+#pragma unroll
+      for (int i1 = 0; i1 < K1; ++i1) {
+        T r = T(0);
+#pragma unroll
+        for (int q1 = 0; q1 < M; ++q1) r = fma(t1.b(q1, i1), h[q1], r);
+        r += sE1[i1] * f0A + sE0[i1] * f0B;
+        r += l1 * gA1[i1] + l0 * gB1[i1];
+        r += m1 * gA2[i1] + m0 * gB2[i1];
+        const int64_t o = (e * 3 + a) * NB + i1 + K1 * line;
+        T v = c2 * (r * ia);
+        if (c1 != T(0)) v += c1 * us[o];
+        if (c0 != T(0)) v += c0 * u0[o];
+        out[o] = v;
+      }
+    }
+    __syncwarp();
   }
 }
 

@@ -63,6 +63,26 @@ def test_hex_apply_fp32(k):
         assert err < 1e-6
 
 
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_hex_apply_wind_is_field(k, prec, tol):
+    """The apply with the wind the convected field itself (one tensor for both: the kernel
+    that interpolates each component once), on noisy Taylor-Green data."""
+    hb = W.hex_box((3, 4, 3), jitter=0.2, shear=0.3, seed=40 + k)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    g = _ctx(hb, k, prec)
+    _, u = _fields(m, ref, 50 * k)
+    if prec == "f32":
+        u = u.astype(np.float32).astype(np.float64)
+    ud = _dev(g, u)
+    for l in (-1, k - 1):
+        y = g.apply(ud, ud, l).cpu().numpy().astype(np.float64).reshape(u.shape)
+        ref_y = H.apply(m, ref, u, u, l)
+        err = _rel(y, ref_y)
+        print(f"hex w=u k={k} l={l} {prec}: normwise {err:.2e}")
+        assert err < tol
+
+
 def test_hex_constant_state_and_errors():
     from paper_2408_06698_gb300 import _lib as L
     hb = W.hex_box(3, jitter=0.1, shear=0.2, seed=3)
@@ -114,7 +134,8 @@ def test_hex_full_size_sampled(prec, tol):
     w = u
     if prec == "f32":
         u = w = u.astype(np.float32).astype(np.float64)
-    y = g.apply(_dev(g, w), _dev(g, u), k - 1).cpu().numpy().astype(np.float64).reshape(u.shape)
+    ud = _dev(g, u)
+    y = g.apply(ud, ud, k - 1).cpu().numpy().astype(np.float64).reshape(u.shape)   # w = u: one tensor
     rng = np.random.default_rng(3)
     cells = rng.choice(mfull.n_elems, size=64, replace=False)
     want = _sampled_apply(mfull, ref, w, u, k - 1, cells)
