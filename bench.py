@@ -416,7 +416,7 @@ def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
     row["f32_apply_rel_error_vs_f64"] = float(np.linalg.norm(ya - yb) / np.linalg.norm(yb))
     row[f"f32_{substeps}_substeps_rel_error_vs_f64"] = float(np.linalg.norm(sa - sb) / np.linalg.norm(sb))
     row["fp32_over_fp64_speedup"] = row["f64"]["ms_per_substep"] / row["f32"]["ms_per_substep"]
-    vol, fac = hex_flops(k)
+    vol, fac = hex_flops(k, same=True)    # the apply and substeps run with w = u
     flops = vol * n ** 3 + fac * 3 * n ** 3
     ach = flops / (row["f32"]["ms_per_apply"] / 1e3) / 1e12
     peak = fp32_alu_peak_tflops(2070.0)
@@ -427,16 +427,19 @@ def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
     return row
 
 
-def hex_flops(k):
+def hex_flops(k, same=True):
     """Algorithmic flops (2 per multiply-add) of the hexahedral kernels, per cell (volume:
-    six fields' value + gradient passes, the point integrands, the three test passes, the
-    lift) and per facet (12 traces, 11 point fields to the points, 9 moment fields back)."""
+    the value + gradient passes of the fields (three when the wind is the convected field,
+    six otherwise), the point integrands, the three test passes, the lift) and per facet
+    (the traces (6 or 12), 11 point fields to the points, 9 moment fields back)."""
     K1, M = k + 1, (3 * k + 2) // 2
     NB, NQ, NFM, NQF = K1 ** 3, M ** 3, K1 ** 2, M ** 2
+    nfield = 3 if same else 6
     interp = K1 * (2 * K1 * K1 * M + 3 * K1 * M * M + 4 * M ** 3)
     test = M ** 3 * K1 + K1 ** 2 * M ** 2 + K1 ** 3 * M
-    vol = 2 * (6 * interp + 3 * test + 33 * NQ + 18 * NB)
-    fac = 2 * (12 * NFM * K1 + 11 * (K1 * M * K1 + M * M * K1) + 27 * NQF + 9 * (M * M * K1 + K1 * K1 * M))
+    vol = 2 * (nfield * interp + 3 * test + 33 * NQ + 18 * NB)
+    fac = 2 * (2 * nfield * NFM * K1 + 11 * (K1 * M * K1 + M * M * K1) + 27 * NQF
+               + 9 * (M * M * K1 + K1 * K1 * M))
     return vol, fac
 
 

@@ -120,6 +120,7 @@ struct Fac {
   static constexpr int K1o = K1 | 1, Mo = M | 1;  // odd line strides
   static constexpr int WARPS = 4;
   static constexpr bool REG = sizeof(T) == 4;
+  static constexpr int MINB = sizeof(T) == 4 && K <= 4 ? 5 : 1;  // resident CTAs per SM the registers allow
   static constexpr int NV = 11;  // point fields: w.n, [[w.n]], [[u]] (3), <u> (3), (I-Pi)[[u]] (3)
   static constexpr int NM = 9;   // moment fields: S (3), T (3), h (3)
   static constexpr int O_TR = 0;                     // traces: u^A, w^A, u^B, w^B (3 each)
@@ -170,7 +171,7 @@ __device__ __forceinline__ int64_t cell_shift(const MeshDev& m, int64_t e, int d
 //   gA = S + T + Ph, gB = S - T - Ph,  S = -1/2 (w.n) [[u]] - 1/2 [[w.n]] <u>,  T = -1/4 [[w.n]] [[u]]
 // (S + T = -1/2 (w.n)[[u]] - 1/2 [[w.n]] u^A, S - T the same with u^B).
 template <typename T, int K>
-__global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
+__global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     k_hex_facet(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* __restrict__ uL, int l,
                 T* __restrict__ gam) {
   using C = Fac<T, K>;
@@ -191,9 +192,12 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS)
   T* buf = sm + C::TAB + warp * C::PER_WARP;
   const int64_t NF = 3 * m.E;
   const bool same = wL == uL;
-  for (int64_t F = (int64_t)blockIdx.x * C::WARPS + warp; F < NF; F += (int64_t)gridDim.x * C::WARPS) {
-    const int d = int(F / m.E);
-    const int64_t eB = F - d * m.E;
+  // work item wi -> the facet of direction wi % 3 below cell wi / 3: the three facets of a
+  // cell are taken together, so that its coefficients are read from DRAM once
+  for (int64_t wi = (int64_t)blockIdx.x * C::WARPS + warp; wi < NF; wi += (int64_t)gridDim.x * C::WARPS) {
+    const int d = int(wi % 3);
+    const int64_t eB = wi / 3;
+    const int64_t F = d * m.E + eB;
     const int64_t eA = cell_shift(m, eB, d, -1);
     const T n0 = T(m.nF[F * 3 + 0]), n1 = T(m.nF[F * 3 + 1]), n2 = T(m.nF[F * 3 + 2]);
     const T aF = T(m.aF[F]);
