@@ -380,18 +380,27 @@ def other_configs(dev, stream, world):
 
 def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
     """The hexahedral path: 32^3 parallelepipeds (jittered spacings, sheared), k = 4, l = 3,
-    seeded U[-1, 1] coefficients (timing does not depend on the data; the smooth-field
-    accuracy is covered by the parity tests); FP32 and FP64 apply and STAGE substeps (CUDA
-    events), the FP32 apply and substeps against FP64 on the same rounded input."""
+    piecewise Taylor-Green data with noise (the smooth-field accuracy against the oracle is
+    covered by the parity tests); FP32 and FP64 apply and STAGE substeps (CUDA events), the
+    FP32 apply and substeps against FP64 on the same rounded input."""
     import numpy as np
     import torch
 
     import workloads as W
     from paper_2408_06698_gb300 import HopuHex
     hb = W.hex_box(n, jitter=0.1, shear=0.2, seed=11)
-    nl2 = n ** 3 * 3 * (k + 1) ** 3
-    u0 = W.uniform_noise(nl2, 1.0, 77).astype(np.float32).astype(np.float64)
-    row = {"workload": f"{n}^3 hexahedra (parallelepipeds), k={k}, l={l}, STAGE wind, U[-1,1] coefficients",
+    nb = (k + 1) ** 3
+    nl2 = n ** 3 * 3 * nb
+    # cell means (coefficient 0 of each component block, L_0 = 1) from Taylor-Green at the
+    # cell centres, U[-1e-3, 1e-3] on every coefficient
+    mid = [0.5 * (x[1:] + x[:-1]) for x in hb.lines]
+    c2, c1, c0 = np.meshgrid(mid[2], mid[1], mid[0], indexing="ij")    # cell index: axis 0 fastest
+    xc = np.stack([c0.reshape(-1), c1.reshape(-1), c2.reshape(-1)], axis=-1) @ np.asarray(hb.A).T
+    u0 = W.uniform_noise(nl2, 1e-3, 77).reshape(n ** 3, 3, nb)
+    u0[:, :, 0] += W.taylor_green(xc)
+    u0 = u0.reshape(-1).astype(np.float32).astype(np.float64)
+    row = {"workload": f"{n}^3 hexahedra (parallelepipeds), k={k}, l={l}, STAGE wind; cell means from "
+                       "Taylor-Green at the cell centres, U[-1e-3, 1e-3] on every coefficient",
            "cells": n ** 3, "l2_dofs": nl2}
     res = {}
     for prec in ("f32", "f64"):
