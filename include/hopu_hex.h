@@ -61,6 +61,16 @@ int hopu_hex_apply(hopu_hex* h, const void* wL, const void* uL, int l, void* yL)
  * L2 vector uL (the wind is the stage's own field). */
 int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l);
 
+/* FP64 reductions (row a8 of the hot path; synchronises the stream):
+ *   host_out[0] = 1/2 int |u|^2                             (kinetic energy)
+ *   host_out[1] = c(w; u, u)                                (0 if wL is NULL)
+ *   host_out[2] = sum_F int 1/2 |w.n| |(I-Pi^l)[[u]]|^2     (facet dissipation; 0 if NULL)
+ * The point values are those of the working precision, summed in FP64.  Uses the
+ * context's stage scratch (not to be called while substeps are in flight on another
+ * stream).  For a divergence-free w with a continuous normal component,
+ * host_out[1] == host_out[2] >= 0. */
+int hopu_hex_energy(hopu_hex* h, const void* wL, const void* uL, int l, double* host_out);
+
 /* Text of the last failure of h (NULL: of the last failed hopu_hex_create); never NULL. */
 const char* hopu_hex_last_error(const hopu_hex* h);
 

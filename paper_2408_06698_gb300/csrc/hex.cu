@@ -2,6 +2,7 @@
 // host in FP64, the sum-factorised kernels of kernels_hex.cuh on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,9 @@ struct hopu_hex {
   void* d_gam = nullptr;     // facet moments [3E][2][3][(k+1)^2] (side A, side B)
   void* d_u1 = nullptr;      // two stage vectors
   void* d_u2 = nullptr;
+  int grid[3] = {0, 0, 0};  // facet, volume, volume (w = u): set at the first launch
+  double* d_part = nullptr;  // FP64 partial sums of the reductions
+  int64_t n_part = 0;
   std::string err;
 };
 
@@ -133,8 +137,12 @@ Tabs<T> tabs_dev(const hopu_hex* h) {
   return tb;
 }
 
+// grid of a persistent launch (resident CTAs x SMs, at most one CTA per items_per_block
+// items); computed once per context and kernel (the dynamic shared memory attribute is set
+// on that first call)
 template <typename Kern>
 int grid_for(Kern kern, int threads, size_t smem, int64_t items_per_block, int64_t items, int* grid) {
+  if (*grid > 0) return 0;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
@@ -150,25 +158,28 @@ int grid_for(Kern kern, int threads, size_t smem, int64_t items_per_block, int64
 
 // one apply: facet moments, then volume + lift + inverse mass + out = c0 u0 + c1 us + c2 y
 template <typename T, int K>
-int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, T c2, T* out) {
+int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, T c2, T* out,
+          double* diss = nullptr) {
   const MeshDev m = mesh_dev(h);
   const Tabs<T> tb = tabs_dev<T, K>(h);
   T* gam = static_cast<T*>(h->d_gam);
-  int gf = 0, gv = 0;
+  int& gf = h->grid[0];
   auto kf = k_hex_facet<T, K>;
   using CF = Fac<T, K>;
   if (grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf))
     return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
-  kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam);
+  kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam, diss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_facet launch");
   if (w == us) {  // the wind is the convected field: each component interpolated once
+    int& gv = h->grid[2];
     auto kv = k_hex_volume_same<T, K>;
     using CV = VolS<T, K>;
     if (grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
       return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
     kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, us, gam, u0, c0, c1, c2, out);
   } else {
+    int& gv = h->grid[1];
     auto kv = k_hex_volume<T, K>;
     using CV = Vol<T, K>;
     if (grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
@@ -196,14 +207,56 @@ int substeps(hopu_hex* h, T* u, double dt, int n, int l) {
 }
 
 template <typename T>
-int dispatch_apply(hopu_hex* h, const T* w, const T* u, int l, T* y) {
+int dispatch_apply(hopu_hex* h, const T* w, const T* u, int l, T* y, double* diss = nullptr) {
   switch (h->k) {
-    case 2: return stage<T, 2>(h, w, u, l, u, T(0), T(0), T(1), y);
-    case 3: return stage<T, 3>(h, w, u, l, u, T(0), T(0), T(1), y);
-    case 4: return stage<T, 4>(h, w, u, l, u, T(0), T(0), T(1), y);
-    case 5: return stage<T, 5>(h, w, u, l, u, T(0), T(0), T(1), y);
+    case 2: return stage<T, 2>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
+    case 3: return stage<T, 3>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
+    case 4: return stage<T, 4>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
+    case 5: return stage<T, 5>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
   }
   return fail(h, HOPU_ENOTSUP, "hopu_hex: order");
+}
+
+// kinetic energy, c(w; u, u) and the facet dissipation in FP64 (see hopu_hex_energy)
+template <typename T>
+int energy(hopu_hex* h, const T* w, const T* u, int l, double* out) {
+  const int64_t K1 = h->k + 1, nl = h->E * 3 * K1 * K1 * K1;
+  int dev = 0, sms = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ce != cudaSuccess) return cuda_fail(h, ce, "hopu_hex_energy: device");
+  const int ge = (int)std::min<int64_t>((nl + 255) / 256, 4LL * sms);
+  const int64_t nfac = (int64_t)sms * 32 * 4;  // facet partials: at most 32 CTAs of 4 warps per SM
+  if (!h->d_part) {
+    h->n_part = nfac + 2 * ge;
+    if ((ce = cudaMalloc(&h->d_part, h->n_part * sizeof(double))) != cudaSuccess)
+      return cuda_fail(h, ce, "hopu_hex_energy: partial sums");
+  }
+  T* y = static_cast<T*>(h->d_u1);
+  int st;
+  if (w) {
+    if ((ce = cudaMemsetAsync(h->d_part, 0, nfac * sizeof(double), h->stream)) != cudaSuccess)
+      return cuda_fail(h, ce, "hopu_hex_energy: memset");
+    if ((st = dispatch_apply<T>(h, w, u, l, y, h->d_part)) != HOPU_OK) return st;
+  }
+  k_hex_energy<T><<<ge, 256, 0, h->stream>>>(mesh_dev(h), nl, u, w ? y : nullptr, h->d_part + nfac);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, ce, "k_hex_energy launch");
+  std::vector<double> part(h->n_part);
+  if ((ce = cudaMemcpyAsync(part.data(), h->d_part, h->n_part * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream)) != cudaSuccess ||
+      (ce = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return cuda_fail(h, ce, "hopu_hex_energy: read back");
+  double e0 = 0.0, e1 = 0.0, d = 0.0;
+  for (int b = 0; b < ge; ++b) {
+    e0 += part[nfac + 2 * b];
+    e1 += part[nfac + 2 * b + 1];
+  }
+  if (w)
+    for (int64_t j = 0; j < nfac; ++j) d += part[j];
+  out[0] = 0.5 * e0;
+  out[1] = w ? e1 : 0.0;
+  out[2] = w ? d : 0.0;
+  return HOPU_OK;
 }
 
 template <typename T>
@@ -218,6 +271,7 @@ int dispatch_substeps(hopu_hex* h, T* u, double dt, int n, int l) {
 }
 
 void release(hopu_hex* h) {
+  cudaFree(h->d_part);
   cudaFree(h->d_geo);
   cudaFree(h->d_tab);
   cudaFree(h->d_gam);
@@ -352,6 +406,14 @@ int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l) {
   if (!uL || n < 0 || !std::isfinite(dt)) return fail(h, HOPU_EINVAL, "hopu_hex_rk_substeps: bad argument");
   if (h->prec == HOPU_FP64) return dispatch_substeps<double>(h, static_cast<double*>(uL), dt, n, l);
   return dispatch_substeps<float>(h, static_cast<float*>(uL), dt, n, l);
+}
+
+int hopu_hex_energy(hopu_hex* h, const void* wL, const void* uL, int l, double* host_out) {
+  if (!h) return HOPU_EINVAL;
+  if (!uL || !host_out) return fail(h, HOPU_EINVAL, "hopu_hex_energy: NULL argument");
+  if (h->prec == HOPU_FP64)
+    return energy<double>(h, static_cast<const double*>(wL), static_cast<const double*>(uL), l, host_out);
+  return energy<float>(h, static_cast<const float*>(wL), static_cast<const float*>(uL), l, host_out);
 }
 
 const char* hopu_hex_last_error(const hopu_hex* h) { return h ? h->err.c_str() : g_create_err.c_str(); }

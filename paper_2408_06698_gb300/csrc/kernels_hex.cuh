@@ -173,7 +173,7 @@ __device__ __forceinline__ int64_t cell_shift(const MeshDev& m, int64_t e, int d
 template <typename T, int K>
 __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     k_hex_facet(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* __restrict__ uL, int l,
-                T* __restrict__ gam) {
+                T* __restrict__ gam, double* __restrict__ diss_part) {
   using C = Fac<T, K>;
   constexpr int K1 = C::K1, M = C::M, NB = C::NB, NFM = C::NFM, NQF = C::NQF, NV = C::NV, NM = C::NM;
   constexpr int K1o = C::K1o, Mo = C::Mo;
@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
   T* buf = sm + C::TAB + warp * C::PER_WARP;
   const int64_t NF = 3 * m.E;
   const bool same = wL == uL;
+  double dacc = 0.0;  // facet dissipation of this lane's points (when diss_part is given)
   // work item wi -> the facet of direction wi % 3 below cell wi / 3: the three facets of a
   // cell are taken together, so that its coefficients are read from DRAM once
   for (int64_t wi = (int64_t)blockIdx.x * C::WARPS + warp; wi < NF; wi += (int64_t)gridDim.x * C::WARPS) {
@@ -308,6 +309,10 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
       const T* P = buf + C::O_P + p;
       const T wn = P[0], wj = P[NQF];
       const T hw = T(0.5) * fabs(wn) * wgt;
+      if (diss_part) {
+        const double p0 = P[8 * NQF], p1 = P[9 * NQF], p2v = P[10 * NQF];
+        dacc += double(aF) * double(hw) * (p0 * p0 + p1 * p1 + p2v * p2v);
+      }
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const T ju = P[(2 + a) * NQF], au = P[(5 + a) * NQF], pj = P[(8 + a) * NQF];
@@ -364,6 +369,11 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
       }
     }
     __syncwarp();
+  }
+  if (diss_part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if (lane == 0) diss_part[(int64_t)blockIdx.x * C::WARPS + warp] = dacc;
   }
 }
 
@@ -879,6 +889,43 @@ __global__ void __launch_bounds__(32 * VolS<T, K>::WARPS)
       }
     }
     __syncwarp();
+  }
+}
+
+// FP64 reductions over the cells (row a8): part[2 block + 0] = sum |det J| |u|^2 and
+// part[2 block + 1] = sum |det J| u . y over the block's cells (y = M^-1 c(w; u, .), so the
+// latter is c(w; u, u)); the host adds the per-block partials in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_hex_energy(MeshDev m, int64_t nl, const T* __restrict__ u,
+                                                   const T* __restrict__ y, double* __restrict__ part) {
+  __shared__ double s0[8], s1[8];
+  double a0 = 0.0, a1 = 0.0;
+  const int64_t per = nl / m.E;  // 3 (k+1)^3 coefficients per cell
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
+    const double ad = 1.0 / m.invabs[t / per];
+    const double uv = u[t];
+    a0 += ad * uv * uv;
+    if (y) a1 += ad * uv * double(y[t]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s0[warp] = a0;
+    s1[warp] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b0 = 0.0, b1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      b0 += s0[w];
+      b1 += s1[w];
+    }
+    part[2 * blockIdx.x] = b0;
+    part[2 * blockIdx.x + 1] = b1;
   }
 }
 

@@ -571,6 +571,14 @@ class HopuHex:
                     "hopu_hex_rk_substeps")
         return uL
 
+    def energy(self, uL: torch.Tensor, wL: torch.Tensor | None = None, l: int = -1):
+        """(1/2 int |u|^2, c(w; u, u), facet dissipation) in FP64 (hopu_hex_energy)."""
+        out = (c_double * 3)()
+        w = None if wL is None else c_void_p(self._vec(wL, "wL"))
+        self._check(self.lib.hopu_hex_energy(self.h, w, c_void_p(self._vec(uL, "uL")), int(l), out),
+                    "hopu_hex_energy")
+        return out[0], out[1], out[2]
+
     def close(self):
         if getattr(self, "h", None) and self.h.value:
             self.lib.hopu_hex_destroy(self.h)

@@ -83,6 +83,30 @@ def test_hex_apply_wind_is_field(k, prec, tol):
         assert err < tol
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_hex_energy_functionals(prec, tol):
+    """hopu_hex_energy against the oracle's kinetic energy, c(w; u, u) and facet dissipation
+    (w = u, and a separate wind), FP64 sums of the working precision's values."""
+    k = 3
+    hb = W.hex_box((3, 4, 3), jitter=0.2, shear=0.3, seed=9)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    g = _ctx(hb, k, prec)
+    w, u = _fields(m, ref, 90)
+    if prec == "f32":
+        w, u = w.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    ud, wd = _dev(g, u), _dev(g, w)
+    e, c, d = g.energy(ud)
+    assert e == pytest.approx(H.kinetic_energy(m, u), rel=tol) and c == 0.0 and d == 0.0
+    for wind, wn in ((ud, u), (wd, w)):
+        for l in (-1, k - 1):
+            e, c, d = g.energy(ud, wind, l)
+            ce, de = H.form_value(m, ref, wn, u, l), H.facet_dissipation(m, ref, wn, u, l)
+            print(f"hex energy {prec} l={l}: c {c:.6e} / {ce:.6e}, dissipation {d:.6e} / {de:.6e}")
+            assert e == pytest.approx(H.kinetic_energy(m, u), rel=tol)
+            assert abs(c - ce) <= tol * (abs(ce) + de)
+            assert d == pytest.approx(de, rel=tol)
+
+
 def test_hex_constant_state_and_errors():
     from paper_2408_06698_gb300 import _lib as L
     hb = W.hex_box(3, jitter=0.1, shear=0.2, seed=3)
