@@ -204,42 +204,44 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     const T aF = T(m.aF[F]);
     // 1. traces: fields 0-2 u^A, 3-5 w^A, 6-8 u^B, 9-11 w^B, each a compensated sum
     //    (hi + lo: error-free products by FMA, Knuth's TwoSum, L(0 or 1) as hi + lo), so that
-    //    the jumps of nearly equal traces keep their relative accuracy in FP32
-    //    (a compile-time trip count, so that the loads of every output of the lane are
-    //    issued before the sums wait on them)
-    //    (when the wind is the convected field, w = u as in a STAGE substep, only the six
-    //    velocity traces are formed and read for both)
-    constexpr int NTR = (12 * NFM + 31) / 32;
-    const int ntr = same ? 6 * NFM : 12 * NFM;
-#pragma unroll
-    for (int it = 0; it < NTR; ++it) {
-      const int t0 = lane + 32 * it;
-      if (t0 >= ntr) break;
-      const int f0 = t0 / NFM, mm = t0 - f0 * NFM;
+    //    the jumps of nearly equal traces keep their relative accuracy in FP32.  A lane owns
+    //    one line (field, t) of the facet and forms its K1 traces (s = 0..K1-1), all its
+    //    loads issued first; the coefficient of mode (a_d, s, t) sits at a_d sd + s ss + t st.
+    //    When the wind is the convected field (w = u, a STAGE substep) only the six velocity
+    //    traces are formed, and read for both.
+    const int sd = d == 0 ? 1 : (d == 1 ? K1 : K1 * K1);
+    const int ss = d == 0 ? K1 : 1;
+    const int st = d == 2 ? K1 : K1 * K1;
+    const int nlines = (same ? 6 : 12) * K1;
+    for (int L = lane; L < nlines; L += 32) {
+      const int f0 = L / K1, tt = L - f0 * K1;
       const int f = same && f0 >= 3 ? f0 + 3 : f0;
-      const int t = f * NFM + mm;
-      const int s = mm % K1, tt = mm / K1;
       const bool sideA = f < 6;
       const int comp = (f % 6) % 3;
-      const T* src = ((f % 6) < 3 ? uL : wL) + ((sideA ? eA : eB) * 3 + comp) * NB;
+      const T* src = ((f % 6) < 3 ? uL : wL) + ((sideA ? eA : eB) * 3 + comp) * NB + tt * st;
       const T* en = sideA ? sE1 : sE0;
       const T* el = sideA ? sE1l : sE0l;
-      T cv[K1];
+      T cv[K1][K1];
 #pragma unroll
-      for (int ad = 0; ad < K1; ++ad) cv[ad] = __ldg(src + mode_index<K1>(d, ad, s, tt));
-      T hi = T(0), lo = T(0);
+      for (int s2 = 0; s2 < K1; ++s2)
 #pragma unroll
-      for (int ad = 0; ad < K1; ++ad) {
-        const T c = cv[ad];
-        const T p = mul_rn(en[ad], c);
-        const T pe = fma(en[ad], c, -p);
-        const T sum = add_rn(hi, p);
-        const T bb = sub_rn(sum, hi);
-        lo += add_rn(sub_rn(hi, sub_rn(sum, bb)), sub_rn(p, bb)) + fma(el[ad], c, pe);
-        hi = sum;
+        for (int ad = 0; ad < K1; ++ad) cv[s2][ad] = __ldg(src + ad * sd + s2 * ss);
+#pragma unroll
+      for (int s2 = 0; s2 < K1; ++s2) {
+        T hi = T(0), lo = T(0);
+#pragma unroll
+        for (int ad = 0; ad < K1; ++ad) {
+          const T c = cv[s2][ad];
+          const T p = mul_rn(en[ad], c);
+          const T pe = fma(en[ad], c, -p);
+          const T sum = add_rn(hi, p);
+          const T bb = sub_rn(sum, hi);
+          lo += add_rn(sub_rn(hi, sub_rn(sum, bb)), sub_rn(p, bb)) + fma(el[ad], c, pe);
+          hi = sum;
+        }
+        buf[C::O_TR + f * NFM + s2 + K1 * tt] = hi;
+        buf[C::O_TL + f * NFM + s2 + K1 * tt] = lo;
       }
-      buf[C::O_TR + t] = hi;
-      buf[C::O_TL + t] = lo;
     }
     __syncwarp();
     // 2. modal point fields [f][t][s]; the jumps from the pairs (hi_A - hi_B is exact for
