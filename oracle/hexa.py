@@ -27,12 +27,17 @@ the cell below it (periodic wrap), through its local facet 2a+1 (x^_a = 1), side
 through local facet 2a (x^_a = 0); n_F is side A's outward unit normal, [[u]] = u^A - u^B.
 Both sides parametrise the facet by the two other reference coordinates in increasing axis
 order, so their facet points coincide (every cell of a HexBox has the same orientation).
+Directions that are not periodic end in walls or outlets (HexMesh's periodic flags): their
+facets are single-sided and take the cell's own trace as the exterior one, as in the
+simplicial oracle (no term in the paper's form, Section 2.1).
 
 Pins: tests/test_oracle_hexa.py (closed-form Legendre values and Gauss moments,
 orthonormality, finite-difference derivatives, the reference divergence theorem, the box's
 volume and closed cells, facet points that coincide from both sides, zero output for
 constant fields, the energy identity, the l = k limit, the Q^l orthogonality of (I - Pi^l),
-and the form equal to the simplicial oracle's on the same box for polynomial fields).
+the form equal to the simplicial oracle's on the same box for polynomial fields, periodic or
+walled, and with walls the form equal to the volume integral of (grad u) w + (div w) u
+evaluated from the polynomials' analytic gradients).
 """
 from __future__ import annotations
 
@@ -134,9 +139,13 @@ class RefHex:
 
 
 class HexMesh:
-    """Geometry and facets of a periodic workloads.HexBox (FP64)."""
+    """Geometry and facets of a workloads.HexBox (FP64), periodic in the directions a with
+    periodic[a] True.  In another direction the facets at the two ends of the box are
+    boundary facets (walls or outlets): F = a E + e for a cell e at the low end becomes the
+    single-sided facet of e (side A, through local facet 2a, n_F out of e), and the facets
+    of the cells at the high end (local facet 2a+1) are appended after the 3E others."""
 
-    def __init__(self, hb):
+    def __init__(self, hb, periodic=(True, True, True)):
         n0, n1, n2 = hb.n
         self.n = (n0, n1, n2)
         E = n0 * n1 * n2
@@ -162,11 +171,32 @@ class HexMesh:
         self.n_facets = 3 * E
         self.fa = np.stack([below.reshape(-1), np.repeat(2 * np.arange(3) + 1, E)], axis=-1)
         self.fb = np.stack([np.tile(e, 3), np.repeat(2 * np.arange(3), E)], axis=-1)
-        self.boundary = np.zeros(self.n_facets, dtype=bool)
-        # Nanson: n dA = det J J^-T N^ dA^ on side A (local facet 2a+1, N^ = e_a)
-        eA = self.fa[:, 0]
         a_of_F = np.repeat(np.arange(3), E)
-        v = self.detJ[eA, None] * self.Jinv[eA, a_of_F, :]            # row a of J^-1 = (J^-T e_a)^T
+        sgn = np.ones(3 * E)                                          # side A's N^ = sgn e_a
+        fa, fb = self.fa.copy(), self.fb.copy()
+        extra_a, extra_dir = [], []
+        for a in range(3):
+            if periodic[a]:
+                continue
+            low = np.where(self.cell[:, a] == 0)[0]                   # the cells at the low end
+            F = a * E + low
+            fa[F] = np.stack([low, np.full(low.size, 2 * a)], axis=-1)
+            fb[F] = -1
+            sgn[F] = -1.0
+            high = np.where(self.cell[:, a] == self.n[a] - 1)[0]
+            extra_a.append(np.stack([high, np.full(high.size, 2 * a + 1)], axis=-1))
+            extra_dir.append(np.full(high.size, a))
+        if extra_a:
+            fa = np.concatenate([fa] + extra_a)
+            fb = np.concatenate([fb, -np.ones((sum(x.shape[0] for x in extra_a), 2), dtype=np.int64)])
+            a_of_F = np.concatenate([a_of_F] + extra_dir)
+            sgn = np.concatenate([sgn, np.ones(fa.shape[0] - 3 * E)])
+        self.fa, self.fb = fa, fb
+        self.n_facets = fa.shape[0]
+        self.boundary = fb[:, 0] < 0
+        # Nanson: n dA = det J J^-T N^ dA^ on side A (N^ = sgn e_a)
+        eA = self.fa[:, 0]
+        v = sgn[:, None] * self.detJ[eA, None] * self.Jinv[eA, a_of_F, :]   # (J^-T e_a)^T = row a
         self.aF = np.linalg.norm(v, axis=-1)
         self.nF = v / self.aF[:, None]
 
@@ -225,9 +255,17 @@ def complement_projection(ref: RefHex, l: int, nF: np.ndarray, V: np.ndarray) ->
 
 
 def facet_quantities(mesh: HexMesh, ref: RefHex, wL, uL, l: int):
-    """Per facet point: w.n (= <w>.n_F), [[u]], <u>, (I-Pi)[[u]], (I-Pi)[1/2|w.n|(I-Pi)[[u]]]."""
+    """Per facet point: w.n (= <w>.n_F), [[u]], <u>, (I-Pi)[[u]], (I-Pi)[1/2|w.n|(I-Pi)[[u]]].
+
+    Boundary facets (walls and outlets, Section 2.1: no term in the paper's form) take
+    side A's own traces as side B, as the simplicial oracle does: the jump vanishes and the
+    conservative form keeps the flux (w.n) u . v that its cell-wise integration by parts
+    needs to equal the paper's form."""
     uA, uB = _traces(mesh, ref, uL, "A"), _traces(mesh, ref, uL, "B")
     wA, wB = _traces(mesh, ref, wL, "A"), _traces(mesh, ref, wL, "B")
+    b = mesh.boundary
+    if np.any(b):
+        uB[b], wB[b] = uA[b], wA[b]
     wn = 0.5 * np.einsum("Fpa,Fa->Fp", wA + wB, mesh.nF)
     jump = uA - uB
     avg = 0.5 * (uA + uB)

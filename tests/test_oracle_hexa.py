@@ -226,3 +226,81 @@ def test_form_equals_the_simplicial_oracle(k):
         vals.append(float(np.sum(vL * r)))
     assert abs(vals[0]) > 1e-3
     assert vals[0] == pytest.approx(vals[1], rel=1e-11)
+
+
+class _Poly:
+    """A vector polynomial of total degree <= k in y = x / (2 pi), with its gradient."""
+
+    def __init__(self, k, seed, scale=1.0, base=None):
+        rng = np.random.default_rng(seed)
+        self.exps = [(a, b, c) for a in range(k + 1) for b in range(k + 1) for c in range(k + 1) if a + b + c <= k]
+        self.coef = rng.uniform(-1.0, 1.0, size=(len(self.exps), 3)) * scale / len(self.exps)
+        self.base = np.zeros(3) if base is None else np.asarray(base, dtype=float)
+
+    def __call__(self, x):
+        y = x / (2 * math.pi)
+        out = np.zeros(x.shape[:-1] + (3,)) + self.base
+        for (a, b, c), cf in zip(self.exps, self.coef):
+            out += (y[..., 0] ** a * y[..., 1] ** b * y[..., 2] ** c)[..., None] * cf
+        return out
+
+    def grad(self, x):
+        """[..., component, direction]"""
+        y = x / (2 * math.pi)
+        out = np.zeros(x.shape[:-1] + (3, 3))
+        for (a, b, c), cf in zip(self.exps, self.coef):
+            ex = (a, b, c)
+            for d in range(3):
+                if ex[d] == 0:
+                    continue
+                e2 = list(ex)
+                e2[d] -= 1
+                m = ex[d] * y[..., 0] ** e2[0] * y[..., 1] ** e2[1] * y[..., 2] ** e2[2] / (2 * math.pi)
+                out[..., :, d] += m[..., None] * cf
+        return out
+
+
+@pytest.mark.parametrize("k,periodic", [(2, (False, False, False)), (3, (True, False, False)),
+                                        (3, (False, True, False))])
+def test_walls_reduce_to_the_volume_integral(k, periodic):
+    """With walls / outlets in the non-periodic directions and polynomial u, w continuous
+    across every interior facet (no jumps; in a periodic direction the fields must be
+    periodic, so they do not depend on that coordinate there), c(w; u, phi_i e_a) equals
+    int_T ((grad u) w + (div w) u)_a phi_i, evaluated directly from the polynomials'
+    analytic gradients: the boundary flux of the conservative form cancels the cell-wise
+    integration by parts, and Section 2.1's wall / outlet facets add no term."""
+    hb = W.hex_box(3, jitter=0.25, shear=0.0, seed=12)
+    m, ref = H.HexMesh(hb, periodic=periodic), H.RefHex(k)
+    pu, pw = _Poly(k, 21), _Poly(k, 22, 0.3, base=[0.4, -0.3, 0.2])
+    for P in (pu, pw):                                   # drop the periodic coordinates
+        keep = [i for i, ex in enumerate(P.exps) if all(ex[d] == 0 for d in range(3) if periodic[d])]
+        P.exps = [P.exps[i] for i in keep]
+        P.coef = P.coef[keep]
+    uL, wL = H.project(m, ref, pu), H.project(m, ref, pw)
+    r = H.residual(m, ref, wL, uL, -1)
+    X = m.volume_points(ref.xq)
+    U, Wv, GU, GW = pu(X), pw(X), pu.grad(X), pw.grad(X)
+    g = np.einsum("eqab,eqb->eqa", GU, Wv) + np.einsum("eqbb->eq", GW)[..., None] * U
+    direct = np.einsum("q,e,eqa,qi->eai", ref.wq, m.absdet, g, ref.phi)
+    assert np.abs(r - direct).max() < 1e-11 * np.abs(direct).max()
+    assert m.boundary.sum() == sum(2 * m.n_elems // m.n[a] for a in range(3) if not periodic[a])
+
+
+def test_walls_match_the_simplicial_oracle():
+    """A box walled on all six sides, split into tetrahedra (no periodic identification),
+    polynomial fields: the two oracles' forms agree for any HOPU order, every facet jump
+    being zero (interior: continuous fields; walls: the own trace)."""
+    k = 2
+    hb = W.hex_box(3, jitter=0.25, shear=0.3, seed=14)
+    m, ref = H.HexMesh(hb, periodic=(False, False, False)), H.RefHex(k)
+    tets = W.hex_box_tets(hb)
+    topo, tref = MeshTopo(tets.coords, tets.elems, None), ref_element(3, k)
+    assert np.any(topo.boundary)
+    fu, fw, fv = _Poly(k, 31), _Poly(k, 32, 0.3, base=[0.2, 0.5, -0.4]), _Poly(k, 33)
+    for l in (-1, 1):
+        rh = H.residual(m, ref, H.project(m, ref, fw), H.project(m, ref, fu), l)
+        rt = C.residual_conservative(topo, tref, _tet_project(topo, tref, fw), _tet_project(topo, tref, fu), l)
+        ch = float(np.sum(H.project(m, ref, fv) * rh))
+        ct = float(np.sum(_tet_project(topo, tref, fv) * rt))
+        assert abs(ch) > 1e-3
+        assert ch == pytest.approx(ct, rel=1e-11)
