@@ -10,8 +10,11 @@
  * (axis 0 fastest), Cartesian velocity components.  Geometry stays FP64 on the device.
  *
  * Box.  Grid lines lines[a][0..n_a] (increasing, n_a >= 3) and a 3x3 matrix A (row-major,
- * det A > 0): cell (c0, c1, c2) is A applied to [lines0[c0], lines0[c0+1]] x ... ; the box is
- * periodic with periods A (L_a e_a), L_a = lines_a[n_a] - lines_a[0].
+ * det A > 0): cell (c0, c1, c2) is A applied to [lines0[c0], lines0[c0+1]] x ... ; in a
+ * periodic direction a the box is periodic with period A (L_a e_a), L_a = lines_a[n_a] -
+ * lines_a[0]; the two ends of another direction are walls or outlets (Section 2.1: facets
+ * of F^W and F^N, which carry no term in the paper's form; the cell's own trace is the
+ * exterior one).
  *
  * Facets.  The facet between a cell and the next one in direction a is one facet with
  * side A the lower cell; [[u]] = u^A - u^B, n its unit normal out of side A; w.n is
@@ -40,13 +43,14 @@ extern "C" {
 typedef struct hopu_hex hopu_hex; /* opaque; owns its device tables and scratch */
 
 /* Creates a context for the box (n0, n1, n2, lines = the n0+1, n1+1, n2+1 grid-line positions
- * of the three directions one after the other, A) at order k (2..5) and precision prec
- * (HOPU_FP64 or HOPU_FP32).  Copies what it needs (the caller keeps ownership of lines and
- * A).  EINVAL: NULL pointer, n_a < 3, prec not one of the two; ENOTSUP: k outside 2..5;
- * EMESH: lines not increasing or det A <= 0; ENOMEM / ECUDA: allocation or CUDA failure
- * (text in hopu_hex_last_error(NULL)). */
-int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A, int k, int prec,
-                    void* stream, hopu_hex** out);
+ * of the three directions one after the other, A, periodic = bit mask of the periodic
+ * directions, 7 for a fully periodic box) at order k (2..5) and precision prec (HOPU_FP64 or
+ * HOPU_FP32).  Copies what it needs (the caller keeps ownership of lines and A).  EINVAL:
+ * NULL pointer, n_a < 3, periodic outside 0..7, prec not one of the two; ENOTSUP: k outside
+ * 2..5; EMESH: lines not increasing or det A <= 0; ENOMEM / ECUDA: allocation or CUDA
+ * failure (text in hopu_hex_last_error(NULL)). */
+int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A, int periodic, int k,
+                    int prec, void* stream, hopu_hex** out);
 int hopu_hex_destroy(hopu_hex* h);
 
 /* Number of cells and length of an L2 vector (E * 3 * (k+1)^3 elements). */

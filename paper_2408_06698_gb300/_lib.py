@@ -53,7 +53,8 @@ SIGNATURES = {
     "hopu_points": (c_int, [c_void_p, c_int, c_void_p, POINTER(c_int64)]),
     "hopu_interpolate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hopu_last_error": (c_char_p, [c_void_p]),
-    "hopu_hex_create": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p, POINTER(c_void_p)]),
+    "hopu_hex_create": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                POINTER(c_void_p)]),
     "hopu_hex_destroy": (c_int, [c_void_p]),
     "hopu_hex_sizes": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64)]),
     "hopu_hex_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),

@@ -17,7 +17,7 @@ using namespace hopu::hex;
 
 struct hopu_hex {
   int n[3] = {0, 0, 0};
-  int k = 0, prec = 0;
+  int k = 0, prec = 0, bmask = 0;
   int64_t E = 0;
   cudaStream_t stream = nullptr;
   double* d_geo = nullptr;   // G [E][9] | invabs [E] | nF [3E][3] | aF [3E]
@@ -114,6 +114,7 @@ MeshDev mesh_dev(const hopu_hex* h) {
   m.n0 = h->n[0];
   m.n1 = h->n[1];
   m.n2 = h->n[2];
+  m.bmask = h->bmask;
   m.E = h->E;
   m.G = h->d_geo;
   m.invabs = h->d_geo + 9 * h->E;
@@ -283,14 +284,15 @@ void release(hopu_hex* h) {
 
 extern "C" {
 
-int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A, int k, int prec, void* stream,
-                    hopu_hex** out) {
+int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A, int periodic, int k, int prec,
+                    void* stream, hopu_hex** out) {
   if (!out || !lines || !A) return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: NULL argument");
   *out = nullptr;
   if (n0 < 3 || n1 < 3 || n2 < 3) return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: fewer than 3 cells in a direction");
   if (prec != HOPU_FP64 && prec != HOPU_FP32)
     return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: precision must be HOPU_FP64 or HOPU_FP32");
   if (k < 2 || k > 5) return fail(nullptr, HOPU_ENOTSUP, "hopu_hex_create: order k outside 2..5");
+  if (periodic < 0 || periodic > 7) return fail(nullptr, HOPU_EINVAL, "hopu_hex_create: periodic is a 3-bit mask");
   const int n[3] = {n0, n1, n2};
   const double* ln[3] = {lines, lines + n0 + 1, lines + n0 + 1 + n1 + 1};
   for (int a = 0; a < 3; ++a)
@@ -338,6 +340,7 @@ int hopu_hex_create(int n0, int n1, int n2, const double* lines, const double* A
   h->n[2] = n2;
   h->k = k;
   h->prec = prec;
+  h->bmask = (~periodic) & 7;
   h->E = E;
   h->stream = static_cast<cudaStream_t>(stream);
   const size_t ts = prec == HOPU_FP64 ? 8 : 4;

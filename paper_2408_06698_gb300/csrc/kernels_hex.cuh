@@ -51,6 +51,7 @@ struct Shape {
 
 struct MeshDev {
   int n0, n1, n2;
+  int bmask;  // bit d set: direction d is not periodic (walls / outlets at its two ends)
   int64_t E;
   const double* G;       // [E][3][3]  |det J| J^-1
   const double* invabs;  // [E]        1 / |det J|
@@ -199,6 +200,17 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     const int d = int(wi % 3);
     const int64_t eB = wi / 3;
     const int64_t F = d * m.E + eB;
+    if ((m.bmask >> d) & 1) {
+      const int cd = d == 0 ? int(eB % m.n0) : (d == 1 ? int((eB / m.n0) % m.n1) : int(eB / ((int64_t)m.n0 * m.n1)));
+      if (cd == 0) {
+        // the two ends of a non-periodic direction: the facet slot holds the top boundary
+        // facet of the last cell (side A) and the bottom one of the first (side B); walls
+        // and outlets add nothing in the evaluated form (the cell-wise integration by parts
+        // cancels the conservative form's own-trace flux), so both moment sets are zero
+        for (int t = lane; t < 6 * NFM; t += 32) gam[F * 6 * NFM + t] = T(0);
+        continue;
+      }
+    }
     const int64_t eA = cell_shift(m, eB, d, -1);
     const T n0 = T(m.nF[F * 3 + 0]), n1 = T(m.nF[F * 3 + 1]), n2 = T(m.nF[F * 3 + 2]);
     const T aF = T(m.aF[F]);

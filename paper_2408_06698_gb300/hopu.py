@@ -515,10 +515,12 @@ class HopuHex:
     """A structured periodic box of parallelepipeds at order k (mirrors a ``hopu_hex``).
 
     lines: three increasing arrays of grid-line positions (n_a + 1 each); A: 3x3 matrix,
-    det A > 0 (cell (c0, c1, c2) is A [lines0[c0], lines0[c0+1]] x ...).  L2 vectors are
-    [E][3][(k+1)^3] device tensors in the context's precision."""
+    det A > 0 (cell (c0, c1, c2) is A [lines0[c0], lines0[c0+1]] x ...); periodic: per
+    direction, else walls / outlets at its ends.  L2 vectors are [E][3][(k+1)^3] device
+    tensors in the context's precision."""
 
-    def __init__(self, lines, A, k: int = 3, prec: str = "f64", device: str | torch.device = "cuda"):
+    def __init__(self, lines, A, k: int = 3, prec: str = "f64", device: str | torch.device = "cuda",
+                 periodic=(True, True, True)):
         if not torch.cuda.is_available():
             raise RuntimeError("libhopu needs a CUDA device")
         if prec not in ("f64", "f32"):
@@ -535,8 +537,9 @@ class HopuHex:
         self.stream = torch.cuda.current_stream(self.device)
         self.h = c_void_p()
         with torch.cuda.device(self.device):
+            mask = sum(1 << a for a in range(3) if periodic[a])
             st = self.lib.hopu_hex_create(self.n[0], self.n[1], self.n[2], self._lines.ctypes.data,
-                                          self._A.ctypes.data, int(k), _PREC[prec],
+                                          self._A.ctypes.data, mask, int(k), _PREC[prec],
                                           c_void_p(self.stream.cuda_stream), byref(self.h))
         if st != L.HOPU_OK:
             raise L.HopuError(st, "hopu_hex_create", self.lib.hopu_hex_last_error(None).decode())

@@ -107,6 +107,38 @@ def test_hex_energy_functionals(prec, tol):
             assert d == pytest.approx(de, rel=tol)
 
 
+@pytest.mark.parametrize("periodic", [(True, False, True), (False, False, False), (True, True, False)])
+def test_hex_walls(periodic):
+    """Boxes whose non-periodic directions end in walls / outlets: the apply (separate wind
+    and w = u), STAGE substeps and the functionals against the oracle's walled box."""
+    from paper_2408_06698_gb300 import HopuHex
+    k = 3
+    hb = W.hex_box((4, 3, 3), jitter=0.2, shear=0.3, seed=60)
+    m, ref = H.HexMesh(hb, periodic=periodic), H.RefHex(k)
+    assert m.boundary.any()
+    w, u = _fields(m, ref, 70)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-6)):
+        g = HopuHex(hb.lines, hb.A, k=k, prec=prec, periodic=periodic)
+        uu, ww = (u, w) if prec == "f64" else (u.astype(np.float32).astype(np.float64),
+                                              w.astype(np.float32).astype(np.float64))
+        ud = _dev(g, uu)
+        for wind, wn in ((_dev(g, ww), ww), (ud, uu)):
+            for l in (-1, k - 1):
+                y = g.apply(wind, ud, l).cpu().numpy().astype(np.float64).reshape(u.shape)
+                err = _rel(y, H.apply(m, ref, wn, uu, l))
+                print(f"hex walls {periodic} {prec} l={l}: {err:.2e}")
+                assert err < tol
+        e, c, d = g.energy(ud, ud, k - 1)
+        assert d == pytest.approx(H.facet_dissipation(m, ref, uu, uu, k - 1), rel=tol * 20)
+        v = ud.clone()
+        g.rk_substeps(v, 1e-2, 2, k - 1)
+        want = H.substeps_stage(m, ref, uu, 1e-2, 2, k - 1)
+        err = _rel(v.cpu().numpy().astype(np.float64).reshape(u.shape), want)
+        print(f"hex walls {periodic} {prec} substeps: {err:.2e}")
+        assert err < tol
+        g.close()
+
+
 def test_hex_constant_state_and_errors():
     from paper_2408_06698_gb300 import _lib as L
     hb = W.hex_box(3, jitter=0.1, shear=0.2, seed=3)
@@ -199,3 +231,4 @@ class _SubMesh:
     def __init__(self, m, facets):
         self.n_facets = len(facets)
         self.fa, self.fb, self.nF = m.fa[facets], m.fb[facets], m.nF[facets]
+        self.boundary = m.boundary[facets]

@@ -122,12 +122,12 @@ def test_valid_mesh_without_device_fails_on_cuda_only(lib):
     assert st == L.HOPU_ECUDA, msg                            # topology and tables built fine
 
 
-def _hex_create(lib, lines, A, n=(3, 3, 3), k=3, prec=0):
+def _hex_create(lib, lines, A, n=(3, 3, 3), k=3, prec=0, periodic=7):
     from ctypes import byref, c_void_p
     flat = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in lines]))
     Am = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
     h = c_void_p()
-    st = lib.hopu_hex_create(n[0], n[1], n[2], flat.ctypes.data, Am.ctypes.data, k, prec, None, byref(h))
+    st = lib.hopu_hex_create(n[0], n[1], n[2], flat.ctypes.data, Am.ctypes.data, periodic, k, prec, None, byref(h))
     msg = lib.hopu_hex_last_error(None).decode()
     if h.value:
         lib.hopu_hex_destroy(h)
@@ -147,6 +147,7 @@ def test_hex_box_validation(lib):
     assert _hex_create(lib, hb.lines, hb.A, k=6)[0] == L.HOPU_ENOTSUP
     assert _hex_create(lib, hb.lines, hb.A, k=1)[0] == L.HOPU_ENOTSUP
     assert _hex_create(lib, hb.lines, hb.A, prec=2)[0] == L.HOPU_EINVAL  # tensor-core modes: no
+    assert _hex_create(lib, hb.lines, hb.A, periodic=8)[0] == L.HOPU_EINVAL
     small = [x[:3] for x in hb.lines]
     assert _hex_create(lib, small, hb.A, n=(2, 2, 2))[0] == L.HOPU_EINVAL
     if not torch.cuda.is_available():
