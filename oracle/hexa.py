@@ -254,18 +254,22 @@ def complement_projection(ref: RefHex, l: int, nF: np.ndarray, V: np.ndarray) ->
     return V - PiV
 
 
-def facet_quantities(mesh: HexMesh, ref: RefHex, wL, uL, l: int):
+def facet_quantities(mesh: HexMesh, ref: RefHex, wL, uL, l: int, u_inlet=None):
     """Per facet point: w.n (= <w>.n_F), [[u]], <u>, (I-Pi)[[u]], (I-Pi)[1/2|w.n|(I-Pi)[[u]]].
 
     Boundary facets (walls and outlets, Section 2.1: no term in the paper's form) take
     side A's own traces as side B, as the simplicial oracle does: the jump vanishes and the
     conservative form keeps the flux (w.n) u . v that its cell-wise integration by parts
-    needs to equal the paper's form."""
+    needs to equal the paper's form.  Inlet facets (u_inlet: a dict facet index -> the
+    exterior velocity at the facet points [nqf, 3]) take it as side B's velocity (Section
+    2.2) and side A's own wind (the wind's normal component is single-valued)."""
     uA, uB = _traces(mesh, ref, uL, "A"), _traces(mesh, ref, uL, "B")
     wA, wB = _traces(mesh, ref, wL, "A"), _traces(mesh, ref, wL, "B")
     b = mesh.boundary
     if np.any(b):
         uB[b], wB[b] = uA[b], wA[b]
+    for F, val in (u_inlet or {}).items():
+        uB[F] = val
     wn = 0.5 * np.einsum("Fpa,Fa->Fp", wA + wB, mesh.nF)
     jump = uA - uB
     avg = 0.5 * (uA + uB)
@@ -274,13 +278,13 @@ def facet_quantities(mesh: HexMesh, ref: RefHex, wL, uL, l: int):
     return wn, jump, avg, PJ, Ph
 
 
-def residual(mesh: HexMesh, ref: RefHex, wL, uL, l: int) -> np.ndarray:
+def residual(mesh: HexMesh, ref: RefHex, wL, uL, l: int, u_inlet=None) -> np.ndarray:
     """r[e, a, i] = c(w; u, phi_i e_a) (conservative reading)."""
     U = np.einsum("qi,eai->eqa", ref.phi, uL)
     W = np.einsum("qi,eai->eqa", ref.phi, wL)
     Wt = np.einsum("e,ecb,eqb->eqc", mesh.absdet, mesh.Jinv, W)       # |det J| J^-1 w
     r = -np.einsum("q,eqa,qic,eqc->eai", ref.wq, U, ref.dphi, Wt)
-    wn, jump, avg, PJ, Ph = facet_quantities(mesh, ref, wL, uL, l)
+    wn, jump, avg, PJ, Ph = facet_quantities(mesh, ref, wL, uL, l, u_inlet)
     g = wn[..., None] * avg + Ph
     for side, sgn in (("A", 1.0), ("B", -1.0)):
         ef = mesh.fa if side == "A" else mesh.fb
@@ -292,9 +296,25 @@ def residual(mesh: HexMesh, ref: RefHex, wL, uL, l: int) -> np.ndarray:
     return r
 
 
-def apply(mesh: HexMesh, ref: RefHex, wL, uL, l: int) -> np.ndarray:
+def apply(mesh: HexMesh, ref: RefHex, wL, uL, l: int, u_inlet=None) -> np.ndarray:
     """y = M_L^-1 c(w; u, .), M_T = |det J| I."""
-    return residual(mesh, ref, wL, uL, l) / mesh.absdet[:, None, None]
+    return residual(mesh, ref, wL, uL, l, u_inlet) / mesh.absdet[:, None, None]
+
+
+def end_facets(mesh: HexMesh, d: int, end: int) -> np.ndarray:
+    """The boundary facets at the low (end 0) or high (end 1) end of non-periodic direction
+    d, ordered by the cells' two other indices (lower axis fastest)."""
+    E = mesh.n_elems
+    a_other = [b for b in range(3) if b != d]
+    cells = np.where(mesh.cell[:, d] == (0 if end == 0 else mesh.n[d] - 1))[0]
+    key = mesh.cell[cells, a_other[0]] + mesh.n[a_other[0]] * mesh.cell[cells, a_other[1]]
+    cells = cells[np.argsort(key)]
+    local = 2 * d + (0 if end == 0 else 1)
+    out = []
+    for e in cells:
+        F = np.where((mesh.fa[:, 0] == e) & (mesh.fa[:, 1] == local) & mesh.boundary)[0]
+        out.append(int(F[0]))
+    return np.array(out, dtype=np.int64)
 
 
 def form_value(mesh, ref, wL, uL, l) -> float:

@@ -304,3 +304,40 @@ def test_walls_match_the_simplicial_oracle():
         ct = float(np.sum(_tet_project(topo, tref, fv) * rt))
         assert abs(ch) > 1e-3
         assert ch == pytest.approx(ct, rel=1e-11)
+
+
+def test_inlet_matches_the_simplicial_oracle():
+    """A walled box with an inlet at the low end of direction 1 (exterior velocity g, the
+    wind's own trace, Section 2.2): for polynomial fields with inflow (w.n < 0 on the whole
+    inlet, so |w.n| is a polynomial there) the hexahedral and simplicial forms agree; with
+    g the field's own trace the inlet adds nothing (the walled form)."""
+    k = 2
+    hb = W.hex_box(3, jitter=0.25, shear=0.3, seed=15)
+    m, ref = H.HexMesh(hb, periodic=(False, False, False)), H.RefHex(k)
+    tets = W.hex_box_tets(hb)
+    topo, tref = MeshTopo(tets.coords, tets.elems, None), ref_element(3, k)
+    base = hb.A @ np.array([0.0, 0.6, 0.0])                # A^-1 w = (0, 0.6, 0): inflow at y = 0
+    fu, fw, fv, fg = _Poly(k, 41), _Poly(k, 42, 0.2, base=base), _Poly(k, 43), _Poly(k, 44)
+    Ainv = np.linalg.inv(hb.A)
+    # hexahedral inlet facets: the low end of direction 1
+    Fin = H.end_facets(m, 1, 0)
+    pts = m.facet_points(ref, "A")
+    uin = {int(F): fg(pts[F]) for F in Fin}
+    # simplicial inlet facets: boundary facets in the plane (A^-1 x)_1 = 0
+    P = topo.facet_points(tref.sq)
+    xi = np.einsum("ab,Fqb->Fqa", Ainv, P)
+    inlet = topo.boundary & (np.abs(xi[:, :, 1]).max(axis=1) < 1e-12)
+    assert inlet.sum() == 2 * len(Fin)                     # two triangles per quadrilateral
+    wLt, uLt = _tet_project(topo, tref, fw), _tet_project(topo, tref, fu)
+    ext = (fg(P), C.facet_trace(topo, tref, wLt, "A"))
+    for l in (-1,):
+        rh = H.residual(m, ref, H.project(m, ref, fw), H.project(m, ref, fu), l, uin)
+        rt = C.residual_conservative(topo, tref, wLt, uLt, l, exterior=ext, inlet=inlet)
+        ch = float(np.sum(H.project(m, ref, fv) * rh))
+        ct = float(np.sum(_tet_project(topo, tref, fv) * rt))
+        assert ch == pytest.approx(ct, rel=1e-11)
+    # the field's own trace as inlet data: the walled form
+    own = {int(F): H._traces(m, ref, H.project(m, ref, fu), "A")[F] for F in Fin}
+    r_own = H.residual(m, ref, H.project(m, ref, fw), H.project(m, ref, fu), 1, own)
+    r_wall = H.residual(m, ref, H.project(m, ref, fw), H.project(m, ref, fu), 1)
+    assert np.abs(r_own - r_wall).max() < 1e-13 * np.abs(r_wall).max()
