@@ -14,7 +14,7 @@
  * periodic direction a the box is periodic with period A (L_a e_a), L_a = lines_a[n_a] -
  * lines_a[0]; the two ends of another direction are walls or outlets (Section 2.1: facets
  * of F^W and F^N, which carry no term in the paper's form; the cell's own trace is the
- * exterior one).
+ * exterior one), or inlets with data (hopu_hex_set_inlet).
  *
  * Facets.  The facet between a cell and the next one in direction a is one facet with
  * side A the lower cell; [[u]] = u^A - u^B, n its unit normal out of side A; w.n is
@@ -64,6 +64,16 @@ int hopu_hex_apply(hopu_hex* h, const void* wL, const void* uL, int l, void* yL)
 /* n SSP-RK3 substeps (Shu-Osher form) of du/dt = -M^-1 c(u; u, .) in place on the device
  * L2 vector uL (the wind is the stage's own field). */
 int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l);
+
+/* Makes the low (end 0) or high (end 1) end of the non-periodic direction dir an inlet
+ * (Section 2.2: the exterior velocity u_I enters the jump and the average; the wind keeps
+ * its own normal component): modes = device array [n_s * n_t][3][(k+1)^2] in the working
+ * precision, the L2 projection of u_I onto Q^k of each end facet in the facet's orthonormal
+ * basis L_ms(s) L_mt(t), mode m = ms + (k+1) mt, (s, t) the two other reference
+ * coordinates in increasing axis order; facet j = c_s + n_s c_t by the cell's two other
+ * indices.  Copied (stream-ordered); NULL turns the end back into a wall / outlet.
+ * EINVAL: dir / end out of range or dir periodic. */
+int hopu_hex_set_inlet(hopu_hex* h, int dir, int end, const void* modes);
 
 /* FP64 reductions (row a8 of the hot path; synchronises the stream):
  *   host_out[0] = 1/2 int |u|^2                             (kinetic energy)

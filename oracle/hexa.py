@@ -333,11 +333,11 @@ def kinetic_energy(mesh, uL) -> float:
     return 0.5 * float(np.sum(mesh.absdet[:, None, None] * uL * uL))
 
 
-def substeps_stage(mesh, ref, uL, dt: float, n: int, l: int) -> np.ndarray:
+def substeps_stage(mesh, ref, uL, dt: float, n: int, l: int, u_inlet=None) -> np.ndarray:
     """n SSP-RK3 substeps of du/dt = -M^-1 c(u; u, .) in L_h (the STAGE wind w = u;
     the Shu-Osher stages of oracle/rk.py)."""
     from .rk import ssp_rk3
     u = np.array(uL, dtype=np.float64)
     for _ in range(n):
-        u = ssp_rk3(lambda v: apply(mesh, ref, v, v, l), u, dt)
+        u = ssp_rk3(lambda v: apply(mesh, ref, v, v, l, u_inlet), u, dt)
     return u

@@ -26,6 +26,8 @@ struct hopu_hex {
   void* d_u1 = nullptr;      // two stage vectors
   void* d_u2 = nullptr;
   int grid[3] = {0, 0, 0};  // facet, volume, volume (w = u): set at the first launch
+  void* d_inlet[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // inlet modes
+  bool inlet_on[3][2] = {{false, false}, {false, false}, {false, false}};
   double* d_part = nullptr;  // FP64 partial sums of the reductions
   int64_t n_part = 0;
   std::string err;
@@ -120,6 +122,8 @@ MeshDev mesh_dev(const hopu_hex* h) {
   m.invabs = h->d_geo + 9 * h->E;
   m.nF = m.invabs + h->E;
   m.aF = m.nF + 9 * h->E;
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 2; ++e) m.inlet[d][e] = h->inlet_on[d][e] ? h->d_inlet[d][e] : nullptr;
   return m;
 }
 
@@ -272,6 +276,8 @@ int dispatch_substeps(hopu_hex* h, T* u, double dt, int n, int l) {
 }
 
 void release(hopu_hex* h) {
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 2; ++e) cudaFree(h->d_inlet[d][e]);
   cudaFree(h->d_part);
   cudaFree(h->d_geo);
   cudaFree(h->d_tab);
@@ -409,6 +415,26 @@ int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l) {
   if (!uL || n < 0 || !std::isfinite(dt)) return fail(h, HOPU_EINVAL, "hopu_hex_rk_substeps: bad argument");
   if (h->prec == HOPU_FP64) return dispatch_substeps<double>(h, static_cast<double*>(uL), dt, n, l);
   return dispatch_substeps<float>(h, static_cast<float*>(uL), dt, n, l);
+}
+
+int hopu_hex_set_inlet(hopu_hex* h, int dir, int end, const void* modes) {
+  if (!h) return HOPU_EINVAL;
+  if (dir < 0 || dir > 2 || end < 0 || end > 1) return fail(h, HOPU_EINVAL, "hopu_hex_set_inlet: dir / end");
+  if (!((h->bmask >> dir) & 1)) return fail(h, HOPU_EINVAL, "hopu_hex_set_inlet: direction is periodic");
+  if (!modes) {
+    h->inlet_on[dir][end] = false;
+    return HOPU_OK;
+  }
+  const int64_t K1 = h->k + 1;
+  const int64_t nface = (int64_t)h->n[0] * h->n[1] * h->n[2] / h->n[dir];
+  const size_t bytes = (size_t)(nface * 3 * K1 * K1) * (h->prec == HOPU_FP64 ? 8 : 4);
+  cudaError_t ce;
+  if (!h->d_inlet[dir][end] && (ce = cudaMalloc(&h->d_inlet[dir][end], bytes)) != cudaSuccess)
+    return cuda_fail(h, ce, "hopu_hex_set_inlet: allocation");
+  if ((ce = cudaMemcpyAsync(h->d_inlet[dir][end], modes, bytes, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess)
+    return cuda_fail(h, ce, "hopu_hex_set_inlet: copy");
+  h->inlet_on[dir][end] = true;
+  return HOPU_OK;
 }
 
 int hopu_hex_energy(hopu_hex* h, const void* wL, const void* uL, int l, double* host_out) {

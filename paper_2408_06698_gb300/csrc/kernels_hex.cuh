@@ -53,6 +53,10 @@ struct MeshDev {
   int n0, n1, n2;
   int bmask;  // bit d set: direction d is not periodic (walls / outlets at its two ends)
   int64_t E;
+  // inlet data of the two ends of a non-periodic direction (NULL: wall / outlet): the
+  // exterior velocity's facet modes [cell (s, t) of the end][3][(k+1)^2] in the working
+  // precision, s, t the cell indices of the two other directions (lower axis fastest)
+  const void* inlet[3][2];
   const double* G;       // [E][3][3]  |det J| J^-1
   const double* invabs;  // [E]        1 / |det J|
   const double* nF;      // [3E][3]    unit normal of facet F (side A outward)
@@ -200,189 +204,226 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     const int d = int(wi % 3);
     const int64_t eB = wi / 3;
     const int64_t F = d * m.E + eB;
-    if ((m.bmask >> d) & 1) {
-      const int cd = d == 0 ? int(eB % m.n0) : (d == 1 ? int((eB / m.n0) % m.n1) : int(eB / ((int64_t)m.n0 * m.n1)));
-      if (cd == 0) {
-        // the two ends of a non-periodic direction: the facet slot holds the top boundary
-        // facet of the last cell (side A) and the bottom one of the first (side B); walls
-        // and outlets add nothing in the evaluated form (the cell-wise integration by parts
-        // cancels the conservative form's own-trace flux), so both moment sets are zero
-        for (int t = lane; t < 6 * NFM; t += 32) gam[F * 6 * NFM + t] = T(0);
-        continue;
-      }
-    }
-    const int64_t eA = cell_shift(m, eB, d, -1);
-    const T n0 = T(m.nF[F * 3 + 0]), n1 = T(m.nF[F * 3 + 1]), n2 = T(m.nF[F * 3 + 2]);
     const T aF = T(m.aF[F]);
-    // 1. traces: fields 0-2 u^A, 3-5 w^A, 6-8 u^B, 9-11 w^B, each a compensated sum
-    //    (hi + lo: error-free products by FMA, Knuth's TwoSum, L(0 or 1) as hi + lo), so that
-    //    the jumps of nearly equal traces keep their relative accuracy in FP32.  A lane owns
-    //    one line (field, t) of the facet and forms its K1 traces (s = 0..K1-1), all its
-    //    loads issued first; the coefficient of mode (a_d, s, t) sits at a_d sd + s ss + t st.
-    //    When the wind is the convected field (w = u, a STAGE substep) only the six velocity
-    //    traces are formed, and read for both.
-    const int sd = d == 0 ? 1 : (d == 1 ? K1 : K1 * K1);
-    const int ss = d == 0 ? K1 : 1;
-    const int st = d == 2 ? K1 : K1 * K1;
-    const int nlines = (same ? 6 : 12) * K1;
-    for (int L = lane; L < nlines; L += 32) {
-      const int f0 = L / K1, tt = L - f0 * K1;
-      const int f = same && f0 >= 3 ? f0 + 3 : f0;
-      const bool sideA = f < 6;
-      const int comp = (f % 6) % 3;
-      const T* src = ((f % 6) < 3 ? uL : wL) + ((sideA ? eA : eB) * 3 + comp) * NB + tt * st;
-      const T* en = sideA ? sE1 : sE0;
-      const T* el = sideA ? sE1l : sE0l;
-      T cv[K1][K1];
-#pragma unroll
-      for (int s2 = 0; s2 < K1; ++s2)
-#pragma unroll
-        for (int ad = 0; ad < K1; ++ad) cv[s2][ad] = __ldg(src + ad * sd + s2 * ss);
-#pragma unroll
-      for (int s2 = 0; s2 < K1; ++s2) {
-        T hi = T(0), lo = T(0);
-#pragma unroll
-        for (int ad = 0; ad < K1; ++ad) {
-          const T c = cv[s2][ad];
-          const T p = mul_rn(en[ad], c);
-          const T pe = fma(en[ad], c, -p);
-          const T sum = add_rn(hi, p);
-          const T bb = sub_rn(sum, hi);
-          lo += add_rn(sub_rn(hi, sub_rn(sum, bb)), sub_rn(p, bb)) + fma(el[ad], c, pe);
-          hi = sum;
+    // The slot of the first cell of a non-periodic direction holds two boundary facets: the
+    // top one of the last cell (its moments in the slot's side-A part) and the bottom one of
+    // the first (side-B part).  Walls and outlets add nothing in the evaluated form (the
+    // cell-wise integration by parts cancels the conservative form's own-trace flux): zero
+    // moments.  An inlet runs the facet's steps below with the cell as side A (its own
+    // normal), the inlet data as side B's velocity and the cell's own wind on both sides.
+    bool bslot = false;
+    int jend = 0;
+    if ((m.bmask >> d) & 1) {
+      const int c0i = int(eB % m.n0), c1i = int((eB / m.n0) % m.n1), c2i = int(eB / ((int64_t)m.n0 * m.n1));
+      bslot = (d == 0 ? c0i : (d == 1 ? c1i : c2i)) == 0;
+      jend = d == 0 ? c1i + m.n1 * c2i : (d == 1 ? c0i + m.n0 * c2i : c0i + m.n0 * c1i);
+    }
+    const int64_t eBelow = cell_shift(m, eB, d, -1);
+#pragma unroll 1
+    for (int sub = 0; sub < (bslot ? 2 : 1); ++sub) {
+      // sub-facet: side A cell and its end (x_d = 1 or 0), side B cell or inlet data, normal sign
+      int64_t eA = eBelow;
+      bool endA1 = true;
+      T sgn = T(1);
+      const T* ext = nullptr;
+      T* outA = gam + F * 6 * NFM;           // side-A part of the slot
+      T* outB = outA + 3 * NFM;              // side-B part
+      if (bslot) {
+        const void* in = m.inlet[d][sub == 0 ? 1 : 0];
+        T* part = sub == 0 ? outA : outB;
+        if (!in) {
+          for (int t = lane; t < 3 * NFM; t += 32) part[t] = T(0);
+          continue;
         }
-        buf[C::O_TR + f * NFM + s2 + K1 * tt] = hi;
-        buf[C::O_TL + f * NFM + s2 + K1 * tt] = lo;
+        ext = static_cast<const T*>(in) + (int64_t)jend * 3 * NFM;
+        if (sub == 1) {
+          eA = eB;
+          endA1 = false;
+          sgn = T(-1);
+        }
+        outA = part;
+        outB = nullptr;
       }
-    }
-    __syncwarp();
-    // 2. modal point fields [f][t][s]; the jumps from the pairs (hi_A - hi_B is exact for
-    //    close traces)
-    for (int mm = lane; mm < NFM; mm += 32) {
-      const T* tr = buf + C::O_TR;
-      const T* tl = buf + C::O_TL;
-      const int s = mm % K1, tt = mm / K1;
-      T* v = buf + C::O_V + tt * K1o + s;
-      constexpr int FS = K1 * K1o;  // one field
-      T ja[3], wa = T(0), wj = T(0);
-      const T nv[3] = {n0, n1, n2};
+      const bool extB = ext != nullptr;
+      const bool samew = same && !extB;  // w^A, w^B read from the velocity traces
+      const T n0 = sgn * T(m.nF[F * 3 + 0]), n1 = sgn * T(m.nF[F * 3 + 1]), n2 = sgn * T(m.nF[F * 3 + 2]);
+      // 1. traces: fields 0-2 u^A, 3-5 w^A, 6-8 u^B, 9-11 w^B, each a compensated sum
+      //    (hi + lo: error-free products by FMA, Knuth's TwoSum, L(0 or 1) as hi + lo), so
+      //    that the jumps of nearly equal traces keep their relative accuracy in FP32.  A lane
+      //    owns one line (field, t) of the facet and forms its K1 traces (s = 0..K1-1), all
+      //    its loads issued first; the coefficient of mode (a_d, s, t) sits at
+      //    a_d sd + s ss + t st.  When the wind is the convected field (w = u, a STAGE
+      //    substep) only the velocity traces are formed, and read for both.
+      const int sd = d == 0 ? 1 : (d == 1 ? K1 : K1 * K1);
+      const int ss = d == 0 ? K1 : 1;
+      const int st = d == 2 ? K1 : K1 * K1;
+      // lines: w = u: u^A, u^B; else u^A, w^A, u^B, w^B; an inlet: u^A (and w^A unless w = u)
+      const int nlines = (extB ? (same ? 3 : 6) : (same ? 6 : 12)) * K1;
+      for (int L = lane; L < nlines; L += 32) {
+        const int f0 = L / K1, tt = L - f0 * K1;
+        const int f = same && f0 >= 3 ? f0 + 3 : f0;
+        const bool sideA = f < 6;
+        const int comp = (f % 6) % 3;
+        const T* src = ((f % 6) < 3 ? uL : wL) + ((sideA ? eA : eB) * 3 + comp) * NB + tt * st;
+        const bool e1 = sideA ? endA1 : false;
+        const T* en = e1 ? sE1 : sE0;
+        const T* el = e1 ? sE1l : sE0l;
+        T cv[K1][K1];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T uA = tr[a * NFM + mm], uB = tr[(6 + a) * NFM + mm];
-        const int iwA = same ? a : 3 + a, iwB = same ? 6 + a : 9 + a;
-        const T wA = tr[iwA * NFM + mm], wB = tr[iwB * NFM + mm];
-        const T djw = (wA - wB) + (tl[iwA * NFM + mm] - tl[iwB * NFM + mm]);
-        wa += T(0.5) * (wA + wB) * nv[a];
-        wj += djw * nv[a];
-        ja[a] = (uA - uB) + (tl[a * NFM + mm] - tl[(6 + a) * NFM + mm]);
-        v[(2 + a) * FS] = ja[a];
-        v[(5 + a) * FS] = T(0.5) * (uA + uB);
+        for (int s2 = 0; s2 < K1; ++s2)
+#pragma unroll
+          for (int ad = 0; ad < K1; ++ad) cv[s2][ad] = __ldg(src + ad * sd + s2 * ss);
+#pragma unroll
+        for (int s2 = 0; s2 < K1; ++s2) {
+          T hi = T(0), lo = T(0);
+#pragma unroll
+          for (int ad = 0; ad < K1; ++ad) {
+            const T c = cv[s2][ad];
+            const T p = mul_rn(en[ad], c);
+            const T pe = fma(en[ad], c, -p);
+            const T sum = add_rn(hi, p);
+            const T bb = sub_rn(sum, hi);
+            lo += add_rn(sub_rn(hi, sub_rn(sum, bb)), sub_rn(p, bb)) + fma(el[ad], c, pe);
+            hi = sum;
+          }
+          buf[C::O_TR + f * NFM + s2 + K1 * tt] = hi;
+          buf[C::O_TL + f * NFM + s2 + K1 * tt] = lo;
+        }
       }
-      v[0] = wa;
-      v[FS] = wj;
-      const bool low = (s > tt ? s : tt) <= l;
-      const T jn = ja[0] * n0 + ja[1] * n1 + ja[2] * n2;
-      v[8 * FS] = low ? jn * n0 : ja[0];
-      v[9 * FS] = low ? jn * n1 : ja[1];
-      v[10 * FS] = low ? jn * n2 : ja[2];
-    }
-    __syncwarp();
-    // 3. to the points, lanes owning lines: over s (lines (f, t)), then over t (lines (f, p1))
-    for (int L = lane; L < NV * K1; L += 32) {
-      const int f = L / K1, tt = L - f * K1;
-      T c[K1];
-#pragma unroll
-      for (int s = 0; s < K1; ++s) c[s] = buf[C::O_V + L * K1o + s];
-#pragma unroll
-      for (int p1 = 0; p1 < M; ++p1) {
-        T acc = T(0);
-#pragma unroll
-        for (int s = 0; s < K1; ++s) acc = fma(t1.b(p1, s), c[s], acc);
-        buf[C::O_T + (f * M + p1) * K1o + tt] = acc;
+      if (extB) {  // side B's velocity: the inlet modes (exact, no low part)
+        for (int t = lane; t < 3 * NFM; t += 32) {
+          buf[C::O_TR + 6 * NFM + t] = ext[t];
+          buf[C::O_TL + 6 * NFM + t] = T(0);
+        }
       }
-    }
-    __syncwarp();
-    for (int L = lane; L < NV * M; L += 32) {
-      const int f = L / M, p1 = L - f * M;
-      T c[K1];
+      __syncwarp();
+      // 2. modal point fields [f][t][s]; the jumps from the pairs (hi_A - hi_B is exact for
+      //    close traces)
+      for (int mm = lane; mm < NFM; mm += 32) {
+        const T* tr = buf + C::O_TR;
+        const T* tl = buf + C::O_TL;
+        const int s = mm % K1, tt = mm / K1;
+        T* v = buf + C::O_V + tt * K1o + s;
+        constexpr int FS = K1 * K1o;  // one field
+        T ja[3], wa = T(0), wj = T(0);
+        const T nv[3] = {n0, n1, n2};
 #pragma unroll
-      for (int tt = 0; tt < K1; ++tt) c[tt] = buf[C::O_T + L * K1o + tt];
-#pragma unroll
-      for (int p2 = 0; p2 < M; ++p2) {
-        T acc = T(0);
-#pragma unroll
-        for (int tt = 0; tt < K1; ++tt) acc = fma(t1.b(p2, tt), c[tt], acc);
-        buf[C::O_P + f * NQF + p2 * M + p1] = acc;
+        for (int a = 0; a < 3; ++a) {
+          const T uA = tr[a * NFM + mm], uB = tr[(6 + a) * NFM + mm];
+          const int iwA = same ? a : 3 + a, iwB = extB ? iwA : (samew ? 6 + a : 9 + a);
+          const T wA = tr[iwA * NFM + mm], wB = tr[iwB * NFM + mm];
+          const T djw = (wA - wB) + (tl[iwA * NFM + mm] - tl[iwB * NFM + mm]);
+          wa += T(0.5) * (wA + wB) * nv[a];
+          wj += djw * nv[a];
+          ja[a] = (uA - uB) + (tl[a * NFM + mm] - tl[(6 + a) * NFM + mm]);
+          v[(2 + a) * FS] = ja[a];
+          v[(5 + a) * FS] = T(0.5) * (uA + uB);
+        }
+        v[0] = wa;
+        v[FS] = wj;
+        const bool low = (s > tt ? s : tt) <= l;
+        const T jn = ja[0] * n0 + ja[1] * n1 + ja[2] * n2;
+        v[8 * FS] = low ? jn * n0 : ja[0];
+        v[9 * FS] = low ? jn * n1 : ja[1];
+        v[10 * FS] = low ? jn * n2 : ja[2];
       }
-    }
-    __syncwarp();
-    // 4. weighted integrands at the points: 0-2 S, 3-5 T, 6-8 h = 1/2|w.n| (I-Pi)[[u]]
-    for (int p = lane; p < NQF; p += 32) {
-      const int p2 = p / M, p1 = p - p2 * M;
-      const T wgt = sW[p1] * sW[p2];
-      const T* P = buf + C::O_P + p;
-      const T wn = P[0], wj = P[NQF];
-      const T hw = T(0.5) * fabs(wn) * wgt;
-      if (diss_part) {
-        const double p0 = P[8 * NQF], p1 = P[9 * NQF], p2v = P[10 * NQF];
-        dacc += double(aF) * double(hw) * (p0 * p0 + p1 * p1 + p2v * p2v);
+      __syncwarp();
+      // 3. to the points, lanes owning lines: over s (lines (f, t)), then over t (lines (f, p1))
+      for (int L = lane; L < NV * K1; L += 32) {
+        const int f = L / K1, tt = L - f * K1;
+        T c[K1];
+#pragma unroll
+        for (int s = 0; s < K1; ++s) c[s] = buf[C::O_V + L * K1o + s];
+#pragma unroll
+        for (int p1 = 0; p1 < M; ++p1) {
+          T acc = T(0);
+#pragma unroll
+          for (int s = 0; s < K1; ++s) acc = fma(t1.b(p1, s), c[s], acc);
+          buf[C::O_T + (f * M + p1) * K1o + tt] = acc;
+        }
       }
+      __syncwarp();
+      for (int L = lane; L < NV * M; L += 32) {
+        const int f = L / M, p1 = L - f * M;
+        T c[K1];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T ju = P[(2 + a) * NQF], au = P[(5 + a) * NQF], pj = P[(8 + a) * NQF];
-        const int qo = p2 * Mo + p1;
-        buf[C::O_Q + a * M * Mo + qo] = T(-0.5) * wgt * (wn * ju + wj * au);
-        buf[C::O_Q + (3 + a) * M * Mo + qo] = T(-0.25) * wgt * wj * ju;
-        buf[C::O_Q + (6 + a) * M * Mo + qo] = hw * pj;
+        for (int tt = 0; tt < K1; ++tt) c[tt] = buf[C::O_T + L * K1o + tt];
+#pragma unroll
+        for (int p2 = 0; p2 < M; ++p2) {
+          T acc = T(0);
+#pragma unroll
+          for (int tt = 0; tt < K1; ++tt) acc = fma(t1.b(p2, tt), c[tt], acc);
+          buf[C::O_P + f * NQF + p2 * M + p1] = acc;
+        }
       }
-    }
-    __syncwarp();
-    // 5. moments: over p1 (lines (f, p2)), then over p2 (lines (f, s))
-    for (int L = lane; L < NM * M; L += 32) {
-      const int f = L / M, p2 = L - f * M;
-      T q[M];
+      __syncwarp();
+      // 4. weighted integrands at the points: 0-2 S, 3-5 T, 6-8 h = 1/2|w.n| (I-Pi)[[u]]
+      for (int p = lane; p < NQF; p += 32) {
+        const int p2 = p / M, p1 = p - p2 * M;
+        const T wgt = sW[p1] * sW[p2];
+        const T* P = buf + C::O_P + p;
+        const T wn = P[0], wj = P[NQF];
+        const T hw = T(0.5) * fabs(wn) * wgt;
+        if (diss_part) {
+          const double p0 = P[8 * NQF], p1 = P[9 * NQF], p2v = P[10 * NQF];
+          dacc += double(aF) * double(hw) * (p0 * p0 + p1 * p1 + p2v * p2v);
+        }
 #pragma unroll
-      for (int p1 = 0; p1 < M; ++p1) q[p1] = buf[C::O_Q + L * Mo + p1];
-#pragma unroll
-      for (int s = 0; s < K1; ++s) {
-        T acc = T(0);
-#pragma unroll
-        for (int p1 = 0; p1 < M; ++p1) acc = fma(t1.b(p1, s), q[p1], acc);
-        buf[C::O_U + (f * K1 + s) * Mo + p2] = acc;
+        for (int a = 0; a < 3; ++a) {
+          const T ju = P[(2 + a) * NQF], au = P[(5 + a) * NQF], pj = P[(8 + a) * NQF];
+          const int qo = p2 * Mo + p1;
+          buf[C::O_Q + a * M * Mo + qo] = T(-0.5) * wgt * (wn * ju + wj * au);
+          buf[C::O_Q + (3 + a) * M * Mo + qo] = T(-0.25) * wgt * wj * ju;
+          buf[C::O_Q + (6 + a) * M * Mo + qo] = hw * pj;
+        }
       }
-    }
-    __syncwarp();
-    for (int L = lane; L < NM * K1; L += 32) {
-      const int f = L / K1, s = L - f * K1;
-      T u[M];
+      __syncwarp();
+      // 5. moments: over p1 (lines (f, p2)), then over p2 (lines (f, s))
+      for (int L = lane; L < NM * M; L += 32) {
+        const int f = L / M, p2 = L - f * M;
+        T q[M];
 #pragma unroll
-      for (int p2 = 0; p2 < M; ++p2) u[p2] = buf[C::O_U + L * Mo + p2];
+        for (int p1 = 0; p1 < M; ++p1) q[p1] = buf[C::O_Q + L * Mo + p1];
 #pragma unroll
-      for (int tt = 0; tt < K1; ++tt) {
-        T acc = T(0);
+        for (int s = 0; s < K1; ++s) {
+          T acc = T(0);
 #pragma unroll
-        for (int p2 = 0; p2 < M; ++p2) acc = fma(t1.b(p2, tt), u[p2], acc);
-        buf[C::O_MO + f * NFM + s + K1 * tt] = acc;
+          for (int p1 = 0; p1 < M; ++p1) acc = fma(t1.b(p1, s), q[p1], acc);
+          buf[C::O_U + (f * K1 + s) * Mo + p2] = acc;
+        }
       }
-    }
-    __syncwarp();
-    // 6. Ph = (I - Pi^l) h on the moments; gA = S + T + Ph, gB = S - T - Ph; times a_F
-    for (int mm = lane; mm < NFM; mm += 32) {
-      const T* mo = buf + C::O_MO + mm;
-      const int s = mm % K1, tt = mm / K1;
-      const bool low = (s > tt ? s : tt) <= l;
-      const T h0 = mo[6 * NFM], h1 = mo[7 * NFM], h2 = mo[8 * NFM];
-      const T hn = h0 * n0 + h1 * n1 + h2 * n2;
-      const T ph[3] = {low ? hn * n0 : h0, low ? hn * n1 : h1, low ? hn * n2 : h2};
-      T* out = gam + F * 6 * NFM + mm;
+      __syncwarp();
+      for (int L = lane; L < NM * K1; L += 32) {
+        const int f = L / K1, s = L - f * K1;
+        T u[M];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T sv = mo[a * NFM], tv = mo[(3 + a) * NFM];
-        out[a * NFM] = aF * (sv + tv + ph[a]);
-        out[(3 + a) * NFM] = aF * (sv - tv - ph[a]);
+        for (int p2 = 0; p2 < M; ++p2) u[p2] = buf[C::O_U + L * Mo + p2];
+#pragma unroll
+        for (int tt = 0; tt < K1; ++tt) {
+          T acc = T(0);
+#pragma unroll
+          for (int p2 = 0; p2 < M; ++p2) acc = fma(t1.b(p2, tt), u[p2], acc);
+          buf[C::O_MO + f * NFM + s + K1 * tt] = acc;
+        }
       }
-    }
-    __syncwarp();
+      __syncwarp();
+      // 6. Ph = (I - Pi^l) h on the moments; gA = S + T + Ph, gB = S - T - Ph; times a_F
+      for (int mm = lane; mm < NFM; mm += 32) {
+        const T* mo = buf + C::O_MO + mm;
+        const int s = mm % K1, tt = mm / K1;
+        const bool low = (s > tt ? s : tt) <= l;
+        const T h0 = mo[6 * NFM], h1 = mo[7 * NFM], h2 = mo[8 * NFM];
+        const T hn = h0 * n0 + h1 * n1 + h2 * n2;
+        const T ph[3] = {low ? hn * n0 : h0, low ? hn * n1 : h1, low ? hn * n2 : h2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T sv = mo[a * NFM], tv = mo[(3 + a) * NFM];
+          outA[a * NFM + mm] = aF * (sv + tv + ph[a]);
+          if (outB) outB[a * NFM + mm] = aF * (sv - tv - ph[a]);
+        }
+      }
+      __syncwarp();
+    }  // sub-facets
   }
   if (diss_part) {
 #pragma unroll

@@ -574,6 +574,16 @@ class HopuHex:
                     "hopu_hex_rk_substeps")
         return uL
 
+    def set_inlet(self, dir: int, end: int, modes: torch.Tensor | None):
+        """Inlet data of one end of a non-periodic direction (hopu_hex_set_inlet): facet modes
+        [n_s * n_t, 3, (k+1)^2] in the context's precision, or None for a wall / outlet."""
+        ptr = None
+        if modes is not None:
+            if modes.device != self.device or modes.dtype != self.dtype or not modes.is_contiguous():
+                raise ValueError(f"modes: expected a contiguous {self.dtype} tensor on {self.device}")
+            ptr = c_void_p(modes.data_ptr())
+        self._check(self.lib.hopu_hex_set_inlet(self.h, int(dir), int(end), ptr), "hopu_hex_set_inlet")
+
     def energy(self, uL: torch.Tensor, wL: torch.Tensor | None = None, l: int = -1):
         """(1/2 int |u|^2, c(w; u, u), facet dissipation) in FP64 (hopu_hex_energy)."""
         out = (c_double * 3)()

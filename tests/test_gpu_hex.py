@@ -139,6 +139,58 @@ def test_hex_walls(periodic):
         g.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_hex_inlets(prec, tol):
+    """Inlets at both ends of direction 1 (walls in direction 2): the exterior velocity's
+    facet modes given to the library, their point values to the oracle; the apply (separate
+    wind and w = u), STAGE substeps and the dissipation."""
+    from paper_2408_06698_gb300 import HopuHex
+    from paper_2408_06698_gb300 import _lib as L
+    k = 3
+    periodic = (True, False, False)
+    hb = W.hex_box((3, 4, 3), jitter=0.2, shear=0.3, seed=80)
+    m, ref = H.HexMesh(hb, periodic=periodic), H.RefHex(k)
+    w, u = _fields(m, ref, 81)
+    if prec == "f32":
+        w, u = w.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    g = HopuHex(hb.lines, hb.A, k=k, prec=prec, periodic=periodic)
+    nfm = (k + 1) ** 2
+    u_inlet = {}
+    for end in (0, 1):
+        Fs = H.end_facets(m, 1, end)
+        modes = W.uniform_noise(len(Fs) * 3 * nfm, 0.5, 90 + end).reshape(len(Fs), 3, nfm)
+        if prec == "f32":
+            modes = modes.astype(np.float32).astype(np.float64)
+        g.set_inlet(1, end, torch.tensor(modes, dtype=g.dtype, device=g.device))
+        for j, F in enumerate(Fs):
+            u_inlet[int(F)] = np.einsum("pm,am->pa", ref.psi, modes[j])
+    ud = _dev(g, u)
+    for wind, wn in ((_dev(g, w), w), (ud, u)):
+        for l in (-1, k - 1):
+            y = g.apply(wind, ud, l).cpu().numpy().astype(np.float64).reshape(u.shape)
+            err = _rel(y, H.apply(m, ref, wn, u, l, u_inlet))
+            print(f"hex inlets {prec} l={l}: {err:.2e}")
+            assert err < tol
+    e, c, d = g.energy(ud, ud, k - 1)
+    _, _, _, PJ, _ = H.facet_quantities(m, ref, u, u, k - 1, u_inlet)
+    wnv, *_ = H.facet_quantities(m, ref, u, u, k - 1, u_inlet)
+    dref = float(np.sum(m.aF[:, None] * ref.wf[None, :] * 0.5 * np.abs(wnv) * np.sum(PJ * PJ, axis=-1)))
+    assert d == pytest.approx(dref, rel=20 * tol)
+    v = ud.clone()
+    g.rk_substeps(v, 1e-2, 2, k - 1)
+    want = H.substeps_stage(m, ref, u, 1e-2, 2, k - 1, u_inlet)
+    err = _rel(v.cpu().numpy().astype(np.float64).reshape(u.shape), want)
+    print(f"hex inlets {prec} substeps: {err:.2e}")
+    assert err < tol
+    with pytest.raises(L.HopuError):
+        g.set_inlet(0, 0, None)                         # direction 0 is periodic
+    g.set_inlet(1, 0, None)                             # back to a wall
+    g.set_inlet(1, 1, None)
+    y = g.apply(ud, ud, -1).cpu().numpy().astype(np.float64).reshape(u.shape)
+    assert _rel(y, H.apply(m, ref, u, u, -1)) < tol
+    g.close()
+
+
 def test_hex_constant_state_and_errors():
     from paper_2408_06698_gb300 import _lib as L
     hb = W.hex_box(3, jitter=0.1, shear=0.2, seed=3)
