@@ -169,8 +169,9 @@ int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, 
   const Tabs<T> tb = tabs_dev<T, K>(h);
   T* gam = static_cast<T*>(h->d_gam);
   int& gf = h->grid[0];
-  auto kf = k_hex_facet<T, K>;
   using CF = Fac<T, K>;
+  // a fully periodic box runs the facet kernel without the boundary-facet code
+  auto kf = h->bmask ? k_hex_facet<T, K, true> : k_hex_facet<T, K, false>;
   if (grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf))
     return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
   kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam, diss);

@@ -172,10 +172,11 @@ __device__ __forceinline__ int64_t cell_shift(const MeshDev& m, int64_t e, int d
   return i0 + (int64_t)m.n0 * (i1 + (int64_t)m.n1 * i2);
 }
 
-// Facet kernel: gam[F][0][a][m] = a_F (moments of gA_a), gam[F][1][a][m] = a_F (moments of gB_a),
+// Facet kernel (BND: the box has non-periodic directions, whose end facets are walls,
+// outlets or inlets): gam[F][0][a][m] = a_F (moments of gA_a), gam[F][1][a][m] = a_F (moments of gB_a),
 //   gA = S + T + Ph, gB = S - T - Ph,  S = -1/2 (w.n) [[u]] - 1/2 [[w.n]] <u>,  T = -1/4 [[w.n]] [[u]]
 // (S + T = -1/2 (w.n)[[u]] - 1/2 [[w.n]] u^A, S - T the same with u^B).
-template <typename T, int K>
+template <typename T, int K, bool BND>
 __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     k_hex_facet(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* __restrict__ uL, int l,
                 T* __restrict__ gam, double* __restrict__ diss_part) {
@@ -213,14 +214,14 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     // normal), the inlet data as side B's velocity and the cell's own wind on both sides.
     bool bslot = false;
     int jend = 0;
-    if ((m.bmask >> d) & 1) {
+    if (BND && ((m.bmask >> d) & 1)) {
       const int c0i = int(eB % m.n0), c1i = int((eB / m.n0) % m.n1), c2i = int(eB / ((int64_t)m.n0 * m.n1));
       bslot = (d == 0 ? c0i : (d == 1 ? c1i : c2i)) == 0;
       jend = d == 0 ? c1i + m.n1 * c2i : (d == 1 ? c0i + m.n0 * c2i : c0i + m.n0 * c1i);
     }
     const int64_t eBelow = cell_shift(m, eB, d, -1);
 #pragma unroll 1
-    for (int sub = 0; sub < (bslot ? 2 : 1); ++sub) {
+    for (int sub = 0; sub < (BND && bslot ? 2 : 1); ++sub) {
       // sub-facet: side A cell and its end (x_d = 1 or 0), side B cell or inlet data, normal sign
       int64_t eA = eBelow;
       bool endA1 = true;
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
       const T* ext = nullptr;
       T* outA = gam + F * 6 * NFM;           // side-A part of the slot
       T* outB = outA + 3 * NFM;              // side-B part
-      if (bslot) {
+      if (BND && bslot) {
         const void* in = m.inlet[d][sub == 0 ? 1 : 0];
         T* part = sub == 0 ? outA : outB;
         if (!in) {
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
         outA = part;
         outB = nullptr;
       }
-      const bool extB = ext != nullptr;
+      const bool extB = BND && ext != nullptr;
       const bool samew = same && !extB;  // w^A, w^B read from the velocity traces
       const T n0 = sgn * T(m.nF[F * 3 + 0]), n1 = sgn * T(m.nF[F * 3 + 1]), n2 = sgn * T(m.nF[F * 3 + 2]);
       // 1. traces: fields 0-2 u^A, 3-5 w^A, 6-8 u^B, 9-11 w^B, each a compensated sum
