@@ -146,19 +146,20 @@ Tabs<T> tabs_dev(const hopu_hex* h) {
 // items); computed once per context and kernel (the dynamic shared memory attribute is set
 // on that first call)
 template <typename Kern>
-int grid_for(Kern kern, int threads, size_t smem, int64_t items_per_block, int64_t items, int* grid) {
-  if (*grid > 0) return 0;
+cudaError_t grid_for(Kern kern, int threads, size_t smem, int64_t items_per_block, int64_t items, int* grid) {
+  if (*grid > 0) return cudaSuccess;
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return -1;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int64_t need = (items + items_per_block - 1) / items_per_block;
   const int64_t full = (int64_t)sms * per_sm;
   *grid = (int)(need < full ? need : full);
   if (*grid < 1) *grid = 1;
-  return 0;
+  return cudaSuccess;
 }
 
 // one apply: facet moments, then volume + lift + inverse mass + out = c0 u0 + c1 us + c2 y
@@ -172,8 +173,8 @@ int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, 
   using CF = Fac<T, K>;
   // a fully periodic box runs the facet kernel without the boundary-facet code
   auto kf = h->bmask ? k_hex_facet<T, K, true> : k_hex_facet<T, K, false>;
-  if (grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf))
-    return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
+  cudaError_t ga = grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf);
+  if (ga != cudaSuccess) return cuda_fail(h, ga, "hopu_hex: k_hex_facet attributes");
   kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam, diss);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_facet launch");
@@ -181,15 +182,15 @@ int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, 
     int& gv = h->grid[2];
     auto kv = k_hex_volume_same<T, K>;
     using CV = VolS<T, K>;
-    if (grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
-      return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
+    if ((ga = grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv)) != cudaSuccess)
+      return cuda_fail(h, ga, "hopu_hex: k_hex_volume_same attributes");
     kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, us, gam, u0, c0, c1, c2, out);
   } else {
     int& gv = h->grid[1];
     auto kv = k_hex_volume<T, K>;
     using CV = Vol<T, K>;
-    if (grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv))
-      return cuda_fail(h, cudaGetLastError(), "hopu_hex: kernel attributes");
+    if ((ga = grid_for(kv, 32 * CV::WARPS, CV::SMEM, CV::WARPS, h->E, &gv)) != cudaSuccess)
+      return cuda_fail(h, ga, "hopu_hex: k_hex_volume attributes");
     kv<<<gv, 32 * CV::WARPS, CV::SMEM, h->stream>>>(m, tb, w, us, gam, u0, c0, c1, c2, out);
   }
   e = cudaGetLastError();
