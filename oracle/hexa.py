@@ -37,7 +37,9 @@ volume and closed cells, facet points that coincide from both sides, zero output
 constant fields, the energy identity, the l = k limit, the Q^l orthogonality of (I - Pi^l),
 the form equal to the simplicial oracle's on the same box for polynomial fields, periodic or
 walled, and with walls the form equal to the volume integral of (grad u) w + (div w) u
-evaluated from the polynomials' analytic gradients).
+evaluated from the polynomials' analytic gradients; with an inlet, the form equal to the
+simplicial oracle's with the same exterior data; the order-k convergence of the discrete
+(u . grad) u on Taylor-Green).
 """
 from __future__ import annotations
 
