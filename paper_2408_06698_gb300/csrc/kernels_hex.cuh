@@ -733,14 +733,18 @@ struct VolS {
   static constexpr int XS = K1 * M * K1o;   // one x-pass output [line (q1,i3)][i2]
   static constexpr int YS = M * M * K1o;    // one y-pass output [line (q1,q2)][i3]
   static constexpr int GS = K1 * M * Mo;    // one test pass over q3 [line (q1,i3)][q2]
-  static constexpr int O_C = 0;
-  static constexpr int O_X = O_C + 3 * CS;      // [f][B|D]
-  static constexpr int O_Y = O_X + 6 * XS;      // [f][BB|BD|DB]
-  static constexpr int O_G = O_Y + 9 * YS;      // [a]
-  static constexpr int PER_WARP = O_G + 3 * GS;
+  // buffers by lifetime: the x region holds the x-pass outputs, then the test pass over q3;
+  // the y region the cell's coefficients, then the y-pass outputs, then the test pass over q2
+  static constexpr int O_X = 0;                 // [f][B|D], then [a] test over q3
+  static constexpr int O_Y = O_X + 6 * XS;      // coefficients, then [f][BB|BD|DB], then [a] test over q2
+  static constexpr int O_C = O_Y;
+  static constexpr int O_G = O_X;
+  static constexpr int PER_WARP = O_Y + 9 * YS;
   static constexpr int TAB = 2 * M * K1 + M + 4 * K1;
   static constexpr size_t SMEM = size_t(TAB + WARPS * PER_WARP) * sizeof(T);
-  static_assert(3 * K1 * K1 * Mo <= 6 * XS, "test pass over q2 in the x region");
+  static_assert(3 * CS <= 9 * YS, "coefficients in the y region");
+  static_assert(3 * GS <= 6 * XS, "test pass over q3 in the x region");
+  static_assert(3 * K1 * K1 * Mo <= 9 * YS, "test pass over q2 in the y region");
   static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 };
 
@@ -766,7 +770,7 @@ __global__ void __launch_bounds__(32 * VolS<T, K>::WARPS)
   T* X = base + C::O_X;
   T* Y = base + C::O_Y;
   T* Gz = base + C::O_G;
-  T* Hx = X;  // [a][line (i2, i3)][q1]
+  T* Hx = Y;  // [a][line (i2, i3)][q1]
   constexpr int NPRE = (3 * NB + 31) / 32;
   const int64_t estep = (int64_t)gridDim.x * C::WARPS;
   T pre[NPRE];
