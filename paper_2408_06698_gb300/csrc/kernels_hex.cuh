@@ -1,6 +1,7 @@
 // Hexahedral cells: the HOPU convection apply (Section 3.2, eq. "hopudefinition", in the
-// conservative reading) on a structured periodic box of parallelepipeds (Section 2.1: the
-// paper's meshes are hexahedral), with sum-factorised tensor-product contractions.
+// conservative reading) on a structured box of parallelepipeds, periodic or ending in walls,
+// outlets or inlets per direction (Section 2.1: the paper's meshes are hexahedral), with
+// sum-factorised tensor-product contractions.
 //
 // Space: per velocity component, Q^k on the reference cube [0,1]^3 with the orthonormal
 // tensor Legendre basis phi_i = L_i1(x1) L_i2(x2) L_i3(x3), i = i1 + K1 (i2 + K1 i3),
@@ -8,11 +9,14 @@
 // direction, exact to degree 3k per direction (volume and facets).  Affine cells:
 // M_T = |det J| I, so the inverse mass is 1/|det J| per cell.
 //
-// One warp per cell (k_hex_volume) or per facet (k_hex_facet); the contractions run as
-// one-dimensional passes through the warp's shared-memory buffers (the volume kernel's lanes
-// own lines of the tensor, the facet kernel's the outputs of a pass).  Cell e = i0 + n0 (i1 + n1 i2); facet F = d E + e is the low facet of cell e
-// in direction d: side A the cell below (periodic), local facet x_d = 1; side B = e,
-// x_d = 0.  The facet coordinates (s, t) are the two other axes in increasing order.
+// One warp per cell (k_hex_volume, k_hex_volume_same) or per facet (k_hex_facet); the
+// contractions run as one-dimensional passes through the warp's shared-memory buffers, a
+// lane owning one line of the tensor with its inputs and (FP32) the 1D tables in registers.
+// Cell e = i0 + n0 (i1 + n1 i2); facet F = d E + e is the low facet of cell e in direction
+// d: side A the cell below (periodic wrap), local facet x_d = 1; side B = e, x_d = 0.  The
+// facet coordinates (s, t) are the two other axes in increasing order.  At the ends of a
+// non-periodic direction the slot F of the first cell holds two boundary facets (see
+// k_hex_facet).
 //
 // Evaluation: the conservative form is rewritten cell by cell with the divergence theorem
 // (exact under these rules: u w v has degree <= 3k per direction),
