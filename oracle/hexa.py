@@ -243,17 +243,23 @@ def _traces(mesh: HexMesh, ref: RefHex, cL: np.ndarray, side: str) -> np.ndarray
     return out
 
 
-def complement_projection(ref: RefHex, l: int, nF: np.ndarray, V: np.ndarray) -> np.ndarray:
+def complement_projection(ref: RefHex, l, nF: np.ndarray, V: np.ndarray) -> np.ndarray:
     """(I - Pi^l) V at the facet points, V [F, nqf, 3]: Pi^l is the facet-wise L2 projection
     onto tangential Q^l fields (reading H1); on a flat facet that is (I - n n^T) applied to
-    the componentwise Q^l projection.  l < 0: Pi = 0."""
-    if l < 0:
-        return V.copy()
-    P = ref.psi[:, ref.q_modes(l)]
-    coef = np.einsum("p,pm,Fpa->Fma", ref.wf, P, V)
-    PiS = np.einsum("pm,Fma->Fpa", P, coef)
-    PiV = PiS - np.einsum("Fpa,Fa->Fp", PiS, nF)[..., None] * nF[:, None, :]
-    return V - PiV
+    the componentwise Q^l projection.  l < 0: Pi = 0.  l: one order or one per facet."""
+    l_F = np.full(V.shape[0], int(l)) if np.isscalar(l) else np.asarray(l, dtype=np.int64)
+    out = V.copy()
+    for lv in np.unique(l_F):
+        if lv < 0:
+            continue
+        msk = l_F == lv
+        P = ref.psi[:, ref.q_modes(int(lv))]
+        coef = np.einsum("p,pm,Fpa->Fma", ref.wf, P, V[msk])
+        PiS = np.einsum("pm,Fma->Fpa", P, coef)
+        n = nF[msk]
+        PiV = PiS - np.einsum("Fpa,Fa->Fp", PiS, n)[..., None] * n[:, None, :]
+        out[msk] = V[msk] - PiV
+    return out
 
 
 def facet_quantities(mesh: HexMesh, ref: RefHex, wL, uL, l: int, u_inlet=None):
@@ -328,6 +334,18 @@ def facet_dissipation(mesh, ref, wL, uL, l) -> float:
     """sum_F int_F 1/2 |w.n| |(I - Pi^l)[[u]]|^2."""
     wn, jump, avg, PJ, Ph = facet_quantities(mesh, ref, wL, uL, l)
     return float(np.sum(mesh.aF[:, None] * ref.wf[None, :] * 0.5 * np.abs(wn) * np.sum(PJ * PJ, axis=-1)))
+
+
+def facet_eta(mesh: HexMesh, ref: RefHex, uL, l) -> np.ndarray:
+    """Adaptive HOPU's jump indicator per facet (Section 3.2, after eq. "hopudefinition"):
+    eta = int_E |(I - Pi^l)[[u]]| ds / int_E |<u>| ds with the facet's current order l (one
+    or one per facet); the readings of oracle/adaptive.py (a zero average with a non-zero
+    jump: +inf; both zero: 0).  The orders follow from adaptive.order_from_eta."""
+    _, jump, avg, PJ, _ = facet_quantities(mesh, ref, uL, uL, l)
+    num = np.einsum("p,Fp->F", ref.wf, np.linalg.norm(PJ, axis=-1))
+    den = np.einsum("p,Fp->F", ref.wf, np.linalg.norm(avg, axis=-1))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(den > 0, num / np.where(den > 0, den, 1.0), np.where(num > 0, np.inf, 0.0))
 
 
 def kinetic_energy(mesh, uL) -> float:

@@ -356,3 +356,36 @@ def test_order_k_consistency_on_taylor_green(k, ns):
         errs.append(np.sqrt(np.sum(m.absdet[:, None, None] * diff ** 2)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates[-1] > k - 0.25 and np.all(rates > k - 0.35), (errs, rates)   # k = 2: 2.67; k = 3: 2.83
+
+
+def test_eta_closed_forms():
+    """eta for a field constant c1 / c2 on alternate layers of cells in direction 0 (a jump
+    only across the facets of direction 0): |c1 - c2| / |c1 + c2| * 2 there with l = -1,
+    the normal part of the jump only with l >= 0 (Q^0 holds the constant tangential part),
+    0 on the other facets; 0 everywhere for a continuous field."""
+    hb = W.hex_box(4, jitter=0.2, shear=0.0, seed=16)
+    m, ref = H.HexMesh(hb), H.RefHex(2)
+    c1, c2 = np.array([1.0, -0.5, 0.25]), np.array([0.2, 0.4, -0.6])
+    uL = np.zeros((m.n_elems, 3, ref.nb))
+    layer = m.cell[:, 0] % 2 == 0
+    uL[layer, :, 0], uL[~layer, :, 0] = c1, c2
+    E = m.n_elems
+    jump = np.linalg.norm(c1 - c2)
+    want = jump / np.linalg.norm(0.5 * (c1 + c2))
+    eta = H.facet_eta(m, ref, uL, -1)
+    assert np.allclose(eta[:E], want, rtol=1e-12) and np.abs(eta[E:]).max() < 1e-14
+    eta0 = H.facet_eta(m, ref, uL, 0)                    # no shear: n_F = e_0 on those facets
+    assert np.allclose(eta0[:E], abs((c1 - c2)[0]) / np.linalg.norm(0.5 * (c1 + c2)), rtol=1e-12)
+    uc = H.project(m, ref, lambda x: np.stack([np.sin(0 * x[..., 0]) + 1.0, 0 * x[..., 1], 0 * x[..., 2]], -1))
+    assert np.abs(H.facet_eta(m, ref, uc, -1)).max() < 1e-13
+    # per-facet orders act facet by facet: against the uniform l = -1 result, only cells with
+    # a facet of another order change, and a uniform order array equals the scalar order
+    w, u = W.uniform_noise(uL.size, 1.0, 3).reshape(uL.shape), W.uniform_noise(uL.size, 1.0, 4).reshape(uL.shape)
+    lF = np.full(m.n_facets, -1)
+    lF[np.random.default_rng(5).choice(m.n_facets, size=20, replace=False)] = 1
+    diff = np.abs(H.apply(m, ref, w, u, lF) - H.apply(m, ref, w, u, -1)).max(axis=(1, 2))
+    touched = np.zeros(m.n_elems, dtype=bool)
+    touched[m.fa[lF == 1, 0]] = True
+    touched[m.fb[lF == 1, 0]] = True
+    assert diff[~touched].max() == 0.0 and diff[touched].min() > 0.0
+    assert np.abs(H.apply(m, ref, w, u, np.full(m.n_facets, 1)) - H.apply(m, ref, w, u, 1)).max() == 0.0
