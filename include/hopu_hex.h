@@ -75,6 +75,22 @@ int hopu_hex_rk_substeps(hopu_hex* h, void* uL, double dt, int n, int l);
  * EINVAL: dir / end out of range or dir periodic. */
 int hopu_hex_set_inlet(hopu_hex* h, int dir, int end, const void* modes);
 
+/* Per-facet HOPU orders (device int8 [3E], values -1..k, caller-owned, read at every later
+ * apply, substep and hopu_hex_energy; entry F = d E + e is the facet of direction d below
+ * cell e, and on a box with boundary facets the two boundary facets of such a slot share
+ * its order).  NULL restores the l of each call. */
+int hopu_hex_set_facet_l(hopu_hex* h, const int8_t* facet_l);
+
+/* Adaptive HOPU (Section 3.2, after eq. "hopudefinition"): per facet the jump indicator
+ *   eta = int_F |(I - Pi^l)[[u]]| ds / int_F |<u>| ds
+ * of the L2 field uL with l the facet's current order in facet_l (device int8 [3E],
+ * in/out), then the new order: -1 for eta <= eta_0, i for eta_i < eta <= eta_{i+1}, k for
+ * eta > eta_k (a zero average with a non-zero jump counts as eta = +inf), written back to
+ * facet_l.  thresholds: host, k+1 increasing values in (0, 1) (EINVAL otherwise);
+ * eta_out: device FP64 [3E] or NULL.  Sums and the decision in FP64.  ENOTSUP on a box
+ * with boundary facets. */
+int hopu_hex_adapt_l(hopu_hex* h, const void* uL, const double* thresholds, int8_t* facet_l, double* eta_out);
+
 /* FP64 reductions (row a8 of the hot path; synchronises the stream):
  *   host_out[0] = 1/2 int |u|^2                             (kinetic energy)
  *   host_out[1] = c(w; u, u)                                (0 if wL is NULL)

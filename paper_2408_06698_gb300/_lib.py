@@ -60,6 +60,8 @@ SIGNATURES = {
     "hopu_hex_apply": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "hopu_hex_rk_substeps": (c_int, [c_void_p, c_void_p, c_double, c_int, c_int]),
     "hopu_hex_set_inlet": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "hopu_hex_set_facet_l": (c_int, [c_void_p, c_void_p]),
+    "hopu_hex_adapt_l": (c_int, [c_void_p, c_void_p, POINTER(c_double), c_void_p, c_void_p]),
     "hopu_hex_energy": (c_int, [c_void_p, c_void_p, c_void_p, c_int, POINTER(c_double)]),
     "hopu_hex_last_error": (c_char_p, [c_void_p]),
     "hopu_clear_error": (c_int, [c_void_p]),

@@ -25,7 +25,8 @@ struct hopu_hex {
   void* d_gam = nullptr;     // facet moments [3E][2][3][(k+1)^2] (side A, side B)
   void* d_u1 = nullptr;      // two stage vectors
   void* d_u2 = nullptr;
-  int grid[3] = {0, 0, 0};  // facet, volume, volume (w = u): set at the first launch
+  int grid[4] = {0, 0, 0, 0};  // facet, volume, volume (w = u), facet (eta): set at the first launch
+  const int8_t* facet_l = nullptr;  // per-facet orders (hopu_hex_set_facet_l), caller-owned
   void* d_inlet[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // inlet modes
   bool inlet_on[3][2] = {{false, false}, {false, false}, {false, false}};
   double* d_part = nullptr;  // FP64 partial sums of the reductions
@@ -124,6 +125,7 @@ MeshDev mesh_dev(const hopu_hex* h) {
   m.aF = m.nF + 9 * h->E;
   for (int d = 0; d < 3; ++d)
     for (int e = 0; e < 2; ++e) m.inlet[d][e] = h->inlet_on[d][e] ? h->d_inlet[d][e] : nullptr;
+  m.facet_l = h->facet_l;
   return m;
 }
 
@@ -175,7 +177,7 @@ int stage(hopu_hex* h, const T* w, const T* us, int l, const T* u0, T c0, T c1, 
   auto kf = h->bmask ? k_hex_facet<T, K, true> : k_hex_facet<T, K, false>;
   cudaError_t ga = grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &gf);
   if (ga != cudaSuccess) return cuda_fail(h, ga, "hopu_hex: k_hex_facet attributes");
-  kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam, diss);
+  kf<<<gf, 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tb, w, us, l, gam, diss, EtaArgs{});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_facet launch");
   if (w == us) {  // the wind is the convected field: each component interpolated once
@@ -220,6 +222,37 @@ int dispatch_apply(hopu_hex* h, const T* w, const T* u, int l, T* y, double* dis
     case 3: return stage<T, 3>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
     case 4: return stage<T, 4>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
     case 5: return stage<T, 5>(h, w, u, l, u, T(0), T(0), T(1), y, diss);
+  }
+  return fail(h, HOPU_ENOTSUP, "hopu_hex: order");
+}
+
+// the adaptive step (see hopu_hex_adapt_l)
+template <typename T, int K>
+int adapt(hopu_hex* h, const T* u, const double* thr, int8_t* facet_l, double* eta_out) {
+  MeshDev m = mesh_dev(h);
+  m.facet_l = facet_l;
+  EtaArgs ea{};
+  for (int i = 0; i <= K; ++i) ea.thr[i] = thr[i];
+  ea.l_out = facet_l;
+  ea.eta_out = eta_out;
+  using CF = Fac<T, K>;
+  auto kf = k_hex_facet<T, K, false, true>;
+  cudaError_t ga = grid_for(kf, 32 * CF::WARPS, CF::SMEM, CF::WARPS, 3 * h->E, &h->grid[3]);
+  if (ga != cudaSuccess) return cuda_fail(h, ga, "hopu_hex: k_hex_facet (eta) attributes");
+  kf<<<h->grid[3], 32 * CF::WARPS, CF::SMEM, h->stream>>>(m, tabs_dev<T, K>(h), u, u, -1,
+                                                          static_cast<T*>(h->d_gam), nullptr, ea);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "k_hex_facet (eta) launch");
+  return HOPU_OK;
+}
+
+template <typename T>
+int dispatch_adapt(hopu_hex* h, const T* u, const double* thr, int8_t* facet_l, double* eta_out) {
+  switch (h->k) {
+    case 2: return adapt<T, 2>(h, u, thr, facet_l, eta_out);
+    case 3: return adapt<T, 3>(h, u, thr, facet_l, eta_out);
+    case 4: return adapt<T, 4>(h, u, thr, facet_l, eta_out);
+    case 5: return adapt<T, 5>(h, u, thr, facet_l, eta_out);
   }
   return fail(h, HOPU_ENOTSUP, "hopu_hex: order");
 }
@@ -437,6 +470,24 @@ int hopu_hex_set_inlet(hopu_hex* h, int dir, int end, const void* modes) {
     return cuda_fail(h, ce, "hopu_hex_set_inlet: copy");
   h->inlet_on[dir][end] = true;
   return HOPU_OK;
+}
+
+int hopu_hex_set_facet_l(hopu_hex* h, const int8_t* facet_l) {
+  if (!h) return HOPU_EINVAL;
+  h->facet_l = facet_l;
+  return HOPU_OK;
+}
+
+int hopu_hex_adapt_l(hopu_hex* h, const void* uL, const double* thresholds, int8_t* facet_l, double* eta_out) {
+  if (!h) return HOPU_EINVAL;
+  if (!uL || !thresholds || !facet_l) return fail(h, HOPU_EINVAL, "hopu_hex_adapt_l: NULL argument");
+  if (h->bmask) return fail(h, HOPU_ENOTSUP, "hopu_hex_adapt_l: the box has boundary facets");
+  for (int i = 0; i <= h->k; ++i)
+    if (!(thresholds[i] > 0.0 && thresholds[i] < 1.0) || (i > 0 && !(thresholds[i] > thresholds[i - 1])))
+      return fail(h, HOPU_EINVAL, "hopu_hex_adapt_l: thresholds must be k+1 increasing values in (0, 1)");
+  if (h->prec == HOPU_FP64)
+    return dispatch_adapt<double>(h, static_cast<const double*>(uL), thresholds, facet_l, eta_out);
+  return dispatch_adapt<float>(h, static_cast<const float*>(uL), thresholds, facet_l, eta_out);
 }
 
 int hopu_hex_energy(hopu_hex* h, const void* wL, const void* uL, int l, double* host_out) {

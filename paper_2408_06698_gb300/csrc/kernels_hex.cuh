@@ -61,6 +61,9 @@ struct MeshDev {
   // exterior velocity's facet modes [cell (s, t) of the end][3][(k+1)^2] in the working
   // precision, s, t the cell indices of the two other directions (lower axis fastest)
   const void* inlet[3][2];
+  // per-facet HOPU orders [3E] (-1..k; NULL: the launch's l); a boundary slot's two facets
+  // share the slot's order
+  const int8_t* facet_l;
   const double* G;       // [E][3][3]  |det J| J^-1
   const double* invabs;  // [E]        1 / |det J|
   const double* nF;      // [3E][3]    unit normal of facet F (side A outward)
@@ -176,14 +179,27 @@ __device__ __forceinline__ int64_t cell_shift(const MeshDev& m, int64_t e, int d
   return i0 + (int64_t)m.n0 * (i1 + (int64_t)m.n1 * i2);
 }
 
+// The adaptive step of k_hex_facet in its ETA instantiation: thresholds eta_0 < ... < eta_k,
+// the new orders written to l_out[F] (may be the array the orders are read from: each facet
+// reads its own entry first), eta to eta_out[F] when given.
+struct EtaArgs {
+  double thr[6];
+  int8_t* l_out;
+  double* eta_out;
+};
+
 // Facet kernel (BND: the box has non-periodic directions, whose end facets are walls,
 // outlets or inlets): gam[F][0][a][m] = a_F (moments of gA_a), gam[F][1][a][m] = a_F (moments of gB_a),
 //   gA = S + T + Ph, gB = S - T - Ph,  S = -1/2 (w.n) [[u]] - 1/2 [[w.n]] <u>,  T = -1/4 [[w.n]] [[u]]
 // (S + T = -1/2 (w.n)[[u]] - 1/2 [[w.n]] u^A, S - T the same with u^B).
-template <typename T, int K, bool BND>
+// ETA: instead of the moments, the jump indicator of adaptive HOPU (Section 3.2, after eq.
+// "hopudefinition") eta = int |(I - Pi^l)[[u]]| / int |<u>| with the facet's current order,
+// summed in FP64 over the facet points, and the new order (-1 for eta <= eta_0, i for
+// eta_i < eta <= eta_{i+1}, k above eta_k; a zero average with a non-zero jump: +inf).
+template <typename T, int K, bool BND, bool ETA = false>
 __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
-    k_hex_facet(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* __restrict__ uL, int l,
-                T* __restrict__ gam, double* __restrict__ diss_part) {
+    k_hex_facet(MeshDev m, Tabs<T> tb, const T* __restrict__ wL, const T* __restrict__ uL, int l0,
+                T* __restrict__ gam, double* __restrict__ diss_part, EtaArgs ea) {
   using C = Fac<T, K>;
   constexpr int K1 = C::K1, M = C::M, NB = C::NB, NFM = C::NFM, NQF = C::NQF, NV = C::NV, NM = C::NM;
   constexpr int K1o = C::K1o, Mo = C::Mo;
@@ -210,6 +226,7 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
     const int64_t eB = wi / 3;
     const int64_t F = d * m.E + eB;
     const T aF = T(m.aF[F]);
+    const int l = m.facet_l ? int(m.facet_l[F]) : l0;
     // The slot of the first cell of a non-periodic direction holds two boundary facets: the
     // top one of the last cell (its moments in the slot's side-A part) and the bottom one of
     // the first (side-B part).  Walls and outlets add nothing in the evaluated form (the
@@ -362,72 +379,100 @@ __global__ void __launch_bounds__(32 * Fac<T, K>::WARPS, Fac<T, K>::MINB)
         }
       }
       __syncwarp();
-      // 4. weighted integrands at the points: 0-2 S, 3-5 T, 6-8 h = 1/2|w.n| (I-Pi)[[u]]
-      for (int p = lane; p < NQF; p += 32) {
-        const int p2 = p / M, p1 = p - p2 * M;
-        const T wgt = sW[p1] * sW[p2];
-        const T* P = buf + C::O_P + p;
-        const T wn = P[0], wj = P[NQF];
-        const T hw = T(0.5) * fabs(wn) * wgt;
-        if (diss_part) {
-          const double p0 = P[8 * NQF], p1 = P[9 * NQF], p2v = P[10 * NQF];
-          dacc += double(aF) * double(hw) * (p0 * p0 + p1 * p1 + p2v * p2v);
+      if constexpr (ETA) {
+        double sn = 0.0, sdn = 0.0;
+        for (int p = lane; p < NQF; p += 32) {
+          const int p2 = p / M, p1 = p - p2 * M;
+          const double wgt = double(sW[p1]) * double(sW[p2]);
+          const T* P = buf + C::O_P + p;
+          const double j0 = P[8 * NQF], j1 = P[9 * NQF], j2 = P[10 * NQF];
+          const double a0 = P[5 * NQF], a1 = P[6 * NQF], a2 = P[7 * NQF];
+          sn += wgt * sqrt(j0 * j0 + j1 * j1 + j2 * j2);
+          sdn += wgt * sqrt(a0 * a0 + a1 * a1 + a2 * a2);
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const T ju = P[(2 + a) * NQF], au = P[(5 + a) * NQF], pj = P[(8 + a) * NQF];
-          const int qo = p2 * Mo + p1;
-          buf[C::O_Q + a * M * Mo + qo] = T(-0.5) * wgt * (wn * ju + wj * au);
-          buf[C::O_Q + (3 + a) * M * Mo + qo] = T(-0.25) * wgt * wj * ju;
-          buf[C::O_Q + (6 + a) * M * Mo + qo] = hw * pj;
+        for (int o = 16; o > 0; o >>= 1) {
+          sn += __shfl_xor_sync(0xffffffffu, sn, o);
+          sdn += __shfl_xor_sync(0xffffffffu, sdn, o);
         }
-      }
-      __syncwarp();
-      // 5. moments: over p1 (lines (f, p2)), then over p2 (lines (f, s))
-      for (int L = lane; L < NM * M; L += 32) {
-        const int f = L / M, p2 = L - f * M;
-        T q[M];
+        if (lane == 0) {
+          const double eta = sdn > 0.0 ? sn / sdn : (sn > 0.0 ? __longlong_as_double(0x7ff0000000000000LL) : 0.0);
+          int lnew = -1;
 #pragma unroll
-        for (int p1 = 0; p1 < M; ++p1) q[p1] = buf[C::O_Q + L * Mo + p1];
-#pragma unroll
-        for (int s = 0; s < K1; ++s) {
-          T acc = T(0);
-#pragma unroll
-          for (int p1 = 0; p1 < M; ++p1) acc = fma(t1.b(p1, s), q[p1], acc);
-          buf[C::O_U + (f * K1 + s) * Mo + p2] = acc;
+          for (int i = 0; i <= K; ++i)
+            if (eta > ea.thr[i]) lnew = i;
+          if (ea.eta_out) ea.eta_out[F] = eta;
+          ea.l_out[F] = int8_t(lnew);
         }
-      }
-      __syncwarp();
-      for (int L = lane; L < NM * K1; L += 32) {
-        const int f = L / K1, s = L - f * K1;
-        T u[M];
+        __syncwarp();
+      } else {
+        // 4. weighted integrands at the points: 0-2 S, 3-5 T, 6-8 h = 1/2|w.n| (I-Pi)[[u]]
+        for (int p = lane; p < NQF; p += 32) {
+          const int p2 = p / M, p1 = p - p2 * M;
+          const T wgt = sW[p1] * sW[p2];
+          const T* P = buf + C::O_P + p;
+          const T wn = P[0], wj = P[NQF];
+          const T hw = T(0.5) * fabs(wn) * wgt;
+          if (diss_part) {
+            const double p0 = P[8 * NQF], p1 = P[9 * NQF], p2v = P[10 * NQF];
+            dacc += double(aF) * double(hw) * (p0 * p0 + p1 * p1 + p2v * p2v);
+          }
 #pragma unroll
-        for (int p2 = 0; p2 < M; ++p2) u[p2] = buf[C::O_U + L * Mo + p2];
-#pragma unroll
-        for (int tt = 0; tt < K1; ++tt) {
-          T acc = T(0);
-#pragma unroll
-          for (int p2 = 0; p2 < M; ++p2) acc = fma(t1.b(p2, tt), u[p2], acc);
-          buf[C::O_MO + f * NFM + s + K1 * tt] = acc;
+          for (int a = 0; a < 3; ++a) {
+            const T ju = P[(2 + a) * NQF], au = P[(5 + a) * NQF], pj = P[(8 + a) * NQF];
+            const int qo = p2 * Mo + p1;
+            buf[C::O_Q + a * M * Mo + qo] = T(-0.5) * wgt * (wn * ju + wj * au);
+            buf[C::O_Q + (3 + a) * M * Mo + qo] = T(-0.25) * wgt * wj * ju;
+            buf[C::O_Q + (6 + a) * M * Mo + qo] = hw * pj;
+          }
         }
-      }
-      __syncwarp();
-      // 6. Ph = (I - Pi^l) h on the moments; gA = S + T + Ph, gB = S - T - Ph; times a_F
-      for (int mm = lane; mm < NFM; mm += 32) {
-        const T* mo = buf + C::O_MO + mm;
-        const int s = mm % K1, tt = mm / K1;
-        const bool low = (s > tt ? s : tt) <= l;
-        const T h0 = mo[6 * NFM], h1 = mo[7 * NFM], h2 = mo[8 * NFM];
-        const T hn = h0 * n0 + h1 * n1 + h2 * n2;
-        const T ph[3] = {low ? hn * n0 : h0, low ? hn * n1 : h1, low ? hn * n2 : h2};
+        __syncwarp();
+        // 5. moments: over p1 (lines (f, p2)), then over p2 (lines (f, s))
+        for (int L = lane; L < NM * M; L += 32) {
+          const int f = L / M, p2 = L - f * M;
+          T q[M];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const T sv = mo[a * NFM], tv = mo[(3 + a) * NFM];
-          outA[a * NFM + mm] = aF * (sv + tv + ph[a]);
-          if (outB) outB[a * NFM + mm] = aF * (sv - tv - ph[a]);
+          for (int p1 = 0; p1 < M; ++p1) q[p1] = buf[C::O_Q + L * Mo + p1];
+#pragma unroll
+          for (int s = 0; s < K1; ++s) {
+            T acc = T(0);
+#pragma unroll
+            for (int p1 = 0; p1 < M; ++p1) acc = fma(t1.b(p1, s), q[p1], acc);
+            buf[C::O_U + (f * K1 + s) * Mo + p2] = acc;
+          }
         }
-      }
-      __syncwarp();
+        __syncwarp();
+        for (int L = lane; L < NM * K1; L += 32) {
+          const int f = L / K1, s = L - f * K1;
+          T u[M];
+#pragma unroll
+          for (int p2 = 0; p2 < M; ++p2) u[p2] = buf[C::O_U + L * Mo + p2];
+#pragma unroll
+          for (int tt = 0; tt < K1; ++tt) {
+            T acc = T(0);
+#pragma unroll
+            for (int p2 = 0; p2 < M; ++p2) acc = fma(t1.b(p2, tt), u[p2], acc);
+            buf[C::O_MO + f * NFM + s + K1 * tt] = acc;
+          }
+        }
+        __syncwarp();
+        // 6. Ph = (I - Pi^l) h on the moments; gA = S + T + Ph, gB = S - T - Ph; times a_F
+        for (int mm = lane; mm < NFM; mm += 32) {
+          const T* mo = buf + C::O_MO + mm;
+          const int s = mm % K1, tt = mm / K1;
+          const bool low = (s > tt ? s : tt) <= l;
+          const T h0 = mo[6 * NFM], h1 = mo[7 * NFM], h2 = mo[8 * NFM];
+          const T hn = h0 * n0 + h1 * n1 + h2 * n2;
+          const T ph[3] = {low ? hn * n0 : h0, low ? hn * n1 : h1, low ? hn * n2 : h2};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const T sv = mo[a * NFM], tv = mo[(3 + a) * NFM];
+            outA[a * NFM + mm] = aF * (sv + tv + ph[a]);
+            if (outB) outB[a * NFM + mm] = aF * (sv - tv - ph[a]);
+          }
+        }
+        __syncwarp();
+      }  // ETA
     }  // sub-facets
   }
   if (diss_part) {

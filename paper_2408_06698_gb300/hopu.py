@@ -584,6 +584,23 @@ class HopuHex:
             ptr = c_void_p(modes.data_ptr())
         self._check(self.lib.hopu_hex_set_inlet(self.h, int(dir), int(end), ptr), "hopu_hex_set_inlet")
 
+    def set_facet_l(self, facet_l: torch.Tensor | None):
+        """Per-facet orders (int8 [3E] on the device; hopu_hex_set_facet_l); None: per call."""
+        if facet_l is not None and (facet_l.dtype != torch.int8 or facet_l.device != self.device
+                                    or facet_l.numel() != 3 * self.n_elems or not facet_l.is_contiguous()):
+            raise ValueError("facet_l: expected a contiguous int8 tensor of 3E entries on the device")
+        self._facet_l = facet_l                 # kept alive: the library reads it at every launch
+        self._check(self.lib.hopu_hex_set_facet_l(self.h, None if facet_l is None else c_void_p(facet_l.data_ptr())),
+                    "hopu_hex_set_facet_l")
+
+    def adapt_l(self, uL: torch.Tensor, thresholds, facet_l: torch.Tensor, eta: torch.Tensor | None = None):
+        """Adaptive HOPU step (hopu_hex_adapt_l): facet_l (int8 [3E], in/out) gets the new
+        orders from the jump indicator; eta (float64 [3E]) receives it when given."""
+        th = (c_double * (self.k + 1))(*[float(x) for x in thresholds])
+        self._check(self.lib.hopu_hex_adapt_l(self.h, c_void_p(self._vec(uL, "uL")), th, c_void_p(facet_l.data_ptr()),
+                                              None if eta is None else c_void_p(eta.data_ptr())), "hopu_hex_adapt_l")
+        return facet_l
+
     def energy(self, uL: torch.Tensor, wL: torch.Tensor | None = None, l: int = -1):
         """(1/2 int |u|^2, c(w; u, u), facet dissipation) in FP64 (hopu_hex_energy)."""
         out = (c_double * 3)()

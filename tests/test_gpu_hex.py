@@ -191,6 +191,63 @@ def test_hex_inlets(prec, tol):
     g.close()
 
 
+@pytest.mark.parametrize("prec,tol,etol", [("f64", 1e-12, 1e-12), ("f32", 1e-6, 1e-5)])
+def test_hex_adaptive(prec, tol, etol):
+    """Adaptive HOPU on hexahedra: the apply and substeps with per-facet orders, and
+    hopu_hex_adapt_l's indicator and new orders against the oracle (orders compared where
+    eta is not within etol of a threshold)."""
+    from oracle.adaptive import order_from_eta
+    from paper_2408_06698_gb300 import _lib as L
+    k = 3
+    hb = W.hex_box((4, 3, 3), jitter=0.2, shear=0.3, seed=95)
+    m, ref = H.HexMesh(hb), H.RefHex(k)
+    g = _ctx(hb, k, prec)
+    w, u = _fields(m, ref, 96)                  # coarse cells: jumps of several sizes
+    if prec == "f32":
+        w, u = w.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    lF = np.random.default_rng(98).integers(-1, k + 1, size=m.n_facets)
+    ld = torch.tensor(lF, dtype=torch.int8, device=g.device)
+    g.set_facet_l(ld)
+    ud, wd = _dev(g, u), _dev(g, w)
+    for wind, wn in ((wd, w), (ud, u)):
+        y = g.apply(wind, ud, 0).cpu().numpy().astype(np.float64).reshape(u.shape)
+        err = _rel(y, H.apply(m, ref, wn, u, lF))
+        print(f"hex per-facet l {prec}: {err:.2e}")
+        assert err < tol
+    v = ud.clone()
+    g.rk_substeps(v, 1e-2, 1, 0)
+    from oracle.rk import ssp_rk3
+    want = ssp_rk3(lambda x: H.apply(m, ref, x, x, lF), u, 1e-2)
+    assert _rel(v.cpu().numpy().astype(np.float64).reshape(u.shape), want) < tol
+    g.set_facet_l(None)
+    y = g.apply(ud, ud, 1).cpu().numpy().astype(np.float64).reshape(u.shape)
+    assert _rel(y, H.apply(m, ref, u, u, 1)) < tol
+    # the adaptive step
+    thr = [0.3, 0.4, 0.5, 0.7]
+    lcur = torch.tensor(lF, dtype=torch.int8, device=g.device)
+    eta = torch.zeros(m.n_facets, dtype=torch.float64, device=g.device)
+    g.adapt_l(ud, thr, lcur, eta)
+    eta_ref = H.facet_eta(m, ref, u, lF)
+    eg = eta.cpu().numpy()
+    assert np.all(np.abs(eg - eta_ref) <= etol * np.abs(eta_ref) + 1e-300)
+    away = np.min(np.abs(eta_ref[:, None] - np.array(thr)[None, :]), axis=1) > 2 * etol * np.abs(eta_ref)
+    new_ref = order_from_eta(eta_ref, thr, k)
+    got = lcur.cpu().numpy().astype(np.int64)
+    print(f"hex eta {prec}: max rel {np.max(np.abs(eg - eta_ref) / np.abs(eta_ref)):.2e}, orders "
+          f"{np.bincount(new_ref + 1, minlength=k + 2)}")
+    assert np.all(got[away] == new_ref[away]) and away.mean() > 0.95
+    assert len(np.unique(new_ref)) >= 3
+    with pytest.raises(L.HopuError) as ei:
+        g.adapt_l(ud, [0.3, 0.2, 0.1, 0.05], lcur)
+    assert ei.value.status == L.HOPU_EINVAL
+    g.close()
+    from paper_2408_06698_gb300 import HopuHex
+    gw = HopuHex(hb.lines, hb.A, k=k, prec=prec, periodic=(True, True, False))
+    with pytest.raises(L.HopuError) as ei:
+        gw.adapt_l(_dev(gw, u), thr, lcur)
+    assert ei.value.status == L.HOPU_ENOTSUP
+
+
 def test_hex_constant_state_and_errors():
     from paper_2408_06698_gb300 import _lib as L
     hb = W.hex_box(3, jitter=0.1, shear=0.2, seed=3)
