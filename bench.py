@@ -429,11 +429,32 @@ def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
     flops = vol * n ** 3 + fac * 3 * n ** 3
     ach = flops / (row["f32"]["ms_per_apply"] / 1e3) / 1e12
     peak = fp32_alu_peak_tflops(2070.0)
+    row["cpu_baseline"] = hex_cpu_baseline(k=k, l=l)
     row["roofline_f32_apply"] = {"bound": "alu", "flops_per_apply": flops, "achieved": ach, "peak": peak,
                                  "unit": "TFLOP/s", "frac": ach / peak,
                                  "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (maximum SM clock)",
                                  "flops_per_cell_volume": vol, "flops_per_facet": fac}
     return row
+
+
+def hex_cpu_baseline(n=8, k=4, l=3, reps=2):
+    """cpu_baseline leg of the hexahedral row: the FP64 hexahedral oracle's apply (w = u) on
+    an n^3 sample of the same box family, one process, in the row's unit."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import hexa as HX
+    hb = W.hex_box(n, jitter=0.1, shear=0.2, seed=11)
+    mesh, ref = HX.HexMesh(hb), HX.RefHex(k)
+    u = W.uniform_noise(n ** 3 * 3 * ref.nb, 1.0, 5).reshape(n ** 3, 3, ref.nb)
+    HX.apply(mesh, ref, u, u, l)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        HX.apply(mesh, ref, u, u, l)
+    secs = (time.perf_counter() - t0) / reps
+    return {"value": u.size / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n}^3 cells of the same box family, k={k}, l={l}, one FP64 oracle apply (w = u), "
+                      f"one process", "seconds_per_apply": secs}
 
 
 def hex_flops(k, same=True):
