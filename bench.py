@@ -429,7 +429,10 @@ def hex_row(dev, stream, n=32, k=4, l=3, substeps=10, dt=5e-4):
     flops = vol * n ** 3 + fac * 3 * n ** 3
     ach = flops / (row["f32"]["ms_per_apply"] / 1e3) / 1e12
     peak = fp32_alu_peak_tflops(2070.0)
-    row["cpu_baseline"] = hex_cpu_baseline(k=k, l=l)
+    try:
+        row["cpu_baseline"] = hex_cpu_baseline(k=k, l=l)
+    except Exception as exc:            # a context number: never let it stop the bench line
+        row["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"}
     row["roofline_f32_apply"] = {"bound": "alu", "flops_per_apply": flops, "achieved": ach, "peak": peak,
                                  "unit": "TFLOP/s", "frac": ach / peak,
                                  "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (maximum SM clock)",
