@@ -374,7 +374,10 @@ def other_configs(dev, stream, world):
                                    "order_classes": len(b.classes), "substeps": K, "ms_per_substep": ms / K,
                                    "value": l2 * APPLIES_PER_STEP * K / (ms / 1e3), "unit": UNIT}
     b.close()
-    out["hex_box_32cubed_k4"] = hex_row(dev, stream)
+    try:
+        out["hex_box_32cubed_k4"] = hex_row(dev, stream)
+    except Exception as exc:            # an auxiliary row: reported, never the end of the line
+        out["hex_box_32cubed_k4"] = {"error": f"{type(exc).__name__}: {exc}"}
     return out
 
 
