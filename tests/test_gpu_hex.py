@@ -1,7 +1,9 @@
 """The hexahedral path (include/hopu_hex.h) against the hexahedral oracle (oracle/hexa.py):
-the apply element by element in FP64 (1e-12) and FP32, every order 2..5 and HOPU orders
-l = -1, 0, k-1, k, boxes with uneven cell counts, spacings and a shear, and SSP-RK3 STAGE
-substeps; a full-size apply on sampled cells."""
+the apply element by element in FP64 (1e-12) and FP32 (1e-6), every order 2..5 and HOPU
+orders l = -1, 0, k-1, k, boxes with uneven cell counts, spacings and a shear, with a
+separate wind and with w = u; SSP-RK3 STAGE substeps; the FP64 functionals; walls,
+outlets and inlets; per-facet orders and the adaptive step; a full-size apply on sampled
+cells."""
 import numpy as np
 import pytest
 import torch
