@@ -153,6 +153,18 @@ def test_hex_box_validation(lib):
     if not torch.cuda.is_available():
         st, msg = _hex_create(lib, hb.lines, hb.A)
         assert st == L.HOPU_ECUDA, msg                          # valid box: fails on the device only
+    # every other entry point refuses a NULL context before touching the device
+    from ctypes import c_double
+    thr = (c_double * 4)(0.1, 0.2, 0.3, 0.4)
+    out = (c_double * 3)()
+    assert lib.hopu_hex_destroy(None) == L.HOPU_EINVAL
+    assert lib.hopu_hex_apply(None, None, None, 0, None) == L.HOPU_EINVAL
+    assert lib.hopu_hex_rk_substeps(None, None, 1e-3, 1, 0) == L.HOPU_EINVAL
+    assert lib.hopu_hex_set_inlet(None, 0, 0, None) == L.HOPU_EINVAL
+    assert lib.hopu_hex_set_facet_l(None, None) == L.HOPU_EINVAL
+    assert lib.hopu_hex_adapt_l(None, None, thr, None, None) == L.HOPU_EINVAL
+    assert lib.hopu_hex_energy(None, None, None, 0, out) == L.HOPU_EINVAL
+    assert lib.hopu_hex_sizes(None, None, None) == L.HOPU_EINVAL
 
 
 _RANK_SCRIPT = r"""
